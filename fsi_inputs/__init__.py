@@ -1,0 +1,249 @@
+"""Seeded synthetic inputs for the DLM fictitious-domain FSI step.
+
+This module is shared by the CPU oracle (``oracle/``) and by the GPU path
+(``paper_2301_10041_gb300``).  It holds no arithmetic of the method: it only
+draws random numbers and lays out the geometry and initial data that both
+sides receive as plain arrays.
+
+* ``splitmix64`` is the counter-based generator of Steele, Lea and Flood,
+  "Fast splittable pseudorandom number generators" (OOPSLA 2014): value i of
+  stream ``seed`` is the finaliser applied to ``seed + (i + 1) * golden``.
+* ``ring_disk_mesh`` builds the concentric-ring P1 triangulation of a disk
+  used for the immersed body: ring k (k = 1..m) sits at radius k R / m and
+  carries 6k nodes; the strip between ring k-1 and ring k holds 6(2k-1)
+  triangles, so the mesh has 1 + 3m(m+1) nodes and 6 m^2 triangles.
+* ``ellipse_mesh`` maps the unit-disk ring mesh affinely onto an ellipse.
+* ``initial_velocity`` draws u_0 uniform in [-1, 1] per interior velocity
+  dof of the (2N+1)^2 Q2 node grid; boundary nodes carry the wall values.
+
+Workload shapes follow the paper's experiments (Section 6: cavity-like unit
+square, an elastic body at rest in the middle, 3e4 - 2e6 dofs).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+import math
+
+import numpy as np
+
+_GOLDEN = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+
+def splitmix64(seed: int, idx) -> np.ndarray:
+    """Counter-based SplitMix64: uint64 value ``idx`` of stream ``seed``."""
+    idx = np.asarray(idx, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = np.uint64(seed & 0xFFFFFFFFFFFFFFFF) + (idx + np.uint64(1)) * _GOLDEN
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+        z = z ^ (z >> np.uint64(31))
+    return z
+
+
+def uniform01(seed: int, idx) -> np.ndarray:
+    """Doubles in [0, 1) from the top 53 bits of ``splitmix64``."""
+    return (splitmix64(seed, idx) >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+
+
+def _strip(inner: list[int], outer: list[int], tris: list[tuple[int, int, int]]) -> None:
+    """Triangulate the annular strip between two closed rings of nodes.
+
+    Nodes of each ring are equally spaced in angle starting at angle 0.  The
+    two rings are merged in angular order (exact integer comparison of
+    (j+1)/n_out against (i+1)/n_in); each step emits one counter-clockwise
+    triangle, so the strip gets n_in + n_out triangles.
+    """
+    n_in, n_out = len(inner), len(outer)
+    if n_in == 1:
+        c = inner[0]
+        for j in range(n_out):
+            tris.append((c, outer[j], outer[(j + 1) % n_out]))
+        return
+    i = j = 0
+    while i < n_in or j < n_out:
+        adv_outer = j < n_out and (i == n_in or (j + 1) * n_in <= (i + 1) * n_out)
+        if adv_outer:
+            tris.append((inner[i % n_in], outer[j], outer[(j + 1) % n_out]))
+            j += 1
+        else:
+            tris.append((inner[i], outer[j % n_out], inner[(i + 1) % n_in]))
+            i += 1
+
+
+def ring_disk_mesh(m: int, radius: float = 1.0, center=(0.0, 0.0)):
+    """Concentric-ring triangulation of a disk; returns (xy[n,2], tris[t,3])."""
+    if m < 1:
+        raise ValueError("m must be >= 1")
+    xy = [(0.0, 0.0)]
+    rings = [[0]]
+    for k in range(1, m + 1):
+        n = 6 * k
+        base = len(xy)
+        r = radius * k / m
+        for j in range(n):
+            th = 2.0 * math.pi * j / n
+            xy.append((r * math.cos(th), r * math.sin(th)))
+        rings.append(list(range(base, base + n)))
+    tris: list[tuple[int, int, int]] = []
+    for k in range(1, m + 1):
+        _strip(rings[k - 1], rings[k], tris)
+    xy = np.asarray(xy, dtype=np.float64)
+    xy[:, 0] += center[0]
+    xy[:, 1] += center[1]
+    return xy, np.asarray(tris, dtype=np.int32)
+
+
+def ellipse_mesh(m: int, a: float, b: float, angle_deg: float, center=(0.5, 0.5)):
+    """Ring mesh of the unit disk mapped onto an ellipse with semi-axes a, b
+    rotated by ``angle_deg`` about ``center``."""
+    xy, tris = ring_disk_mesh(m, 1.0)
+    th = math.radians(angle_deg)
+    c, s = math.cos(th), math.sin(th)
+    x = a * xy[:, 0]
+    y = b * xy[:, 1]
+    out = np.empty_like(xy)
+    out[:, 0] = center[0] + c * x - s * y
+    out[:, 1] = center[1] + s * x + c * y
+    return out, tris
+
+
+def node_grid_shape(N: int) -> int:
+    """Number of Q2 nodes per side of the N x N cell grid."""
+    return 2 * N + 1
+
+
+def wall_velocity(N: int, lid_u: float) -> np.ndarray:
+    """Nodal Dirichlet data on the (2N+1)^2 grid, shape [(2N+1)^2, 2].
+
+    Walls are at rest; with a lid, the nodes of the top wall strictly between
+    the two corners move with (lid_u, 0); the corners stay at rest.
+    """
+    n1 = 2 * N + 1
+    u = np.zeros((n1 * n1, 2))
+    if lid_u != 0.0:
+        top = (n1 - 1) * n1 + np.arange(1, n1 - 1)
+        u[top, 0] = lid_u
+    return u
+
+
+def initial_velocity(N: int, seed: int, lid_u: float = 0.0, amplitude: float = 1.0) -> np.ndarray:
+    """u_0 on the (2N+1)^2 node grid, shape [(2N+1)^2, 2], node id = iy*(2N+1)+ix.
+
+    Interior dofs are ``amplitude * (2U - 1)`` with U = uniform01(seed, dof id)
+    and dof id = 2 * node id + component; boundary nodes take the wall values.
+    """
+    n1 = 2 * N + 1
+    u = wall_velocity(N, lid_u)
+    if amplitude != 0.0:
+        ix, iy = np.meshgrid(np.arange(n1), np.arange(n1))
+        ix = ix.ravel()
+        iy = iy.ravel()
+        interior = (ix > 0) & (ix < n1 - 1) & (iy > 0) & (iy < n1 - 1)
+        nodes = np.nonzero(interior)[0]
+        for c in range(2):
+            dof = 2 * nodes.astype(np.uint64) + np.uint64(c)
+            u[nodes, c] = amplitude * (2.0 * uniform01(seed, dof) - 1.0)
+    return u
+
+
+@dataclass
+class FsiCase:
+    """One FSI instance: parameters, solid mesh and initial state."""
+    N: int
+    rho_f: float
+    nu: float
+    kappa: float
+    dt: float
+    lid_u: float
+    ref_xy: np.ndarray          # [n_s, 2] reference (= initial) solid node positions
+    tris: np.ndarray            # [n_tri, 3] int32, counter-clockwise
+    u0: np.ndarray              # [(2N+1)^2, 2] nodal velocity
+    X0: np.ndarray              # [n_s, 2] initial solid node positions
+    precond: int = 0            # 0 block-diagonal, 1 block-triangular
+    rtol: float = 1e-8
+    steps: int = 1
+    name: str = ""
+    extra: dict = field(default_factory=dict)
+
+
+BASE_SEED = 2301
+
+
+def config0(seed: int = BASE_SEED + 0) -> FsiCase:
+    """Plain FP64 single step: N=16, nu=1, rho=1, kappa=10, dt=0.01, disk
+    R=0.2 at (0.5, 0.5) with m=6 (216 triangles), u_0 uniform[-1,1]."""
+    N = 16
+    xy, tris = ring_disk_mesh(6, 0.2, (0.5, 0.5))
+    return FsiCase(N=N, rho_f=1.0, nu=1.0, kappa=10.0, dt=0.01, lid_u=0.0,
+                   ref_xy=xy, tris=tris, u0=initial_velocity(N, seed), X0=xy.copy(),
+                   precond=0, rtol=1e-10, steps=1, name="cavity16_disk216_fp64")
+
+
+def config1(seed: int = BASE_SEED + 1, N: int = 128, m: int = 36) -> FsiCase:
+    """Plain vs mixed precision: N=128, nu=0.01, kappa=1e3, dt=1e-3, lid 1,
+    disk R=0.2 with m=36 (7776 triangles), body at rest, fluid at rest."""
+    xy, tris = ring_disk_mesh(m, 0.2, (0.5, 0.5))
+    return FsiCase(N=N, rho_f=1.0, nu=0.01, kappa=1e3, dt=1e-3, lid_u=1.0,
+                   ref_xy=xy, tris=tris, u0=wall_velocity(N, 1.0), X0=xy.copy(),
+                   precond=1, rtol=1e-8, steps=100,
+                   name=f"cavity{N}_lid_disk{len(tris)}")
+
+
+def config2(N: int, seed: int = BASE_SEED + 2) -> FsiCase:
+    """Size sweep member: ellipse 0.2/0.1 rotated 30 degrees, m = ceil(0.4 N),
+    kappa=1e2, nu=1, rho=1, dt=0.01, walls at rest, fluid at rest."""
+    m = int(math.ceil(0.4 * N))
+    xy, tris = ellipse_mesh(m, 0.2, 0.1, 30.0)
+    return FsiCase(N=N, rho_f=1.0, nu=1.0, kappa=1e2, dt=0.01, lid_u=0.0,
+                   ref_xy=xy, tris=tris, u0=wall_velocity(N, 0.0), X0=xy.copy(),
+                   precond=1, rtol=1e-8, steps=20, name=f"ellipse_N{N}")
+
+
+def config3_instance(i: int, seed: int = BASE_SEED + 3) -> FsiCase:
+    """Instance i of the batch of uneven problems: N ~ U{16,32,48,64,96},
+    R ~ U[0.1,0.3], centre ~ U[0.35,0.65]^2, kappa log-uniform [1,1e4],
+    nu log-uniform [1e-3,1], m = ceil(2 R N), walls at rest, u_0 seeded."""
+    r = uniform01(seed, np.arange(8 * i, 8 * i + 8, dtype=np.uint64))
+    N = (16, 32, 48, 64, 96)[min(int(r[0] * 5), 4)]
+    R = 0.1 + 0.2 * r[1]
+    cx, cy = 0.35 + 0.3 * r[2], 0.35 + 0.3 * r[3]
+    kappa = 10.0 ** (4.0 * r[4])
+    nu = 10.0 ** (-3.0 + 3.0 * r[5])
+    m = int(math.ceil(2.0 * R * N))
+    xy, tris = ring_disk_mesh(m, R, (cx, cy))
+    return FsiCase(N=N, rho_f=1.0, nu=nu, kappa=kappa, dt=0.01, lid_u=0.0,
+                   ref_xy=xy, tris=tris, u0=initial_velocity(N, seed * 1000003 + i),
+                   X0=xy.copy(), precond=1, rtol=1e-8, steps=50, name=f"batch{i}_N{N}")
+
+
+def config4_trace(n_requests: int = 2000, rate: float = 200.0, seed: int = BASE_SEED + 4):
+    """Served stream: Poisson arrivals (exponential gaps at ``rate``/s); each
+    request is 50 steps of a cavity problem with N in {32,64,128,256}
+    (p = .4/.3/.2/.1), disk or ellipse (p = 1/2), R ~ U[0.1,0.3],
+    kappa log-uniform [1,1e4].  Returns a list of (arrival_s, FsiCase-args)."""
+    out = []
+    t = 0.0
+    for i in range(n_requests):
+        r = uniform01(seed, np.arange(8 * i, 8 * i + 8, dtype=np.uint64))
+        t += -math.log(1.0 - r[0]) / rate
+        u = r[1]
+        N = 32 if u < 0.4 else 64 if u < 0.7 else 128 if u < 0.9 else 256
+        R = 0.1 + 0.2 * r[3]
+        kappa = 10.0 ** (4.0 * r[4])
+        out.append((t, dict(N=N, ellipse=bool(r[2] < 0.5), R=R, kappa=kappa, index=i)))
+    return out
+
+
+def config4_case(spec: dict, seed: int = BASE_SEED + 4) -> FsiCase:
+    N = spec["N"]
+    R = spec["R"]
+    m = int(math.ceil(2.0 * R * N))
+    if spec["ellipse"]:
+        xy, tris = ellipse_mesh(m, R, 0.5 * R, 30.0)
+    else:
+        xy, tris = ring_disk_mesh(m, R, (0.5, 0.5))
+    return FsiCase(N=N, rho_f=1.0, nu=0.1, kappa=spec["kappa"], dt=0.01, lid_u=1.0,
+                   ref_xy=xy, tris=tris, u0=wall_velocity(N, 1.0), X0=xy.copy(),
+                   precond=1, rtol=1e-8, steps=50, name=f"req{spec['index']}_N{N}")

@@ -1,0 +1,344 @@
+"""Pins of the CPU oracle against facts fixed by the mathematics and the paper.
+
+Each test checks the oracle against something other than itself: closed-form
+integrals, invariants, published quadrature tables, manufactured-solution
+convergence rates and brute-force special cases.  A dropped term, a wrong
+sign, a transposed block or a wrong index in the oracle fails one of these.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import fsi_inputs as fi
+from oracle import fsi_oracle as fo
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+# ---------------------------------------------------------------- quadrature
+
+def test_triangle_rule_matches_published_table():
+    """Constants agree with Dunavant (1985) Table I (p = 4) to its 15 digits."""
+    rows = np.loadtxt(os.path.join(HERE, "golden", "dunavant_deg4.txt"))
+    lam, w = fo.triangle_rule()
+    assert np.allclose(w[[0, 3]], rows[:, 0], atol=1e-15, rtol=0)
+    # representatives: the point whose odd coordinate sits in lam0
+    assert np.allclose(lam[[0, 3]], rows[:, 1:], atol=1e-15, rtol=0)
+    assert abs(w.sum() - 1.0) < 1e-15
+
+
+def test_triangle_rule_exact_to_degree_4():
+    """Integral of lam1^i lam2^j over a triangle of area 1 is 2 i! j!/(i+j+2)!."""
+    lam, w = fo.triangle_rule()
+    for d in range(5):
+        for i in range(d + 1):
+            j = d - i
+            exact = 2.0 * math.factorial(i) * math.factorial(j) / math.factorial(i + j + 2)
+            q = np.sum(w * lam[:, 1] ** i * lam[:, 2] ** j)
+            assert abs(q - exact) < 1e-15
+    # and it is a degree-4 rule, not more
+    q = np.sum(w * lam[:, 1] ** 5)
+    assert abs(q - 2.0 * math.factorial(5) / math.factorial(7)) > 1e-6
+
+
+def test_q2_basis_is_nodal_and_complete():
+    nodes = np.array([0.0, 0.5, 1.0])
+    assert np.allclose(fo.q2_1d(nodes), np.eye(3), atol=0)
+    t = np.linspace(0, 1, 7)
+    L = fo.q2_1d(t)
+    assert np.allclose(L.sum(1), 1.0)
+    assert np.allclose(L @ nodes, t)            # reproduces linears
+    assert np.allclose(L @ nodes ** 2, t ** 2)  # and quadratics
+    assert np.allclose(fo.q2_1d_deriv(t) @ nodes ** 2, 2 * t)
+
+
+# ------------------------------------------------------------- fluid blocks
+
+@pytest.fixture(scope="module")
+def fluid8():
+    g = fo.FluidGrid(8)
+    M, K, B = fo.assemble_fluid(g, nu=0.7)
+    return g, M, K, B
+
+
+def _nodal(g, fx, fy):
+    u = np.zeros(2 * g.n_nodes)
+    u[0::2] = fx(g.node_xy[:, 0], g.node_xy[:, 1])
+    u[1::2] = fy(g.node_xy[:, 0], g.node_xy[:, 1])
+    return u
+
+
+def test_mass_matrix_integrals(fluid8):
+    g, M, K, B = fluid8
+    one = _nodal(g, lambda x, y: 1 + 0 * x, lambda x, y: 0 * x)
+    assert abs(one @ M @ one - 1.0) < 1e-13                # area of the unit square
+    sq = _nodal(g, lambda x, y: x * x, lambda x, y: 0 * x)
+    assert abs(one @ M @ sq - 1.0 / 3.0) < 1e-13           # int x^2
+    xy = _nodal(g, lambda x, y: x * y, lambda x, y: 0 * x)
+    assert abs(xy @ M @ xy - 1.0 / 9.0) < 1e-13            # int x^2 y^2
+    assert abs(M - M.T).max() < 1e-15
+
+
+def test_strain_energy_of_linear_fields(fluid8):
+    """a(u, u) = nu int eps(u):eps(u) with eps the symmetric gradient, no factor 2."""
+    g, M, K, B = fluid8
+    nu = 0.7
+    cases = [((lambda x, y: x, lambda x, y: y), 2 * nu),        # eps = I
+             ((lambda x, y: y, lambda x, y: 0 * x), nu / 2),     # pure shear
+             ((lambda x, y: x, lambda x, y: -y), 2 * nu),
+             ((lambda x, y: 0 * x, lambda x, y: x), nu / 2)]
+    for (fx, fy), val in cases:
+        u = _nodal(g, fx, fy)
+        assert abs(u @ K @ u - val) < 1e-12
+    assert abs(K - K.T).max() < 1e-13
+
+
+def test_rigid_motions_have_no_strain(fluid8):
+    g, M, K, B = fluid8
+    for fx, fy in ((lambda x, y: 1 + 0 * x, lambda x, y: 0 * x),
+                   (lambda x, y: 0 * x, lambda x, y: 1 + 0 * y),
+                   (lambda x, y: -y, lambda x, y: x)):
+        assert np.abs(K @ _nodal(g, fx, fy)).max() < 1e-12
+
+
+def test_divergence_matrix(fluid8):
+    g, M, K, B = fluid8
+    h = g.h
+    # divergence-free quadratic field -> B u = 0 exactly
+    u = _nodal(g, lambda x, y: x * x, lambda x, y: -2 * x * y)
+    assert np.abs(B @ u).max() < 1e-14
+    # div (x, 0) = 1: (B u)_k = int psi_k over the cell = (h^2, 0, 0)
+    b = (B @ _nodal(g, lambda x, y: x, lambda x, y: 0 * x)).reshape(-1, 3)
+    assert np.allclose(b, np.array([h * h, 0, 0])[None, :], atol=1e-15)
+    # div (x^2, 0) = 2x: (2 xc h^2, h^3/6, 0)
+    b = (B @ _nodal(g, lambda x, y: x * x, lambda x, y: 0 * x)).reshape(-1, 3)
+    xc = (np.arange(g.N * g.N) % g.N + 0.5) * h
+    assert np.allclose(b[:, 0], 2 * xc * h * h, atol=1e-15)
+    assert np.allclose(b[:, 1], h ** 3 / 6, atol=1e-15)
+    assert np.allclose(b[:, 2], 0, atol=1e-15)
+    # div (0, y^2) = 2y: third coefficient h^3/6
+    b = (B @ _nodal(g, lambda x, y: 0 * x, lambda x, y: y * y)).reshape(-1, 3)
+    assert np.allclose(b[:, 2], h ** 3 / 6, atol=1e-15)
+    assert np.allclose(b[:, 1], 0, atol=1e-15)
+
+
+def _manufactured(nu, rho, dt):
+    pi = math.pi
+    s, c = np.sin, np.cos
+
+    def u(x, y):
+        return np.stack([2 * pi * s(pi * x) ** 2 * s(pi * y) * c(pi * y),
+                         -2 * pi * s(pi * x) * c(pi * x) * s(pi * y) ** 2], 1)
+
+    def gu(x, y):
+        a = 2 * pi * pi
+        ux_x = a * 2 * s(pi * x) * c(pi * x) * s(pi * y) * c(pi * y)
+        ux_y = a * s(pi * x) ** 2 * (c(pi * y) ** 2 - s(pi * y) ** 2)
+        uy_x = -a * (c(pi * x) ** 2 - s(pi * x) ** 2) * s(pi * y) ** 2
+        uy_y = -a * s(pi * x) * c(pi * x) * 2 * s(pi * y) * c(pi * y)
+        return np.stack([np.stack([ux_x, ux_y], 1), np.stack([uy_x, uy_y], 1)], 1)
+
+    def p(x, y):
+        return c(pi * x) * c(pi * y)
+
+    def lap(x, y):
+        # Laplacian of u, componentwise
+        a = 2 * pi ** 3
+        lx = a * (2 * c(2 * pi * x) * s(pi * y) * c(pi * y) - 4 * s(pi * x) ** 2 * s(pi * y) * c(pi * y))
+        ly = -a * (2 * c(2 * pi * y) * s(pi * x) * c(pi * x) - 4 * s(pi * y) ** 2 * s(pi * x) * c(pi * x))
+        return np.stack([lx, ly], 1)
+
+    def f(x, y):
+        # (rho/dt) u - div(nu eps(u)) + grad p, with div(eps(u)) = lap(u)/2 for div-free u
+        gp = np.stack([-pi * s(pi * x) * c(pi * y), -pi * c(pi * x) * s(pi * y)], 1)
+        return (rho / dt) * u(x, y) - 0.5 * nu * lap(x, y) + gp
+
+    return u, gu, p, f
+
+
+def test_stokes_manufactured_convergence_rates():
+    """Q2/P1disc generalized Stokes: ||u-u_h|| = O(h^3), |u-u_h|_1 = O(h^2),
+    ||p-p_h|| = O(h^2)."""
+    u, gu, p, f = _manufactured(nu=1.0, rho=1.0, dt=0.1)
+    errs = [fo.stokes_manufactured(N, 1.0, 1.0, 0.1, u, gu, p, f) for N in (4, 8, 16)]
+    errs = np.array(errs)
+    rates = np.log2(errs[:-1] / errs[1:])
+    assert rates[-1, 0] > 2.8, rates
+    assert rates[-1, 1] > 1.85, rates
+    assert rates[-1, 2] > 1.85, rates
+
+
+# ------------------------------------------------------------- solid blocks
+
+def test_solid_mass_and_stiffness():
+    xy, tris = fi.ring_disk_mesh(5, 0.3, (0.4, 0.6))
+    C, A = fo.assemble_solid(xy, tris, kappa=3.0)
+    one = np.ones(xy.shape[0])
+    # polygon area of the outer ring by the shoelace formula
+    ring = xy[-30:]
+    area = 0.5 * abs(np.sum(ring[:, 0] * np.roll(ring[:, 1], -1) - np.roll(ring[:, 0], -1) * ring[:, 1]))
+    assert abs(one @ C @ one - area) < 1e-14
+    assert np.abs(A @ one).max() < 1e-12                   # constants have no gradient
+    # kappa int |grad x|^2 = kappa * area
+    x = xy[:, 0]
+    assert abs(x @ A @ x - 3.0 * area) < 1e-12
+    # mass entries by the (independent) degree-4 rule: exact for P1 x P1
+    lam, w = fo.triangle_rule()
+    area_t, _ = fo.p1_geometry(xy, tris)
+    Cq = np.zeros((xy.shape[0],) * 2)
+    for t in range(tris.shape[0]):
+        for a in range(3):
+            for b in range(3):
+                Cq[tris[t, a], tris[t, b]] += area_t[t] * np.sum(w * lam[:, a] * lam[:, b])
+    assert np.abs(C.toarray() - Cq).max() < 1e-15
+
+
+# ------------------------------------------------------------ point location
+
+def test_locate_matches_floor_rule_and_grid_lines():
+    N = 7
+    rng = np.random.default_rng(0)
+    x = rng.uniform(0, 1, size=(4000, 2))
+    lines = np.arange(N + 1) / N
+    x[:64, 0] = np.resize(lines, 64)
+    x[64:128, 1] = np.resize(lines, 64)
+    x[128] = (1.0, 1.0)
+    x[129] = (0.0, 0.0)
+    x[130] = (np.nextafter(1.0, 0), np.nextafter(0.0, 1))
+    x[131] = (-1e-300, 0.5)
+    x[132] = (0.5, 1.0 + 2 ** -52)
+    x[133] = (np.nan, 0.5)
+    cell, xi, eta = fo.locate_brute_force(x, N)
+    t = x * N
+    ok = (x >= 0).all(1) & (x <= 1).all(1)
+    i = np.where(ok[:, None], np.minimum(np.floor(np.where(ok[:, None], t, 0)), N - 1), -1).astype(int)
+    expect = np.where(ok, i[:, 1] * N + i[:, 0], -1)
+    assert np.array_equal(cell, expect)
+    assert cell[131] == -1 and cell[132] == -1 and cell[133] == -1
+    assert cell[128] == N * N - 1 and cell[129] == 0
+    m = cell >= 0
+    assert np.array_equal(xi[m], (t[:, 0] - i[:, 0])[m])
+    assert np.array_equal(eta[m], (t[:, 1] - i[:, 1])[m])
+    assert (xi[m] >= 0).all() and (xi[m] <= 1).all()
+
+
+# ------------------------------------------------------------------ coupling
+
+def _deformed(xy, shear=0.3, rot=0.4, center=(0.5, 0.5)):
+    c, s = math.cos(rot), math.sin(rot)
+    x = xy[:, 0] - center[0]
+    y = xy[:, 1] - center[1]
+    X = np.stack([c * x - s * y + shear * y, s * x + c * y + 0.1 * x * x], 1)
+    return X + np.array(center)
+
+
+def test_coupling_partition_of_unity_and_reproduction():
+    """C_f 1 = C_s 1 (partition of unity); C_f reproduces linear and quadratic
+    fields exactly because the rule integrates degree <= 4."""
+    N = 12
+    g = fo.FluidGrid(N)
+    xy, tris = fi.ring_disk_mesh(7, 0.22, (0.5, 0.5))
+    X = _deformed(xy)
+    C, (xq, cell, xi, eta) = fo.assemble_coupling(g, xy, tris, X)
+    Cs, _ = fo.assemble_solid(xy, tris, 1.0)
+    one = np.ones(g.n_nodes)
+    rs = C @ one
+    assert np.abs(rs - Cs @ np.ones(xy.shape[0])).max() < 1e-12 * np.abs(rs).max()
+    # linear reproduction: (C x_nodal)_l = int chi_l X_x = (C_s X_x)_l
+    for comp in range(2):
+        lin = C @ g.node_xy[:, comp]
+        assert np.abs(lin - Cs @ X[:, comp]).max() < 1e-13
+    # quadratic: (C x^2)_l = int chi_l (X_x)^2 by the closed form
+    # int_T lam_a lam_b lam_c = 2|T| a_! b_! c_!/(n+2)! over multiplicities
+    area_t, _ = fo.p1_geometry(xy, tris)
+    ref = np.zeros(xy.shape[0])
+    for t in range(tris.shape[0]):
+        v = tris[t]
+        for a in range(3):
+            s = 0.0
+            for b in range(3):
+                for c in range(3):
+                    mult = np.bincount([a, b, c], minlength=3)
+                    integ = 2 * area_t[t] * np.prod([math.factorial(k) for k in mult]) / math.factorial(5)
+                    s += integ * X[v[b], 0] * X[v[c], 0]
+            ref[v[a]] += s
+    quad = C @ g.node_xy[:, 0] ** 2
+    assert np.abs(quad - ref).max() < 1e-13
+
+
+def test_coupling_rejects_points_outside():
+    g = fo.FluidGrid(8)
+    xy, tris = fi.ring_disk_mesh(3, 0.2, (0.5, 0.5))
+    X = xy + np.array([0.45, 0.0])
+    with pytest.raises(ValueError):
+        fo.assemble_coupling(g, xy, tris, X)
+
+
+# ------------------------------------------------------------------- one step
+
+def test_step_residual_and_scipy_agreement():
+    c = fi.config0()
+    prob = fo.OracleProblem(c.N, c.rho_f, c.nu, c.kappa, c.dt, c.lid_u, c.ref_xy, c.tris)
+    Kmat, rhs, _ = prob.system(c.u0, c.X0)
+    x = prob.solve_system(Kmat, rhs, c.X0)
+    assert np.linalg.norm(rhs - Kmat @ x) / np.linalg.norm(rhs) < 1e-12
+    # an unscaled, differently ordered library solve of the bordered system
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spla
+    n_u, n_p, n_x = prob.sizes()
+    e = np.zeros(Kmat.shape[0])
+    e[n_u:n_u + n_p:3] = 1.0
+    big = sp.bmat([[Kmat, sp.csr_matrix(e[:, None])], [sp.csr_matrix(e[None, :]), None]], format="csc")
+    x2 = spla.spsolve(big, np.concatenate([rhs, [0.0]]))[:-1]
+    assert np.linalg.norm(x - x2) / np.linalg.norm(x2) < 1e-9
+
+
+def test_pressure_has_zero_mean_and_velocity_is_discretely_solenoidal():
+    c = fi.config0()
+    prob, u, p, X, lam = fo.run_steps(c, 1)
+    assert abs(p[:, 0].sum()) < 1e-10 * np.abs(p[:, 0]).max()
+    div = prob.B @ u.reshape(-1)
+    assert np.abs(div).max() < 1e-12 * np.abs(prob.B).max() * np.abs(u).max()
+
+
+def test_discrete_energy_identity():
+    """Testing Eq. (matrix) with (u^{n+1}, p, (X^{n+1}-X^n)/dt, -lambda) gives
+    rho/(2dt)(|u1|_M^2 - |u0|_M^2 + |u1-u0|_M^2) + a(u1, u1)
+      + kappa/(2dt)(|grad X1|^2 - |grad X0|^2 + |grad(X1-X0)|^2) = 0
+    with walls at rest: the coupling and pressure terms cancel in pairs."""
+    c = fi.config0()
+    prob, u1, p, X1, lam = fo.run_steps(c, 1)
+    u0 = c.u0.reshape(-1)
+    u1 = u1.reshape(-1)
+    M, K, As = prob.M, prob.K, prob.As
+    X0 = c.X0.reshape(-1)
+    X1 = X1.reshape(-1)
+    r, dt = prob.rho, prob.dt
+    kin = r / (2 * dt) * (u1 @ M @ u1 - u0 @ M @ u0 + (u1 - u0) @ M @ (u1 - u0))
+    visc = u1 @ K @ u1
+    ela = 1.0 / (2 * dt) * (X1 @ As @ X1 - X0 @ As @ X0 + (X1 - X0) @ As @ (X1 - X0))
+    scale = max(abs(kin), abs(visc), abs(ela), r / (2 * dt) * (u0 @ M @ u0))
+    assert abs(kin + visc + ela) < 1e-9 * scale
+
+
+def test_kappa_zero_body_at_rest_stays_at_rest():
+    xy, tris = fi.ring_disk_mesh(4, 0.2, (0.5, 0.5))
+    prob = fo.OracleProblem(8, 1.0, 0.5, 0.0, 0.01, 0.0, xy, tris)
+    u, p, X, lam = prob.step(np.zeros((prob.grid.n_nodes, 2)), xy)
+    assert np.abs(u).max() < 1e-13
+    assert np.abs(X - xy).max() < 1e-14
+    assert np.abs(lam).max() < 1e-10
+    assert np.abs(p).max() < 1e-10
+
+
+def test_lid_driven_cavity_conserves_no_mass_through_walls():
+    """With the lid, B u^{n+1} = 0 for the full field (interior + wall data)."""
+    xy, tris = fi.ring_disk_mesh(4, 0.2, (0.5, 0.5))
+    prob = fo.OracleProblem(8, 1.0, 0.1, 50.0, 0.01, 1.0, xy, tris)
+    u0 = fi.wall_velocity(8, 1.0)
+    u, p, X, lam = prob.step(u0, xy)
+    assert np.abs(prob.B @ u.reshape(-1)).max() < 1e-11 * np.abs(prob.B).max()
+    top = (prob.grid.n1 - 1) * prob.grid.n1 + np.arange(1, prob.grid.n1 - 1)
+    assert np.all(u[top, 0] == 1.0)
