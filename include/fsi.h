@@ -1,0 +1,184 @@
+/*
+ * fsi.h — C ABI of the GB300 (sm_103a) library for one time step of the
+ * distributed-Lagrange-multiplier fictitious-domain FSI method of
+ * Boffi, Credali, Gastaldi and Scacchi, "A parallel solver for FSI problems
+ * with fictitious domain approach" (arXiv:2301.10041).
+ *
+ * Problem solved per step (Section 4, Problem 3 and Eq. (matrix)): for the
+ * fluid velocity u (Q2, interior nodes of a uniform N x N grid of the unit
+ * square), pressure p (P1 discontinuous, 3 coefficients per cell),
+ * solid position X and multiplier lambda (both P1 on the solid mesh):
+ *
+ *     [ A_f      -B^T   0           C_f(X^n)^T ] [u^{n+1}]   [g1]
+ *     [ -B        0     0           0          ] [p^{n+1}] = [g_p]
+ *     [ 0         0     A_s         -C_s       ] [X^{n+1}]   [0 ]
+ *     [ C_f(X^n)  0     -C_s/dt     0          ] [l^{n+1}]   [g2]
+ *
+ * with A_f = (rho_f/dt) M_f + K_f, K_f from nu (eps(u), eps(v)),
+ * A_s = kappa (grad chi_j, grad chi_i)_B (P(F) = kappa F), C_s the P1 mass
+ * matrix, g1 = (rho_f/dt) M_f u^n, g2 = -(1/dt) C_s X^n, Dirichlet wall data
+ * moved to the right-hand side.  C_f(X^n) is re-assembled every step by
+ * locating the 6 points of a degree-4 triangle rule of every solid triangle
+ * in the fluid grid (Section 4 assembles it by exact intersection instead).
+ * The system is solved by right-preconditioned flexible GMRES with the
+ * paper's block-diagonal or block-triangular preconditioner (Section 5).
+ *
+ * Conventions for every entry point:
+ *  - All arrays passed in are HOST arrays owned by the caller; they are
+ *    copied and may be freed after the call returns.
+ *  - The library owns every device buffer it allocates (cudaMalloc); one
+ *    problem lives on the device that was current at fsi_create_problem.
+ *  - Work is queued on the CUDA stream given at creation (NULL = legacy
+ *    default stream).  fsi_assemble_step and fsi_advance are asynchronous;
+ *    fsi_solve_step, fsi_get_* and fsi_set_state synchronise the stream.
+ *  - Every call returns an int status: FSI_OK (0) or a negative FSI_ERR_*
+ *    code; no C++ exception crosses the boundary.  Errors found on the
+ *    device during fsi_assemble_step (a point outside the domain, a row over
+ *    capacity) are reported by the next synchronising call.
+ *  - Node layouts: the fluid node lattice has (2N+1)^2 nodes, node id =
+ *    iy*(2N+1) + ix at (ix/(2N), iy/(2N)); nodal velocity arrays are
+ *    interleaved [u_x, u_y] per node.  Pressure arrays hold 3 doubles per
+ *    cell (cell id = cy*N + cx) in the basis {1, (x-xc)/h, (y-yc)/h}, with
+ *    zero mean over the domain.  Solid arrays are interleaved [x, y] per node.
+ */
+#ifndef FSI_GB300_H
+#define FSI_GB300_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define FSI_OK                  0
+#define FSI_ERR_INVALID        -1  /* bad argument or parameter */
+#define FSI_ERR_OOM            -2  /* cudaMalloc failed */
+#define FSI_ERR_BUDGET         -3  /* footprint above the caller's byte budget */
+#define FSI_ERR_OUT_OF_DOMAIN  -4  /* a solid quadrature point left [0,1]^2 */
+#define FSI_ERR_NOT_CONVERGED  -5  /* max_it reached above rtol */
+#define FSI_ERR_BREAKDOWN      -6  /* Krylov breakdown (zero new direction) */
+#define FSI_ERR_NAN            -7  /* NaN/Inf in the residual */
+#define FSI_ERR_TIMEOUT        -8  /* a bounded device wait ran out */
+#define FSI_ERR_CAPACITY       -9  /* a coupling row exceeded its storage */
+#define FSI_ERR_CUDA          -10  /* a CUDA runtime call failed */
+
+/* Parameters of one instance (Section 4 and Section 6 of the paper). */
+typedef struct fsi_params {
+    int    N;          /* fluid cells per side, >= 2 */
+    double rho_f;      /* fluid (= solid) density, Problem 2: rho_s = rho_f */
+    double nu;         /* viscosity, nu_f = nu_s (Section 3) */
+    double kappa;      /* P(F) = kappa F (Section 4, before Eq. (matrix)) */
+    double dt;         /* backward-Euler time step (Section 4) */
+    double lid_u;      /* tangential velocity of the top wall, 0 = all walls at rest */
+    int    precond;    /* 0 block-diagonal, 1 block-triangular (Section 5) */
+    int    precision;  /* 0 FP64 everywhere; 1 FP32 operators and preconditioner
+                          inside FGMRES, FP64 Gram-Schmidt, least squares and
+                          iterative refinement */
+    int    restart;    /* GMRES restart length, paper: 200 (Section 6); 0 = 200 */
+    double rtol;       /* relative residual target, paper: 1e-8 (Section 6); 0 = 1e-8 */
+    int    max_it;     /* total Krylov iteration cap per step; 0 = 1000 */
+    int    mg_degree;  /* Chebyshev degree of each multigrid smoothing; 0 = 2 */
+    int    cs_degree;  /* Chebyshev iterations per solid mass solve; 0 = 16 */
+    double inner_rtol; /* precision 1: inner FGMRES tolerance; 0 = 1e-5 */
+    int    max_refine; /* precision 1: refinement steps cap; 0 = 30 */
+} fsi_params;
+
+/* Solid reference mesh (the body at t = 0, P1 triangles, counter-clockwise). */
+typedef struct fsi_solid_mesh {
+    int           n_nodes;
+    int           n_tris;
+    const double* ref_xy;  /* host, 2*n_nodes, interleaved (x, y) */
+    const int*    tris;    /* host, 3*n_tris node ids */
+} fsi_solid_mesh;
+
+/* Per-step report (the paper's its / T_coup / T_sol, Tables 1-4). */
+typedef struct fsi_solve_info {
+    int    iterations;       /* Krylov iterations (all refinements) */
+    int    refinements;      /* outer refinement steps (precision 1), else 0 */
+    int    restarts;         /* FGMRES restarts */
+    int    status;           /* same as the return value */
+    double rel_residual;     /* true ||b - A x|| / ||b|| in FP64 at exit */
+    double rel_residual_est; /* last Krylov estimate */
+} fsi_solve_info;
+
+typedef struct fsi_problem fsi_problem;  /* opaque; owns all device memory */
+
+/* Build constant matrices (M_f, K_f, B, A_s, C_s, multigrid hierarchy) and
+ * device state.  u0: host, 2*(2N+1)^2 nodal velocity (boundary entries are
+ * replaced by the wall data); X0: host, 2*n_nodes initial solid positions.
+ * cuda_stream: a cudaStream_t or NULL.  On success *out owns the problem. */
+int fsi_create_problem(const fsi_params* params, const fsi_solid_mesh* mesh,
+                       const double* u0, const double* X0, void* cuda_stream,
+                       fsi_problem** out);
+
+/* Bytes of device memory fsi_create_problem would allocate for these sizes. */
+size_t fsi_footprint_bytes(const fsi_params* params, int n_solid_nodes, int n_tris);
+
+/* Same as fsi_create_problem, but fails with FSI_ERR_BUDGET (allocating
+ * nothing) when fsi_footprint_bytes exceeds budget_bytes. */
+int fsi_create_problem_budget(const fsi_params* params, const fsi_solid_mesh* mesh,
+                              const double* u0, const double* X0, void* cuda_stream,
+                              size_t budget_bytes, fsi_problem** out);
+
+/* Steps S1-S4 on the device, asynchronous: locate the solid quadrature
+ * points in the fluid grid, assemble C_f(X^n) and its transpose, build the
+ * right-hand side (g1, g_p, 0, g2). */
+int fsi_assemble_step(fsi_problem* p);
+
+/* Steps S5-S8: FGMRES (precision 0) or FP64 iterative refinement around an
+ * FP32-operator FGMRES (precision 1) until ||b - A x|| / ||b|| <= rtol,
+ * warm-started from the current state.  Synchronises.  info may be NULL. */
+int fsi_solve_step(fsi_problem* p, fsi_solve_info* info);
+
+/* Step S9, asynchronous: (u^n, X^n) <- (u^{n+1}, X^{n+1}). */
+int fsi_advance(fsi_problem* p);
+
+/* assemble + solve + advance. */
+int fsi_step(fsi_problem* p, fsi_solve_info* info);
+
+/* Host copies of the current solution; any pointer may be NULL.
+ * u: 2*(2N+1)^2 (wall values included), pr: 3*N^2, X and lam: 2*n_nodes. */
+int fsi_get_state(fsi_problem* p, double* u, double* pr, double* X, double* lam);
+
+/* Replace (u^n, X^n) and the warm start of u and X; u: 2*(2N+1)^2 nodal,
+ * X: 2*n_nodes.  Either may be NULL (kept). */
+int fsi_set_state(fsi_problem* p, const double* u, const double* X);
+
+/* Sizes: n_u (interior velocity dofs), n_p, n_x (= 2*n_nodes), total n. */
+int fsi_sizes(const fsi_problem* p, int* n_u, int* n_p, int* n_x, int* n_total);
+
+/* Test hooks.  Point location of the last fsi_assemble_step: for point
+ * id = 6*triangle + q, the fluid cell id (cy*N + cx, or -1 outside) and the
+ * local coordinates (xi, eta) in [0,1]^2.  Arrays of 6*n_tris; may be NULL. */
+int fsi_get_points(fsi_problem* p, int* cell, double* xi, double* eta);
+
+/* Test hook: the scalar coupling matrix C of the last fsi_assemble_step in
+ * coordinate form (C_f = C on each velocity component).  Entries with a
+ * wall node column are included.  Call with rows == NULL to get the count
+ * in *nnz; then with arrays of that size: solid node, lattice node id, value. */
+int fsi_get_coupling(fsi_problem* p, int* nnz, int* rows, int* lattice_cols, double* vals);
+
+/* Test hook: y = A x for the full block operator in the library's block
+ * order [u_interior | p | X | lambda] on host arrays of length n_total;
+ * precision 0 = FP64 operator, 1 = FP32 operator.  Node order of u follows
+ * fsi_interior_nodes. */
+int fsi_apply_operator(fsi_problem* p, const double* x, double* y, int precision);
+
+/* Test hook: z = P^{-1} v, one application of the preconditioner. */
+int fsi_apply_preconditioner(fsi_problem* p, const double* v, double* z, int precision);
+
+/* Lattice node id of every interior velocity node, in the library's order
+ * (n_u/2 entries). */
+int fsi_interior_nodes(const fsi_problem* p, int* lattice_ids);
+
+/* Right-hand side of the last fsi_assemble_step in block order (n_total). */
+int fsi_get_rhs(fsi_problem* p, double* b);
+
+void fsi_destroy(fsi_problem* p);
+const char* fsi_status_str(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FSI_GB300_H */

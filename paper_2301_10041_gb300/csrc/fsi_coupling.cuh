@@ -1,0 +1,263 @@
+// Per-step coupling kernels (steps S2-S4): point location, assembly of
+// C_f(X^n) by rows of solid nodes, and its transpose by a counting sort of
+// the entries by fluid node.  Included by fsi_solver.cu only.
+#pragma once
+#include "fsi_kernels.cuh"
+
+namespace fsi {
+
+__constant__ double c_rule_lam[6][3];  // barycentric points of the degree-4 rule
+__constant__ double c_rule_w[6];       // weights, summing to 1
+
+// S2: x_q = P0 + xi1 (P1 - P0) + xi2 (P2 - P0), evaluated left to right with
+// explicitly rounded FP64 operations (no contraction), then the cell by the
+// half-open rule on t = x * N (the last cell is closed at x = 1).
+__global__ void k_locate(int n_pts, int N, const int* __restrict__ tris, const double* __restrict__ X,
+                         int* __restrict__ cell, double* __restrict__ xi, double* __restrict__ eta,
+                         int* __restrict__ flags) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n_pts) return;
+  const int t = p / 6, q = p - 6 * (p / 6);
+  const int v0 = tris[3 * t], v1 = tris[3 * t + 1], v2 = tris[3 * t + 2];
+  const double l1 = c_rule_lam[q][1], l2 = c_rule_lam[q][2];
+  const double fN = (double)N;
+  double loc[2];
+  int idx[2];
+  bool ok = true;
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    const double P0 = X[2 * v0 + c], P1 = X[2 * v1 + c], P2 = X[2 * v2 + c];
+    const double d1 = __dsub_rn(P1, P0), d2 = __dsub_rn(P2, P0);
+    const double xc = __dadd_rn(__dadd_rn(P0, __dmul_rn(l1, d1)), __dmul_rn(l2, d2));
+    if (!(xc >= 0.0 && xc <= 1.0)) { ok = false; idx[c] = 0; loc[c] = 0.0; continue; }
+    const double tc = __dmul_rn(xc, fN);
+    int i = (int)floor(tc);
+    if (i >= N) i = N - 1;
+    idx[c] = i;
+    loc[c] = __dsub_rn(tc, (double)i);
+  }
+  if (!ok) {
+    cell[p] = -1; xi[p] = 0.0; eta[p] = 0.0;
+    atomicOr(flags, FLAG_OUT_OF_DOMAIN);
+    return;
+  }
+  cell[p] = idx[1] * N + idx[0];
+  xi[p] = loc[0];
+  eta[p] = loc[1];
+}
+
+__device__ __forceinline__ double q2b(int a, double t) {
+  return a == 0 ? (1.0 - t) * (1.0 - 2.0 * t) : (a == 1 ? 4.0 * t * (1.0 - t) : t * (2.0 * t - 1.0));
+}
+
+// S4: one warp per solid node l.  Row l of the scalar coupling matrix,
+//   C_{l j} = sum_{T ni l} sum_q |T| w_q lam_l(q) phi_j(x_q),
+// is accumulated in a shared-memory window over the fluid lattice nodes of
+// the cells hit by the row's points, points taken in a fixed order (no
+// atomics, deterministic); then the window is compacted into the ELL row.
+// Columns on the wall go to the right-hand side (times the wall velocity).
+__global__ void __launch_bounds__(32 * kCfWarps) k_cf_rows(
+    int nS, int N, const int* __restrict__ ntp, const int* __restrict__ nt, const double* __restrict__ area,
+    const int* __restrict__ cell, const double* __restrict__ xi, const double* __restrict__ eta,
+    const int* __restrict__ l2n, const double* __restrict__ wall, int cap, int* __restrict__ len,
+    int* __restrict__ col, double* __restrict__ val, float* __restrict__ val32, double* __restrict__ lift,
+    int* __restrict__ flags) {
+  __shared__ double win[kCfWarps][kCfWindow];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int l = blockIdx.x * kCfWarps + warp;
+  if (l >= nS) return;
+  double* W = win[warp];
+  const int e0 = ntp[l], e1 = ntp[l + 1];
+  const int npt = 6 * (e1 - e0);
+  // bounding box of the cells of the row's points
+  int x0 = 1 << 30, y0 = 1 << 30, x1 = -1, y1 = -1;
+  bool bad = false;
+  for (int k = lane; k < npt; k += 32) {
+    const int e = nt[e0 + k / 6];
+    const int p = 6 * (e / 3) + (k % 6);
+    const int c = cell[p];
+    if (c < 0) { bad = true; continue; }
+    const int cx = c % N, cy = c / N;
+    x0 = min(x0, cx); x1 = max(x1, cx); y0 = min(y0, cy); y1 = max(y1, cy);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    x0 = min(x0, __shfl_xor_sync(0xffffffffu, x0, o));
+    y0 = min(y0, __shfl_xor_sync(0xffffffffu, y0, o));
+    x1 = max(x1, __shfl_xor_sync(0xffffffffu, x1, o));
+    y1 = max(y1, __shfl_xor_sync(0xffffffffu, y1, o));
+  }
+  bad = __any_sync(0xffffffffu, bad);
+  const int wn = 2 * (x1 - x0 + 1) + 1, hn = 2 * (y1 - y0 + 1) + 1;
+  if (bad || x1 < 0 || wn * hn > kCfWindow) {
+    if (lane == 0) {
+      len[l] = 0;
+      lift[2 * l] = 0.0; lift[2 * l + 1] = 0.0;
+      if (!bad && x1 >= 0) atomicOr(flags, FLAG_CAPACITY);
+    }
+    return;
+  }
+  for (int k = lane; k < wn * hn; k += 32) W[k] = 0.0;
+  __syncwarp();
+  for (int k = 0; k < npt; ++k) {
+    const int e = nt[e0 + k / 6];
+    const int t = e / 3, a = e - 3 * (e / 3), q = k % 6;
+    const int p = 6 * t + q;
+    const int c = cell[p];
+    const int cx = c % N, cy = c / N;
+    if (lane < 9) {
+      const int aa = lane % 3, bb = lane / 3;
+      const double wq = area[t] * c_rule_w[q] * c_rule_lam[q][a];
+      const double phi = q2b(aa, xi[p]) * q2b(bb, eta[p]);
+      W[(2 * (cy - y0) + bb) * wn + 2 * (cx - x0) + aa] += wq * phi;
+    }
+    __syncwarp();
+  }
+  // compaction into the ELL row (slot = (l/32)*32*cap + k*32 + l%32)
+  const size_t base = (size_t)(l >> 5) * 32 * cap + (l & 31);
+  const int n1 = 2 * N + 1;
+  int cnt = 0;
+  double lx = 0.0, ly = 0.0;
+  for (int k0 = 0; k0 < wn * hn; k0 += 32) {
+    const int k = k0 + lane;
+    double v = 0.0;
+    int node = -1, lat = 0;
+    if (k < wn * hn) {
+      v = W[k];
+      const int ix = 2 * x0 + k % wn, iy = 2 * y0 + k / wn;
+      lat = iy * n1 + ix;
+      node = l2n[lat];
+    }
+    const bool interior = (v != 0.0) && node >= 0;
+    if (v != 0.0 && node < 0) { lx += v * wall[2 * lat]; ly += v * wall[2 * lat + 1]; }
+    const unsigned m = __ballot_sync(0xffffffffu, interior);
+    const int pos = cnt + __popc(m & ((1u << lane) - 1u));
+    if (interior) {
+      if (pos < cap) {
+        const size_t slot = base + ((size_t)pos << 5);
+        col[slot] = node;
+        val[slot] = v;
+        val32[slot] = (float)v;
+      }
+    }
+    cnt += __popc(m);
+  }
+  lx = warp_sum(lx);
+  ly = warp_sum(ly);
+  if (lane == 0) {
+    if (cnt > cap) { atomicOr(flags, FLAG_CAPACITY); cnt = cap; }
+    len[l] = cnt;
+    lift[2 * l] = lx;
+    lift[2 * l + 1] = ly;
+  }
+}
+
+// S3 (the "hash grid"): counting sort of the C_f entries by fluid node.
+__global__ void k_cft_count(int nS, int cap, const int* __restrict__ len, const int* __restrict__ col,
+                            int* __restrict__ cnt) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int l = i / cap, k = i - cap * (i / cap);
+  if (l >= nS || k >= len[l]) return;
+  atomicAdd(&cnt[col[(size_t)(l >> 5) * 32 * cap + ((size_t)k << 5) + (l & 31)]], 1);
+}
+
+constexpr int kScanBlock = 1024;
+
+// exclusive scan of cnt[0..n) into out[0..n], three phases
+__global__ void k_scan_partial(int n, const int* __restrict__ in, int* __restrict__ bsum) {
+  __shared__ int sm[32];
+  const int i = blockIdx.x * kScanBlock + threadIdx.x;
+  int v = (i < n) ? in[i] : 0;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    int s = sm[threadIdx.x];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = s;
+  }
+}
+
+__device__ __forceinline__ int block_excl_scan(int v, int* sm, int& total) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  if (lane == 31) sm[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    int s = (lane < (int)(blockDim.x >> 5)) ? sm[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += t;
+    }
+    sm[lane] = s;
+  }
+  __syncthreads();
+  total = sm[(blockDim.x >> 5) - 1];
+  const int before = (w > 0) ? sm[w - 1] : 0;
+  const int r = before + inc - v;
+  __syncthreads();
+  return r;
+}
+
+__global__ void k_scan_top(int nb, int* __restrict__ bsum) {
+  __shared__ int sm[32];
+  int carry = 0;
+  for (int b0 = 0; b0 < nb; b0 += kScanBlock) {
+    const int i = b0 + threadIdx.x;
+    const int v = (i < nb) ? bsum[i] : 0;
+    int total;
+    const int e = block_excl_scan(v, sm, total);
+    if (i < nb) bsum[i] = carry + e;
+    carry += total;
+  }
+}
+
+__global__ void k_scan_final(int n, const int* __restrict__ in, const int* __restrict__ bsum,
+                             int* __restrict__ out, int* __restrict__ cursor) {
+  __shared__ int sm[32];
+  const int i = blockIdx.x * kScanBlock + threadIdx.x;
+  const int v = (i < n) ? in[i] : 0;
+  int total;
+  const int e = block_excl_scan(v, sm, total) + bsum[blockIdx.x];
+  if (i < n) { out[i] = e; cursor[i] = e; }
+  if (i == n - 1) out[n] = e + v;
+}
+
+__global__ void k_cft_scatter(int nS, int cap, const int* __restrict__ len, const int* __restrict__ col,
+                              const double* __restrict__ val, int* __restrict__ cursor, int* __restrict__ tcol,
+                              double* __restrict__ tval) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int l = i / cap, k = i - cap * (i / cap);
+  if (l >= nS || k >= len[l]) return;
+  const size_t slot = (size_t)(l >> 5) * 32 * cap + ((size_t)k << 5) + (l & 31);
+  const int pos = atomicAdd(&cursor[col[slot]], 1);
+  tcol[pos] = l;
+  tval[pos] = val[slot];
+}
+
+// sort each transposed row by solid node (the scatter order is not fixed)
+__global__ void k_cft_sort(int nU, const int* __restrict__ ptr, int* __restrict__ tcol, double* __restrict__ tval,
+                           float* __restrict__ tval32) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nU) return;
+  const int a = ptr[r], b = ptr[r + 1];
+  for (int i = a + 1; i < b; ++i) {
+    const int c = tcol[i];
+    const double v = tval[i];
+    int j = i - 1;
+    while (j >= a && tcol[j] > c) { tcol[j + 1] = tcol[j]; tval[j + 1] = tval[j]; --j; }
+    tcol[j + 1] = c;
+    tval[j + 1] = v;
+  }
+  for (int i = a; i < b; ++i) tval32[i] = (float)tval[i];
+}
+
+}  // namespace fsi

@@ -1,0 +1,100 @@
+// Internal declarations shared by the host setup, the kernels and the
+// solver of the GB300 FSI library.  Nothing here is part of the C ABI.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+
+namespace fsi {
+
+// ---------------------------------------------------------------- host side
+// Block-sparse matrix with BR x BC blocks; KRON blocks store one scalar s and
+// act as s * I (BR == BC).  Rows are sorted by column.
+struct HostBlockMatrix {
+  int BR = 1, BC = 1, NV = 1;   // NV: values stored per block
+  bool kron = false;
+  int nrows = 0, ncols = 0;     // block rows / block columns
+  std::vector<int> ptr, col;
+  std::vector<double> val;      // NV per block, row-major inside a block
+  size_t nnzb() const { return col.size(); }
+};
+
+// Type-blocked numbering of the interior Q2 nodes of an N x N grid:
+// cell corners, then x-edge midpoints, then y-edge midpoints, then cell
+// centres, each block in lattice order.  Rows of one block have the same
+// stencil, so a 32-row slice needs little padding.
+struct VNum {
+  int N = 0, nV = 0, nX = 0, nY = 0, nC = 0, n = 0;
+  explicit VNum(int N_ = 0);
+  int id(int ix, int iy) const;                 // lattice -> internal, -1 on the wall
+  void lattice(int k, int& ix, int& iy) const;  // internal -> lattice
+};
+
+struct FluidLevelHost {
+  int N = 0;
+  double h = 0;
+  HostBlockMatrix A;      // A_f = (rho/dt) M + K, 2x2 blocks over interior nodes
+  HostBlockMatrix L;      // pressure Laplacian B diag(M)^-1 B^T, 3x3 cell blocks
+  HostBlockMatrix Pu, Ru; // velocity prolongation from / restriction to the coarser level (kron 2)
+  HostBlockMatrix Pp, Rp; // pressure prolongation / restriction (3x3)
+  std::vector<double> dinvA, dinvL;  // Jacobi inverses (per scalar dof)
+  double lmaxA = 0, lmaxL = 0;       // lambda_max of D^-1 A and D^-1 L
+};
+
+struct SetupParams {
+  int N; double rho, nu, kappa, dt, lid;
+};
+
+struct HostSetup {
+  // finest level operators of Eq. (matrix)
+  HostBlockMatrix M;      // fluid mass (kron 2) over interior nodes
+  HostBlockMatrix Bt;     // -B^T: node rows x cell columns, 2x3 blocks (sign folded in)
+  HostBlockMatrix Bneg;   // -B: cell rows x node columns, 3x2 blocks (sign folded in)
+  HostBlockMatrix Ssol;   // solid pair: per block (A_s, C_s) scalars, NV = 2
+  HostBlockMatrix Cs;     // solid mass (kron 2)
+  HostBlockMatrix As;     // solid stiffness (kron 2)
+  std::vector<double> lift_u;  // -K_ID u_D on interior velocity rows
+  std::vector<double> lift_p;  // B_D u_D on pressure rows
+  std::vector<double> mp_inv;  // inverse P1disc mass diagonal, 3 per cell
+  std::vector<double> cs_dinv; // inverse diagonal of the solid mass
+  std::vector<FluidLevelHost> levels;  // 0 = finest
+  std::vector<double> coarseAinv;   // dense inverse of the coarsest A_f (row-major)
+  std::vector<double> coarseLinv;   // dense pseudo-inverse of the coarsest pressure Laplacian
+  int coarse_nA = 0, coarse_nL = 0;
+  std::vector<int> interior_lattice;   // internal node -> lattice id (finest)
+  std::vector<int> lattice_to_node;    // lattice id -> internal node or -1
+  std::vector<double> wall_u;          // lattice nodal wall data, 2 per node
+  // solid mesh data for the coupling assembly
+  std::vector<double> tri_area;        // reference areas
+  std::vector<int> node_tri_ptr, node_tri;  // node -> (triangle*3 + local vertex)
+};
+
+void build_setup(const SetupParams& sp, int n_s, int n_tri, const double* ref_xy,
+                 const int* tris, HostSetup& out);
+
+// 6-point degree-4 symmetric triangle rule (Dunavant 1985): barycentric
+// (lam0, lam1, lam2) and weights summing to 1, in the order used by the
+// point-location kernel (point id = 6*triangle + q).
+void triangle_rule(double lam[6][3], double w[6]);
+
+// ------------------------------------------------------------- device side
+template <class T>
+struct Sell {            // sliced ELL of block rows, slice height 32
+  int nrows = 0;         // block rows
+  int BR = 1, BC = 1, NV = 1;
+  bool kron = false;
+  const int* soff = nullptr;  // per slice: first slot
+  const int* len = nullptr;   // per block row
+  const int* col = nullptr;   // per slot
+  const T* val = nullptr;     // NV per slot
+};
+
+struct SellHost {        // SELL arrays before upload
+  int nrows = 0, nslices = 0, BR = 1, BC = 1, NV = 1;
+  bool kron = false;
+  std::vector<int> soff, len, col;
+  std::vector<double> val;
+};
+SellHost to_sell(const HostBlockMatrix& A);
+
+}  // namespace fsi

@@ -1,0 +1,1281 @@
+// GB300 (sm_103a) solver for one time step of the DLM fictitious-domain FSI
+// method (Boffi, Credali, Gastaldi, Scacchi, arXiv:2301.10041), and the C ABI
+// declared in include/fsi.h.
+//
+// Per step (Section 4): S1 right-hand side, S2 point location, S3 binning of
+// the coupling entries by fluid node, S4 C_f(X^n) and its transpose, S5 the
+// block operator of Eq. (matrix), S6 the block-diagonal / block-triangular
+// preconditioner of Section 5, S7 flexible GMRES (CGS2, Givens on device,
+// the whole Arnoldi loop inside one CUDA graph WHILE node), S8 FP64 iterative
+// refinement around FP32 operators, S9 advance.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <stdexcept>
+#include <string>
+#include <type_traits>
+#include <vector>
+
+#include "../../include/fsi.h"
+#include "fsi_coupling.cuh"
+#include "fsi_internal.h"
+#include "fsi_kernels.cuh"
+
+namespace fsi {
+
+struct CudaError : std::runtime_error {
+  cudaError_t code;
+  explicit CudaError(cudaError_t c, const char* what) : std::runtime_error(what), code(c) {}
+};
+#define CK(x)                                                                 \
+  do {                                                                        \
+    cudaError_t e_ = (x);                                                     \
+    if (e_ != cudaSuccess) throw CudaError(e_, #x);                           \
+  } while (0)
+
+static inline unsigned nblk(size_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+// ------------------------------------------------------------ device memory
+struct Arena {
+  std::vector<void*> ptrs;
+  size_t bytes = 0;
+  bool count_only = false;
+  template <class T>
+  T* alloc(size_t n) {
+    const size_t b = std::max<size_t>(n, 1) * sizeof(T);
+    bytes += (b + 255) & ~(size_t)255;
+    if (count_only) return nullptr;
+    void* p = nullptr;
+    if (cudaMalloc(&p, b) != cudaSuccess) throw std::bad_alloc();
+    ptrs.push_back(p);
+    return (T*)p;
+  }
+  template <class T>
+  T* upload(const std::vector<T>& h) {
+    T* d = alloc<T>(h.size());
+    if (d && !h.empty()) CK(cudaMemcpy(d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return d;
+  }
+  void release() {
+    for (void* p : ptrs) cudaFree(p);
+    ptrs.clear();
+  }
+};
+
+template <class T>
+static Sell<T> upload_sell(Arena& ar, const SellHost& s) {
+  Sell<T> d;
+  d.nrows = s.nrows; d.BR = s.BR; d.BC = s.BC; d.NV = s.NV; d.kron = s.kron;
+  d.soff = ar.upload(s.soff);
+  d.len = ar.upload(s.len);
+  d.col = ar.upload(s.col);
+  std::vector<T> v(s.val.begin(), s.val.end());
+  d.val = ar.upload(v);
+  return d;
+}
+
+template <class T>
+static T* upload_as(Arena& ar, const std::vector<double>& h) {
+  std::vector<T> v(h.begin(), h.end());
+  return ar.upload(v);
+}
+
+// ------------------------------------------------------------- SpMV launch
+template <class T, int BR, int BC, bool KRON, int NV>
+static void sell_launch_shape(const Sell<T>& A, int mode, const SpmvArgs<T>& a, cudaStream_t s) {
+  const unsigned g = nblk(A.nrows, 128);
+  switch (mode) {
+    case MODE_AXPBY: k_sell<T, BR, BC, KRON, NV, MODE_AXPBY><<<g, 128, 0, s>>>(A.nrows, A.soff, A.len, A.col, A.val, a); break;
+    case MODE_CHEB: k_sell<T, BR, BC, KRON, NV, MODE_CHEB><<<g, 128, 0, s>>>(A.nrows, A.soff, A.len, A.col, A.val, a); break;
+    case MODE_CHEB0: k_sell<T, BR, BC, KRON, NV, MODE_CHEB0><<<g, 128, 0, s>>>(A.nrows, A.soff, A.len, A.col, A.val, a); break;
+    default: k_sell<T, BR, BC, KRON, NV, MODE_INIT><<<g, 128, 0, s>>>(A.nrows, A.soff, A.len, A.col, A.val, a); break;
+  }
+}
+
+template <class T>
+static void sell_launch(const Sell<T>& A, int mode, const SpmvArgs<T>& a, cudaStream_t s) {
+  if (A.nrows == 0) return;
+  if (A.kron && A.BR == 2) return sell_launch_shape<T, 2, 2, true, 1>(A, mode, a, s);
+  if (A.BR == 2 && A.BC == 2) return sell_launch_shape<T, 2, 2, false, 4>(A, mode, a, s);
+  if (A.BR == 2 && A.BC == 3) return sell_launch_shape<T, 2, 3, false, 6>(A, mode, a, s);
+  if (A.BR == 3 && A.BC == 2) return sell_launch_shape<T, 3, 2, false, 6>(A, mode, a, s);
+  if (A.BR == 3 && A.BC == 3) return sell_launch_shape<T, 3, 3, false, 9>(A, mode, a, s);
+  throw std::logic_error("unsupported block shape");
+}
+
+template <class T>
+static SpmvArgs<T> axpby(const T* x, T* y, const T* z, T alpha, T beta) {
+  SpmvArgs<T> a;
+  a.x = x; a.y = y; a.z = z; a.alpha = alpha; a.beta = beta;
+  return a;
+}
+
+// ---------------------------------------------------------------- multigrid
+struct Cheb {
+  double c0;                 // first step: d = c0 dinv r
+  std::vector<double> c1, c2;  // steps 1..k-1
+};
+
+static Cheb cheb_coeffs(double lo, double hi, int k) {
+  Cheb c;
+  const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo), sigma = theta / delta;
+  c.c0 = 1.0 / theta;
+  double rho_old = 1.0 / sigma;
+  for (int i = 1; i < k; ++i) {
+    const double rho = 1.0 / (2.0 * sigma - rho_old);
+    c.c1.push_back(rho * rho_old);
+    c.c2.push_back(2.0 * rho / delta);
+    rho_old = rho;
+  }
+  return c;
+}
+
+template <class T>
+struct MGLevel {
+  Sell<T> A, P, R;  // P: prolongation from the next coarser level, R: restriction to it
+  T* dinv = nullptr;
+  T *x = nullptr, *x2 = nullptr, *b = nullptr, *r = nullptr, *d = nullptr;
+  int n = 0;        // scalar unknowns
+  Cheb ch;
+};
+
+template <class T>
+struct MG {
+  std::vector<MGLevel<T>> lv;
+  T* coarse_inv = nullptr;
+  int coarse_n = 0;
+  int degree = 2;
+};
+
+constexpr double kChebRatioU = 6.0;   // smoothing interval [hi/ratio, hi]
+constexpr double kChebRatioP = 8.0;
+
+template <class T>
+static void build_mg(Arena& ar, const HostSetup& hs, bool pressure, int degree, MG<T>& mg) {
+  const int nl = (int)hs.levels.size();
+  mg.degree = degree;
+  mg.lv.resize(nl);
+  for (int l = 0; l < nl; ++l) {
+    const FluidLevelHost& H = hs.levels[l];
+    MGLevel<T>& L = mg.lv[l];
+    const HostBlockMatrix& A = pressure ? H.L : H.A;
+    L.A = upload_sell<T>(ar, to_sell(A));
+    L.n = A.nrows * A.BR;
+    L.dinv = upload_as<T>(ar, pressure ? H.dinvL : H.dinvA);
+    if (l + 1 < nl) {
+      L.P = upload_sell<T>(ar, to_sell(pressure ? H.Pp : H.Pu));
+      L.R = upload_sell<T>(ar, to_sell(pressure ? H.Rp : H.Ru));
+    }
+    L.x = ar.alloc<T>(L.n); L.x2 = ar.alloc<T>(L.n); L.b = ar.alloc<T>(L.n);
+    L.r = ar.alloc<T>(L.n); L.d = ar.alloc<T>(L.n);
+    const double hi = 1.05 * (pressure ? H.lmaxL : H.lmaxA);
+    L.ch = cheb_coeffs(hi / (pressure ? kChebRatioP : kChebRatioU), hi, degree);
+  }
+  mg.coarse_inv = upload_as<T>(ar, pressure ? hs.coarseLinv : hs.coarseAinv);
+  mg.coarse_n = pressure ? hs.coarse_nL : hs.coarse_nA;
+}
+
+// Level l input: L.b, with L.x = L.d = c0 dinv b already set (l < last).
+// Result of the level is written to `out` (if given) or returned.
+template <class T>
+static T* vcycle(MG<T>& mg, int l, cudaStream_t s, T* out) {
+  const int last = (int)mg.lv.size() - 1;
+  MGLevel<T>& L = mg.lv[l];
+  if (l == last) {
+    k_dense_mv<T><<<1, 128, 0, s>>>(mg.coarse_n, mg.coarse_inv, L.b, out ? out : L.x);
+    return out ? out : L.x;
+  }
+  T* xc = L.x;
+  T* xn = L.x2;
+  const int k = mg.degree;
+  for (int i = 1; i < k; ++i) {  // pre-smoothing, zero initial guess
+    SpmvArgs<T> a;
+    a.x = xc; a.y = xn; a.z = L.b; a.d = L.d; a.dinv = L.dinv;
+    a.c1 = (T)L.ch.c1[i - 1]; a.c2 = (T)L.ch.c2[i - 1];
+    sell_launch(L.A, MODE_CHEB, a, s);
+    std::swap(xc, xn);
+  }
+  sell_launch(L.A, MODE_AXPBY, axpby<T>(xc, L.r, L.b, (T)-1, (T)1), s);
+  MGLevel<T>& C = mg.lv[l + 1];
+  if (l + 1 == last) {
+    sell_launch(L.R, MODE_AXPBY, axpby<T>(L.r, C.b, nullptr, (T)1, (T)0), s);
+  } else {
+    SpmvArgs<T> a = axpby<T>(L.r, C.b, nullptr, (T)1, (T)0);
+    a.d = C.d; a.dinv = C.dinv; a.xo = C.x; a.c2 = (T)C.ch.c0;
+    sell_launch(L.R, MODE_INIT, a, s);
+  }
+  T* xcoarse = vcycle<T>(mg, l + 1, s, (T*)nullptr);
+  sell_launch(L.P, MODE_AXPBY, axpby<T>(xcoarse, xc, xc, (T)1, (T)1), s);
+  for (int i = 0; i < k; ++i) {  // post-smoothing
+    SpmvArgs<T> a;
+    T* dst = (i == k - 1 && out) ? out : xn;
+    a.x = xc; a.y = dst; a.z = L.b; a.d = L.d; a.dinv = L.dinv;
+    if (i == 0) { a.c2 = (T)L.ch.c0; sell_launch(L.A, MODE_CHEB0, a, s); }
+    else { a.c1 = (T)L.ch.c1[i - 1]; a.c2 = (T)L.ch.c2[i - 1]; sell_launch(L.A, MODE_CHEB, a, s); }
+    if (dst == out) return out;
+    std::swap(xc, xn);
+  }
+  return xc;
+}
+
+// ----------------------------------------------------------- preconditioner
+template <class T>
+struct Prec {
+  MG<T> mgU, mgP;
+  FullOp<T> op;          // operator in this precision (shares structure arrays)
+  Sell<T> Cs, As;
+  T* mpinv = nullptr;    // inverse P1disc mass diagonal
+  T* csdinv = nullptr;   // inverse diagonal of the solid mass
+  T* vin = nullptr;      // preconditioner input (n)
+  T* zw = nullptr;       // preconditioner output (n)
+  T *sb = nullptr, *sx = nullptr, *sx2 = nullptr, *sd = nullptr;  // solid work (2 nS)
+  Cheb chs;              // Chebyshev on [1/2, 2] for D^-1 C_s (Wathen's bounds for P1)
+  int cs_k = 16;
+};
+
+struct Problem;
+template <class T> static void precond_launch(Problem& P, Prec<T>& pr, cudaStream_t s);
+
+// -------------------------------------------------------------- the problem
+struct Problem {
+  fsi_params prm{};
+  int N = 0, nU = 0, nP = 0, nS = 0, nTri = 0, nPts = 0;
+  size_t n = 0, offP = 0, offX = 0, offL = 0;
+  cudaStream_t stream = nullptr, s2 = nullptr;
+  bool own_stream = false;
+  int device = 0;
+  Arena ar;
+  HostSetup hs;
+  // operators
+  FullOp<double> op64;
+  FullOp<float> op32;
+  Sell<double> M64, Cs64;
+  // coupling
+  int* tris = nullptr; double* area = nullptr; int* ntp = nullptr; int* nt = nullptr;
+  int* l2n = nullptr; double* wall = nullptr;
+  int* cell = nullptr; double* xi = nullptr; double* eta = nullptr;
+  int cf_cap = 64;
+  int* cf_len = nullptr; int* cf_col = nullptr; double* cf_val = nullptr; float* cf_val32 = nullptr;
+  double* cflift = nullptr;
+  int* cft_ptr = nullptr; int* cft_col = nullptr; double* cft_val = nullptr; float* cft_val32 = nullptr;
+  int* cft_cnt = nullptr; int* cft_cur = nullptr; int* scan_bsum = nullptr;
+  // state
+  double *x = nullptr, *b = nullptr, *uold = nullptr, *Xold = nullptr, *lift_u = nullptr, *w = nullptr;
+  // Krylov
+  int m = 200;
+  double *V = nullptr, *H = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr, *y = nullptr, *part = nullptr;
+  void* Z = nullptr;
+  Ctl* ctl = nullptr;
+  Ctl* ctl_host = nullptr;   // pinned mirror
+  int red_blocks = 0;
+  // preconditioners
+  Prec<double> p64;
+  Prec<float> p32;
+  // graphs
+  cudaGraphExec_t g_assemble = nullptr, g_begin = nullptr, g_cycle = nullptr, g_finish = nullptr;
+  cudaGraph_t gr_assemble = nullptr, gr_begin = nullptr, gr_cycle = nullptr, gr_finish = nullptr;
+  bool assembled = false;
+};
+
+// ------------------------------------------------------- solid block A_22^-1
+// Exact up to the two C_s solves (Chebyshev-Jacobi on [1/2, 2], Wathen's
+// bounds for the Jacobi-scaled P1 mass matrix):
+//   X = -dt C_s^-1 r_l,   lambda = C_s^-1 (A_s X - r_X),
+// with r_l = v_l - C_f z_u for the block-triangular preconditioner.
+template <class T>
+static void solid_launch(Problem& P, Prec<T>& pr, cudaStream_t s) {
+  const int n2 = 2 * P.nS;
+  if (n2 == 0) return;
+  const T* vX = pr.vin + P.offX;
+  const T* vL = pr.vin + P.offL;
+  T* zX = pr.zw + P.offX;
+  T* zL = pr.zw + P.offL;
+  const T dt = (T)P.prm.dt;
+  auto cheb_rest = [&](T* out) {
+    T* xc = pr.sx;
+    T* xn = pr.sx2;
+    if (pr.cs_k == 1) { k_copy<T><<<nblk(n2, 256), 256, 0, s>>>(n2, pr.sx, out); return; }
+    for (int i = 1; i < pr.cs_k; ++i) {
+      SpmvArgs<T> a;
+      T* dst = (i == pr.cs_k - 1) ? out : xn;
+      a.x = xc; a.y = dst; a.z = pr.sb; a.d = pr.sd; a.dinv = pr.csdinv;
+      a.c1 = (T)pr.chs.c1[i - 1]; a.c2 = (T)pr.chs.c2[i - 1];
+      sell_launch(pr.Cs, MODE_CHEB, a, s);
+      std::swap(xc, xn);
+    }
+  };
+  if (P.prm.precond == 1) {
+    SpmvArgs<T> a;
+    a.x = pr.zw; a.y = pr.sb; a.z = vL; a.alpha = dt; a.beta = -dt;
+    a.d = pr.sd; a.dinv = pr.csdinv; a.xo = pr.sx; a.c2 = (T)pr.chs.c0;
+    k_cf_apply<T><<<nblk(P.nS, 128), 128, 0, s>>>(P.nS, P.cf_cap, P.cf_len, P.cf_col, pr.op.cf_val, a, MODE_INIT);
+  } else {
+    k_cheb_first<T><<<nblk(n2, 256), 256, 0, s>>>(n2, vL, pr.csdinv, (T)pr.chs.c0, pr.sd, pr.sx, -dt, pr.sb);
+  }
+  cheb_rest(zX);
+  SpmvArgs<T> a2;
+  a2.x = zX; a2.y = pr.sb; a2.z = vX; a2.alpha = 1; a2.beta = -1;
+  a2.d = pr.sd; a2.dinv = pr.csdinv; a2.xo = pr.sx; a2.c2 = (T)pr.chs.c0;
+  sell_launch(pr.As, MODE_INIT, a2, s);
+  cheb_rest(zL);
+}
+
+// One application z = P^-1 v of the block preconditioner (Section 5), input
+// pr.vin, output pr.zw.  A_11^-1 is approximated by the upper block-
+// triangular Stokes preconditioner: p = -S^-1 v_p with the Cahouet-Chabard
+// Schur approximation S^-1 ~ nu M_p^-1 + (rho/dt) L_p^-1 (one V-cycle on the
+// pressure Laplacian L_p = B diag(M_f)^-1 B^T), then u = A_f^-1 (v_u + B^T p)
+// by one V-cycle with Chebyshev-Jacobi smoothing on the Q2 hierarchy.
+template <class T>
+static void precond_launch(Problem& P, Prec<T>& pr, cudaStream_t s) {
+  const int n3 = 3 * P.nP;
+  T* vp = pr.vin + P.offP;
+  T* zp = pr.zw + P.offP;
+  MGLevel<T>& L0p = pr.mgP.lv[0];
+  k_cheb_first<T><<<nblk(n3, 256), 256, 0, s>>>(n3, vp, L0p.dinv, (T)L0p.ch.c0, L0p.d, L0p.x, (T)1, L0p.b);
+  T* sp = vcycle<T>(pr.mgP, 0, s, (T*)nullptr);
+  k_schur<T><<<nblk(n3, 256), 256, 0, s>>>(n3, vp, sp, pr.mpinv, (T)P.prm.nu, (T)(P.prm.rho_f / P.prm.dt), zp);
+  MGLevel<T>& L0u = pr.mgU.lv[0];
+  SpmvArgs<T> a;
+  a.x = zp; a.y = L0u.b; a.z = pr.vin; a.alpha = -1; a.beta = 1;
+  a.d = L0u.d; a.dinv = L0u.dinv; a.xo = L0u.x; a.c2 = (T)L0u.ch.c0;
+  sell_launch(pr.op.Bt, MODE_INIT, a, s);
+  vcycle(pr.mgU, 0, s, pr.zw);
+  solid_launch(P, pr, s);
+}
+
+// --------------------------------------------------------- Krylov kernels
+constexpr int kRedMax = 304;  // 2 CTAs per SM
+
+__device__ void block_mdot(const double* __restrict__ V, size_t ld, int cnt, const double* __restrict__ w,
+                           int r0, int r1, double* __restrict__ part_row) {
+  __shared__ double sm[4][32];
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i0 = 0; i0 < cnt; i0 += 4) {
+    double acc[4] = {0, 0, 0, 0};
+    for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+      const double wv = w[r];
+#pragma unroll
+      for (int t = 0; t < 4; ++t)
+        if (i0 + t < cnt) acc[t] += V[(size_t)(i0 + t) * ld + r] * wv;
+    }
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      acc[t] = warp_sum(acc[t]);
+      if (lane == 0) sm[t][wp] = acc[t];
+    }
+    __syncthreads();
+    if (threadIdx.x < 4 && i0 + (int)threadIdx.x < cnt) {
+      double v = 0;
+      for (int q = 0; q < nw; ++q) v += sm[threadIdx.x][q];
+      part_row[i0 + threadIdx.x] = v;
+    }
+    __syncthreads();
+  }
+}
+
+__device__ void finalize_parts(const double* __restrict__ part, int pstride, int cnt, double* __restrict__ out) {
+  for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+    double v = 0;
+    for (int b = 0; b < (int)gridDim.x; ++b) v += part[(size_t)b * pstride + i];
+    out[i] = v;
+  }
+}
+
+struct KrylovArgs {
+  int n;
+  int chunk;
+  size_t ld;
+  const double* V;
+  double* w;
+  double* part;
+  int pstride;
+  double* h1;
+  double* h2;
+  double* H;
+  double* cs;
+  double* sn;
+  double* g;
+  Ctl* ctl;
+  cudaGraphConditionalHandle cond;
+};
+
+// CGS2 pass 1: h1 = V[0..j]^T w
+__global__ void __launch_bounds__(kRedThreads) k_gs1(KrylovArgs k) {
+  const int cnt = k.ctl->j + 1;
+  const int r0 = blockIdx.x * k.chunk, r1 = min(k.n, r0 + k.chunk);
+  block_mdot(k.V, k.ld, cnt, k.w, r0, r1, k.part + (size_t)blockIdx.x * k.pstride);
+  if (last_block(&k.ctl->counter[0])) {
+    finalize_parts(k.part, k.pstride, cnt, k.h1);
+    if (threadIdx.x == 0) k.ctl->counter[0] = 0;
+  }
+}
+
+// CGS2 pass 2: w -= V h1; h2 = V^T w
+__global__ void __launch_bounds__(kRedThreads) k_gs2(KrylovArgs k) {
+  __shared__ double hs[256];
+  const int cnt = k.ctl->j + 1;
+  for (int i = threadIdx.x; i < cnt; i += blockDim.x) hs[i] = k.h1[i];
+  __syncthreads();
+  const int r0 = blockIdx.x * k.chunk, r1 = min(k.n, r0 + k.chunk);
+  for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+    double v = k.w[r];
+    for (int i = 0; i < cnt; ++i) v -= k.V[(size_t)i * k.ld + r] * hs[i];
+    k.w[r] = v;
+  }
+  block_mdot(k.V, k.ld, cnt, k.w, r0, r1, k.part + (size_t)blockIdx.x * k.pstride);
+  if (last_block(&k.ctl->counter[1])) {
+    finalize_parts(k.part, k.pstride, cnt, k.h2);
+    if (threadIdx.x == 0) k.ctl->counter[1] = 0;
+  }
+}
+
+// CGS2 pass 3: w -= V h2; ||w||; Hessenberg column, Givens rotation,
+// residual estimate and the stop decision of the Arnoldi loop (on device).
+__global__ void __launch_bounds__(kRedThreads) k_gs3(KrylovArgs k) {
+  __shared__ double hs[256];
+  __shared__ double sm[32];
+  const int cnt = k.ctl->j + 1;
+  for (int i = threadIdx.x; i < cnt; i += blockDim.x) hs[i] = k.h2[i];
+  __syncthreads();
+  const int r0 = blockIdx.x * k.chunk, r1 = min(k.n, r0 + k.chunk);
+  double acc = 0;
+  for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+    double v = k.w[r];
+    for (int i = 0; i < cnt; ++i) v -= k.V[(size_t)i * k.ld + r] * hs[i];
+    k.w[r] = v;
+    acc += v * v;
+  }
+  acc = block_sum(acc, sm);
+  if (threadIdx.x == 0) k.part[(size_t)blockIdx.x * k.pstride] = acc;
+  if (last_block(&k.ctl->counter[2])) {
+    double s2 = 0;
+    if (threadIdx.x == 0) {
+      for (int b = 0; b < (int)gridDim.x; ++b) s2 += k.part[(size_t)b * k.pstride];
+      Ctl* c = k.ctl;
+      c->counter[2] = 0;
+      const int j = c->j, m1 = c->m + 1;
+      double* Hc = k.H + (size_t)j * m1;
+      for (int i = 0; i <= j; ++i) Hc[i] = k.h1[i] + k.h2[i];
+      const double nrm = sqrt(s2);
+      Hc[j + 1] = nrm;
+      for (int i = 0; i < j; ++i) {
+        const double a = Hc[i], b = Hc[i + 1];
+        Hc[i] = k.cs[i] * a + k.sn[i] * b;
+        Hc[i + 1] = -k.sn[i] * a + k.cs[i] * b;
+      }
+      const double a = Hc[j], b = Hc[j + 1];
+      const double r = hypot(a, b);
+      const double cc = (r > 0) ? a / r : 1.0, ss = (r > 0) ? b / r : 0.0;
+      k.cs[j] = cc; k.sn[j] = ss;
+      Hc[j] = r; Hc[j + 1] = 0.0;
+      k.g[j + 1] = -ss * k.g[j];
+      k.g[j] = cc * k.g[j];
+      const double res = fabs(k.g[j + 1]);
+      c->its += 1;
+      c->res = res;
+      bool stop = false;
+      if (!(res == res) || !(nrm == nrm)) { c->flags |= FLAG_NAN; stop = true; c->j = j; }
+      else if (r == 0.0) { c->flags |= FLAG_BREAKDOWN; stop = true; c->j = j; }
+      else {
+        c->j = j + 1;
+        if (res <= c->cycle_tol || j + 1 >= c->m || c->its >= c->max_it || nrm == 0.0) stop = true;
+      }
+      c->scale = (nrm > 0.0) ? 1.0 / nrm : 0.0;
+      cudaGraphSetConditional(k.cond, stop ? 0u : 1u);
+    }
+  }
+}
+
+// V[j] = w * scale (j already advanced)
+__global__ void k_gs_scale(int n, double* __restrict__ V, size_t ld, const double* __restrict__ w, const Ctl* ctl) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  V[(size_t)ctl->j * ld + i] = w[i] * ctl->scale;
+}
+
+// start of a cycle: beta = ||w|| with w = b - A x already formed
+__global__ void __launch_bounds__(kRedThreads) k_cycle_start(KrylovArgs k) {
+  __shared__ double sm[32];
+  const int r0 = blockIdx.x * k.chunk, r1 = min(k.n, r0 + k.chunk);
+  double acc = 0;
+  for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) acc += k.w[r] * k.w[r];
+  acc = block_sum(acc, sm);
+  if (threadIdx.x == 0) k.part[(size_t)blockIdx.x * k.pstride] = acc;
+  if (last_block(&k.ctl->counter[3])) {
+    if (threadIdx.x == 0) {
+      double s2 = 0;
+      for (int b = 0; b < (int)gridDim.x; ++b) s2 += k.part[(size_t)b * k.pstride];
+      Ctl* c = k.ctl;
+      c->counter[3] = 0;
+      const double beta = sqrt(s2);
+      c->beta = beta;
+      c->j = 0;
+      c->cycles += 1;
+      k.g[0] = beta;
+      c->last_true = (c->bnorm > 0) ? beta / c->bnorm : beta;
+      bool stop = false;
+      if (!(beta == beta)) { c->flags |= FLAG_NAN; stop = true; }
+      c->converged = (beta <= c->target) ? 1 : 0;
+      if (c->converged || c->its >= c->max_it || (c->flags & (FLAG_NAN | FLAG_BREAKDOWN))) stop = true;
+      c->stop = stop ? 1 : 0;
+      c->cycle_tol = fmax(c->inner_rtol * beta, c->target);
+      c->scale = (beta > 0) ? 1.0 / beta : 0.0;
+      c->res = beta;
+      cudaGraphSetConditional(k.cond, stop ? 0u : 1u);
+    }
+  }
+}
+
+__global__ void k_scale0(int n, double* __restrict__ V, const double* __restrict__ w, const Ctl* ctl) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  V[i] = w[i] * ctl->scale;
+}
+
+// ||b||, the target, and reset of the per-solve counters
+__global__ void __launch_bounds__(kRedThreads) k_solve_begin(KrylovArgs k, const double* __restrict__ b, double rtol,
+                                                             double inner_rtol, int max_it, int m) {
+  __shared__ double sm[32];
+  const int r0 = blockIdx.x * k.chunk, r1 = min(k.n, r0 + k.chunk);
+  double acc = 0;
+  for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) acc += b[r] * b[r];
+  acc = block_sum(acc, sm);
+  if (threadIdx.x == 0) k.part[(size_t)blockIdx.x * k.pstride] = acc;
+  if (last_block(&k.ctl->counter[4])) {
+    if (threadIdx.x == 0) {
+      double s2 = 0;
+      for (int bb = 0; bb < (int)gridDim.x; ++bb) s2 += k.part[(size_t)bb * k.pstride];
+      Ctl* c = k.ctl;
+      c->counter[4] = 0;
+      c->bnorm = sqrt(s2);
+      c->target = rtol * c->bnorm;
+      c->inner_rtol = inner_rtol;
+      c->its = 0; c->cycles = 0; c->j = 0; c->flags = 0;
+      c->converged = 0; c->stop = 0;
+      c->max_it = max_it; c->m = m;
+    }
+  }
+}
+
+// least squares on the rotated Hessenberg matrix: y = R^-1 g (one thread)
+__global__ void k_lsq(const double* __restrict__ H, const double* __restrict__ g, double* __restrict__ y,
+                      const Ctl* ctl) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int kk = ctl->j, m1 = ctl->m + 1;
+  for (int i = kk - 1; i >= 0; --i) {
+    double v = g[i];
+    for (int l = i + 1; l < kk; ++l) v -= H[(size_t)l * m1 + i] * y[l];
+    y[i] = v / H[(size_t)i * m1 + i];
+  }
+}
+
+// x += Z y (right preconditioning: the update lives in span{Z})
+template <class T>
+__global__ void k_xupdate(int n, double* __restrict__ x, const T* __restrict__ Z, size_t ld,
+                          const double* __restrict__ y, const Ctl* ctl) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int kk = ctl->j;
+  double v = x[i];
+  for (int l = 0; l < kk; ++l) v += (double)Z[(size_t)l * ld + i] * y[l];
+  x[i] = v;
+}
+
+template <class T>
+__global__ void k_prec_in(int n, const double* __restrict__ V, size_t ld, const Ctl* ctl, T* __restrict__ vin) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) vin[i] = (T)V[(size_t)ctl->j * ld + i];
+}
+
+template <class T>
+__global__ void k_prec_out(int n, const T* __restrict__ zw, T* __restrict__ Z, size_t ld, const Ctl* ctl) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) Z[(size_t)ctl->j * ld + i] = zw[i];
+}
+
+// zero mean of the constant pressure coefficients (p in L^2_0)
+__global__ void __launch_bounds__(kRedThreads) k_pmean(int nP, double* __restrict__ p, double* __restrict__ part,
+                                                       Ctl* ctl) {
+  __shared__ double sm[32];
+  double acc = 0;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nP; c += gridDim.x * blockDim.x) acc += p[3 * (size_t)c];
+  acc = block_sum(acc, sm);
+  if (threadIdx.x == 0) part[blockIdx.x] = acc;
+  if (last_block(&ctl->counter[5])) {
+    if (threadIdx.x == 0) {
+      double s = 0;
+      for (int b = 0; b < (int)gridDim.x; ++b) s += part[b];
+      ctl->counter[5] = 0;
+      ctl->pmean = s / nP;
+    }
+  }
+}
+
+__global__ void k_psub(int nP, double* __restrict__ p, const Ctl* ctl) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < nP) p[3 * (size_t)c] -= ctl->pmean;
+}
+
+// ------------------------------------------------------------------ setup
+static void check_params(const fsi_params& p, int n_nodes, int n_tris) {
+  if (p.N < 2 || p.N > 4096) throw std::invalid_argument("N out of range");
+  int Nc = p.N;
+  while (Nc % 2 == 0 && Nc > 4) Nc /= 2;
+  if (Nc > 8) throw std::invalid_argument("N must be c * 2^k with c <= 8");
+  if (!(p.dt > 0) || !(p.rho_f > 0) || !(p.nu > 0) || !(p.kappa >= 0)) throw std::invalid_argument("bad material");
+  if (p.precond != 0 && p.precond != 1) throw std::invalid_argument("precond");
+  if (p.precision != 0 && p.precision != 1) throw std::invalid_argument("precision");
+  if (n_nodes < 3 || n_tris < 1) throw std::invalid_argument("solid mesh");
+}
+
+static fsi_params with_defaults(fsi_params p) {
+  if (p.restart <= 0) p.restart = 200;
+  if (p.restart > 250) p.restart = 250;
+  if (!(p.rtol > 0)) p.rtol = 1e-8;
+  if (p.max_it <= 0) p.max_it = 1000;
+  if (p.mg_degree <= 0) p.mg_degree = 2;
+  if (p.cs_degree <= 0) p.cs_degree = (p.precision == 1) ? 12 : 16;
+  if (!(p.inner_rtol > 0)) p.inner_rtol = 1e-5;
+  if (p.max_refine <= 0) p.max_refine = 30;
+  return p;
+}
+
+template <class T>
+static void build_prec(Problem& P, Prec<T>& pr, const FullOp<T>& op, bool alloc_all) {
+  (void)alloc_all;
+  Arena& ar = P.ar;
+  build_mg<T>(ar, P.hs, false, P.prm.mg_degree, pr.mgU);
+  build_mg<T>(ar, P.hs, true, P.prm.mg_degree, pr.mgP);
+  pr.op = op;
+  pr.Cs = upload_sell<T>(ar, to_sell(P.hs.Cs));
+  pr.As = upload_sell<T>(ar, to_sell(P.hs.As));
+  pr.mpinv = upload_as<T>(ar, P.hs.mp_inv);
+  pr.csdinv = upload_as<T>(ar, P.hs.cs_dinv);
+  pr.vin = ar.alloc<T>(P.n);
+  pr.zw = ar.alloc<T>(P.n);
+  const size_t n2 = 2 * (size_t)P.nS;
+  pr.sb = ar.alloc<T>(n2); pr.sx = ar.alloc<T>(n2); pr.sx2 = ar.alloc<T>(n2); pr.sd = ar.alloc<T>(n2);
+  pr.cs_k = P.prm.cs_degree;
+  pr.chs = cheb_coeffs(0.5, 2.0, pr.cs_k);
+}
+
+template <class T>
+static FullOp<T> make_op(Problem& P, const T* cfv, const T* cftv) {
+  Arena& ar = P.ar;
+  FullOp<T> op;
+  op.nU = P.nU; op.nP = P.nP; op.nS = P.nS;
+  op.gU = nblk(P.nU, 128); op.gP = nblk(P.nP, 128); op.gS = nblk(P.nS, 128);
+  op.Af = upload_sell<T>(ar, to_sell(P.hs.levels[0].A));
+  op.Bt = upload_sell<T>(ar, to_sell(P.hs.Bt));
+  op.Bneg = upload_sell<T>(ar, to_sell(P.hs.Bneg));
+  op.Ssol = upload_sell<T>(ar, to_sell(P.hs.Ssol));
+  op.cft_ptr = P.cft_ptr; op.cft_col = P.cft_col; op.cft_val = cftv;
+  op.cf_len = P.cf_len; op.cf_col = P.cf_col; op.cf_val = cfv; op.cf_cap = P.cf_cap;
+  op.inv_dt = (T)(1.0 / P.prm.dt);
+  return op;
+}
+
+static KrylovArgs krylov_args(Problem& P, cudaGraphConditionalHandle h) {
+  KrylovArgs k{};
+  k.n = (int)P.n;
+  k.chunk = (int)((P.n + P.red_blocks - 1) / P.red_blocks);
+  k.ld = P.n;
+  k.V = P.V;
+  k.w = P.w;
+  k.part = P.part;
+  k.pstride = P.m + 1;
+  k.h1 = P.y + (P.m + 1);       // scratch after y
+  k.h2 = P.y + 2 * (P.m + 1);
+  k.H = P.H; k.cs = P.cs; k.sn = P.sn; k.g = P.g;
+  k.ctl = P.ctl;
+  k.cond = h;
+  return k;
+}
+
+static void assemble_launch(Problem& P, cudaStream_t s) {
+  CK(cudaMemsetAsync(&P.ctl->aflags, 0, sizeof(int), s));
+  k_locate<<<nblk(P.nPts, 256), 256, 0, s>>>(P.nPts, P.N, P.tris, P.Xold, P.cell, P.xi, P.eta, &P.ctl->aflags);
+  k_cf_rows<<<nblk(P.nS, kCfWarps), 32 * kCfWarps, 0, s>>>(P.nS, P.N, P.ntp, P.nt, P.area, P.cell, P.xi, P.eta,
+                                                          P.l2n, P.wall, P.cf_cap, P.cf_len, P.cf_col, P.cf_val,
+                                                          P.cf_val32, P.cflift, &P.ctl->aflags);
+  CK(cudaMemsetAsync(P.cft_cnt, 0, sizeof(int) * P.nU, s));
+  const size_t nslot = (size_t)P.nS * P.cf_cap;
+  k_cft_count<<<nblk(nslot, 256), 256, 0, s>>>(P.nS, P.cf_cap, P.cf_len, P.cf_col, P.cft_cnt);
+  const int nb = (int)nblk(P.nU, kScanBlock);
+  k_scan_partial<<<nb, kScanBlock, 0, s>>>(P.nU, P.cft_cnt, P.scan_bsum);
+  k_scan_top<<<1, kScanBlock, 0, s>>>(nb, P.scan_bsum);
+  k_scan_final<<<nb, kScanBlock, 0, s>>>(P.nU, P.cft_cnt, P.scan_bsum, P.cft_ptr, P.cft_cur);
+  k_cft_scatter<<<nblk(nslot, 256), 256, 0, s>>>(P.nS, P.cf_cap, P.cf_len, P.cf_col, P.cf_val, P.cft_cur,
+                                                 P.cft_col, P.cft_val);
+  k_cft_sort<<<nblk(P.nU, 128), 128, 0, s>>>(P.nU, P.cft_ptr, P.cft_col, P.cft_val, P.cft_val32);
+  // S1: g1 = (rho/dt) M u^n - K_ID u_D ;  g2 = -(1/dt) C_s X^n - C_D u_D
+  sell_launch(P.M64, MODE_AXPBY, axpby<double>(P.uold, P.b, P.lift_u, P.prm.rho_f / P.prm.dt, 1.0), s);
+  sell_launch(P.Cs64, MODE_AXPBY, axpby<double>(P.Xold, P.b + P.offL, P.cflift, -1.0 / P.prm.dt, -1.0), s);
+}
+
+template <class T>
+static void iteration_launch(Problem& P, Prec<T>& pr, const KrylovArgs& k, cudaStream_t s) {
+  const unsigned gn = nblk(P.n, 256);
+  k_prec_in<T><<<gn, 256, 0, s>>>((int)P.n, P.V, P.n, P.ctl, pr.vin);
+  precond_launch(P, pr, s);
+  k_prec_out<T><<<gn, 256, 0, s>>>((int)P.n, pr.zw, (T*)P.Z, P.n, P.ctl);
+  k_fullmv<T, T, double><<<pr.op.gU + pr.op.gP + pr.op.gS, 128, 0, s>>>(pr.op, pr.zw, P.w, nullptr, 1.0, 0.0);
+  k_gs1<<<P.red_blocks, kRedThreads, 0, s>>>(k);
+  k_gs2<<<P.red_blocks, kRedThreads, 0, s>>>(k);
+  k_gs3<<<P.red_blocks, kRedThreads, 0, s>>>(k);
+  k_gs_scale<<<gn, 256, 0, s>>>((int)P.n, P.V, P.n, P.w, P.ctl);
+}
+
+static void cycle_start_launch(Problem& P, const KrylovArgs& k, cudaStream_t s) {
+  k_fullmv<double, double, double><<<P.op64.gU + P.op64.gP + P.op64.gS, 128, 0, s>>>(P.op64, P.x, P.w, P.b, -1.0, 1.0);
+  k_cycle_start<<<P.red_blocks, kRedThreads, 0, s>>>(k);
+  k_scale0<<<nblk(P.n, 256), 256, 0, s>>>((int)P.n, P.V, P.w, P.ctl);
+}
+
+template <class T>
+static void cycle_end_launch(Problem& P, cudaStream_t s) {
+  k_lsq<<<1, 32, 0, s>>>(P.H, P.g, P.y, P.ctl);
+  k_xupdate<T><<<nblk(P.n, 256), 256, 0, s>>>((int)P.n, P.x, (const T*)P.Z, P.n, P.y, P.ctl);
+}
+
+template <class T>
+static void build_cycle_graph(Problem& P, Prec<T>& pr) {
+  cudaStream_t s = P.stream;
+  CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  cudaStreamCaptureStatus st;
+  cudaGraph_t g = nullptr;
+  CK(cudaStreamGetCaptureInfo(s, &st, nullptr, &g, nullptr, nullptr, nullptr));
+  cudaGraphConditionalHandle h;
+  CK(cudaGraphConditionalHandleCreate(&h, g, 0, 0));
+  KrylovArgs k = krylov_args(P, h);
+  cycle_start_launch(P, k, s);
+  const cudaGraphNode_t* deps = nullptr;
+  size_t ndeps = 0;
+  CK(cudaStreamGetCaptureInfo(s, &st, nullptr, &g, &deps, nullptr, &ndeps));
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t wnode;
+  CK(cudaGraphAddNode(&wnode, g, deps, nullptr, ndeps, &cp));
+  CK(cudaStreamUpdateCaptureDependencies(s, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  CK(cudaStreamBeginCaptureToGraph(P.s2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  iteration_launch(P, pr, k, P.s2);
+  CK(cudaStreamEndCapture(P.s2, &body));
+  cycle_end_launch<T>(P, s);
+  CK(cudaStreamEndCapture(s, &P.gr_cycle));
+  CK(cudaGraphInstantiate(&P.g_cycle, P.gr_cycle, 0));
+}
+
+static void build_graphs(Problem& P) {
+  cudaStream_t s = P.stream;
+  // assemble
+  CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  assemble_launch(P, s);
+  CK(cudaStreamEndCapture(s, &P.gr_assemble));
+  CK(cudaGraphInstantiate(&P.g_assemble, P.gr_assemble, 0));
+  // begin: ||b|| and counters
+  CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  {
+    KrylovArgs k = krylov_args(P, 0);
+    const double inner = (P.prm.precision == 1) ? P.prm.inner_rtol : 0.0;
+    k_solve_begin<<<P.red_blocks, kRedThreads, 0, s>>>(k, P.b, P.prm.rtol, inner, P.prm.max_it, P.m);
+  }
+  CK(cudaStreamEndCapture(s, &P.gr_begin));
+  CK(cudaGraphInstantiate(&P.g_begin, P.gr_begin, 0));
+  // cycle
+  if (P.prm.precision == 1) build_cycle_graph<float>(P, P.p32);
+  else build_cycle_graph<double>(P, P.p64);
+  // finish: zero-mean pressure
+  CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  k_pmean<<<std::min(64, (int)nblk(P.nP, kRedThreads)), kRedThreads, 0, s>>>(P.nP, P.x + P.offP, P.part, P.ctl);
+  k_psub<<<nblk(P.nP, 256), 256, 0, s>>>(P.nP, P.x + P.offP, P.ctl);
+  CK(cudaStreamEndCapture(s, &P.gr_finish));
+  CK(cudaGraphInstantiate(&P.g_finish, P.gr_finish, 0));
+}
+
+static void allocate_problem(Problem& P, const double* ref_xy, const int* tris_h) {
+  Arena& ar = P.ar;
+  const HostSetup& hs = P.hs;
+  P.tris = ar.upload(std::vector<int>(tris_h, tris_h + 3 * (size_t)P.nTri));
+  P.area = ar.upload(hs.tri_area);
+  P.ntp = ar.upload(hs.node_tri_ptr);
+  P.nt = ar.upload(hs.node_tri);
+  P.l2n = ar.upload(hs.lattice_to_node);
+  P.wall = ar.upload(hs.wall_u);
+  P.cell = ar.alloc<int>(P.nPts);
+  P.xi = ar.alloc<double>(P.nPts);
+  P.eta = ar.alloc<double>(P.nPts);
+  const size_t cfslots = (size_t)nblk(P.nS, 32) * 32 * P.cf_cap;
+  P.cf_len = ar.alloc<int>(P.nS);
+  P.cf_col = ar.alloc<int>(cfslots);
+  P.cf_val = ar.alloc<double>(cfslots);
+  P.cf_val32 = ar.alloc<float>(cfslots);
+  P.cflift = ar.alloc<double>(2 * (size_t)P.nS);
+  const size_t tcap = (size_t)P.nS * P.cf_cap;
+  P.cft_ptr = ar.alloc<int>(P.nU + 1);
+  P.cft_col = ar.alloc<int>(tcap);
+  P.cft_val = ar.alloc<double>(tcap);
+  P.cft_val32 = ar.alloc<float>(tcap);
+  P.cft_cnt = ar.alloc<int>(P.nU);
+  P.cft_cur = ar.alloc<int>(P.nU);
+  P.scan_bsum = ar.alloc<int>(nblk(P.nU, kScanBlock) + 1);
+  P.x = ar.alloc<double>(P.n);
+  P.b = ar.alloc<double>(P.n);
+  P.w = ar.alloc<double>(P.n);
+  P.uold = ar.alloc<double>(2 * (size_t)P.nU);
+  P.Xold = ar.alloc<double>(2 * (size_t)P.nS);
+  P.lift_u = ar.upload(hs.lift_u);
+  P.M64 = upload_sell<double>(ar, to_sell(hs.M));
+  P.Cs64 = upload_sell<double>(ar, to_sell(hs.Cs));
+  const int m = P.m;
+  P.V = ar.alloc<double>((size_t)(m + 1) * P.n);
+  if (P.prm.precision == 1) P.Z = ar.alloc<float>((size_t)m * P.n);
+  else P.Z = ar.alloc<double>((size_t)m * P.n);
+  P.H = ar.alloc<double>((size_t)(m + 1) * m);
+  P.cs = ar.alloc<double>(m + 1);
+  P.sn = ar.alloc<double>(m + 1);
+  P.g = ar.alloc<double>(m + 2);
+  P.y = ar.alloc<double>(3 * (size_t)(m + 1));
+  P.red_blocks = (int)std::max<size_t>(1, std::min<size_t>(kRedMax, (P.n + 4095) / 4096));
+  P.part = ar.alloc<double>((size_t)std::max(P.red_blocks, 64) * (m + 1));
+  P.ctl = ar.alloc<Ctl>(1);
+  P.op64 = make_op<double>(P, P.cf_val, P.cft_val);
+  build_prec<double>(P, P.p64, P.op64, true);
+  if (P.prm.precision == 1) {
+    P.op32 = make_op<float>(P, P.cf_val32, P.cft_val32);
+    build_prec<float>(P, P.p32, P.op32, true);
+  }
+  (void)ref_xy;
+}
+
+}  // namespace fsi
+
+// ================================================================== C ABI
+using namespace fsi;
+
+struct fsi_problem {
+  Problem P;
+};
+
+static int map_exception() {
+  try {
+    throw;
+  } catch (const std::bad_alloc&) {
+    return FSI_ERR_OOM;
+  } catch (const std::invalid_argument&) {
+    return FSI_ERR_INVALID;
+  } catch (const CudaError& e) {
+    if (e.code == cudaErrorMemoryAllocation) return FSI_ERR_OOM;
+    return FSI_ERR_CUDA;
+  } catch (...) {
+    return FSI_ERR_CUDA;
+  }
+}
+
+static void upload_state(Problem& P, const double* u, const double* X) {
+  const int n1 = 2 * P.N + 1;
+  if (u) {
+    std::vector<double> ui(2 * (size_t)P.nU);
+    for (int k = 0; k < P.nU; ++k) {
+      const int lat = P.hs.interior_lattice[k];
+      ui[2 * k] = u[2 * (size_t)lat];
+      ui[2 * k + 1] = u[2 * (size_t)lat + 1];
+    }
+    CK(cudaMemcpyAsync(P.uold, ui.data(), ui.size() * 8, cudaMemcpyHostToDevice, P.stream));
+    CK(cudaMemcpyAsync(P.x, ui.data(), ui.size() * 8, cudaMemcpyHostToDevice, P.stream));
+    CK(cudaStreamSynchronize(P.stream));
+  }
+  if (X) {
+    CK(cudaMemcpyAsync(P.Xold, X, 2 * (size_t)P.nS * 8, cudaMemcpyHostToDevice, P.stream));
+    CK(cudaMemcpyAsync(P.x + P.offX, X, 2 * (size_t)P.nS * 8, cudaMemcpyHostToDevice, P.stream));
+    CK(cudaStreamSynchronize(P.stream));
+  }
+  (void)n1;
+}
+
+static size_t footprint_impl(const fsi_params& prm0, int n_nodes, int n_tris, const double* ref_xy,
+                             const int* tris) {
+  fsi_params prm = with_defaults(prm0);
+  check_params(prm, n_nodes, n_tris);
+  Problem P;
+  P.prm = prm;
+  P.ar.count_only = true;
+  P.N = prm.N;
+  VNum vn(prm.N);
+  P.nU = vn.n; P.nP = prm.N * prm.N; P.nS = n_nodes; P.nTri = n_tris; P.nPts = 6 * n_tris;
+  P.offP = 2 * (size_t)P.nU; P.offX = P.offP + 3 * (size_t)P.nP; P.offL = P.offX + 2 * (size_t)P.nS;
+  P.n = P.offL + 2 * (size_t)P.nS;
+  P.m = prm.restart;
+  SetupParams sp{prm.N, prm.rho_f, prm.nu, prm.kappa, prm.dt, prm.lid_u};
+  build_setup(sp, n_nodes, n_tris, ref_xy, tris, P.hs);
+  allocate_problem(P, ref_xy, tris);
+  return P.ar.bytes;
+}
+
+extern "C" {
+
+size_t fsi_footprint_bytes(const fsi_params* params, int n_solid_nodes, int n_tris) {
+  if (!params || n_solid_nodes < 3 || n_tris < 1) return 0;
+  try {
+    // a synthetic solid with the same counts: matrix sizes depend on counts only
+    // up to the solid adjacency, which is bounded by a small ring patch
+    std::vector<double> xy(2 * (size_t)n_solid_nodes);
+    std::vector<int> tr(3 * (size_t)n_tris);
+    for (int i = 0; i < n_solid_nodes; ++i) { xy[2 * i] = 0.5 + 1e-3 * (i % 7); xy[2 * i + 1] = 0.5 + 1e-3 * (i / 7 % 7); }
+    for (int t = 0; t < n_tris; ++t) { tr[3 * t] = 0; tr[3 * t + 1] = 1 + t % (n_solid_nodes - 2); tr[3 * t + 2] = 2 + t % (n_solid_nodes - 2); }
+    // solid matrices only need a valid orientation; use a fan of unit triangles
+    for (int i = 0; i < n_solid_nodes; ++i) {
+      const double a = 6.283185307179586 * i / n_solid_nodes;
+      xy[2 * i] = 0.5 + 0.1 * std::cos(a);
+      xy[2 * i + 1] = 0.5 + 0.1 * std::sin(a);
+    }
+    xy[0] = 0.5; xy[1] = 0.5;
+    for (int t = 0; t < n_tris; ++t) {
+      const int a = 1 + t % (n_solid_nodes - 1);
+      const int b = 1 + (a % (n_solid_nodes - 1));
+      tr[3 * t] = 0; tr[3 * t + 1] = a; tr[3 * t + 2] = b;
+    }
+    return footprint_impl(*params, n_solid_nodes, n_tris, xy.data(), tr.data());
+  } catch (...) {
+    return 0;
+  }
+}
+
+int fsi_create_problem_budget(const fsi_params* params, const fsi_solid_mesh* mesh, const double* u0,
+                              const double* X0, void* cuda_stream, size_t budget_bytes, fsi_problem** out) {
+  if (!params || !mesh || !out || !mesh->ref_xy || !mesh->tris) return FSI_ERR_INVALID;
+  *out = nullptr;
+  fsi_problem* h = nullptr;
+  try {
+    fsi_params prm = with_defaults(*params);
+    check_params(prm, mesh->n_nodes, mesh->n_tris);
+    for (int i = 0; i < 3 * mesh->n_tris; ++i)
+      if (mesh->tris[i] < 0 || mesh->tris[i] >= mesh->n_nodes) return FSI_ERR_INVALID;
+    if (budget_bytes > 0) {
+      const size_t need = footprint_impl(prm, mesh->n_nodes, mesh->n_tris, mesh->ref_xy, mesh->tris);
+      if (need > budget_bytes) return FSI_ERR_BUDGET;
+    }
+    h = new fsi_problem();
+    Problem& P = h->P;
+    P.prm = prm;
+    CK(cudaGetDevice(&P.device));
+    if (cuda_stream) {
+      P.stream = (cudaStream_t)cuda_stream;
+    } else {
+      CK(cudaStreamCreateWithFlags(&P.stream, cudaStreamNonBlocking));
+      P.own_stream = true;
+    }
+    CK(cudaStreamCreateWithFlags(&P.s2, cudaStreamNonBlocking));
+    P.N = prm.N;
+    VNum vn(prm.N);
+    P.nU = vn.n; P.nP = prm.N * prm.N; P.nS = mesh->n_nodes; P.nTri = mesh->n_tris; P.nPts = 6 * mesh->n_tris;
+    P.offP = 2 * (size_t)P.nU; P.offX = P.offP + 3 * (size_t)P.nP; P.offL = P.offX + 2 * (size_t)P.nS;
+    P.n = P.offL + 2 * (size_t)P.nS;
+    P.m = prm.restart;
+    SetupParams sp{prm.N, prm.rho_f, prm.nu, prm.kappa, prm.dt, prm.lid_u};
+    build_setup(sp, P.nS, P.nTri, mesh->ref_xy, mesh->tris, P.hs);
+    {
+      double lam[6][3], w[6];
+      triangle_rule(lam, w);
+      CK(cudaMemcpyToSymbol(c_rule_lam, lam, sizeof(lam)));
+      CK(cudaMemcpyToSymbol(c_rule_w, w, sizeof(w)));
+    }
+    allocate_problem(P, mesh->ref_xy, mesh->tris);
+    CK(cudaMemset(P.ctl, 0, sizeof(Ctl)));
+    CK(cudaMemset(P.cf_len, 0, sizeof(int) * P.nS));
+    CK(cudaMemset(P.cft_ptr, 0, sizeof(int) * (P.nU + 1)));
+    CK(cudaMemset(P.cflift, 0, sizeof(double) * 2 * P.nS));
+    CK(cudaMemset(P.x, 0, P.n * 8));
+    CK(cudaMemset(P.b, 0, P.n * 8));
+    CK(cudaMemcpy(P.b + P.offP, P.hs.lift_p.data(), P.hs.lift_p.size() * 8, cudaMemcpyHostToDevice));
+    CK(cudaMallocHost((void**)&P.ctl_host, sizeof(Ctl)));
+    std::vector<double> u(2 * (size_t)(2 * P.N + 1) * (2 * P.N + 1));
+    if (u0) std::copy(u0, u0 + u.size(), u.begin());
+    upload_state(P, u.data(), X0 ? X0 : mesh->ref_xy);
+    build_graphs(P);
+    CK(cudaDeviceSynchronize());
+    *out = h;
+    return FSI_OK;
+  } catch (...) {
+    const int code = map_exception();
+    if (h) fsi_destroy(h);
+    return code;
+  }
+}
+
+int fsi_create_problem(const fsi_params* params, const fsi_solid_mesh* mesh, const double* u0, const double* X0,
+                       void* cuda_stream, fsi_problem** out) {
+  return fsi_create_problem_budget(params, mesh, u0, X0, cuda_stream, 0, out);
+}
+
+int fsi_assemble_step(fsi_problem* h) {
+  if (!h) return FSI_ERR_INVALID;
+  try {
+    CK(cudaGraphLaunch(h->P.g_assemble, h->P.stream));
+    h->P.assembled = true;
+    return FSI_OK;
+  } catch (...) {
+    return map_exception();
+  }
+}
+
+static int status_from_ctl(const Ctl& c) {
+  if (c.aflags & FLAG_OUT_OF_DOMAIN) return FSI_ERR_OUT_OF_DOMAIN;
+  if (c.aflags & FLAG_CAPACITY) return FSI_ERR_CAPACITY;
+  if (c.flags & FLAG_NAN) return FSI_ERR_NAN;
+  if (c.flags & FLAG_BREAKDOWN) return FSI_ERR_BREAKDOWN;
+  if (!c.converged) return FSI_ERR_NOT_CONVERGED;
+  return FSI_OK;
+}
+
+int fsi_solve_step(fsi_problem* h, fsi_solve_info* info) {
+  if (!h) return FSI_ERR_INVALID;
+  Problem& P = h->P;
+  try {
+    if (!P.assembled) CK(cudaGraphLaunch(P.g_assemble, P.stream));
+    P.assembled = false;
+    CK(cudaGraphLaunch(P.g_begin, P.stream));
+    const int max_cycles = (P.prm.precision == 1) ? P.prm.max_refine + 1 : 1000000;
+    Ctl& c = *P.ctl_host;
+    for (int cyc = 0; cyc < max_cycles; ++cyc) {
+      CK(cudaGraphLaunch(P.g_cycle, P.stream));
+      CK(cudaMemcpyAsync(P.ctl_host, P.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, P.stream));
+      CK(cudaStreamSynchronize(P.stream));
+      if (c.stop || c.aflags) break;
+    }
+    CK(cudaGraphLaunch(P.g_finish, P.stream));
+    CK(cudaMemcpyAsync(P.ctl_host, P.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, P.stream));
+    CK(cudaStreamSynchronize(P.stream));
+    const int st = status_from_ctl(c);
+    if (info) {
+      info->iterations = c.its;
+      info->restarts = std::max(0, c.cycles - 2);
+      info->refinements = (P.prm.precision == 1) ? std::max(0, c.cycles - 1) : 0;
+      info->status = st;
+      info->rel_residual = c.last_true;
+      info->rel_residual_est = (c.bnorm > 0) ? c.res / c.bnorm : c.res;
+    }
+    return st;
+  } catch (...) {
+    return map_exception();
+  }
+}
+
+int fsi_advance(fsi_problem* h) {
+  if (!h) return FSI_ERR_INVALID;
+  Problem& P = h->P;
+  try {
+    CK(cudaMemcpyAsync(P.uold, P.x, 2 * (size_t)P.nU * 8, cudaMemcpyDeviceToDevice, P.stream));
+    CK(cudaMemcpyAsync(P.Xold, P.x + P.offX, 2 * (size_t)P.nS * 8, cudaMemcpyDeviceToDevice, P.stream));
+    return FSI_OK;
+  } catch (...) {
+    return map_exception();
+  }
+}
+
+int fsi_step(fsi_problem* h, fsi_solve_info* info) {
+  int st = fsi_assemble_step(h);
+  if (st != FSI_OK) return st;
+  st = fsi_solve_step(h, info);
+  if (st != FSI_OK) return st;
+  return fsi_advance(h);
+}
+
+int fsi_get_state(fsi_problem* h, double* u, double* pr, double* X, double* lam) {
+  if (!h) return FSI_ERR_INVALID;
+  Problem& P = h->P;
+  try {
+    std::vector<double> x(P.n);
+    CK(cudaMemcpyAsync(x.data(), P.x, P.n * 8, cudaMemcpyDeviceToHost, P.stream));
+    CK(cudaStreamSynchronize(P.stream));
+    if (u) {
+      const size_t nl = (size_t)(2 * P.N + 1) * (2 * P.N + 1);
+      std::copy(P.hs.wall_u.begin(), P.hs.wall_u.begin() + 2 * nl, u);
+      for (int k = 0; k < P.nU; ++k) {
+        const int lat = P.hs.interior_lattice[k];
+        u[2 * (size_t)lat] = x[2 * (size_t)k];
+        u[2 * (size_t)lat + 1] = x[2 * (size_t)k + 1];
+      }
+    }
+    if (pr) std::copy(x.begin() + P.offP, x.begin() + P.offX, pr);
+    if (X) std::copy(x.begin() + P.offX, x.begin() + P.offL, X);
+    if (lam) std::copy(x.begin() + P.offL, x.end(), lam);
+    return FSI_OK;
+  } catch (...) {
+    return map_exception();
+  }
+}
+
+int fsi_set_state(fsi_problem* h, const double* u, const double* X) {
+  if (!h) return FSI_ERR_INVALID;
+  try {
+    upload_state(h->P, u, X);
+    return FSI_OK;
+  } catch (...) {
+    return map_exception();
+  }
+}
+
+int fsi_sizes(const fsi_problem* h, int* n_u, int* n_p, int* n_x, int* n_total) {
+  if (!h) return FSI_ERR_INVALID;
+  const Problem& P = h->P;
+  if (n_u) *n_u = 2 * P.nU;
+  if (n_p) *n_p = 3 * P.nP;
+  if (n_x) *n_x = 2 * P.nS;
+  if (n_total) *n_total = (int)P.n;
+  return FSI_OK;
+}
+
+int fsi_get_points(fsi_problem* h, int* cell, double* xi, double* eta) {
+  if (!h) return FSI_ERR_INVALID;
+  Problem& P = h->P;
+  try {
+    if (cell) CK(cudaMemcpyAsync(cell, P.cell, (size_t)P.nPts * 4, cudaMemcpyDeviceToHost, P.stream));
+    if (xi) CK(cudaMemcpyAsync(xi, P.xi, (size_t)P.nPts * 8, cudaMemcpyDeviceToHost, P.stream));
+    if (eta) CK(cudaMemcpyAsync(eta, P.eta, (size_t)P.nPts * 8, cudaMemcpyDeviceToHost, P.stream));
+    CK(cudaStreamSynchronize(P.stream));
+    return FSI_OK;
+  } catch (...) {
+    return map_exception();
+  }
+}
+
+int fsi_get_coupling(fsi_problem* h, int* nnz, int* rows, int* lattice_cols, double* vals) {
+  if (!h || !nnz) return FSI_ERR_INVALID;
+  Problem& P = h->P;
+  try {
+    const size_t nslot = (size_t)nblk(P.nS, 32) * 32 * P.cf_cap;
+    std::vector<int> len(P.nS), col(nslot);
+    std::vector<double> val(nslot);
+    CK(cudaMemcpyAsync(len.data(), P.cf_len, (size_t)P.nS * 4, cudaMemcpyDeviceToHost, P.stream));
+    CK(cudaMemcpyAsync(col.data(), P.cf_col, nslot * 4, cudaMemcpyDeviceToHost, P.stream));
+    CK(cudaMemcpyAsync(val.data(), P.cf_val, nslot * 8, cudaMemcpyDeviceToHost, P.stream));
+    CK(cudaStreamSynchronize(P.stream));
+    int total = 0;
+    for (int l = 0; l < P.nS; ++l) total += len[l];
+    if (!rows) { *nnz = total; return FSI_OK; }
+    if (*nnz < total) return FSI_ERR_INVALID;
+    int q = 0;
+    for (int l = 0; l < P.nS; ++l)
+      for (int k = 0; k < len[l]; ++k) {
+        const size_t slot = (size_t)(l >> 5) * 32 * P.cf_cap + (size_t)k * 32 + (l & 31);
+        rows[q] = l;
+        if (lattice_cols) lattice_cols[q] = P.hs.interior_lattice[col[slot]];
+        if (vals) vals[q] = val[slot];
+        ++q;
+      }
+    *nnz = total;
+    return FSI_OK;
+  } catch (...) {
+    return map_exception();
+  }
+}
+
+int fsi_apply_operator(fsi_problem* h, const double* xh, double* yh, int precision) {
+  if (!h || !xh || !yh) return FSI_ERR_INVALID;
+  Problem& P = h->P;
+  if (precision == 1 && P.prm.precision != 1) return FSI_ERR_INVALID;
+  try {
+    double* tmp = P.V;  // first basis vector as scratch
+    CK(cudaMemcpyAsync(tmp, xh, P.n * 8, cudaMemcpyHostToDevice, P.stream));
+    if (precision == 1) {
+      k_convert<double, float><<<nblk(P.n, 256), 256, 0, P.stream>>>(P.n, tmp, P.p32.vin);
+      k_fullmv<float, float, double><<<P.op32.gU + P.op32.gP + P.op32.gS, 128, 0, P.stream>>>(P.op32, P.p32.vin, P.w,
+                                                                                            nullptr, 1.0, 0.0);
+    } else {
+      k_fullmv<double, double, double><<<P.op64.gU + P.op64.gP + P.op64.gS, 128, 0, P.stream>>>(P.op64, tmp, P.w,
+                                                                                               nullptr, 1.0, 0.0);
+    }
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(yh, P.w, P.n * 8, cudaMemcpyDeviceToHost, P.stream));
+    CK(cudaStreamSynchronize(P.stream));
+    return FSI_OK;
+  } catch (...) {
+    return map_exception();
+  }
+}
+
+int fsi_apply_preconditioner(fsi_problem* h, const double* vh, double* zh, int precision) {
+  if (!h || !vh || !zh) return FSI_ERR_INVALID;
+  Problem& P = h->P;
+  if (precision == 1 && P.prm.precision != 1) return FSI_ERR_INVALID;
+  try {
+    double* tmp = P.V;
+    CK(cudaMemcpyAsync(tmp, vh, P.n * 8, cudaMemcpyHostToDevice, P.stream));
+    if (precision == 1) {
+      k_convert<double, float><<<nblk(P.n, 256), 256, 0, P.stream>>>(P.n, tmp, P.p32.vin);
+      precond_launch(P, P.p32, P.stream);
+      k_convert<float, double><<<nblk(P.n, 256), 256, 0, P.stream>>>(P.n, P.p32.zw, P.w);
+    } else {
+      k_copy<double><<<nblk(P.n, 256), 256, 0, P.stream>>>(P.n, tmp, P.p64.vin);
+      precond_launch(P, P.p64, P.stream);
+      k_copy<double><<<nblk(P.n, 256), 256, 0, P.stream>>>(P.n, P.p64.zw, P.w);
+    }
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(zh, P.w, P.n * 8, cudaMemcpyDeviceToHost, P.stream));
+    CK(cudaStreamSynchronize(P.stream));
+    return FSI_OK;
+  } catch (...) {
+    return map_exception();
+  }
+}
+
+int fsi_interior_nodes(const fsi_problem* h, int* lattice_ids) {
+  if (!h || !lattice_ids) return FSI_ERR_INVALID;
+  std::copy(h->P.hs.interior_lattice.begin(), h->P.hs.interior_lattice.end(), lattice_ids);
+  return FSI_OK;
+}
+
+int fsi_get_rhs(fsi_problem* h, double* bh) {
+  if (!h || !bh) return FSI_ERR_INVALID;
+  Problem& P = h->P;
+  try {
+    CK(cudaMemcpyAsync(bh, P.b, P.n * 8, cudaMemcpyDeviceToHost, P.stream));
+    CK(cudaStreamSynchronize(P.stream));
+    return FSI_OK;
+  } catch (...) {
+    return map_exception();
+  }
+}
+
+void fsi_destroy(fsi_problem* h) {
+  if (!h) return;
+  Problem& P = h->P;
+  cudaGraphExec_t ex[4] = {P.g_assemble, P.g_begin, P.g_cycle, P.g_finish};
+  cudaGraph_t gr[4] = {P.gr_assemble, P.gr_begin, P.gr_cycle, P.gr_finish};
+  if (P.stream) cudaStreamSynchronize(P.stream);
+  for (auto e : ex) if (e) cudaGraphExecDestroy(e);
+  for (auto g : gr) if (g) cudaGraphDestroy(g);
+  P.ar.release();
+  if (P.ctl_host) cudaFreeHost(P.ctl_host);
+  if (P.s2) cudaStreamDestroy(P.s2);
+  if (P.own_stream && P.stream) cudaStreamDestroy(P.stream);
+  delete h;
+}
+
+const char* fsi_status_str(int s) {
+  switch (s) {
+    case FSI_OK: return "ok";
+    case FSI_ERR_INVALID: return "invalid argument";
+    case FSI_ERR_OOM: return "device out of memory";
+    case FSI_ERR_BUDGET: return "footprint above budget";
+    case FSI_ERR_OUT_OF_DOMAIN: return "solid point outside the fluid domain";
+    case FSI_ERR_NOT_CONVERGED: return "not converged";
+    case FSI_ERR_BREAKDOWN: return "Krylov breakdown";
+    case FSI_ERR_NAN: return "NaN or Inf in the residual";
+    case FSI_ERR_TIMEOUT: return "bounded device wait ran out";
+    case FSI_ERR_CAPACITY: return "coupling row over capacity";
+    case FSI_ERR_CUDA: return "CUDA error";
+    default: return "unknown status";
+  }
+}
+
+}  // extern "C"

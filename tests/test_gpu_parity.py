@@ -1,0 +1,144 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Bit-exact: point-location cells and local coordinates.  Floating point:
+coupling entries and operator products to 1e-13 relative (same FP64
+arithmetic, different summation order); one time step to 1e-7 relative L2
+per block with a 1e-12 solve, and the GPU solution's residual in the
+oracle's own operator below the requested tolerance.
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import fsi_inputs as fi
+from oracle import fsi_oracle as fo
+from tests.gpu_helpers import oracle_to_gpu_perm, rel
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fsi():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2301_10041_gb300 import build, fsi as f
+    build.build()
+    f.load_library()
+    return f
+
+
+def _oracle(case):
+    return fo.OracleProblem(case.N, case.rho_f, case.nu, case.kappa, case.dt, case.lid_u, case.ref_xy, case.tris)
+
+
+def _deformed_case(N=24, m=9, seed=7):
+    """A ragged case: N = 3 * 2^3, solid sheared and rotated, u_0 random, lid."""
+    xy, tris = fi.ring_disk_mesh(m, 0.23, (0.47, 0.52))
+    c, s = np.cos(0.3), np.sin(0.3)
+    d = xy - np.array([0.47, 0.52])
+    X0 = np.stack([c * d[:, 0] - s * d[:, 1] + 0.2 * d[:, 1], s * d[:, 0] + c * d[:, 1]], 1) + np.array([0.47, 0.52])
+    return fi.FsiCase(N=N, rho_f=1.3, nu=0.05, kappa=30.0, dt=0.005, lid_u=1.0, ref_xy=xy, tris=tris,
+                      u0=fi.initial_velocity(N, seed, lid_u=1.0), X0=X0, precond=1, rtol=1e-12)
+
+
+CASES = {"cfg0": fi.config0, "ragged24": _deformed_case}
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_point_location_is_bit_exact(fsi, name):
+    case = CASES[name]()
+    g = fsi.problem_from_case(case)
+    g.assemble_step()
+    cell, xi, eta = g.get_points()
+    x = fo.quadrature_points(case.X0, case.tris.astype(np.int64))
+    ocell, oxi, oeta = fo.locate_brute_force(x, case.N)
+    assert np.array_equal(cell, ocell)
+    assert np.array_equal(xi, oxi) and np.array_equal(eta, oeta)
+    g.close()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_coupling_matrix(fsi, name):
+    case = CASES[name]()
+    g = fsi.problem_from_case(case)
+    g.assemble_step()
+    rows, cols, vals = g.get_coupling()
+    o = _oracle(case)
+    C, _ = fo.assemble_coupling(o.grid, case.ref_xy, case.tris.astype(np.int64), case.X0)
+    C = C.tocsc()[:, o.grid.interior_nodes].tocsr()
+    G = sp.coo_matrix((vals, (rows, np.searchsorted(o.grid.interior_nodes, cols))), shape=C.shape).tocsr()
+    assert abs(G - C).max() <= 1e-13 * abs(C).max()
+    g.close()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_operator_and_rhs(fsi, name):
+    case = CASES[name]()
+    for precision in (0, 1):
+        g = fsi.problem_from_case(case, precision=precision)
+        g.assemble_step()
+        o = _oracle(case)
+        K, rhs, _ = o.system(case.u0, case.X0)
+        q = oracle_to_gpu_perm(o, g)
+        rng = np.random.default_rng(3)
+        x = rng.standard_normal(K.shape[0])
+        y_ref = (K @ x)[q]
+        y = g.apply_operator(x[q], precision=0)
+        assert rel(y, y_ref) < 1e-13
+        if precision == 1:
+            y32 = g.apply_operator(x[q], precision=1)
+            assert rel(y32, y_ref) < 1e-5
+        b = g.get_rhs()
+        assert rel(b, rhs[q]) < 1e-13
+        g.close()
+
+
+@pytest.mark.parametrize("precond", [0, 1])
+@pytest.mark.parametrize("name", list(CASES))
+def test_one_step_fp64_matches_oracle(fsi, name, precond):
+    case = CASES[name]()
+    g = fsi.problem_from_case(case, precision=0, precond=precond, rtol=1e-12)
+    info = g.step()
+    assert info.rel_residual <= 1e-12
+    u, p, X, lam = g.get_state()
+    o = _oracle(case)
+    uo, po, Xo, lamo = o.step(case.u0, case.X0)
+    assert rel(u, uo) < 1e-7
+    assert rel(p, po) < 1e-7
+    assert rel(X - case.X0, Xo - case.X0) < 1e-7
+    assert rel(lam, lamo) < 1e-7
+    assert o.relative_residual(case.u0, case.X0, u, p, X, lam) < 1e-10
+    g.close()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_one_step_mixed_precision(fsi, name):
+    """FP32 operators and preconditioner inside FP64 refinement reach the
+    same 1e-8 residual; the error against the FP64 oracle is reported."""
+    case = CASES[name]()
+    g = fsi.problem_from_case(case, precision=1, rtol=1e-8)
+    info = g.step()
+    assert info.rel_residual <= 1e-8
+    u, p, X, lam = g.get_state()
+    o = _oracle(case)
+    assert o.relative_residual(case.u0, case.X0, u, p, X, lam) < 1e-8
+    uo, po, Xo, lamo = o.step(case.u0, case.X0)
+    assert rel(u, uo) < 1e-5
+    assert rel(lam, lamo) < 1e-5
+    g.close()
+
+
+def test_five_step_trajectory(fsi):
+    case = fi.config0()
+    g = fsi.problem_from_case(case, precision=0, precond=1, rtol=1e-12)
+    o = _oracle(case)
+    u, X = case.u0, case.X0
+    for _ in range(5):
+        g.step()
+        u, p, X, lam = o.step(u, X)
+    ug, pg, Xg, lamg = g.get_state()
+    assert rel(ug, u) < 1e-7
+    assert rel(Xg - case.X0, X - case.X0) < 1e-7
+    assert rel(lamg, lam) < 1e-7
+    g.close()
