@@ -1,0 +1,367 @@
+#!/usr/bin/env python3
+"""FSI time steps per second on one GB300: the 128 x 128 Q2/P1disc lid-driven
+cavity with an immersed elastic disk (7776 P1 triangles), kappa = 1e3,
+nu = 0.01, dt = 1e-3, block-triangular preconditioner, 1e-8 relative residual.
+
+One bench step = one time step of the method (assemble C_f(X^n) and the
+right-hand side, solve the saddle-point system, advance).  The headline
+``value`` is the mixed-precision path (FP32 operators and multigrid inside
+FP64 refinement); the FP64 path is reported beside it under ``fp64``.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun) every rank runs its own replica of the workload (the
+solve of one instance does not shard); ``value`` sums the ranks' steps over
+the slowest rank's time.  ``--impl reference`` times the CPU oracle (sparse
+direct solve per step) on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FSI time-steps/s & HBM GB/s: mixed vs FP64 @1e-8 resid; p50/p99 latency"
+L2_FLUSH_BYTES = 512 << 20
+
+
+def workload():
+    import fsi_inputs as fi
+    return fi.config1()
+
+
+def workload_config(case):
+    return {"workload": "cavity128_lid_disk7776: N=128 Q2/P1disc fluid, disk R=0.2 m=36 (3997 nodes, 7776 P1 "
+                        "triangles), kappa=1e3, nu=0.01, rho=1, dt=1e-3, lid 1, block-triangular, rtol 1e-8",
+            "N": case.N, "solid_nodes": int(case.ref_xy.shape[0]), "solid_tris": int(case.tris.shape[0]),
+            "dofs": None, "l2": "flushed between timed steps (512 MiB write)"}
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines: list[str] = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------ our GPU arm
+PRECOND = 2      # block upper-triangular
+MAX_IT = 6000
+
+
+def time_arm(fsi, torch, case, precision, steps, warmup, stream, flush):
+    prob = fsi.problem_from_case(case, precision=precision, precond=PRECOND, rtol=1e-8, stream=stream.cuda_stream,
+                                 max_it=MAX_IT)
+    infos = []
+    for _ in range(warmup):
+        prob.step()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    torch.cuda.synchronize()
+    for k in range(steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(k & 0xFF)          # evict L2 between timed steps (outside the events)
+        ev[k][0].record(stream)
+        infos.append(prob.step())
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    counts = prob.graph_kernel_counts()
+    launches = 0
+    for inf in infos:
+        cycles = inf.refinements + 1 if precision == 1 else inf.restarts + 2
+        launches += int(counts[0] + counts[1] + cycles * counts[2] + inf.iterations * counts[3] + counts[4])
+    stats = {
+        "ms": ms,
+        "iterations": [i.iterations for i in infos],
+        "refinements": [i.refinements for i in infos],
+        "rel_residual_max": max(i.rel_residual for i in infos),
+        "launches": launches,
+    }
+    return prob, stats
+
+
+def time_e2e(fsi, case, precision, steps, stream):
+    """Through the C ABI with host buffers: set_state (H2D) + step + get_state (D2H)."""
+    prob = fsi.problem_from_case(case, precision=precision, precond=PRECOND, rtol=1e-8, stream=stream.cuda_stream,
+                                 max_it=MAX_IT)
+    u, p, X, lam = prob.get_state()
+    prob.step()
+    u, p, X, lam = prob.get_state()
+    t = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        prob.set_state(u, X)
+        prob.step()
+        u, p, X, lam = prob.get_state()
+        t.append(time.perf_counter() - t0)
+    h2d = (u.size + X.size) * 8
+    d2h = (u.size + p.size + X.size + lam.size) * 8
+    prob.close()
+    return t, h2d, d2h
+
+
+def run_ours(args):
+    import torch
+    from paper_2301_10041_gb300 import build, fsi
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0:
+        build.build()
+    if dist:
+        dist.barrier()
+    fsi.load_library()
+    case = workload()
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = start_cpu_baseline(args)
+
+    stream = torch.cuda.Stream()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    clocks = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t_wall0 = time.perf_counter()
+    prob_m, mixed = time_arm(fsi, torch, case, 1, args.steps, args.warmup, stream, flush)
+    t_wall1 = time.perf_counter()
+    clk = clocks.stop()
+    prob_d, fp64 = time_arm(fsi, torch, case, 0, args.steps, args.warmup, stream, flush)
+    roof = roofline(prob_m, args)
+    e2e_t, h2d, d2h = time_e2e(fsi, case, 1, max(3, min(args.steps, 10)), stream)
+    prob_m.close()
+    prob_d.close()
+
+    mixed_s = sum(mixed["ms"]) / 1000.0
+    fp64_s = sum(fp64["ms"]) / 1000.0
+    if dist:
+        t = torch.tensor([mixed_s, fp64_s, sum(e2e_t)], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        mixed_s, fp64_s, e2e_s = t.tolist()
+    else:
+        e2e_s = sum(e2e_t)
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    ms = mixed["ms"]
+    out = {
+        "metric": METRIC,
+        "value": world * args.steps / mixed_s,
+        "unit": "time-steps/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": 1000.0 * mixed_s / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32 operators + f64 refinement",
+        "data": "synthetic (analytic disk mesh, fluid at rest, lid 1)",
+        "config": workload_config(case),
+        "latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99)),
+                       "mean": float(np.mean(ms))},
+        "iterations_per_step": float(np.mean(mixed["iterations"])),
+        "refinements_per_step": float(np.mean(mixed["refinements"])),
+        "rel_residual_max": mixed["rel_residual_max"],
+        "fp64": {"value": world * args.steps / fp64_s, "unit": "time-steps/s",
+                 "ms_per_step": 1000.0 * fp64_s / args.steps,
+                 "latency_ms": {"p50": float(np.percentile(fp64["ms"], 50)),
+                                "p99": float(np.percentile(fp64["ms"], 99))},
+                 "iterations_per_step": float(np.mean(fp64["iterations"])),
+                 "rel_residual_max": fp64["rel_residual_max"]},
+        "e2e": {"value": world * len(e2e_t) / e2e_s, "unit": "time-steps/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": mixed["launches"],
+        "roofline": roof,
+        "clocks": clk,
+        "wall_s": t_wall1 - t_wall0,
+    }
+    out["config"]["dofs"] = int(prob_dofs(case))
+    out["config"]["parallelism"] = f"replicas x{world}"
+    if cpu is not None:
+        out["cpu_baseline"] = finish_cpu_baseline(cpu)
+    print(json.dumps(out))
+    if dist:
+        dist.destroy_process_group()
+
+
+def prob_dofs(case):
+    n_u = 2 * (2 * case.N - 1) ** 2
+    return n_u + 3 * case.N ** 2 + 4 * case.ref_xy.shape[0]
+
+
+def roofline(prob, args):
+    """Roofline of the dominant kernel of the mixed path (the FP32 full-system
+    operator, one launch per Krylov iteration), timed live on the library's
+    stream with CUDA events, L2 evicted before every launch."""
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    peak = peaks.get("hbm_gbs", 6800.0)
+    out = {}
+    for name, which in (("full_operator_f32", 0), ("velocity_chebyshev_f32", 2)):
+        ms, by = prob.time_kernel(which, reps=30)
+        out[name] = {"ms": ms, "bytes": by, "gbs": by / ms / 1e6}
+    dom = out["full_operator_f32"]
+    return {"bound": "hbm", "kernel": "k_fullmv<float,float,double>", "achieved": dom["gbs"], "peak": peak,
+            "unit": "GB/s", "frac": dom["gbs"] / peak, "traffic": None,
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6800 GB/s",
+            "launch_us": dom["ms"] * 1e3, "algorithmic_bytes": dom["bytes"], "others": out}
+
+
+# ------------------------------------------------------- CPU oracle timing
+CPU_SCRIPT = r"""
+import json, os, sys, time
+sys.path.insert(0, sys.argv[1])
+import numpy as np
+import fsi_inputs as fi
+from oracle import fsi_oracle as fo
+steps = int(sys.argv[2]); budget = float(sys.argv[3])
+case = fi.config1()
+t0 = time.perf_counter()
+prob = fo.OracleProblem(case.N, case.rho_f, case.nu, case.kappa, case.dt, case.lid_u, case.ref_xy, case.tris)
+setup = time.perf_counter() - t0
+u, X = case.u0, case.X0
+times = []
+start = time.perf_counter()
+for k in range(steps):
+    t = time.perf_counter()
+    u, p, X, lam = prob.step(u, X)
+    times.append(time.perf_counter() - t)
+    if time.perf_counter() - start > budget:
+        break
+print(json.dumps({"setup_s": setup, "step_s": times}))
+"""
+
+
+def start_cpu_baseline(args):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    env.pop("CUDA_VISIBLE_DEVICES", None)
+    return subprocess.Popen([sys.executable, "-c", CPU_SCRIPT, ROOT, str(args.cpu_steps), str(args.cpu_budget)],
+                            stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True, env=env)
+
+
+def finish_cpu_baseline(proc):
+    out, err = proc.communicate()
+    try:
+        r = json.loads(out.strip().splitlines()[-1])
+    except Exception:
+        return {"value": None, "unit": "time-steps/s", "cores": 1, "kind": "oracle",
+                "sample": "failed: " + (err or "")[-300:]}
+    st = r["step_s"]
+    return {"value": len(st) / sum(st), "unit": "time-steps/s", "cores": 1, "kind": "oracle",
+            "sample": f"{len(st)} full time step(s) of the same N=128 workload (C_f by brute-force point "
+                      f"location + bordered sparse LU of Eq. (matrix)), single thread, {sum(st):.1f} s; "
+                      f"constant-matrix setup {r['setup_s']:.1f} s excluded"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    env_cores = 1
+    proc = subprocess.run([sys.executable, "-c", CPU_SCRIPT, ROOT, str(max(1, args.steps)), str(args.cpu_budget)],
+                          capture_output=True, text=True,
+                          env=dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1"))
+    try:
+        r = json.loads(proc.stdout.strip().splitlines()[-1])
+    except Exception:
+        print(json.dumps({"impl": "reference", "unavailable": "oracle run failed: " + proc.stderr[-200:]}))
+        return
+    st = r["step_s"]
+    v = len(st) / sum(st)
+    sample = (f"{len(st)} of {args.steps} requested time steps of the N=128 workload within a "
+              f"{args.cpu_budget:.0f} s budget; constant-matrix setup ({r['setup_s']:.1f} s) is the warm-up")
+    case = workload()
+    out = {"metric": METRIC, "value": v, "unit": "time-steps/s", "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
+           "steps": len(st), "warmup": args.warmup, "ms_per_step": 1000.0 * sum(st) / len(st),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic (analytic disk mesh, fluid at rest, lid 1)", "config": workload_config(case),
+           "impl": "reference",
+           "cpu_baseline": {"value": v, "unit": "time-steps/s", "cores": env_cores, "kind": "oracle", "sample": sample},
+           "e2e": {"value": v, "unit": "time-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    out["config"]["dofs"] = int(prob_dofs(case))
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-steps", type=int, default=1)
+    ap.add_argument("--cpu-budget", type=float, default=240.0)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -28,8 +28,10 @@
  *    copied and may be freed after the call returns.
  *  - The library owns every device buffer it allocates (cudaMalloc); one
  *    problem lives on the device that was current at fsi_create_problem.
- *  - Work is queued on the CUDA stream given at creation (NULL = legacy
- *    default stream).  fsi_assemble_step and fsi_advance are asynchronous;
+ *  - Work is queued on the CUDA stream given at creation (NULL: the library
+ *    creates and owns a non-blocking stream; the legacy default stream cannot
+ *    be used because the step is captured in CUDA graphs).
+ *    fsi_assemble_step and fsi_advance are asynchronous;
  *    fsi_solve_step, fsi_get_* and fsi_set_state synchronise the stream.
  *  - Every call returns an int status: FSI_OK (0) or a negative FSI_ERR_*
  *    code; no C++ exception crosses the boundary.  Errors found on the
@@ -65,13 +67,15 @@ extern "C" {
 
 /* Parameters of one instance (Section 4 and Section 6 of the paper). */
 typedef struct fsi_params {
-    int    N;          /* fluid cells per side, >= 2 */
+    int    N;          /* fluid cells per side: even, N = c * 2^k with c <= 8 */
     double rho_f;      /* fluid (= solid) density, Problem 2: rho_s = rho_f */
     double nu;         /* viscosity, nu_f = nu_s (Section 3) */
     double kappa;      /* P(F) = kappa F (Section 4, before Eq. (matrix)) */
     double dt;         /* backward-Euler time step (Section 4) */
     double lid_u;      /* tangential velocity of the top wall, 0 = all walls at rest */
-    int    precond;    /* 0 block-diagonal, 1 block-triangular (Section 5) */
+    int    precond;    /* 0 block-diagonal, 1 block lower-triangular (the two
+                          preconditioners of Section 5), 2 block upper-triangular
+                          [[A11, A12], [0, A22]] (solid block first) */
     int    precision;  /* 0 FP64 everywhere; 1 FP32 operators and preconditioner
                           inside FGMRES, FP64 Gram-Schmidt, least squares and
                           iterative refinement */
@@ -154,8 +158,9 @@ int fsi_sizes(const fsi_problem* p, int* n_u, int* n_p, int* n_x, int* n_total);
 int fsi_get_points(fsi_problem* p, int* cell, double* xi, double* eta);
 
 /* Test hook: the scalar coupling matrix C of the last fsi_assemble_step in
- * coordinate form (C_f = C on each velocity component).  Entries with a
- * wall node column are included.  Call with rows == NULL to get the count
+ * coordinate form (C_f = C on each velocity component), interior fluid node
+ * columns only (wall columns enter the right-hand side g2, see
+ * fsi_get_rhs).  Call with rows == NULL to get the count
  * in *nnz; then with arrays of that size: solid node, lattice node id, value. */
 int fsi_get_coupling(fsi_problem* p, int* nnz, int* rows, int* lattice_cols, double* vals);
 
@@ -171,6 +176,23 @@ int fsi_apply_preconditioner(fsi_problem* p, const double* v, double* z, int pre
 /* Lattice node id of every interior velocity node, in the library's order
  * (n_u/2 entries). */
 int fsi_interior_nodes(const fsi_problem* p, int* lattice_ids);
+
+/* Kernel nodes in the captured graphs: counts[0] assembly (S1-S4),
+ * counts[1] solve set-up, counts[2] one refinement/restart cycle outside
+ * the Arnoldi loop, counts[3] one Arnoldi iteration (S5-S7), counts[4]
+ * pressure normalisation.  Kernels per step = c0 + c1 + cycles*c2 +
+ * iterations*c3 + c4 (cycles = refinements + 1). */
+int fsi_graph_kernel_counts(const fsi_problem* p, int* counts);
+
+/* Measurement hook: time `reps` launches of one kernel on the problem's
+ * stream with CUDA events, each launch after a 256 MiB write that evicts
+ * L2, on the current data of the problem.  which: 0 full operator in FP32
+ * (precision 1 only), 1 full operator in FP64 (residual form), 2 finest
+ * velocity Chebyshev smoothing step in FP32 (precision 1 only), 3 the same in
+ * FP64.  avg_ms: mean launch time; bytes: algorithmic bytes of one launch
+ * (stored blocks and indices without padding, each vector once).  Allocates
+ * and frees a 256 MiB scratch buffer. */
+int fsi_time_kernel(fsi_problem* p, int which, int reps, double* avg_ms, double* bytes);
 
 /* Right-hand side of the last fsi_assemble_step in block order (n_total). */
 int fsi_get_rhs(fsi_problem* p, double* b);

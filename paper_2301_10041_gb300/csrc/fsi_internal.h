@@ -79,7 +79,7 @@ void triangle_rule(double lam[6][3], double w[6]);
 
 // ------------------------------------------------------------- device side
 template <class T>
-struct Sell {            // sliced ELL of block rows, slice height 32
+struct Sell {            // sliced ELL of block rows, slice height 8
   int nrows = 0;         // block rows
   int BR = 1, BC = 1, NV = 1;
   bool kron = false;

@@ -37,7 +37,10 @@ struct Ctl {
   double scale;     // 1 / ||w|| for the next basis vector
   double pmean;     // mean of the constant pressure coefficients
   int aflags;       // FLAG_* bits raised by the assembly (S2-S4)
-  int pad2;
+  int cyc_active;   // 1 while the Arnoldi loop of the current cycle continues
+  int refine;       // 1 when the current Gram-Schmidt step needs a second pass
+  int refines;      // second passes taken in this solve
+  double wnorm2;    // ||w||^2 before orthogonalisation
   unsigned int counter[8];  // last-block counters for reductions
 };
 
@@ -64,77 +67,131 @@ struct SpmvArgs {
   T c1 = 0, c2 = 0;
 };
 
+// Sliced ELL with slice height 8 ("SELL-8"): slot(s, k, r) = soff[s] + 8k + r.
+// One warp owns one slice and gives each block row 4 threads: lane = 8 t + r,
+// thread t takes the entries k = t, t + 4, ...  For a fixed round the warp
+// reads 32 consecutive slots (coalesced), and 4x more threads are in flight
+// than with one thread per row.  Partial sums meet through two shuffles.
+constexpr int kSliceRows = 8;
+constexpr int kRowThreads = 4;
+
 template <class T>
-__device__ __forceinline__ void load_vals(const T* p, T* v, int nv) {
+struct Vec2;
+template <>
+struct Vec2<float> { using type = float2; };
+template <>
+struct Vec2<double> { using type = double2; };
+
+template <class T, int NV>
+__device__ __forceinline__ void load_block(const T* __restrict__ p, T* v) {
+  if constexpr (NV == 4 && sizeof(T) == 4) {
+    const float4 q = __ldg(reinterpret_cast<const float4*>(p));
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+  } else if constexpr (NV % 2 == 0) {
+    using V2 = typename Vec2<T>::type;
 #pragma unroll
-  for (int i = 0; i < 9; ++i)
-    if (i < nv) v[i] = p[i];
+    for (int i = 0; i < NV / 2; ++i) {
+      const V2 q = __ldg(reinterpret_cast<const V2*>(p) + i);
+      v[2 * i] = q.x; v[2 * i + 1] = q.y;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) v[i] = __ldg(p + i);
+  }
 }
 
-template <class T, int BR, int BC, bool KRON, int NV, int MODE>
-__global__ void __launch_bounds__(128) k_sell(int nrows, const int* __restrict__ soff,
-                                              const int* __restrict__ len, const int* __restrict__ col,
-                                              const T* __restrict__ val, SpmvArgs<T> a) {
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= nrows) return;
-  const int s = r >> 5, lane = r & 31;
-  const int base = soff[s] + lane;
-  const int n = len[r];
-  T acc[BR];
+template <class TX, class TA, int BC>
+__device__ __forceinline__ void load_x(const TX* __restrict__ x, int c, TA* xv) {
+  if constexpr (BC == 2) {
+    using V2 = typename Vec2<TX>::type;
+    const V2 q = *reinterpret_cast<const V2*>(x + 2 * (size_t)c);
+    xv[0] = (TA)q.x; xv[1] = (TA)q.y;
+  } else {
 #pragma unroll
-  for (int i = 0; i < BR; ++i) acc[i] = 0;
-  const T* __restrict__ x = a.x;
-  for (int k = 0; k < n; ++k) {
-    const int slot = base + (k << 5);
-    const int c = __ldg(col + slot);
-    if (KRON) {
-      const T v = __ldg(val + slot);
+    for (int j = 0; j < BC; ++j) xv[j] = (TA)x[(size_t)c * BC + j];
+  }
+}
+
+// accumulate this thread's share of block row `row` of A (BR x BC blocks) times x
+template <class TA, class TX, int BR, int BC, bool KRON, int NV>
+__device__ __forceinline__ void sell_row(const Sell<TA>& A, int row, int t, const TX* __restrict__ x, TA* acc) {
+  const int base = A.soff[row >> 3] + (row & 7);
+  const int n = A.len[row];
+#pragma unroll 2
+  for (int k = t; k < n; k += kRowThreads) {
+    const int slot = base + (k << 3);
+    const int c = __ldg(A.col + slot);
+    TA xv[BC];
+    load_x<TX, TA, BC>(x, c, xv);
+    if constexpr (KRON) {
+      const TA v = __ldg(A.val + slot);
 #pragma unroll
-      for (int i = 0; i < BR; ++i) acc[i] += v * x[c * BC + i];
+      for (int i = 0; i < BR; ++i) acc[i] += v * xv[i];
     } else {
-      T v[NV];
-#pragma unroll
-      for (int i = 0; i < NV; ++i) v[i] = __ldg(val + (size_t)slot * NV + i);
-      T xv[BC];
-#pragma unroll
-      for (int jj = 0; jj < BC; ++jj) xv[jj] = x[c * BC + jj];
+      TA v[NV];
+      load_block<TA, NV>(A.val + (size_t)slot * NV, v);
 #pragma unroll
       for (int i = 0; i < BR; ++i)
 #pragma unroll
-        for (int jj = 0; jj < BC; ++jj) acc[i] += v[i * BC + jj] * xv[jj];
+        for (int j = 0; j < BC; ++j) acc[i] += v[i * BC + j] * xv[j];
     }
   }
+}
+
+template <class T, int BR>
+__device__ __forceinline__ void row_reduce(T* acc) {
 #pragma unroll
   for (int i = 0; i < BR; ++i) {
-    const int row = r * BR + i;
+    acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], 8);
+    acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], 16);
+  }
+}
+
+template <class T, int BR, int BC, bool KRON, int NV, int MODE>
+__global__ void __launch_bounds__(128) k_sell(Sell<T> A, SpmvArgs<T> a) {
+  const int lane = threadIdx.x & 31;
+  const int row = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * kSliceRows + (lane & 7);
+  const int t = lane >> 3;
+  const bool live = row < A.nrows;
+  T acc[BR];
+#pragma unroll
+  for (int i = 0; i < BR; ++i) acc[i] = 0;
+  if (live) sell_row<T, T, BR, BC, KRON, NV>(A, row, t, a.x, acc);
+  row_reduce<T, BR>(acc);
+  if (!live || t != 0) return;
+  const T* __restrict__ x = a.x;
+#pragma unroll
+  for (int i = 0; i < BR; ++i) {
+    const int r = row * BR + i;
     if (MODE == MODE_AXPBY) {
       T out = a.alpha * acc[i];
-      if (a.z) out += a.beta * a.z[row];
-      a.y[row] = out;
+      if (a.z) out += a.beta * a.z[r];
+      a.y[r] = out;
     } else if (MODE == MODE_CHEB) {
-      const T res = a.z[row] - acc[i];
-      const T dn = a.c1 * a.d[row] + a.c2 * a.dinv[row] * res;
-      a.d[row] = dn;
-      a.y[row] = x[row] + dn;
+      const T res = a.z[r] - acc[i];
+      const T dn = a.c1 * a.d[r] + a.c2 * a.dinv[r] * res;
+      a.d[r] = dn;
+      a.y[r] = x[r] + dn;
     } else if (MODE == MODE_CHEB0) {
-      const T res = a.z[row] - acc[i];
-      const T dn = a.c2 * a.dinv[row] * res;
-      a.d[row] = dn;
-      a.y[row] = x[row] + dn;
+      const T res = a.z[r] - acc[i];
+      const T dn = a.c2 * a.dinv[r] * res;
+      a.d[r] = dn;
+      a.y[r] = x[r] + dn;
     } else {  // MODE_INIT
-      T t = a.alpha * acc[i];
-      if (a.z) t += a.beta * a.z[row];
-      a.y[row] = t;
-      const T dn = a.c2 * a.dinv[row] * t;
-      a.d[row] = dn;
-      a.xo[row] = dn;
+      T tt = a.alpha * acc[i];
+      if (a.z) tt += a.beta * a.z[r];
+      a.y[r] = tt;
+      const T dn = a.c2 * a.dinv[r] * tt;
+      a.d[r] = dn;
+      a.xo[r] = dn;
     }
   }
 }
 
 // --------------------------------------------------- full-system operator
 // y = alpha * A x + beta * z for the block operator of Eq. (matrix) in the
-// layout [u (2 nU) | p (3 nP) | X (2 nS) | lambda (2 nS)].
+// layout [u (2 nU) | p (3 nP) | X (2 nS) | lambda (2 nS)].  One launch covers
+// the three row segments; each CTA (4 warps, 32 block rows) lies in one.
 template <class TA>
 struct FullOp {
   int nU = 0, nP = 0, nS = 0;
@@ -153,57 +210,39 @@ struct FullOp {
 template <class TA, class TX, class TY>
 __global__ void __launch_bounds__(128) k_fullmv(FullOp<TA> op, const TX* __restrict__ x, TY* __restrict__ y,
                                                 const TY* __restrict__ z, TY alpha, TY beta) {
+  const int lane = threadIdx.x & 31, t = lane >> 3;
   const int b = blockIdx.x;
+  const int wrow = (threadIdx.x >> 5) * kSliceRows + (lane & 7);
   const size_t offP = 2 * (size_t)op.nU, offX = offP + 3 * (size_t)op.nP, offL = offX + 2 * (size_t)op.nS;
   if (b < op.gU) {
-    const int r = b * blockDim.x + threadIdx.x;
-    if (r >= op.nU) return;
-    TA a0 = 0, a1 = 0;
-    {
-      const int base = op.Af.soff[r >> 5] + (r & 31), n = op.Af.len[r];
-      for (int k = 0; k < n; ++k) {
-        const int slot = base + (k << 5);
-        const int c = __ldg(op.Af.col + slot);
-        const TA* v = op.Af.val + (size_t)slot * 4;
-        const TA x0 = (TA)x[2 * c], x1 = (TA)x[2 * c + 1];
-        a0 += __ldg(v) * x0 + __ldg(v + 1) * x1;
-        a1 += __ldg(v + 2) * x0 + __ldg(v + 3) * x1;
+    const int r = b * 32 + wrow;
+    const bool live = r < op.nU;
+    TA a[2] = {0, 0};
+    if (live) {
+      sell_row<TA, TX, 2, 2, false, 4>(op.Af, r, t, x, a);
+      sell_row<TA, TX, 2, 3, false, 6>(op.Bt, r, t, x + offP, a);
+      for (int k = op.cft_ptr[r] + t; k < op.cft_ptr[r + 1]; k += kRowThreads) {
+        const int c = op.cft_col[k];
+        const TA v = op.cft_val[k];
+        TA lv[2];
+        load_x<TX, TA, 2>(x + offL, c, lv);
+        a[0] += v * lv[0];
+        a[1] += v * lv[1];
       }
     }
-    {
-      const int base = op.Bt.soff[r >> 5] + (r & 31), n = op.Bt.len[r];
-      for (int k = 0; k < n; ++k) {
-        const int slot = base + (k << 5);
-        const int c = __ldg(op.Bt.col + slot);
-        const TA* v = op.Bt.val + (size_t)slot * 6;
-        const TA p0 = (TA)x[offP + 3 * c], p1 = (TA)x[offP + 3 * c + 1], p2 = (TA)x[offP + 3 * c + 2];
-        a0 += __ldg(v) * p0 + __ldg(v + 1) * p1 + __ldg(v + 2) * p2;
-        a1 += __ldg(v + 3) * p0 + __ldg(v + 4) * p1 + __ldg(v + 5) * p2;
-      }
-    }
-    for (int k = op.cft_ptr[r]; k < op.cft_ptr[r + 1]; ++k) {
-      const int c = op.cft_col[k];
-      const TA v = op.cft_val[k];
-      a0 += v * (TA)x[offL + 2 * c];
-      a1 += v * (TA)x[offL + 2 * c + 1];
-    }
-    TY o0 = alpha * (TY)a0, o1 = alpha * (TY)a1;
+    row_reduce<TA, 2>(a);
+    if (!live || t != 0) return;
+    TY o0 = alpha * (TY)a[0], o1 = alpha * (TY)a[1];
     if (z) { o0 += beta * z[2 * r]; o1 += beta * z[2 * r + 1]; }
     y[2 * r] = o0;
     y[2 * r + 1] = o1;
   } else if (b < op.gU + op.gP) {
-    const int r = (b - op.gU) * blockDim.x + threadIdx.x;
-    if (r >= op.nP) return;
+    const int r = (b - op.gU) * 32 + wrow;
+    const bool live = r < op.nP;
     TA a[3] = {0, 0, 0};
-    const int base = op.Bneg.soff[r >> 5] + (r & 31), n = op.Bneg.len[r];
-    for (int k = 0; k < n; ++k) {
-      const int slot = base + (k << 5);
-      const int c = __ldg(op.Bneg.col + slot);
-      const TA* v = op.Bneg.val + (size_t)slot * 6;
-      const TA x0 = (TA)x[2 * c], x1 = (TA)x[2 * c + 1];
-#pragma unroll
-      for (int i = 0; i < 3; ++i) a[i] += __ldg(v + 2 * i) * x0 + __ldg(v + 2 * i + 1) * x1;
-    }
+    if (live) sell_row<TA, TX, 3, 2, false, 6>(op.Bneg, r, t, x, a);
+    row_reduce<TA, 3>(a);
+    if (!live || t != 0) return;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       TY o = alpha * (TY)a[i];
@@ -211,31 +250,38 @@ __global__ void __launch_bounds__(128) k_fullmv(FullOp<TA> op, const TX* __restr
       y[offP + 3 * r + i] = o;
     }
   } else {
-    const int r = (b - op.gU - op.gP) * blockDim.x + threadIdx.x;
-    if (r >= op.nS) return;
-    TA ax0 = 0, ax1 = 0, al0 = 0, al1 = 0;
-    const int base = op.Ssol.soff[r >> 5] + (r & 31), n = op.Ssol.len[r];
-    for (int k = 0; k < n; ++k) {
-      const int slot = base + (k << 5);
-      const int c = __ldg(op.Ssol.col + slot);
-      const TA as = __ldg(op.Ssol.val + 2 * (size_t)slot), cs = __ldg(op.Ssol.val + 2 * (size_t)slot + 1);
-      const TA X0 = (TA)x[offX + 2 * c], X1 = (TA)x[offX + 2 * c + 1];
-      const TA L0 = (TA)x[offL + 2 * c], L1 = (TA)x[offL + 2 * c + 1];
-      ax0 += as * X0 - cs * L0;
-      ax1 += as * X1 - cs * L1;
-      al0 -= op.inv_dt * cs * X0;
-      al1 -= op.inv_dt * cs * X1;
+    const int r = (b - op.gU - op.gP) * 32 + wrow;
+    const bool live = r < op.nS;
+    TA a[4] = {0, 0, 0, 0};
+    if (live) {
+      const int base = op.Ssol.soff[r >> 3] + (r & 7), n = op.Ssol.len[r];
+      for (int k = t; k < n; k += kRowThreads) {
+        const int slot = base + (k << 3);
+        const int c = __ldg(op.Ssol.col + slot);
+        const TA as = __ldg(op.Ssol.val + 2 * (size_t)slot), cs = __ldg(op.Ssol.val + 2 * (size_t)slot + 1);
+        TA Xv[2], Lv[2];
+        load_x<TX, TA, 2>(x + offX, c, Xv);
+        load_x<TX, TA, 2>(x + offL, c, Lv);
+        a[0] += as * Xv[0] - cs * Lv[0];
+        a[1] += as * Xv[1] - cs * Lv[1];
+        a[2] -= op.inv_dt * cs * Xv[0];
+        a[3] -= op.inv_dt * cs * Xv[1];
+      }
+      const size_t cbase = (size_t)(r >> 5) * 32 * op.cf_cap + (r & 31);
+      const int nc = op.cf_len[r];
+      for (int k = t; k < nc; k += kRowThreads) {
+        const size_t slot = cbase + ((size_t)k << 5);
+        const int c = op.cf_col[slot];
+        const TA v = op.cf_val[slot];
+        TA uv[2];
+        load_x<TX, TA, 2>(x, c, uv);
+        a[2] += v * uv[0];
+        a[3] += v * uv[1];
+      }
     }
-    const size_t cbase = (size_t)(r >> 5) * 32 * op.cf_cap + (r & 31);
-    const int nc = op.cf_len[r];
-    for (int k = 0; k < nc; ++k) {
-      const size_t slot = cbase + ((size_t)k << 5);
-      const int c = op.cf_col[slot];
-      const TA v = op.cf_val[slot];
-      al0 += v * (TA)x[2 * c];
-      al1 += v * (TA)x[2 * c + 1];
-    }
-    TY o[4] = {alpha * (TY)ax0, alpha * (TY)ax1, alpha * (TY)al0, alpha * (TY)al1};
+    row_reduce<TA, 4>(a);
+    if (!live || t != 0) return;
+    TY o[4] = {alpha * (TY)a[0], alpha * (TY)a[1], alpha * (TY)a[2], alpha * (TY)a[3]};
     if (z) {
       o[0] += beta * z[offX + 2 * r]; o[1] += beta * z[offX + 2 * r + 1];
       o[2] += beta * z[offL + 2 * r]; o[3] += beta * z[offL + 2 * r + 1];
@@ -273,14 +319,22 @@ __global__ void k_cf_apply(int nS, int cap, const int* __restrict__ len, const i
 }
 
 // ------------------------------------------------------------ small dense
-// y = A x for a dense row-major n x n matrix (coarsest multigrid level).
+// y = A x for a dense row-major n x n matrix (coarsest multigrid level):
+// one warp per row, lanes over the columns, 8 rows per CTA
 template <class T>
 __global__ void k_dense_mv(int n, const T* __restrict__ A, const T* __restrict__ x, T* __restrict__ y) {
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    T s = 0;
-    for (int j = 0; j < n; ++j) s += A[(size_t)i * n + j] * x[j];
-    y[i] = s;
-  }
+  const int lane = threadIdx.x & 31;
+  const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (i >= n) return;
+  const T* __restrict__ a = A + (size_t)i * n;
+  T s0 = 0, s1 = 0;
+  int j = lane;
+  for (; j + 32 < n; j += 64) { s0 += a[j] * x[j]; s1 += a[j + 32] * x[j + 32]; }
+  if (j < n) s0 += a[j] * x[j];
+  T s = s0 + s1;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if (lane == 0) y[i] = s;
 }
 
 // ----------------------------------------------------------- vector kernels

@@ -475,9 +475,10 @@ void build_setup(const SetupParams& sp, int n_s, int n_tri, const double* ref_xy
     out.interior_lattice[k] = iy * n1 + ix;
     out.lattice_to_node[(size_t)iy * n1 + ix] = k;
   }
-  // ---- multigrid hierarchy: N, N/2, ... while even and > 4
+  // ---- multigrid hierarchy: N, N/2, ... while even and > 8 (coarsest <= 8:
+  // at most 2*15^2 = 450 velocity unknowns, inverted densely)
   std::vector<int> Ns{N};
-  while (Ns.back() % 2 == 0 && Ns.back() > 4) Ns.push_back(Ns.back() / 2);
+  while (Ns.back() % 2 == 0 && Ns.back() > 8) Ns.push_back(Ns.back() / 2);
   out.levels.resize(Ns.size());
   for (size_t l = 0; l < Ns.size(); ++l) {
     FluidLevelHost& L = out.levels[l];
@@ -586,22 +587,22 @@ void build_setup(const SetupParams& sp, int n_s, int n_tri, const double* ref_xy
 SellHost to_sell(const HostBlockMatrix& A) {
   SellHost s;
   s.nrows = A.nrows; s.BR = A.BR; s.BC = A.BC; s.NV = A.NV; s.kron = A.kron;
-  s.nslices = (A.nrows + 31) / 32;
+  s.nslices = (A.nrows + 7) / 8;
   s.soff.assign(s.nslices + 1, 0);
   s.len.assign(A.nrows, 0);
   for (int r = 0; r < A.nrows; ++r) s.len[r] = A.ptr[r + 1] - A.ptr[r];
   for (int sl = 0; sl < s.nslices; ++sl) {
     int w = 0;
-    for (int r = sl * 32; r < std::min(A.nrows, sl * 32 + 32); ++r) w = std::max(w, s.len[r]);
-    s.soff[sl + 1] = s.soff[sl] + 32 * w;
+    for (int r = sl * 8; r < std::min(A.nrows, sl * 8 + 8); ++r) w = std::max(w, s.len[r]);
+    s.soff[sl + 1] = s.soff[sl] + 8 * w;
   }
   const size_t nslot = (size_t)s.soff[s.nslices];
   s.col.assign(nslot, 0);
   s.val.assign(nslot * s.NV, 0.0);
   for (int r = 0; r < A.nrows; ++r) {
-    const int sl = r / 32, lane = r % 32;
+    const int sl = r / 8, lane = r % 8;
     for (int k = 0; k < s.len[r]; ++k) {
-      const size_t slot = (size_t)s.soff[sl] + (size_t)k * 32 + lane;
+      const size_t slot = (size_t)s.soff[sl] + (size_t)k * 8 + lane;
       const int j = A.ptr[r] + k;
       s.col[slot] = A.col[j];
       for (int v = 0; v < s.NV; ++v) s.val[slot * s.NV + v] = A.val[(size_t)j * A.NV + v];

@@ -11,6 +11,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -87,12 +88,12 @@ static T* upload_as(Arena& ar, const std::vector<double>& h) {
 // ------------------------------------------------------------- SpMV launch
 template <class T, int BR, int BC, bool KRON, int NV>
 static void sell_launch_shape(const Sell<T>& A, int mode, const SpmvArgs<T>& a, cudaStream_t s) {
-  const unsigned g = nblk(A.nrows, 128);
+  const unsigned g = nblk(A.nrows, 32);  // 4 warps x 8 block rows
   switch (mode) {
-    case MODE_AXPBY: k_sell<T, BR, BC, KRON, NV, MODE_AXPBY><<<g, 128, 0, s>>>(A.nrows, A.soff, A.len, A.col, A.val, a); break;
-    case MODE_CHEB: k_sell<T, BR, BC, KRON, NV, MODE_CHEB><<<g, 128, 0, s>>>(A.nrows, A.soff, A.len, A.col, A.val, a); break;
-    case MODE_CHEB0: k_sell<T, BR, BC, KRON, NV, MODE_CHEB0><<<g, 128, 0, s>>>(A.nrows, A.soff, A.len, A.col, A.val, a); break;
-    default: k_sell<T, BR, BC, KRON, NV, MODE_INIT><<<g, 128, 0, s>>>(A.nrows, A.soff, A.len, A.col, A.val, a); break;
+    case MODE_AXPBY: k_sell<T, BR, BC, KRON, NV, MODE_AXPBY><<<g, 128, 0, s>>>(A, a); break;
+    case MODE_CHEB: k_sell<T, BR, BC, KRON, NV, MODE_CHEB><<<g, 128, 0, s>>>(A, a); break;
+    case MODE_CHEB0: k_sell<T, BR, BC, KRON, NV, MODE_CHEB0><<<g, 128, 0, s>>>(A, a); break;
+    default: k_sell<T, BR, BC, KRON, NV, MODE_INIT><<<g, 128, 0, s>>>(A, a); break;
   }
 }
 
@@ -175,8 +176,8 @@ static void build_mg(Arena& ar, const HostSetup& hs, bool pressure, int degree, 
     const double hi = 1.05 * (pressure ? H.lmaxL : H.lmaxA);
     L.ch = cheb_coeffs(hi / (pressure ? kChebRatioP : kChebRatioU), hi, degree);
   }
-  mg.coarse_inv = upload_as<T>(ar, pressure ? hs.coarseLinv : hs.coarseAinv);
   mg.coarse_n = pressure ? hs.coarse_nL : hs.coarse_nA;
+  mg.coarse_inv = upload_as<T>(ar, pressure ? hs.coarseLinv : hs.coarseAinv);  // row-major
 }
 
 // Level l input: L.b, with L.x = L.d = c0 dinv b already set (l < last).
@@ -186,7 +187,7 @@ static T* vcycle(MG<T>& mg, int l, cudaStream_t s, T* out) {
   const int last = (int)mg.lv.size() - 1;
   MGLevel<T>& L = mg.lv[l];
   if (l == last) {
-    k_dense_mv<T><<<1, 128, 0, s>>>(mg.coarse_n, mg.coarse_inv, L.b, out ? out : L.x);
+    k_dense_mv<T><<<nblk(mg.coarse_n, 8), 256, 0, s>>>(mg.coarse_n, mg.coarse_inv, L.b, out ? out : L.x);
     return out ? out : L.x;
   }
   T* xc = L.x;
@@ -245,7 +246,8 @@ struct Problem {
   fsi_params prm{};
   int N = 0, nU = 0, nP = 0, nS = 0, nTri = 0, nPts = 0;
   size_t n = 0, offP = 0, offX = 0, offL = 0;
-  cudaStream_t stream = nullptr, s2 = nullptr;
+  cudaStream_t stream = nullptr, s2 = nullptr, s3 = nullptr;  // s3: parallel branch of the preconditioner
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   bool own_stream = false;
   int device = 0;
   Arena ar;
@@ -278,7 +280,13 @@ struct Problem {
   // graphs
   cudaGraphExec_t g_assemble = nullptr, g_begin = nullptr, g_cycle = nullptr, g_finish = nullptr;
   cudaGraph_t gr_assemble = nullptr, gr_begin = nullptr, gr_cycle = nullptr, gr_finish = nullptr;
+  // host-driven Arnoldi loop (FSI_HOST_LOOP=1): no conditional nodes, so that
+  // per-kernel profilers can see the kernels; same kernels, one sync per iteration
+  bool host_loop = false;
+  cudaGraphExec_t g_cstart = nullptr, g_body = nullptr, g_cend = nullptr;
+  cudaGraph_t gr_cstart = nullptr, gr_body = nullptr, gr_cend = nullptr;
   bool assembled = false;
+  int kn_assemble = 0, kn_begin = 0, kn_cycle = 0, kn_body = 0, kn_finish = 0;  // kernel nodes per graph
 };
 
 // ------------------------------------------------------- solid block A_22^-1
@@ -308,7 +316,7 @@ static void solid_launch(Problem& P, Prec<T>& pr, cudaStream_t s) {
       std::swap(xc, xn);
     }
   };
-  if (P.prm.precond == 1) {
+  if (P.prm.precond == 1) {  // lower block-triangular: r_l = v_l - C_f z_u
     SpmvArgs<T> a;
     a.x = pr.zw; a.y = pr.sb; a.z = vL; a.alpha = dt; a.beta = -dt;
     a.d = pr.sd; a.dinv = pr.csdinv; a.xo = pr.sx; a.c2 = (T)pr.chs.c0;
@@ -330,60 +338,123 @@ static void solid_launch(Problem& P, Prec<T>& pr, cudaStream_t s) {
 // Schur approximation S^-1 ~ nu M_p^-1 + (rho/dt) L_p^-1 (one V-cycle on the
 // pressure Laplacian L_p = B diag(M_f)^-1 B^T), then u = A_f^-1 (v_u + B^T p)
 // by one V-cycle with Chebyshev-Jacobi smoothing on the Q2 hierarchy.
+// C_f^T applied to the multiplier part: y_u = z_u - C_f^T lambda (CSR over interior nodes)
+template <class T>
+__global__ void k_cft_sub(int nU, const int* __restrict__ ptr, const int* __restrict__ col, const T* __restrict__ val,
+                          const T* __restrict__ lam, const T* __restrict__ zu, T* __restrict__ y) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nU) return;
+  T a0 = zu[2 * r], a1 = zu[2 * r + 1];
+  for (int k = ptr[r]; k < ptr[r + 1]; ++k) {
+    const T v = val[k];
+    const int c = col[k];
+    a0 -= v * lam[2 * c];
+    a1 -= v * lam[2 * c + 1];
+  }
+  y[2 * r] = a0;
+  y[2 * r + 1] = a1;
+}
+
+// One application z = P^-1 v of the block preconditioner (Section 5), input
+// pr.vin, output pr.zw.  A_11^-1 is approximated by the upper block-
+// triangular Stokes preconditioner: p = -S^-1 v_p with the Cahouet-Chabard
+// Schur approximation S^-1 ~ nu M_p^-1 + (rho/dt) L_p^-1 (one V-cycle on the
+// pressure Laplacian L_p = B diag(M_f)^-1 B^T), then u = A_f^-1 (v_u + B^T p)
+// by one V-cycle with Chebyshev-Jacobi smoothing on the Q2 hierarchy.
+//   precond 0: diag(A_11, A_22)                      (block-diagonal)
+//   precond 1: [[A_11, 0], [A_21, A_22]]             (block lower-triangular)
+//   precond 2: [[A_11, A_12], [0, A_22]]             (block upper-triangular:
+//              the solid block first, then the fluid with v_u - C_f^T z_l)
 template <class T>
 static void precond_launch(Problem& P, Prec<T>& pr, cudaStream_t s) {
   const int n3 = 3 * P.nP;
   T* vp = pr.vin + P.offP;
   T* zp = pr.zw + P.offP;
+  // the solid block does not depend on the fluid for precond 0 and 2: run it
+  // on a parallel branch (its kernels are small and latency-bound)
+  const bool fork = P.prm.precond != 1;
+  if (fork) {
+    CK(cudaEventRecord(P.ev_fork, s));
+    CK(cudaStreamWaitEvent(P.s3, P.ev_fork, 0));
+    solid_launch(P, pr, P.s3);
+    CK(cudaEventRecord(P.ev_join, P.s3));
+  }
   MGLevel<T>& L0p = pr.mgP.lv[0];
   k_cheb_first<T><<<nblk(n3, 256), 256, 0, s>>>(n3, vp, L0p.dinv, (T)L0p.ch.c0, L0p.d, L0p.x, (T)1, L0p.b);
   T* sp = vcycle<T>(pr.mgP, 0, s, (T*)nullptr);
   k_schur<T><<<nblk(n3, 256), 256, 0, s>>>(n3, vp, sp, pr.mpinv, (T)P.prm.nu, (T)(P.prm.rho_f / P.prm.dt), zp);
   MGLevel<T>& L0u = pr.mgU.lv[0];
+  const T* vu = pr.vin;
+  if (P.prm.precond == 2) {
+    CK(cudaStreamWaitEvent(s, P.ev_join, 0));
+    k_cft_sub<T><<<nblk(P.nU, 128), 128, 0, s>>>(P.nU, P.cft_ptr, P.cft_col, pr.op.cft_val, pr.zw + P.offL, pr.vin,
+                                                  L0u.r);
+    vu = L0u.r;
+  }
   SpmvArgs<T> a;
-  a.x = zp; a.y = L0u.b; a.z = pr.vin; a.alpha = -1; a.beta = 1;
+  a.x = zp; a.y = L0u.b; a.z = vu; a.alpha = -1; a.beta = 1;
   a.d = L0u.d; a.dinv = L0u.dinv; a.xo = L0u.x; a.c2 = (T)L0u.ch.c0;
   sell_launch(pr.op.Bt, MODE_INIT, a, s);
   vcycle(pr.mgU, 0, s, pr.zw);
-  solid_launch(P, pr, s);
+  if (P.prm.precond == 1) solid_launch(P, pr, s);
+  if (P.prm.precond == 0) CK(cudaStreamWaitEvent(s, P.ev_join, 0));
 }
 
 // --------------------------------------------------------- Krylov kernels
-constexpr int kRedMax = 304;  // 2 CTAs per SM
+// Reductions over the n unknowns use a fixed grid of nb CTAs of 256 threads,
+// CTA b owning rows [512 b, 512 b + 512); per-CTA partials are summed in a
+// fixed order, so every result is deterministic.  On GB300 these kernels are
+// bound by the FP64 pipe (2 DFMA per clock per SM), so the multi-dot gives
+// each warp whole vectors and each lane 16 rows of a vector: 16 DFMA against
+// the 8 DADD of its partial sums and warp shuffle.
+constexpr int kChunk = 512;
 
-__device__ void block_mdot(const double* __restrict__ V, size_t ld, int cnt, const double* __restrict__ w,
-                           int r0, int r1, double* __restrict__ part_row) {
-  __shared__ double sm[4][32];
+__device__ void mdot_warps(const double* __restrict__ V, size_t ld, int cnt, const double* __restrict__ ws, int r0,
+                           int nrow, double* __restrict__ part, int nb) {
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int i0 = 0; i0 < cnt; i0 += 4) {
-    double acc[4] = {0, 0, 0, 0};
-    for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
-      const double wv = w[r];
+  for (int i = wp; i < cnt; i += nw) {
+    const double* __restrict__ v = V + (size_t)i * ld + r0;
+    double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+    if (nrow == kChunk) {
 #pragma unroll
-      for (int t = 0; t < 4; ++t)
-        if (i0 + t < cnt) acc[t] += V[(size_t)(i0 + t) * ld + r] * wv;
+      for (int q = 0; q < kChunk / 128; ++q) {
+        const int r = lane + 128 * q;
+        a0 += v[r] * ws[r];
+        a1 += v[r + 32] * ws[r + 32];
+        a2 += v[r + 64] * ws[r + 64];
+        a3 += v[r + 96] * ws[r + 96];
+      }
+    } else {
+      for (int r = lane; r < nrow; r += 32) a0 += v[r] * ws[r];
     }
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      acc[t] = warp_sum(acc[t]);
-      if (lane == 0) sm[t][wp] = acc[t];
-    }
-    __syncthreads();
-    if (threadIdx.x < 4 && i0 + (int)threadIdx.x < cnt) {
-      double v = 0;
-      for (int q = 0; q < nw; ++q) v += sm[threadIdx.x][q];
-      part_row[i0 + threadIdx.x] = v;
-    }
-    __syncthreads();
+    const double sa = warp_sum((a0 + a1) + (a2 + a3));
+    if (lane == 0) part[(size_t)i * nb + blockIdx.x] = sa;
   }
 }
 
-__device__ void finalize_parts(const double* __restrict__ part, int pstride, int cnt, double* __restrict__ out) {
-  for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
-    double v = 0;
-    for (int b = 0; b < (int)gridDim.x; ++b) v += part[(size_t)b * pstride + i];
-    out[i] = v;
+__device__ void finalize_warps(const double* __restrict__ part, int nb, int cnt, double* __restrict__ out) {
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i = wp; i < cnt; i += nw) {
+    double acc = 0;
+    for (int b = lane; b < nb; b += 32) acc += part[(size_t)i * nb + b];
+    acc = warp_sum(acc);
+    if (lane == 0) out[i] = acc;
   }
+}
+
+// w[r] - sum_i V[i][r] h[i] with four independent partial sums
+__device__ __forceinline__ double gs_update(const double* __restrict__ V, size_t ld, int cnt, const double* hs,
+                                            double w, int r) {
+  double s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+  int i = 0;
+  for (; i + 3 < cnt; i += 4) {
+    s0 += V[(size_t)i * ld + r] * hs[i];
+    s1 += V[(size_t)(i + 1) * ld + r] * hs[i + 1];
+    s2 += V[(size_t)(i + 2) * ld + r] * hs[i + 2];
+    s3 += V[(size_t)(i + 3) * ld + r] * hs[i + 3];
+  }
+  for (; i < cnt; ++i) s0 += V[(size_t)i * ld + r] * hs[i];
+  return w - ((s0 + s1) + (s2 + s3));
 }
 
 struct KrylovArgs {
@@ -393,7 +464,7 @@ struct KrylovArgs {
   const double* V;
   double* w;
   double* part;
-  int pstride;
+  int pstride;   // unused by the partial layout part[i * nb + block]
   double* h1;
   double* h2;
   double* H;
@@ -404,89 +475,143 @@ struct KrylovArgs {
   cudaGraphConditionalHandle cond;
 };
 
-// CGS2 pass 1: h1 = V[0..j]^T w
+// Classical Gram-Schmidt with one refinement pass when needed (Daniel,
+// Gragg, Kaufman and Stewart 1976; the "refine if needed" rule of PETSc's
+// GMRES): pass 1 forms h1 = V^T w and ||w||; pass 2 updates w -= V h1 and
+// forms ||w||; if the norm fell below ||w|| / sqrt(2), passes 3-4 repeat the
+// projection (h2 = V^T w, w -= V h2).  Passes 3-4 return at once otherwise.
+
+// Hessenberg column j, Givens rotation, residual estimate and the stop
+// decision of the Arnoldi loop (one thread)
+__device__ void arnoldi_finish(const KrylovArgs& k, double s2) {
+  Ctl* c = k.ctl;
+  const int j = c->j, m1 = c->m + 1;
+  double* Hc = k.H + (size_t)j * m1;
+  for (int i = 0; i <= j; ++i) Hc[i] = k.h1[i] + (c->refine ? k.h2[i] : 0.0);
+  const double nrm = sqrt(s2);
+  Hc[j + 1] = nrm;
+  for (int i = 0; i < j; ++i) {
+    const double a = Hc[i], b = Hc[i + 1];
+    Hc[i] = k.cs[i] * a + k.sn[i] * b;
+    Hc[i + 1] = -k.sn[i] * a + k.cs[i] * b;
+  }
+  const double a = Hc[j], b = Hc[j + 1];
+  const double r = hypot(a, b);
+  const double cc = (r > 0) ? a / r : 1.0, ss = (r > 0) ? b / r : 0.0;
+  k.cs[j] = cc; k.sn[j] = ss;
+  Hc[j] = r; Hc[j + 1] = 0.0;
+  k.g[j + 1] = -ss * k.g[j];
+  k.g[j] = cc * k.g[j];
+  const double res = fabs(k.g[j + 1]);
+  c->its += 1;
+  c->res = res;
+  bool stop = false;
+  if (!(res == res) || !(nrm == nrm)) { c->flags |= FLAG_NAN; stop = true; c->j = j; }
+  else if (r == 0.0) { c->flags |= FLAG_BREAKDOWN; stop = true; c->j = j; }
+  else {
+    c->j = j + 1;
+    if (res <= c->cycle_tol || j + 1 >= c->m || c->its >= c->max_it || nrm == 0.0) stop = true;
+  }
+  c->scale = (nrm > 0.0) ? 1.0 / nrm : 0.0;
+  c->cyc_active = stop ? 0 : 1;
+  if (k.cond) cudaGraphSetConditional(k.cond, stop ? 0u : 1u);
+}
+
+// pass 1: h1 = V[0..j]^T w and ||w||^2 (w is stored as vector j+1 of the dots)
 __global__ void __launch_bounds__(kRedThreads) k_gs1(KrylovArgs k) {
+  __shared__ double ws[kChunk];
+  __shared__ double sm[32];
   const int cnt = k.ctl->j + 1;
-  const int r0 = blockIdx.x * k.chunk, r1 = min(k.n, r0 + k.chunk);
-  block_mdot(k.V, k.ld, cnt, k.w, r0, r1, k.part + (size_t)blockIdx.x * k.pstride);
-  if (last_block(&k.ctl->counter[0])) {
-    finalize_parts(k.part, k.pstride, cnt, k.h1);
-    if (threadIdx.x == 0) k.ctl->counter[0] = 0;
-  }
-}
-
-// CGS2 pass 2: w -= V h1; h2 = V^T w
-__global__ void __launch_bounds__(kRedThreads) k_gs2(KrylovArgs k) {
-  __shared__ double hs[256];
-  const int cnt = k.ctl->j + 1;
-  for (int i = threadIdx.x; i < cnt; i += blockDim.x) hs[i] = k.h1[i];
-  __syncthreads();
-  const int r0 = blockIdx.x * k.chunk, r1 = min(k.n, r0 + k.chunk);
+  const int r0 = blockIdx.x * kChunk, r1 = min(k.n, r0 + kChunk);
+  double acc = 0;
   for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
-    double v = k.w[r];
-    for (int i = 0; i < cnt; ++i) v -= k.V[(size_t)i * k.ld + r] * hs[i];
-    k.w[r] = v;
+    const double v = k.w[r];
+    ws[r - r0] = v;
+    acc += v * v;
   }
-  block_mdot(k.V, k.ld, cnt, k.w, r0, r1, k.part + (size_t)blockIdx.x * k.pstride);
-  if (last_block(&k.ctl->counter[1])) {
-    finalize_parts(k.part, k.pstride, cnt, k.h2);
-    if (threadIdx.x == 0) k.ctl->counter[1] = 0;
+  acc = block_sum(acc, sm);
+  if (threadIdx.x == 0) k.part[(size_t)cnt * gridDim.x + blockIdx.x] = acc;
+  __syncthreads();
+  mdot_warps(k.V, k.ld, cnt, ws, r0, r1 - r0, k.part, gridDim.x);
+  if (last_block(&k.ctl->counter[0])) {
+    finalize_warps(k.part, gridDim.x, cnt + 1, k.h1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      k.ctl->wnorm2 = k.h1[cnt];
+      k.ctl->counter[0] = 0;
+    }
   }
 }
 
-// CGS2 pass 3: w -= V h2; ||w||; Hessenberg column, Givens rotation,
-// residual estimate and the stop decision of the Arnoldi loop (on device).
-__global__ void __launch_bounds__(kRedThreads) k_gs3(KrylovArgs k) {
+// pass 2: w -= V h1 and ||w||^2; finish the step or ask for refinement
+__global__ void __launch_bounds__(kRedThreads) k_gs2(KrylovArgs k) {
   __shared__ double hs[256];
   __shared__ double sm[32];
   const int cnt = k.ctl->j + 1;
-  for (int i = threadIdx.x; i < cnt; i += blockDim.x) hs[i] = k.h2[i];
+  for (int i = threadIdx.x; i < cnt; i += blockDim.x) hs[i] = k.h1[i];
   __syncthreads();
-  const int r0 = blockIdx.x * k.chunk, r1 = min(k.n, r0 + k.chunk);
+  const int r0 = blockIdx.x * kChunk, r1 = min(k.n, r0 + kChunk);
   double acc = 0;
   for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
-    double v = k.w[r];
-    for (int i = 0; i < cnt; ++i) v -= k.V[(size_t)i * k.ld + r] * hs[i];
+    const double v = gs_update(k.V, k.ld, cnt, hs, k.w[r], r);
     k.w[r] = v;
     acc += v * v;
   }
   acc = block_sum(acc, sm);
-  if (threadIdx.x == 0) k.part[(size_t)blockIdx.x * k.pstride] = acc;
-  if (last_block(&k.ctl->counter[2])) {
-    double s2 = 0;
+  if (threadIdx.x == 0) k.part[blockIdx.x] = acc;
+  if (last_block(&k.ctl->counter[1])) {
+    double a = 0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) a += k.part[b];
+    const double s2 = block_sum(a, sm);
     if (threadIdx.x == 0) {
-      for (int b = 0; b < (int)gridDim.x; ++b) s2 += k.part[(size_t)b * k.pstride];
       Ctl* c = k.ctl;
-      c->counter[2] = 0;
-      const int j = c->j, m1 = c->m + 1;
-      double* Hc = k.H + (size_t)j * m1;
-      for (int i = 0; i <= j; ++i) Hc[i] = k.h1[i] + k.h2[i];
-      const double nrm = sqrt(s2);
-      Hc[j + 1] = nrm;
-      for (int i = 0; i < j; ++i) {
-        const double a = Hc[i], b = Hc[i + 1];
-        Hc[i] = k.cs[i] * a + k.sn[i] * b;
-        Hc[i + 1] = -k.sn[i] * a + k.cs[i] * b;
-      }
-      const double a = Hc[j], b = Hc[j + 1];
-      const double r = hypot(a, b);
-      const double cc = (r > 0) ? a / r : 1.0, ss = (r > 0) ? b / r : 0.0;
-      k.cs[j] = cc; k.sn[j] = ss;
-      Hc[j] = r; Hc[j + 1] = 0.0;
-      k.g[j + 1] = -ss * k.g[j];
-      k.g[j] = cc * k.g[j];
-      const double res = fabs(k.g[j + 1]);
-      c->its += 1;
-      c->res = res;
-      bool stop = false;
-      if (!(res == res) || !(nrm == nrm)) { c->flags |= FLAG_NAN; stop = true; c->j = j; }
-      else if (r == 0.0) { c->flags |= FLAG_BREAKDOWN; stop = true; c->j = j; }
-      else {
-        c->j = j + 1;
-        if (res <= c->cycle_tol || j + 1 >= c->m || c->its >= c->max_it || nrm == 0.0) stop = true;
-      }
-      c->scale = (nrm > 0.0) ? 1.0 / nrm : 0.0;
-      cudaGraphSetConditional(k.cond, stop ? 0u : 1u);
+      c->counter[1] = 0;
+      c->refine = (s2 < 0.5 * c->wnorm2) ? 1 : 0;
+      if (c->refine) c->refines += 1;
+      else arnoldi_finish(k, s2);
+    }
+  }
+}
+
+// pass 3 (refinement only): h2 = V^T w
+__global__ void __launch_bounds__(kRedThreads) k_gs3(KrylovArgs k) {
+  __shared__ double ws[kChunk];
+  if (!k.ctl->refine) return;
+  const int cnt = k.ctl->j + 1;
+  const int r0 = blockIdx.x * kChunk, r1 = min(k.n, r0 + kChunk);
+  for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) ws[r - r0] = k.w[r];
+  __syncthreads();
+  mdot_warps(k.V, k.ld, cnt, ws, r0, r1 - r0, k.part, gridDim.x);
+  if (last_block(&k.ctl->counter[2])) {
+    finalize_warps(k.part, gridDim.x, cnt, k.h2);
+    if (threadIdx.x == 0) k.ctl->counter[2] = 0;
+  }
+}
+
+// pass 4 (refinement only): w -= V h2, ||w||^2, finish the step
+__global__ void __launch_bounds__(kRedThreads) k_gs4(KrylovArgs k) {
+  __shared__ double hs[256];
+  __shared__ double sm[32];
+  if (!k.ctl->refine) return;
+  const int cnt = k.ctl->j + 1;
+  for (int i = threadIdx.x; i < cnt; i += blockDim.x) hs[i] = k.h2[i];
+  __syncthreads();
+  const int r0 = blockIdx.x * kChunk, r1 = min(k.n, r0 + kChunk);
+  double acc = 0;
+  for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+    const double v = gs_update(k.V, k.ld, cnt, hs, k.w[r], r);
+    k.w[r] = v;
+    acc += v * v;
+  }
+  acc = block_sum(acc, sm);
+  if (threadIdx.x == 0) k.part[blockIdx.x] = acc;
+  if (last_block(&k.ctl->counter[6])) {
+    double a = 0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) a += k.part[b];
+    const double s2 = block_sum(a, sm);
+    if (threadIdx.x == 0) {
+      k.ctl->counter[6] = 0;
+      arnoldi_finish(k, s2);
     }
   }
 }
@@ -505,11 +630,12 @@ __global__ void __launch_bounds__(kRedThreads) k_cycle_start(KrylovArgs k) {
   double acc = 0;
   for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) acc += k.w[r] * k.w[r];
   acc = block_sum(acc, sm);
-  if (threadIdx.x == 0) k.part[(size_t)blockIdx.x * k.pstride] = acc;
+  if (threadIdx.x == 0) k.part[blockIdx.x] = acc;
   if (last_block(&k.ctl->counter[3])) {
+    double a = 0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) a += k.part[b];
+    const double s2 = block_sum(a, sm);
     if (threadIdx.x == 0) {
-      double s2 = 0;
-      for (int b = 0; b < (int)gridDim.x; ++b) s2 += k.part[(size_t)b * k.pstride];
       Ctl* c = k.ctl;
       c->counter[3] = 0;
       const double beta = sqrt(s2);
@@ -526,7 +652,8 @@ __global__ void __launch_bounds__(kRedThreads) k_cycle_start(KrylovArgs k) {
       c->cycle_tol = fmax(c->inner_rtol * beta, c->target);
       c->scale = (beta > 0) ? 1.0 / beta : 0.0;
       c->res = beta;
-      cudaGraphSetConditional(k.cond, stop ? 0u : 1u);
+      c->cyc_active = stop ? 0 : 1;
+      if (k.cond) cudaGraphSetConditional(k.cond, stop ? 0u : 1u);
     }
   }
 }
@@ -545,17 +672,18 @@ __global__ void __launch_bounds__(kRedThreads) k_solve_begin(KrylovArgs k, const
   double acc = 0;
   for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) acc += b[r] * b[r];
   acc = block_sum(acc, sm);
-  if (threadIdx.x == 0) k.part[(size_t)blockIdx.x * k.pstride] = acc;
+  if (threadIdx.x == 0) k.part[blockIdx.x] = acc;
   if (last_block(&k.ctl->counter[4])) {
+    double a = 0;
+    for (int bb = threadIdx.x; bb < (int)gridDim.x; bb += blockDim.x) a += k.part[bb];
+    const double s2 = block_sum(a, sm);
     if (threadIdx.x == 0) {
-      double s2 = 0;
-      for (int bb = 0; bb < (int)gridDim.x; ++bb) s2 += k.part[(size_t)bb * k.pstride];
       Ctl* c = k.ctl;
       c->counter[4] = 0;
       c->bnorm = sqrt(s2);
       c->target = rtol * c->bnorm;
       c->inner_rtol = inner_rtol;
-      c->its = 0; c->cycles = 0; c->j = 0; c->flags = 0;
+      c->its = 0; c->cycles = 0; c->j = 0; c->flags = 0; c->refines = 0; c->refine = 0;
       c->converged = 0; c->stop = 0;
       c->max_it = max_it; c->m = m;
     }
@@ -623,12 +751,12 @@ __global__ void k_psub(int nP, double* __restrict__ p, const Ctl* ctl) {
 
 // ------------------------------------------------------------------ setup
 static void check_params(const fsi_params& p, int n_nodes, int n_tris) {
-  if (p.N < 2 || p.N > 4096) throw std::invalid_argument("N out of range");
+  if (p.N < 2 || p.N > 4096 || (p.N & 1)) throw std::invalid_argument("N must be even, 2..4096");
   int Nc = p.N;
   while (Nc % 2 == 0 && Nc > 4) Nc /= 2;
   if (Nc > 8) throw std::invalid_argument("N must be c * 2^k with c <= 8");
   if (!(p.dt > 0) || !(p.rho_f > 0) || !(p.nu > 0) || !(p.kappa >= 0)) throw std::invalid_argument("bad material");
-  if (p.precond != 0 && p.precond != 1) throw std::invalid_argument("precond");
+  if (p.precond < 0 || p.precond > 2) throw std::invalid_argument("precond");
   if (p.precision != 0 && p.precision != 1) throw std::invalid_argument("precision");
   if (n_nodes < 3 || n_tris < 1) throw std::invalid_argument("solid mesh");
 }
@@ -669,7 +797,7 @@ static FullOp<T> make_op(Problem& P, const T* cfv, const T* cftv) {
   Arena& ar = P.ar;
   FullOp<T> op;
   op.nU = P.nU; op.nP = P.nP; op.nS = P.nS;
-  op.gU = nblk(P.nU, 128); op.gP = nblk(P.nP, 128); op.gS = nblk(P.nS, 128);
+  op.gU = nblk(P.nU, 32); op.gP = nblk(P.nP, 32); op.gS = nblk(P.nS, 32);
   op.Af = upload_sell<T>(ar, to_sell(P.hs.levels[0].A));
   op.Bt = upload_sell<T>(ar, to_sell(P.hs.Bt));
   op.Bneg = upload_sell<T>(ar, to_sell(P.hs.Bneg));
@@ -683,14 +811,14 @@ static FullOp<T> make_op(Problem& P, const T* cfv, const T* cftv) {
 static KrylovArgs krylov_args(Problem& P, cudaGraphConditionalHandle h) {
   KrylovArgs k{};
   k.n = (int)P.n;
-  k.chunk = (int)((P.n + P.red_blocks - 1) / P.red_blocks);
+  k.chunk = kChunk;
   k.ld = P.n;
   k.V = P.V;
   k.w = P.w;
   k.part = P.part;
   k.pstride = P.m + 1;
-  k.h1 = P.y + (P.m + 1);       // scratch after y
-  k.h2 = P.y + 2 * (P.m + 1);
+  k.h1 = P.y + (P.m + 2);       // scratch after y (m+2 entries each)
+  k.h2 = P.y + 2 * (P.m + 2);
   k.H = P.H; k.cs = P.cs; k.sn = P.sn; k.g = P.g;
   k.ctl = P.ctl;
   k.cond = h;
@@ -728,6 +856,7 @@ static void iteration_launch(Problem& P, Prec<T>& pr, const KrylovArgs& k, cudaS
   k_gs1<<<P.red_blocks, kRedThreads, 0, s>>>(k);
   k_gs2<<<P.red_blocks, kRedThreads, 0, s>>>(k);
   k_gs3<<<P.red_blocks, kRedThreads, 0, s>>>(k);
+  k_gs4<<<P.red_blocks, kRedThreads, 0, s>>>(k);
   k_gs_scale<<<gn, 256, 0, s>>>((int)P.n, P.V, P.n, P.w, P.ctl);
 }
 
@@ -741,6 +870,20 @@ template <class T>
 static void cycle_end_launch(Problem& P, cudaStream_t s) {
   k_lsq<<<1, 32, 0, s>>>(P.H, P.g, P.y, P.ctl);
   k_xupdate<T><<<nblk(P.n, 256), 256, 0, s>>>((int)P.n, P.x, (const T*)P.Z, P.n, P.y, P.ctl);
+}
+
+static int count_kernel_nodes(cudaGraph_t g) {
+  size_t n = 0;
+  CK(cudaGraphGetNodes(g, nullptr, &n));
+  std::vector<cudaGraphNode_t> nodes(n);
+  CK(cudaGraphGetNodes(g, nodes.data(), &n));
+  int k = 0;
+  for (auto nd : nodes) {
+    cudaGraphNodeType t;
+    CK(cudaGraphNodeGetType(nd, &t));
+    if (t == cudaGraphNodeTypeKernel) ++k;
+  }
+  return k;
 }
 
 template <class T>
@@ -769,9 +912,29 @@ static void build_cycle_graph(Problem& P, Prec<T>& pr) {
   CK(cudaStreamBeginCaptureToGraph(P.s2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
   iteration_launch(P, pr, k, P.s2);
   CK(cudaStreamEndCapture(P.s2, &body));
+  P.kn_body = count_kernel_nodes(body);
   cycle_end_launch<T>(P, s);
   CK(cudaStreamEndCapture(s, &P.gr_cycle));
   CK(cudaGraphInstantiate(&P.g_cycle, P.gr_cycle, 0));
+}
+
+template <class T>
+static void build_host_loop_graphs(Problem& P, Prec<T>& pr) {
+  cudaStream_t s = P.stream;
+  KrylovArgs k = krylov_args(P, 0);
+  CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  cycle_start_launch(P, k, s);
+  CK(cudaStreamEndCapture(s, &P.gr_cstart));
+  CK(cudaGraphInstantiate(&P.g_cstart, P.gr_cstart, 0));
+  CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  iteration_launch(P, pr, k, s);
+  CK(cudaStreamEndCapture(s, &P.gr_body));
+  CK(cudaGraphInstantiate(&P.g_body, P.gr_body, 0));
+  CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  cycle_end_launch<T>(P, s);
+  CK(cudaStreamEndCapture(s, &P.gr_cend));
+  CK(cudaGraphInstantiate(&P.g_cend, P.gr_cend, 0));
+  P.kn_body = count_kernel_nodes(P.gr_body);
 }
 
 static void build_graphs(Problem& P) {
@@ -791,14 +954,26 @@ static void build_graphs(Problem& P) {
   CK(cudaStreamEndCapture(s, &P.gr_begin));
   CK(cudaGraphInstantiate(&P.g_begin, P.gr_begin, 0));
   // cycle
-  if (P.prm.precision == 1) build_cycle_graph<float>(P, P.p32);
-  else build_cycle_graph<double>(P, P.p64);
+  const char* hl = getenv("FSI_HOST_LOOP");
+  P.host_loop = hl && hl[0] == '1';
+  if (P.host_loop) {
+    if (P.prm.precision == 1) build_host_loop_graphs<float>(P, P.p32);
+    else build_host_loop_graphs<double>(P, P.p64);
+  } else {
+    if (P.prm.precision == 1) build_cycle_graph<float>(P, P.p32);
+    else build_cycle_graph<double>(P, P.p64);
+  }
   // finish: zero-mean pressure
   CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
   k_pmean<<<std::min(64, (int)nblk(P.nP, kRedThreads)), kRedThreads, 0, s>>>(P.nP, P.x + P.offP, P.part, P.ctl);
   k_psub<<<nblk(P.nP, 256), 256, 0, s>>>(P.nP, P.x + P.offP, P.ctl);
   CK(cudaStreamEndCapture(s, &P.gr_finish));
   CK(cudaGraphInstantiate(&P.g_finish, P.gr_finish, 0));
+  P.kn_assemble = count_kernel_nodes(P.gr_assemble);
+  P.kn_begin = count_kernel_nodes(P.gr_begin);
+  P.kn_cycle = P.host_loop ? count_kernel_nodes(P.gr_cstart) + count_kernel_nodes(P.gr_cend)
+                           : count_kernel_nodes(P.gr_cycle);
+  P.kn_finish = count_kernel_nodes(P.gr_finish);
 }
 
 static void allocate_problem(Problem& P, const double* ref_xy, const int* tris_h) {
@@ -843,9 +1018,9 @@ static void allocate_problem(Problem& P, const double* ref_xy, const int* tris_h
   P.cs = ar.alloc<double>(m + 1);
   P.sn = ar.alloc<double>(m + 1);
   P.g = ar.alloc<double>(m + 2);
-  P.y = ar.alloc<double>(3 * (size_t)(m + 1));
-  P.red_blocks = (int)std::max<size_t>(1, std::min<size_t>(kRedMax, (P.n + 4095) / 4096));
-  P.part = ar.alloc<double>((size_t)std::max(P.red_blocks, 64) * (m + 1));
+  P.y = ar.alloc<double>(3 * (size_t)(m + 2));
+  P.red_blocks = (int)((P.n + kChunk - 1) / kChunk);
+  P.part = ar.alloc<double>((size_t)std::max(P.red_blocks, 64) * (m + 2));
   P.ctl = ar.alloc<Ctl>(1);
   P.op64 = make_op<double>(P, P.cf_val, P.cft_val);
   build_prec<double>(P, P.p64, P.op64, true);
@@ -854,6 +1029,27 @@ static void allocate_problem(Problem& P, const double* ref_xy, const int* tris_h
     build_prec<float>(P, P.p32, P.op32, true);
   }
   (void)ref_xy;
+}
+
+
+// ----------------------------------------------------------- timing hook
+template <class T>
+static double sell_bytes(const HostBlockMatrix& A) {
+  return (double)A.nnzb() * (A.NV * sizeof(T) + sizeof(int)) + (double)A.nrows * sizeof(int);
+}
+
+template <class T>
+static double fullop_bytes(Problem& P, double cfnnz, size_t xbytes, size_t ybytes) {
+  const HostSetup& hs = P.hs;
+  double b = sell_bytes<T>(hs.levels[0].A) + sell_bytes<T>(hs.Bt) + sell_bytes<T>(hs.Bneg) + sell_bytes<T>(hs.Ssol);
+  b += 2.0 * cfnnz * (sizeof(T) + sizeof(int)) + (P.nU + 1) * 4.0 + P.nS * 4.0;
+  b += (double)P.n * (xbytes + ybytes);
+  return b;
+}
+
+__global__ void k_flush(size_t n, uint4* __restrict__ buf, unsigned v) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    buf[i] = make_uint4(v, v, v, v);
 }
 
 }  // namespace fsi
@@ -974,6 +1170,9 @@ int fsi_create_problem_budget(const fsi_params* params, const fsi_solid_mesh* me
       P.own_stream = true;
     }
     CK(cudaStreamCreateWithFlags(&P.s2, cudaStreamNonBlocking));
+    CK(cudaStreamCreateWithFlags(&P.s3, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&P.ev_fork, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&P.ev_join, cudaEventDisableTiming));
     P.N = prm.N;
     VNum vn(prm.N);
     P.nU = vn.n; P.nP = prm.N * prm.N; P.nS = mesh->n_nodes; P.nTri = mesh->n_tris; P.nPts = 6 * mesh->n_tris;
@@ -1046,7 +1245,19 @@ int fsi_solve_step(fsi_problem* h, fsi_solve_info* info) {
     const int max_cycles = (P.prm.precision == 1) ? P.prm.max_refine + 1 : 1000000;
     Ctl& c = *P.ctl_host;
     for (int cyc = 0; cyc < max_cycles; ++cyc) {
-      CK(cudaGraphLaunch(P.g_cycle, P.stream));
+      if (P.host_loop) {
+        CK(cudaGraphLaunch(P.g_cstart, P.stream));
+        CK(cudaMemcpyAsync(P.ctl_host, P.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, P.stream));
+        CK(cudaStreamSynchronize(P.stream));
+        while (c.cyc_active) {
+          CK(cudaGraphLaunch(P.g_body, P.stream));
+          CK(cudaMemcpyAsync(P.ctl_host, P.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, P.stream));
+          CK(cudaStreamSynchronize(P.stream));
+        }
+        CK(cudaGraphLaunch(P.g_cend, P.stream));
+      } else {
+        CK(cudaGraphLaunch(P.g_cycle, P.stream));
+      }
       CK(cudaMemcpyAsync(P.ctl_host, P.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, P.stream));
       CK(cudaStreamSynchronize(P.stream));
       if (c.stop || c.aflags) break;
@@ -1228,6 +1439,83 @@ int fsi_apply_preconditioner(fsi_problem* h, const double* vh, double* zh, int p
   }
 }
 
+int fsi_graph_kernel_counts(const fsi_problem* h, int* counts) {
+  if (!h || !counts) return FSI_ERR_INVALID;
+  const Problem& P = h->P;
+  counts[0] = P.kn_assemble; counts[1] = P.kn_begin; counts[2] = P.kn_cycle;
+  counts[3] = P.kn_body; counts[4] = P.kn_finish;
+  return FSI_OK;
+}
+
+int fsi_time_kernel(fsi_problem* h, int which, int reps, double* avg_ms, double* bytes) {
+  if (!h || !avg_ms || !bytes || reps <= 0) return FSI_ERR_INVALID;
+  Problem& P = h->P;
+  if ((which == 0 || which == 2) && P.prm.precision != 1) return FSI_ERR_INVALID;
+  try {
+    // total C_f entries of the last assembly
+    std::vector<int> len(P.nS);
+    CK(cudaMemcpy(len.data(), P.cf_len, (size_t)P.nS * 4, cudaMemcpyDeviceToHost));
+    double cfnnz = 0;
+    for (int v : len) cfnnz += v;
+    const size_t flush_n = (size_t)(256u << 20) / sizeof(uint4);
+    uint4* fl = nullptr;
+    CK(cudaMalloc(&fl, flush_n * sizeof(uint4)));
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    double total = 0;
+    cudaStream_t s = P.stream;
+    const HostBlockMatrix& A0 = P.hs.levels[0].A;
+    for (int r = 0; r < reps + 1; ++r) {
+      k_flush<<<2 * 152, 512, 0, s>>>(flush_n, fl, (unsigned)r);
+      CK(cudaEventRecord(e0, s));
+      switch (which) {
+        case 0:  // full operator, FP32 (mixed inner iteration)
+          k_fullmv<float, float, double><<<P.op32.gU + P.op32.gP + P.op32.gS, 128, 0, s>>>(P.op32, P.p32.zw, P.w,
+                                                                                          nullptr, 1.0, 0.0);
+          *bytes = fullop_bytes<float>(P, cfnnz, sizeof(float), sizeof(double));
+          break;
+        case 1:  // full operator, FP64 (residual / FP64 iteration)
+          k_fullmv<double, double, double><<<P.op64.gU + P.op64.gP + P.op64.gS, 128, 0, s>>>(P.op64, P.x, P.w, P.b,
+                                                                                            -1.0, 1.0);
+          *bytes = fullop_bytes<double>(P, cfnnz, 16, 8);
+          break;
+        case 2: {  // finest velocity Chebyshev step, FP32
+          MGLevel<float>& L = P.p32.mgU.lv[0];
+          SpmvArgs<float> a;
+          a.x = L.x; a.y = L.x2; a.z = L.b; a.d = L.d; a.dinv = L.dinv; a.c1 = 0.5f; a.c2 = 0.5f;
+          sell_launch(L.A, MODE_CHEB, a, s);
+          *bytes = sell_bytes<float>(A0) + 6.0 * L.n * sizeof(float);
+          break;
+        }
+        case 3: {  // finest velocity Chebyshev step, FP64
+          MGLevel<double>& L = P.p64.mgU.lv[0];
+          SpmvArgs<double> a;
+          a.x = L.x; a.y = L.x2; a.z = L.b; a.d = L.d; a.dinv = L.dinv; a.c1 = 0.5; a.c2 = 0.5;
+          sell_launch(L.A, MODE_CHEB, a, s);
+          *bytes = sell_bytes<double>(A0) + 6.0 * L.n * sizeof(double);
+          break;
+        }
+        default:
+          cudaFree(fl);
+          return FSI_ERR_INVALID;
+      }
+      CK(cudaEventRecord(e1, s));
+      CK(cudaEventSynchronize(e1));
+      float ms = 0;
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+      if (r > 0) total += ms;  // first launch is a warm-up
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(fl);
+    *avg_ms = total / reps;
+    return FSI_OK;
+  } catch (...) {
+    return map_exception();
+  }
+}
+
 int fsi_interior_nodes(const fsi_problem* h, int* lattice_ids) {
   if (!h || !lattice_ids) return FSI_ERR_INVALID;
   std::copy(h->P.hs.interior_lattice.begin(), h->P.hs.interior_lattice.end(), lattice_ids);
@@ -1249,14 +1537,17 @@ int fsi_get_rhs(fsi_problem* h, double* bh) {
 void fsi_destroy(fsi_problem* h) {
   if (!h) return;
   Problem& P = h->P;
-  cudaGraphExec_t ex[4] = {P.g_assemble, P.g_begin, P.g_cycle, P.g_finish};
-  cudaGraph_t gr[4] = {P.gr_assemble, P.gr_begin, P.gr_cycle, P.gr_finish};
+  cudaGraphExec_t ex[7] = {P.g_assemble, P.g_begin, P.g_cycle, P.g_finish, P.g_cstart, P.g_body, P.g_cend};
+  cudaGraph_t gr[7] = {P.gr_assemble, P.gr_begin, P.gr_cycle, P.gr_finish, P.gr_cstart, P.gr_body, P.gr_cend};
   if (P.stream) cudaStreamSynchronize(P.stream);
   for (auto e : ex) if (e) cudaGraphExecDestroy(e);
   for (auto g : gr) if (g) cudaGraphDestroy(g);
   P.ar.release();
   if (P.ctl_host) cudaFreeHost(P.ctl_host);
   if (P.s2) cudaStreamDestroy(P.s2);
+  if (P.s3) cudaStreamDestroy(P.s3);
+  if (P.ev_fork) cudaEventDestroy(P.ev_fork);
+  if (P.ev_join) cudaEventDestroy(P.ev_join);
   if (P.own_stream && P.stream) cudaStreamDestroy(P.stream);
   delete h;
 }

@@ -65,6 +65,8 @@ EXPORTS = {
     "fsi_apply_preconditioner": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "fsi_interior_nodes": (C.c_int, [C.c_void_p, C.c_void_p]),
     "fsi_get_rhs": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "fsi_graph_kernel_counts": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "fsi_time_kernel": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "fsi_destroy": (None, [C.c_void_p]),
     "fsi_status_str": (C.c_char_p, [C.c_int]),
 }
@@ -239,6 +241,19 @@ class Problem:
         ids = np.empty(self.n_u // 2, dtype=np.int32)
         self._check(load_library().fsi_interior_nodes(self._h, _ptr(ids)), "fsi_interior_nodes")
         return ids
+
+    def graph_kernel_counts(self):
+        c = np.zeros(5, dtype=np.int32)
+        self._check(load_library().fsi_graph_kernel_counts(self._h, _ptr(c)), "fsi_graph_kernel_counts")
+        return c
+
+    def time_kernel(self, which: int, reps: int = 20):
+        """(mean launch ms, algorithmic bytes per launch) of one kernel."""
+        ms = C.c_double()
+        by = C.c_double()
+        self._check(load_library().fsi_time_kernel(self._h, int(which), int(reps), C.byref(ms), C.byref(by)),
+                    "fsi_time_kernel")
+        return ms.value, by.value
 
     def get_rhs(self):
         b = np.empty(self.n)
