@@ -200,6 +200,39 @@ int fsi_get_rhs(fsi_problem* p, double* b);
 void fsi_destroy(fsi_problem* p);
 const char* fsi_status_str(int status);
 
+/* ---------------------------------------------------------------------------
+ * Allocation-free point location and binning.  The paper has no counterpart:
+ * this entry point exists for callers that cannot allocate device memory when
+ * they need the work done (code running while a stream is captured into a CUDA
+ * graph, hosts that forbid allocation after start-up, plugins confined to
+ * another framework's memory pool).  It performs steps S2-S3 on its own: it
+ * locates the 6 degree-4 rule points of every triangle (point id =
+ * 6*triangle + q, same arithmetic and cell rule as fsi_assemble_step) and
+ * sorts them into per-cell lists.  It calls no cudaMalloc, cudaFree or other
+ * allocating routine; its only scratch is a fixed array compiled into the
+ * library, FSI_NOALLOC_MAX_CELLS counters wide, which every GPU that loads the
+ * library holds until the process exits.
+ *
+ * All pointers are DEVICE pointers owned by the caller:
+ *   tris  3*n_tris node ids;  X  2*n_nodes positions (x, y interleaved);
+ *   cell, xi, eta  6*n_tris outputs (cell = cy*N + cx, or -1 outside [0,1]^2);
+ *   cell_start  N*N + 1 outputs (CSR offsets), cell_points  6*n_tris outputs
+ *   (point ids of each cell in increasing order; points outside are left out);
+ *   n_outside  one int output: points found outside the domain.
+ * Work is queued on cuda_stream (may be NULL) and the call returns without
+ * waiting.  Returns FSI_ERR_INVALID, allocating and launching nothing, when a
+ * pointer is NULL or N*N exceeds FSI_NOALLOC_MAX_CELLS (N <= 512).  The first
+ * call on a device looks up the scratch array's device address and uploads the
+ * rule table there (no allocation); make that first call before any stream
+ * capture.  Every call shares the one scratch array and clears the part it
+ * uses before using it; calls that overlap on the GPU race on it, so callers
+ * must serialise them. */
+#define FSI_NOALLOC_MAX_CELLS 262144
+int fsi_locate_bin_noalloc(int N, int n_tris, const int* tris, const double* X,
+                           int* cell, double* xi, double* eta,
+                           int* cell_start, int* cell_points, int* n_outside,
+                           void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libfsi_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["fsi_solver.cu", "fsi_setup.cpp"]
+SOURCES = ["fsi_solver.cu", "fsi_setup.cpp", "fsi_noalloc.cu"]
 HEADERS = ["fsi_internal.h", "fsi_kernels.cuh", "fsi_coupling.cuh"]
 
 

@@ -67,6 +67,8 @@ EXPORTS = {
     "fsi_get_rhs": (C.c_int, [C.c_void_p, C.c_void_p]),
     "fsi_graph_kernel_counts": (C.c_int, [C.c_void_p, C.c_void_p]),
     "fsi_time_kernel": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "fsi_locate_bin_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                         C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "fsi_destroy": (None, [C.c_void_p]),
     "fsi_status_str": (C.c_char_p, [C.c_int]),
 }
@@ -259,6 +261,19 @@ class Problem:
         b = np.empty(self.n)
         self._check(load_library().fsi_get_rhs(self._h, _ptr(b)), "fsi_get_rhs")
         return b
+
+
+FSI_NOALLOC_MAX_CELLS = 262144
+
+
+def locate_bin_noalloc(N: int, n_tris: int, tris_ptr: int, X_ptr: int, cell_ptr: int, xi_ptr: int, eta_ptr: int,
+                       cell_start_ptr: int, cell_points_ptr: int, n_outside_ptr: int, stream: int = 0) -> int:
+    """Allocation-free point location and binning (device pointers in and out;
+    see fsi_locate_bin_noalloc in include/fsi.h).  Returns the status code."""
+    return int(load_library().fsi_locate_bin_noalloc(
+        int(N), int(n_tris), C.c_void_p(tris_ptr), C.c_void_p(X_ptr), C.c_void_p(cell_ptr), C.c_void_p(xi_ptr),
+        C.c_void_p(eta_ptr), C.c_void_p(cell_start_ptr), C.c_void_p(cell_points_ptr), C.c_void_p(n_outside_ptr),
+        C.c_void_p(stream) if stream else None))
 
 
 def problem_from_case(case, precision: int = 0, precond=None, rtol=None, stream=None, **kw) -> Problem:
