@@ -75,7 +75,9 @@ typedef struct fsi_params {
     double lid_u;      /* tangential velocity of the top wall, 0 = all walls at rest */
     int    precond;    /* 0 block-diagonal, 1 block lower-triangular (the two
                           preconditioners of Section 5), 2 block upper-triangular
-                          [[A11, A12], [0, A22]] (solid block first) */
+                          [[A11, A12], [0, A22]] (solid block first), 3 as 2 with
+                          the velocity and pressure parts of A11^-1 applied
+                          side by side (block-diagonal Stokes approximation) */
     int    precision;  /* 0 FP64 everywhere; 1 FP32 operators and preconditioner
                           inside FGMRES, FP64 Gram-Schmidt, least squares and
                           iterative refinement */
@@ -86,6 +88,10 @@ typedef struct fsi_params {
     int    cs_degree;  /* Chebyshev iterations per solid mass solve; 0 = 16 */
     double inner_rtol; /* precision 1: inner FGMRES tolerance; 0 = 1e-5 */
     int    max_refine; /* precision 1: refinement steps cap; 0 = 30 */
+    int    stokes_its; /* Richardson steps on the fluid (Stokes) block inside one
+                          preconditioner application, each one V-cycle pair;
+                          0 = 1 (the one-shot approximation) */
+    double stokes_omega; /* damping of the Richardson corrections after the first; 0 = 1 */
 } fsi_params;
 
 /* Solid reference mesh (the body at t = 0, P1 triangles, counter-clockwise). */

@@ -291,6 +291,47 @@ __global__ void __launch_bounds__(128) k_fullmv(FullOp<TA> op, const TX* __restr
   }
 }
 
+// Residual of the fluid (Stokes) block A_11 = [[A_f, -B^T], [-B, 0]]:
+// t_u = r_u - (A_f z_u - B^T z_p), t_p = r_p + B z_u.  Vectors hold
+// [u (2 nU) | p (3 nP)] at offset 0; same CTA layout as k_fullmv's first two
+// segments.
+template <class T>
+__global__ void __launch_bounds__(128) k_stokes_res(FullOp<T> op, const T* __restrict__ z, const T* __restrict__ ru,
+                                                    const T* __restrict__ rp, T* __restrict__ t) {
+  const int lane = threadIdx.x & 31, tt = lane >> 3;
+  const int b = blockIdx.x;
+  const int wrow = (threadIdx.x >> 5) * kSliceRows + (lane & 7);
+  const size_t offP = 2 * (size_t)op.nU;
+  if (b < op.gU) {
+    const int r = b * 32 + wrow;
+    const bool live = r < op.nU;
+    T a[2] = {0, 0};
+    if (live) {
+      sell_row<T, T, 2, 2, false, 4>(op.Af, r, tt, z, a);
+      sell_row<T, T, 2, 3, false, 6>(op.Bt, r, tt, z + offP, a);
+    }
+    row_reduce<T, 2>(a);
+    if (!live || tt != 0) return;
+    t[2 * r] = ru[2 * r] - a[0];
+    t[2 * r + 1] = ru[2 * r + 1] - a[1];
+  } else {
+    const int r = (b - op.gU) * 32 + wrow;
+    const bool live = r < op.nP;
+    T a[3] = {0, 0, 0};
+    if (live) sell_row<T, T, 3, 2, false, 6>(op.Bneg, r, tt, z, a);
+    row_reduce<T, 3>(a);
+    if (!live || tt != 0) return;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) t[offP + 3 * r + i] = rp[3 * r + i] - a[i];
+  }
+}
+
+template <class T>
+__global__ void k_axpy(size_t n, T a, const T* __restrict__ x, T* __restrict__ y) {
+  const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i < n) y[i] += a * x[i];
+}
+
 // C_f (ELL over solid nodes, kron 2) times a velocity vector:
 // y = alpha C_f u + beta z on 2 nS entries; MODE_INIT also sets d = xo = c2 dinv y.
 template <class T>

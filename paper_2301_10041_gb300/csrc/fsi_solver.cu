@@ -236,6 +236,11 @@ struct Prec {
   T *sb = nullptr, *sx = nullptr, *sx2 = nullptr, *sd = nullptr;  // solid work (2 nS)
   Cheb chs;              // Chebyshev on [1/2, 2] for D^-1 C_s (Wathen's bounds for P1)
   int cs_k = 16;
+  // inner Richardson on the Stokes block: velocity right-hand side, residual
+  // and correction, each [u (2 nU) | p (3 nP)]
+  T *ru = nullptr, *t = nullptr, *dz = nullptr;
+  int stokes_its = 1;
+  T stokes_omega = 1;
 };
 
 struct Problem;
@@ -246,8 +251,8 @@ struct Problem {
   fsi_params prm{};
   int N = 0, nU = 0, nP = 0, nS = 0, nTri = 0, nPts = 0;
   size_t n = 0, offP = 0, offX = 0, offL = 0;
-  cudaStream_t stream = nullptr, s2 = nullptr, s3 = nullptr;  // s3: parallel branch of the preconditioner
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaStream_t stream = nullptr, s2 = nullptr, s3 = nullptr, s4 = nullptr;  // s3, s4: parallel branches
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_fork2 = nullptr, ev_join2 = nullptr;
   bool own_stream = false;
   int device = 0;
   Arena ar;
@@ -365,39 +370,81 @@ __global__ void k_cft_sub(int nU, const int* __restrict__ ptr, const int* __rest
 //   precond 1: [[A_11, 0], [A_21, A_22]]             (block lower-triangular)
 //   precond 2: [[A_11, A_12], [0, A_22]]             (block upper-triangular:
 //              the solid block first, then the fluid with v_u - C_f^T z_l)
+// One application of the upper block-triangular Stokes approximation
+// [[A_f, -B^T], [0, -S]]^-1 to (in_u, in_p): p = -S^-1 in_p with the
+// Cahouet-Chabard Schur approximation S^-1 ~ nu M_p^-1 + (rho/dt) L_p^-1
+// (one V-cycle on the pressure Laplacian L_p = B diag(M_f)^-1 B^T), then
+// u = A_f^-1 (in_u + B^T p) by one V-cycle with Chebyshev-Jacobi smoothing on
+// the Q2 hierarchy.  With split = true the pressure part runs on stream s4
+// beside the velocity part and the B^T p term is dropped (block-diagonal).
+template <class T>
+static void stokes_apply(Problem& P, Prec<T>& pr, const T* in_u, const T* in_p, T* out_u, T* out_p, cudaStream_t s,
+                         bool split) {
+  const int n3 = 3 * P.nP;
+  MGLevel<T>& L0p = pr.mgP.lv[0];
+  MGLevel<T>& L0u = pr.mgU.lv[0];
+  cudaStream_t sp_stream = split ? P.s4 : s;
+  if (split) {
+    CK(cudaEventRecord(P.ev_fork2, s));
+    CK(cudaStreamWaitEvent(P.s4, P.ev_fork2, 0));
+  }
+  k_cheb_first<T><<<nblk(n3, 256), 256, 0, sp_stream>>>(n3, in_p, L0p.dinv, (T)L0p.ch.c0, L0p.d, L0p.x, (T)1, L0p.b);
+  T* sp = vcycle<T>(pr.mgP, 0, sp_stream, (T*)nullptr);
+  k_schur<T><<<nblk(n3, 256), 256, 0, sp_stream>>>(n3, in_p, sp, pr.mpinv, (T)P.prm.nu, (T)(P.prm.rho_f / P.prm.dt),
+                                                   out_p);
+  if (split) {
+    CK(cudaEventRecord(P.ev_join2, P.s4));
+    const int n2 = 2 * P.nU;
+    k_cheb_first<T><<<nblk(n2, 256), 256, 0, s>>>(n2, in_u, L0u.dinv, (T)L0u.ch.c0, L0u.d, L0u.x, (T)1, L0u.b);
+  } else {
+    SpmvArgs<T> a;
+    a.x = out_p; a.y = L0u.b; a.z = in_u; a.alpha = -1; a.beta = 1;
+    a.d = L0u.d; a.dinv = L0u.dinv; a.xo = L0u.x; a.c2 = (T)L0u.ch.c0;
+    sell_launch(pr.op.Bt, MODE_INIT, a, s);
+  }
+  vcycle(pr.mgU, 0, s, out_u);
+  if (split) CK(cudaStreamWaitEvent(s, P.ev_join2, 0));
+}
+
+// One application z = P^-1 v of the block preconditioner (Section 5), input
+// pr.vin, output pr.zw.
+//   precond 0: diag(A_11, A_22)                      (block-diagonal)
+//   precond 1: [[A_11, 0], [A_21, A_22]]             (block lower-triangular)
+//   precond 2: [[A_11, A_12], [0, A_22]]             (block upper-triangular:
+//              the solid block first, then the fluid with v_u - C_f^T z_l)
+//   precond 3: as 2, velocity and pressure parts of A_11^-1 side by side.
+// A_11^-1 is stokes_its steps of Richardson on the Stokes block, each step one
+// application of stokes_apply (one step = the plain one-shot approximation).
 template <class T>
 static void precond_launch(Problem& P, Prec<T>& pr, cudaStream_t s) {
-  const int n3 = 3 * P.nP;
+  const int pc = P.prm.precond;
   T* vp = pr.vin + P.offP;
   T* zp = pr.zw + P.offP;
-  // the solid block does not depend on the fluid for precond 0 and 2: run it
-  // on a parallel branch (its kernels are small and latency-bound)
-  const bool fork = P.prm.precond != 1;
-  if (fork) {
+  const bool split = (pc == 3);
+  // the solid block does not depend on the fluid for precond 0, 2 and 3: run
+  // it on a parallel branch (its kernels are small and latency-bound)
+  if (pc != 1) {
     CK(cudaEventRecord(P.ev_fork, s));
     CK(cudaStreamWaitEvent(P.s3, P.ev_fork, 0));
     solid_launch(P, pr, P.s3);
     CK(cudaEventRecord(P.ev_join, P.s3));
   }
-  MGLevel<T>& L0p = pr.mgP.lv[0];
-  k_cheb_first<T><<<nblk(n3, 256), 256, 0, s>>>(n3, vp, L0p.dinv, (T)L0p.ch.c0, L0p.d, L0p.x, (T)1, L0p.b);
-  T* sp = vcycle<T>(pr.mgP, 0, s, (T*)nullptr);
-  k_schur<T><<<nblk(n3, 256), 256, 0, s>>>(n3, vp, sp, pr.mpinv, (T)P.prm.nu, (T)(P.prm.rho_f / P.prm.dt), zp);
-  MGLevel<T>& L0u = pr.mgU.lv[0];
   const T* vu = pr.vin;
-  if (P.prm.precond == 2) {
+  if (pc == 2 || pc == 3) {
     CK(cudaStreamWaitEvent(s, P.ev_join, 0));
     k_cft_sub<T><<<nblk(P.nU, 128), 128, 0, s>>>(P.nU, P.cft_ptr, P.cft_col, pr.op.cft_val, pr.zw + P.offL, pr.vin,
-                                                  L0u.r);
-    vu = L0u.r;
+                                                  pr.ru);
+    vu = pr.ru;
   }
-  SpmvArgs<T> a;
-  a.x = zp; a.y = L0u.b; a.z = vu; a.alpha = -1; a.beta = 1;
-  a.d = L0u.d; a.dinv = L0u.dinv; a.xo = L0u.x; a.c2 = (T)L0u.ch.c0;
-  sell_launch(pr.op.Bt, MODE_INIT, a, s);
-  vcycle(pr.mgU, 0, s, pr.zw);
-  if (P.prm.precond == 1) solid_launch(P, pr, s);
-  if (P.prm.precond == 0) CK(cudaStreamWaitEvent(s, P.ev_join, 0));
+  stokes_apply(P, pr, vu, vp, pr.zw, zp, s, split);
+  const size_t nf = 2 * (size_t)P.nU + 3 * (size_t)P.nP;
+  for (int it = 1; it < pr.stokes_its; ++it) {
+    k_stokes_res<T><<<pr.op.gU + pr.op.gP, 128, 0, s>>>(pr.op, pr.zw, vu, vp, pr.t);
+    stokes_apply(P, pr, pr.t, pr.t + P.offP, pr.dz, pr.dz + P.offP, s, split);
+    k_axpy<T><<<nblk(nf, 256), 256, 0, s>>>(nf, pr.stokes_omega, pr.dz, pr.zw);
+  }
+  if (pc == 1) solid_launch(P, pr, s);
+  if (pc == 0) CK(cudaStreamWaitEvent(s, P.ev_join, 0));
 }
 
 // --------------------------------------------------------- Krylov kernels
@@ -756,7 +803,7 @@ static void check_params(const fsi_params& p, int n_nodes, int n_tris) {
   while (Nc % 2 == 0 && Nc > 4) Nc /= 2;
   if (Nc > 8) throw std::invalid_argument("N must be c * 2^k with c <= 8");
   if (!(p.dt > 0) || !(p.rho_f > 0) || !(p.nu > 0) || !(p.kappa >= 0)) throw std::invalid_argument("bad material");
-  if (p.precond < 0 || p.precond > 2) throw std::invalid_argument("precond");
+  if (p.precond < 0 || p.precond > 3) throw std::invalid_argument("precond");
   if (p.precision != 0 && p.precision != 1) throw std::invalid_argument("precision");
   if (n_nodes < 3 || n_tris < 1) throw std::invalid_argument("solid mesh");
 }
@@ -770,6 +817,9 @@ static fsi_params with_defaults(fsi_params p) {
   if (p.cs_degree <= 0) p.cs_degree = (p.precision == 1) ? 12 : 16;
   if (!(p.inner_rtol > 0)) p.inner_rtol = 1e-5;
   if (p.max_refine <= 0) p.max_refine = 30;
+  if (p.stokes_its <= 0) p.stokes_its = 1;
+  if (p.stokes_its > 16) p.stokes_its = 16;
+  if (!(p.stokes_omega > 0)) p.stokes_omega = 1.0;
   return p;
 }
 
@@ -790,6 +840,12 @@ static void build_prec(Problem& P, Prec<T>& pr, const FullOp<T>& op, bool alloc_
   pr.sb = ar.alloc<T>(n2); pr.sx = ar.alloc<T>(n2); pr.sx2 = ar.alloc<T>(n2); pr.sd = ar.alloc<T>(n2);
   pr.cs_k = P.prm.cs_degree;
   pr.chs = cheb_coeffs(0.5, 2.0, pr.cs_k);
+  const size_t nf = 2 * (size_t)P.nU + 3 * (size_t)P.nP;
+  pr.ru = ar.alloc<T>(2 * (size_t)P.nU);
+  pr.t = ar.alloc<T>(nf);
+  pr.dz = ar.alloc<T>(nf);
+  pr.stokes_its = P.prm.stokes_its;
+  pr.stokes_omega = (T)P.prm.stokes_omega;
 }
 
 template <class T>
@@ -1171,6 +1227,9 @@ int fsi_create_problem_budget(const fsi_params* params, const fsi_solid_mesh* me
     }
     CK(cudaStreamCreateWithFlags(&P.s2, cudaStreamNonBlocking));
     CK(cudaStreamCreateWithFlags(&P.s3, cudaStreamNonBlocking));
+    CK(cudaStreamCreateWithFlags(&P.s4, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&P.ev_join2, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&P.ev_fork2, cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&P.ev_fork, cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&P.ev_join, cudaEventDisableTiming));
     P.N = prm.N;
@@ -1546,6 +1605,9 @@ void fsi_destroy(fsi_problem* h) {
   if (P.ctl_host) cudaFreeHost(P.ctl_host);
   if (P.s2) cudaStreamDestroy(P.s2);
   if (P.s3) cudaStreamDestroy(P.s3);
+  if (P.s4) cudaStreamDestroy(P.s4);
+  if (P.ev_join2) cudaEventDestroy(P.ev_join2);
+  if (P.ev_fork2) cudaEventDestroy(P.ev_fork2);
   if (P.ev_fork) cudaEventDestroy(P.ev_fork);
   if (P.ev_join) cudaEventDestroy(P.ev_join);
   if (P.own_stream && P.stream) cudaStreamDestroy(P.stream);
