@@ -147,6 +147,14 @@ int fsi_advance(fsi_problem* p);
 /* assemble + solve + advance. */
 int fsi_step(fsi_problem* p, fsi_solve_info* info);
 
+/* Batched step of several instances: queues assemble + solve + advance of
+ * every problem on its own stream (the library-owned streams of problems
+ * created with NULL run concurrently on the device), then waits for all of
+ * them.  infos (may be NULL) receives one report per problem.  Returns FSI_OK
+ * or the first failing status.  Problems built with FSI_HOST_LOOP=1 are
+ * rejected (FSI_ERR_INVALID). */
+int fsi_step_batch(fsi_problem* const* problems, int count, fsi_solve_info* infos);
+
 /* Host copies of the current solution; any pointer may be NULL.
  * u: 2*(2N+1)^2 (wall values included), pr: 3*N^2, X and lam: 2*n_nodes. */
 int fsi_get_state(fsi_problem* p, double* u, double* pr, double* X, double* lam);

@@ -15,6 +15,7 @@ __constant__ double c_rule_w[6];       // weights, summing to 1
 __global__ void k_locate(int n_pts, int N, const int* __restrict__ tris, const double* __restrict__ X,
                          int* __restrict__ cell, double* __restrict__ xi, double* __restrict__ eta,
                          int* __restrict__ flags) {
+  pdl_begin();
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n_pts) return;
   const int t = p / 6, q = p - 6 * (p / 6);
@@ -62,6 +63,7 @@ __global__ void __launch_bounds__(32 * kCfWarps) k_cf_rows(
     const int* __restrict__ l2n, const double* __restrict__ wall, int cap, int* __restrict__ len,
     int* __restrict__ col, double* __restrict__ val, float* __restrict__ val32, double* __restrict__ lift,
     int* __restrict__ flags) {
+  pdl_begin();
   __shared__ double win[kCfWarps][kCfWindow];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int l = blockIdx.x * kCfWarps + warp;
@@ -155,6 +157,7 @@ __global__ void __launch_bounds__(32 * kCfWarps) k_cf_rows(
 // S3 (the "hash grid"): counting sort of the C_f entries by fluid node.
 __global__ void k_cft_count(int nS, int cap, const int* __restrict__ len, const int* __restrict__ col,
                             int* __restrict__ cnt) {
+  pdl_begin();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int l = i / cap, k = i - cap * (i / cap);
   if (l >= nS || k >= len[l]) return;
@@ -165,6 +168,7 @@ constexpr int kScanBlock = 1024;
 
 // exclusive scan of cnt[0..n) into out[0..n], three phases
 __global__ void k_scan_partial(int n, const int* __restrict__ in, int* __restrict__ bsum) {
+  pdl_begin();
   __shared__ int sm[32];
   const int i = blockIdx.x * kScanBlock + threadIdx.x;
   int v = (i < n) ? in[i] : 0;
@@ -208,6 +212,7 @@ __device__ __forceinline__ int block_excl_scan(int v, int* sm, int& total) {
 }
 
 __global__ void k_scan_top(int nb, int* __restrict__ bsum) {
+  pdl_begin();
   __shared__ int sm[32];
   int carry = 0;
   for (int b0 = 0; b0 < nb; b0 += kScanBlock) {
@@ -222,6 +227,7 @@ __global__ void k_scan_top(int nb, int* __restrict__ bsum) {
 
 __global__ void k_scan_final(int n, const int* __restrict__ in, const int* __restrict__ bsum,
                              int* __restrict__ out, int* __restrict__ cursor) {
+  pdl_begin();
   __shared__ int sm[32];
   const int i = blockIdx.x * kScanBlock + threadIdx.x;
   const int v = (i < n) ? in[i] : 0;
@@ -234,6 +240,7 @@ __global__ void k_scan_final(int n, const int* __restrict__ in, const int* __res
 __global__ void k_cft_scatter(int nS, int cap, const int* __restrict__ len, const int* __restrict__ col,
                               const double* __restrict__ val, int* __restrict__ cursor, int* __restrict__ tcol,
                               double* __restrict__ tval) {
+  pdl_begin();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int l = i / cap, k = i - cap * (i / cap);
   if (l >= nS || k >= len[l]) return;
@@ -246,6 +253,7 @@ __global__ void k_cft_scatter(int nS, int cap, const int* __restrict__ len, cons
 // sort each transposed row by solid node (the scatter order is not fixed)
 __global__ void k_cft_sort(int nU, const int* __restrict__ ptr, int* __restrict__ tcol, double* __restrict__ tval,
                            float* __restrict__ tval32) {
+  pdl_begin();
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= nU) return;
   const int a = ptr[r], b = ptr[r + 1];

@@ -8,6 +8,16 @@
 
 namespace fsi {
 
+// Programmatic dependent launch: kernels are launched so that the next one
+// may be scheduled while the previous one finishes.  Every kernel first lets
+// its dependents launch, then waits until all the grids it depends on have
+// completed and their writes are visible, before it reads anything.  Launched
+// without the attribute, both instructions are no-ops.
+__device__ __forceinline__ void pdl_begin() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 // device error flags (OR-ed into Ctl::flags)
 enum : int {
   FLAG_OUT_OF_DOMAIN = 1,
@@ -39,6 +49,7 @@ struct Ctl {
   int aflags;       // FLAG_* bits raised by the assembly (S2-S4)
   int cyc_active;   // 1 while the Arnoldi loop of the current cycle continues
   int refine;       // 1 when the current Gram-Schmidt step needs a second pass
+  int max_cycles;   // cap on restart / refinement cycles of one solve
   int refines;      // second passes taken in this solve
   double wnorm2;    // ||w||^2 before orthogonalisation
   unsigned int counter[8];  // last-block counters for reductions
@@ -149,6 +160,7 @@ __device__ __forceinline__ void row_reduce(T* acc) {
 
 template <class T, int BR, int BC, bool KRON, int NV, int MODE>
 __global__ void __launch_bounds__(128) k_sell(Sell<T> A, SpmvArgs<T> a) {
+  pdl_begin();
   const int lane = threadIdx.x & 31;
   const int row = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * kSliceRows + (lane & 7);
   const int t = lane >> 3;
@@ -210,6 +222,7 @@ struct FullOp {
 template <class TA, class TX, class TY>
 __global__ void __launch_bounds__(128) k_fullmv(FullOp<TA> op, const TX* __restrict__ x, TY* __restrict__ y,
                                                 const TY* __restrict__ z, TY alpha, TY beta) {
+  pdl_begin();
   const int lane = threadIdx.x & 31, t = lane >> 3;
   const int b = blockIdx.x;
   const int wrow = (threadIdx.x >> 5) * kSliceRows + (lane & 7);
@@ -298,6 +311,7 @@ __global__ void __launch_bounds__(128) k_fullmv(FullOp<TA> op, const TX* __restr
 template <class T>
 __global__ void __launch_bounds__(128) k_stokes_res(FullOp<T> op, const T* __restrict__ z, const T* __restrict__ ru,
                                                     const T* __restrict__ rp, T* __restrict__ t) {
+  pdl_begin();
   const int lane = threadIdx.x & 31, tt = lane >> 3;
   const int b = blockIdx.x;
   const int wrow = (threadIdx.x >> 5) * kSliceRows + (lane & 7);
@@ -328,6 +342,7 @@ __global__ void __launch_bounds__(128) k_stokes_res(FullOp<T> op, const T* __res
 
 template <class T>
 __global__ void k_axpy(size_t n, T a, const T* __restrict__ x, T* __restrict__ y) {
+  pdl_begin();
   const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (i < n) y[i] += a * x[i];
 }
@@ -337,6 +352,7 @@ __global__ void k_axpy(size_t n, T a, const T* __restrict__ x, T* __restrict__ y
 template <class T>
 __global__ void k_cf_apply(int nS, int cap, const int* __restrict__ len, const int* __restrict__ col,
                            const T* __restrict__ val, SpmvArgs<T> a, int mode) {
+  pdl_begin();
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= nS) return;
   const size_t cbase = (size_t)(r >> 5) * 32 * cap + (r & 31);
@@ -364,6 +380,7 @@ __global__ void k_cf_apply(int nS, int cap, const int* __restrict__ len, const i
 // one warp per row, lanes over the columns, 8 rows per CTA
 template <class T>
 __global__ void k_dense_mv(int n, const T* __restrict__ A, const T* __restrict__ x, T* __restrict__ y) {
+  pdl_begin();
   const int lane = threadIdx.x & 31;
   const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (i >= n) return;
@@ -382,6 +399,7 @@ __global__ void k_dense_mv(int n, const T* __restrict__ A, const T* __restrict__
 template <class T>
 __global__ void k_cheb_first(int n, const T* __restrict__ b, const T* __restrict__ dinv, T c, T* __restrict__ d,
                              T* __restrict__ x, T scale, T* __restrict__ bout) {
+  pdl_begin();
   // b' = scale * b (stored in bout when given); d = x = c dinv b'
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -394,12 +412,14 @@ __global__ void k_cheb_first(int n, const T* __restrict__ b, const T* __restrict
 
 template <class TI, class TO>
 __global__ void k_convert(size_t n, const TI* __restrict__ in, TO* __restrict__ out) {
+  pdl_begin();
   const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (i < n) out[i] = (TO)in[i];
 }
 
 template <class T>
 __global__ void k_copy(size_t n, const T* __restrict__ in, T* __restrict__ out) {
+  pdl_begin();
   const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (i < n) out[i] = in[i];
 }
@@ -409,6 +429,7 @@ __global__ void k_copy(size_t n, const T* __restrict__ in, T* __restrict__ out) 
 template <class T>
 __global__ void k_schur(int n, const T* __restrict__ vp, const T* __restrict__ sp, const T* __restrict__ mpinv,
                         T nu, T rdt, T* __restrict__ zp) {
+  pdl_begin();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   zp[i] = -(nu * mpinv[i] * vp[i] + rdt * sp[i]);

@@ -19,6 +19,7 @@
 #include <stdexcept>
 #include <string>
 #include <type_traits>
+#include <utility>
 #include <vector>
 
 #include "../../include/fsi.h"
@@ -39,6 +40,38 @@ struct CudaError : std::runtime_error {
   } while (0)
 
 static inline unsigned nblk(size_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+// Every kernel of the library is launched through here.  With FSI_PDL=1 in
+// the environment the launches carry programmatic stream serialisation, so a
+// kernel may be scheduled while its predecessor on the stream finishes (each
+// kernel waits for its producers in pdl_begin()).  On the bench workload this
+// measured slower than plain launches (5.4 vs 6.4 steps/s), so it is off by
+// default.
+static bool pdl_enabled() {
+  static const bool on = [] {
+    const char* e = getenv("FSI_PDL");
+    return e && e[0] == '1';
+  }();
+  return on;
+}
+
+template <typename... KArgs, typename... Args>
+static void launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t stream,
+                   Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl_enabled() ? 1 : 0;
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(std::forward<Args>(args))...);
+  if (e != cudaSuccess) throw CudaError(e, "cudaLaunchKernelEx");
+}
+
 
 // ------------------------------------------------------------ device memory
 struct Arena {
@@ -90,10 +123,10 @@ template <class T, int BR, int BC, bool KRON, int NV>
 static void sell_launch_shape(const Sell<T>& A, int mode, const SpmvArgs<T>& a, cudaStream_t s) {
   const unsigned g = nblk(A.nrows, 32);  // 4 warps x 8 block rows
   switch (mode) {
-    case MODE_AXPBY: k_sell<T, BR, BC, KRON, NV, MODE_AXPBY><<<g, 128, 0, s>>>(A, a); break;
-    case MODE_CHEB: k_sell<T, BR, BC, KRON, NV, MODE_CHEB><<<g, 128, 0, s>>>(A, a); break;
-    case MODE_CHEB0: k_sell<T, BR, BC, KRON, NV, MODE_CHEB0><<<g, 128, 0, s>>>(A, a); break;
-    default: k_sell<T, BR, BC, KRON, NV, MODE_INIT><<<g, 128, 0, s>>>(A, a); break;
+    case MODE_AXPBY: launch(k_sell<T, BR, BC, KRON, NV, MODE_AXPBY>, g, 128, 0, s, A, a); break;
+    case MODE_CHEB: launch(k_sell<T, BR, BC, KRON, NV, MODE_CHEB>, g, 128, 0, s, A, a); break;
+    case MODE_CHEB0: launch(k_sell<T, BR, BC, KRON, NV, MODE_CHEB0>, g, 128, 0, s, A, a); break;
+    default: launch(k_sell<T, BR, BC, KRON, NV, MODE_INIT>, g, 128, 0, s, A, a); break;
   }
 }
 
@@ -187,7 +220,7 @@ static T* vcycle(MG<T>& mg, int l, cudaStream_t s, T* out) {
   const int last = (int)mg.lv.size() - 1;
   MGLevel<T>& L = mg.lv[l];
   if (l == last) {
-    k_dense_mv<T><<<nblk(mg.coarse_n, 8), 256, 0, s>>>(mg.coarse_n, mg.coarse_inv, L.b, out ? out : L.x);
+    launch(k_dense_mv<T>, nblk(mg.coarse_n, 8), 256, 0, s, mg.coarse_n, mg.coarse_inv, L.b, out ? out : L.x);
     return out ? out : L.x;
   }
   T* xc = L.x;
@@ -251,7 +284,7 @@ struct Problem {
   fsi_params prm{};
   int N = 0, nU = 0, nP = 0, nS = 0, nTri = 0, nPts = 0;
   size_t n = 0, offP = 0, offX = 0, offL = 0;
-  cudaStream_t stream = nullptr, s2 = nullptr, s3 = nullptr, s4 = nullptr;  // s3, s4: parallel branches
+  cudaStream_t stream = nullptr, s2 = nullptr, s3 = nullptr, s4 = nullptr, s5 = nullptr;  // capture helpers
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_fork2 = nullptr, ev_join2 = nullptr;
   bool own_stream = false;
   int device = 0;
@@ -311,7 +344,7 @@ static void solid_launch(Problem& P, Prec<T>& pr, cudaStream_t s) {
   auto cheb_rest = [&](T* out) {
     T* xc = pr.sx;
     T* xn = pr.sx2;
-    if (pr.cs_k == 1) { k_copy<T><<<nblk(n2, 256), 256, 0, s>>>(n2, pr.sx, out); return; }
+    if (pr.cs_k == 1) { launch(k_copy<T>, nblk(n2, 256), 256, 0, s, n2, pr.sx, out); return; }
     for (int i = 1; i < pr.cs_k; ++i) {
       SpmvArgs<T> a;
       T* dst = (i == pr.cs_k - 1) ? out : xn;
@@ -325,9 +358,9 @@ static void solid_launch(Problem& P, Prec<T>& pr, cudaStream_t s) {
     SpmvArgs<T> a;
     a.x = pr.zw; a.y = pr.sb; a.z = vL; a.alpha = dt; a.beta = -dt;
     a.d = pr.sd; a.dinv = pr.csdinv; a.xo = pr.sx; a.c2 = (T)pr.chs.c0;
-    k_cf_apply<T><<<nblk(P.nS, 128), 128, 0, s>>>(P.nS, P.cf_cap, P.cf_len, P.cf_col, pr.op.cf_val, a, MODE_INIT);
+    launch(k_cf_apply<T>, nblk(P.nS, 128), 128, 0, s, P.nS, P.cf_cap, P.cf_len, P.cf_col, pr.op.cf_val, a, MODE_INIT);
   } else {
-    k_cheb_first<T><<<nblk(n2, 256), 256, 0, s>>>(n2, vL, pr.csdinv, (T)pr.chs.c0, pr.sd, pr.sx, -dt, pr.sb);
+    launch(k_cheb_first<T>, nblk(n2, 256), 256, 0, s, n2, vL, pr.csdinv, (T)pr.chs.c0, pr.sd, pr.sx, -dt, pr.sb);
   }
   cheb_rest(zX);
   SpmvArgs<T> a2;
@@ -347,6 +380,7 @@ static void solid_launch(Problem& P, Prec<T>& pr, cudaStream_t s) {
 template <class T>
 __global__ void k_cft_sub(int nU, const int* __restrict__ ptr, const int* __restrict__ col, const T* __restrict__ val,
                           const T* __restrict__ lam, const T* __restrict__ zu, T* __restrict__ y) {
+  pdl_begin();
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= nU) return;
   T a0 = zu[2 * r], a1 = zu[2 * r + 1];
@@ -388,14 +422,14 @@ static void stokes_apply(Problem& P, Prec<T>& pr, const T* in_u, const T* in_p, 
     CK(cudaEventRecord(P.ev_fork2, s));
     CK(cudaStreamWaitEvent(P.s4, P.ev_fork2, 0));
   }
-  k_cheb_first<T><<<nblk(n3, 256), 256, 0, sp_stream>>>(n3, in_p, L0p.dinv, (T)L0p.ch.c0, L0p.d, L0p.x, (T)1, L0p.b);
+  launch(k_cheb_first<T>, nblk(n3, 256), 256, 0, sp_stream, n3, in_p, L0p.dinv, (T)L0p.ch.c0, L0p.d, L0p.x, (T)1, L0p.b);
   T* sp = vcycle<T>(pr.mgP, 0, sp_stream, (T*)nullptr);
-  k_schur<T><<<nblk(n3, 256), 256, 0, sp_stream>>>(n3, in_p, sp, pr.mpinv, (T)P.prm.nu, (T)(P.prm.rho_f / P.prm.dt),
+  launch(k_schur<T>, nblk(n3, 256), 256, 0, sp_stream, n3, in_p, sp, pr.mpinv, (T)P.prm.nu, (T)(P.prm.rho_f / P.prm.dt),
                                                    out_p);
   if (split) {
     CK(cudaEventRecord(P.ev_join2, P.s4));
     const int n2 = 2 * P.nU;
-    k_cheb_first<T><<<nblk(n2, 256), 256, 0, s>>>(n2, in_u, L0u.dinv, (T)L0u.ch.c0, L0u.d, L0u.x, (T)1, L0u.b);
+    launch(k_cheb_first<T>, nblk(n2, 256), 256, 0, s, n2, in_u, L0u.dinv, (T)L0u.ch.c0, L0u.d, L0u.x, (T)1, L0u.b);
   } else {
     SpmvArgs<T> a;
     a.x = out_p; a.y = L0u.b; a.z = in_u; a.alpha = -1; a.beta = 1;
@@ -432,16 +466,16 @@ static void precond_launch(Problem& P, Prec<T>& pr, cudaStream_t s) {
   const T* vu = pr.vin;
   if (pc == 2 || pc == 3) {
     CK(cudaStreamWaitEvent(s, P.ev_join, 0));
-    k_cft_sub<T><<<nblk(P.nU, 128), 128, 0, s>>>(P.nU, P.cft_ptr, P.cft_col, pr.op.cft_val, pr.zw + P.offL, pr.vin,
+    launch(k_cft_sub<T>, nblk(P.nU, 128), 128, 0, s, P.nU, P.cft_ptr, P.cft_col, pr.op.cft_val, pr.zw + P.offL, pr.vin,
                                                   pr.ru);
     vu = pr.ru;
   }
   stokes_apply(P, pr, vu, vp, pr.zw, zp, s, split);
   const size_t nf = 2 * (size_t)P.nU + 3 * (size_t)P.nP;
   for (int it = 1; it < pr.stokes_its; ++it) {
-    k_stokes_res<T><<<pr.op.gU + pr.op.gP, 128, 0, s>>>(pr.op, pr.zw, vu, vp, pr.t);
+    launch(k_stokes_res<T>, pr.op.gU + pr.op.gP, 128, 0, s, pr.op, pr.zw, vu, vp, pr.t);
     stokes_apply(P, pr, pr.t, pr.t + P.offP, pr.dz, pr.dz + P.offP, s, split);
-    k_axpy<T><<<nblk(nf, 256), 256, 0, s>>>(nf, pr.stokes_omega, pr.dz, pr.zw);
+    launch(k_axpy<T>, nblk(nf, 256), 256, 0, s, nf, pr.stokes_omega, pr.dz, pr.zw);
   }
   if (pc == 1) solid_launch(P, pr, s);
   if (pc == 0) CK(cudaStreamWaitEvent(s, P.ev_join, 0));
@@ -519,7 +553,8 @@ struct KrylovArgs {
   double* sn;
   double* g;
   Ctl* ctl;
-  cudaGraphConditionalHandle cond;
+  cudaGraphConditionalHandle cond;        // Arnoldi loop
+  cudaGraphConditionalHandle cond_outer;  // restart / refinement loop
 };
 
 // Classical Gram-Schmidt with one refinement pass when needed (Daniel,
@@ -566,6 +601,7 @@ __device__ void arnoldi_finish(const KrylovArgs& k, double s2) {
 
 // pass 1: h1 = V[0..j]^T w and ||w||^2 (w is stored as vector j+1 of the dots)
 __global__ void __launch_bounds__(kRedThreads) k_gs1(KrylovArgs k) {
+  pdl_begin();
   __shared__ double ws[kChunk];
   __shared__ double sm[32];
   const int cnt = k.ctl->j + 1;
@@ -592,6 +628,7 @@ __global__ void __launch_bounds__(kRedThreads) k_gs1(KrylovArgs k) {
 
 // pass 2: w -= V h1 and ||w||^2; finish the step or ask for refinement
 __global__ void __launch_bounds__(kRedThreads) k_gs2(KrylovArgs k) {
+  pdl_begin();
   __shared__ double hs[256];
   __shared__ double sm[32];
   const int cnt = k.ctl->j + 1;
@@ -622,6 +659,7 @@ __global__ void __launch_bounds__(kRedThreads) k_gs2(KrylovArgs k) {
 
 // pass 3 (refinement only): h2 = V^T w
 __global__ void __launch_bounds__(kRedThreads) k_gs3(KrylovArgs k) {
+  pdl_begin();
   __shared__ double ws[kChunk];
   if (!k.ctl->refine) return;
   const int cnt = k.ctl->j + 1;
@@ -637,6 +675,7 @@ __global__ void __launch_bounds__(kRedThreads) k_gs3(KrylovArgs k) {
 
 // pass 4 (refinement only): w -= V h2, ||w||^2, finish the step
 __global__ void __launch_bounds__(kRedThreads) k_gs4(KrylovArgs k) {
+  pdl_begin();
   __shared__ double hs[256];
   __shared__ double sm[32];
   if (!k.ctl->refine) return;
@@ -665,6 +704,7 @@ __global__ void __launch_bounds__(kRedThreads) k_gs4(KrylovArgs k) {
 
 // V[j] = w * scale (j already advanced)
 __global__ void k_gs_scale(int n, double* __restrict__ V, size_t ld, const double* __restrict__ w, const Ctl* ctl) {
+  pdl_begin();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   V[(size_t)ctl->j * ld + i] = w[i] * ctl->scale;
@@ -672,6 +712,7 @@ __global__ void k_gs_scale(int n, double* __restrict__ V, size_t ld, const doubl
 
 // start of a cycle: beta = ||w|| with w = b - A x already formed
 __global__ void __launch_bounds__(kRedThreads) k_cycle_start(KrylovArgs k) {
+  pdl_begin();
   __shared__ double sm[32];
   const int r0 = blockIdx.x * k.chunk, r1 = min(k.n, r0 + k.chunk);
   double acc = 0;
@@ -694,18 +735,22 @@ __global__ void __launch_bounds__(kRedThreads) k_cycle_start(KrylovArgs k) {
       bool stop = false;
       if (!(beta == beta)) { c->flags |= FLAG_NAN; stop = true; }
       c->converged = (beta <= c->target) ? 1 : 0;
-      if (c->converged || c->its >= c->max_it || (c->flags & (FLAG_NAN | FLAG_BREAKDOWN))) stop = true;
+      if (c->converged || c->its >= c->max_it || c->cycles > c->max_cycles ||
+          (c->flags & (FLAG_NAN | FLAG_BREAKDOWN)) || c->aflags)
+        stop = true;
       c->stop = stop ? 1 : 0;
       c->cycle_tol = fmax(c->inner_rtol * beta, c->target);
       c->scale = (beta > 0) ? 1.0 / beta : 0.0;
       c->res = beta;
       c->cyc_active = stop ? 0 : 1;
       if (k.cond) cudaGraphSetConditional(k.cond, stop ? 0u : 1u);
+      if (k.cond_outer) cudaGraphSetConditional(k.cond_outer, stop ? 0u : 1u);
     }
   }
 }
 
 __global__ void k_scale0(int n, double* __restrict__ V, const double* __restrict__ w, const Ctl* ctl) {
+  pdl_begin();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   V[i] = w[i] * ctl->scale;
@@ -713,7 +758,8 @@ __global__ void k_scale0(int n, double* __restrict__ V, const double* __restrict
 
 // ||b||, the target, and reset of the per-solve counters
 __global__ void __launch_bounds__(kRedThreads) k_solve_begin(KrylovArgs k, const double* __restrict__ b, double rtol,
-                                                             double inner_rtol, int max_it, int m) {
+                                                             double inner_rtol, int max_it, int m, int max_cycles) {
+  pdl_begin();
   __shared__ double sm[32];
   const int r0 = blockIdx.x * k.chunk, r1 = min(k.n, r0 + k.chunk);
   double acc = 0;
@@ -732,7 +778,7 @@ __global__ void __launch_bounds__(kRedThreads) k_solve_begin(KrylovArgs k, const
       c->inner_rtol = inner_rtol;
       c->its = 0; c->cycles = 0; c->j = 0; c->flags = 0; c->refines = 0; c->refine = 0;
       c->converged = 0; c->stop = 0;
-      c->max_it = max_it; c->m = m;
+      c->max_it = max_it; c->m = m; c->max_cycles = max_cycles;
     }
   }
 }
@@ -740,6 +786,7 @@ __global__ void __launch_bounds__(kRedThreads) k_solve_begin(KrylovArgs k, const
 // least squares on the rotated Hessenberg matrix: y = R^-1 g (one thread)
 __global__ void k_lsq(const double* __restrict__ H, const double* __restrict__ g, double* __restrict__ y,
                       const Ctl* ctl) {
+  pdl_begin();
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   const int kk = ctl->j, m1 = ctl->m + 1;
   for (int i = kk - 1; i >= 0; --i) {
@@ -753,6 +800,7 @@ __global__ void k_lsq(const double* __restrict__ H, const double* __restrict__ g
 template <class T>
 __global__ void k_xupdate(int n, double* __restrict__ x, const T* __restrict__ Z, size_t ld,
                           const double* __restrict__ y, const Ctl* ctl) {
+  pdl_begin();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int kk = ctl->j;
@@ -763,12 +811,14 @@ __global__ void k_xupdate(int n, double* __restrict__ x, const T* __restrict__ Z
 
 template <class T>
 __global__ void k_prec_in(int n, const double* __restrict__ V, size_t ld, const Ctl* ctl, T* __restrict__ vin) {
+  pdl_begin();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) vin[i] = (T)V[(size_t)ctl->j * ld + i];
 }
 
 template <class T>
 __global__ void k_prec_out(int n, const T* __restrict__ zw, T* __restrict__ Z, size_t ld, const Ctl* ctl) {
+  pdl_begin();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) Z[(size_t)ctl->j * ld + i] = zw[i];
 }
@@ -776,6 +826,7 @@ __global__ void k_prec_out(int n, const T* __restrict__ zw, T* __restrict__ Z, s
 // zero mean of the constant pressure coefficients (p in L^2_0)
 __global__ void __launch_bounds__(kRedThreads) k_pmean(int nP, double* __restrict__ p, double* __restrict__ part,
                                                        Ctl* ctl) {
+  pdl_begin();
   __shared__ double sm[32];
   double acc = 0;
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nP; c += gridDim.x * blockDim.x) acc += p[3 * (size_t)c];
@@ -792,6 +843,7 @@ __global__ void __launch_bounds__(kRedThreads) k_pmean(int nP, double* __restric
 }
 
 __global__ void k_psub(int nP, double* __restrict__ p, const Ctl* ctl) {
+  pdl_begin();
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c < nP) p[3 * (size_t)c] -= ctl->pmean;
 }
@@ -883,20 +935,20 @@ static KrylovArgs krylov_args(Problem& P, cudaGraphConditionalHandle h) {
 
 static void assemble_launch(Problem& P, cudaStream_t s) {
   CK(cudaMemsetAsync(&P.ctl->aflags, 0, sizeof(int), s));
-  k_locate<<<nblk(P.nPts, 256), 256, 0, s>>>(P.nPts, P.N, P.tris, P.Xold, P.cell, P.xi, P.eta, &P.ctl->aflags);
-  k_cf_rows<<<nblk(P.nS, kCfWarps), 32 * kCfWarps, 0, s>>>(P.nS, P.N, P.ntp, P.nt, P.area, P.cell, P.xi, P.eta,
+  launch(k_locate, nblk(P.nPts, 256), 256, 0, s, P.nPts, P.N, P.tris, P.Xold, P.cell, P.xi, P.eta, &P.ctl->aflags);
+  launch(k_cf_rows, nblk(P.nS, kCfWarps), 32 * kCfWarps, 0, s, P.nS, P.N, P.ntp, P.nt, P.area, P.cell, P.xi, P.eta,
                                                           P.l2n, P.wall, P.cf_cap, P.cf_len, P.cf_col, P.cf_val,
                                                           P.cf_val32, P.cflift, &P.ctl->aflags);
   CK(cudaMemsetAsync(P.cft_cnt, 0, sizeof(int) * P.nU, s));
   const size_t nslot = (size_t)P.nS * P.cf_cap;
-  k_cft_count<<<nblk(nslot, 256), 256, 0, s>>>(P.nS, P.cf_cap, P.cf_len, P.cf_col, P.cft_cnt);
+  launch(k_cft_count, nblk(nslot, 256), 256, 0, s, P.nS, P.cf_cap, P.cf_len, P.cf_col, P.cft_cnt);
   const int nb = (int)nblk(P.nU, kScanBlock);
-  k_scan_partial<<<nb, kScanBlock, 0, s>>>(P.nU, P.cft_cnt, P.scan_bsum);
-  k_scan_top<<<1, kScanBlock, 0, s>>>(nb, P.scan_bsum);
-  k_scan_final<<<nb, kScanBlock, 0, s>>>(P.nU, P.cft_cnt, P.scan_bsum, P.cft_ptr, P.cft_cur);
-  k_cft_scatter<<<nblk(nslot, 256), 256, 0, s>>>(P.nS, P.cf_cap, P.cf_len, P.cf_col, P.cf_val, P.cft_cur,
+  launch(k_scan_partial, nb, kScanBlock, 0, s, P.nU, P.cft_cnt, P.scan_bsum);
+  launch(k_scan_top, 1, kScanBlock, 0, s, nb, P.scan_bsum);
+  launch(k_scan_final, nb, kScanBlock, 0, s, P.nU, P.cft_cnt, P.scan_bsum, P.cft_ptr, P.cft_cur);
+  launch(k_cft_scatter, nblk(nslot, 256), 256, 0, s, P.nS, P.cf_cap, P.cf_len, P.cf_col, P.cf_val, P.cft_cur,
                                                  P.cft_col, P.cft_val);
-  k_cft_sort<<<nblk(P.nU, 128), 128, 0, s>>>(P.nU, P.cft_ptr, P.cft_col, P.cft_val, P.cft_val32);
+  launch(k_cft_sort, nblk(P.nU, 128), 128, 0, s, P.nU, P.cft_ptr, P.cft_col, P.cft_val, P.cft_val32);
   // S1: g1 = (rho/dt) M u^n - K_ID u_D ;  g2 = -(1/dt) C_s X^n - C_D u_D
   sell_launch(P.M64, MODE_AXPBY, axpby<double>(P.uold, P.b, P.lift_u, P.prm.rho_f / P.prm.dt, 1.0), s);
   sell_launch(P.Cs64, MODE_AXPBY, axpby<double>(P.Xold, P.b + P.offL, P.cflift, -1.0 / P.prm.dt, -1.0), s);
@@ -905,27 +957,27 @@ static void assemble_launch(Problem& P, cudaStream_t s) {
 template <class T>
 static void iteration_launch(Problem& P, Prec<T>& pr, const KrylovArgs& k, cudaStream_t s) {
   const unsigned gn = nblk(P.n, 256);
-  k_prec_in<T><<<gn, 256, 0, s>>>((int)P.n, P.V, P.n, P.ctl, pr.vin);
+  launch(k_prec_in<T>, gn, 256, 0, s, (int)P.n, P.V, P.n, P.ctl, pr.vin);
   precond_launch(P, pr, s);
-  k_prec_out<T><<<gn, 256, 0, s>>>((int)P.n, pr.zw, (T*)P.Z, P.n, P.ctl);
-  k_fullmv<T, T, double><<<pr.op.gU + pr.op.gP + pr.op.gS, 128, 0, s>>>(pr.op, pr.zw, P.w, nullptr, 1.0, 0.0);
-  k_gs1<<<P.red_blocks, kRedThreads, 0, s>>>(k);
-  k_gs2<<<P.red_blocks, kRedThreads, 0, s>>>(k);
-  k_gs3<<<P.red_blocks, kRedThreads, 0, s>>>(k);
-  k_gs4<<<P.red_blocks, kRedThreads, 0, s>>>(k);
-  k_gs_scale<<<gn, 256, 0, s>>>((int)P.n, P.V, P.n, P.w, P.ctl);
+  launch(k_prec_out<T>, gn, 256, 0, s, (int)P.n, pr.zw, (T*)P.Z, P.n, P.ctl);
+  launch(k_fullmv<T, T, double>, pr.op.gU + pr.op.gP + pr.op.gS, 128, 0, s, pr.op, pr.zw, P.w, nullptr, 1.0, 0.0);
+  launch(k_gs1, P.red_blocks, kRedThreads, 0, s, k);
+  launch(k_gs2, P.red_blocks, kRedThreads, 0, s, k);
+  launch(k_gs3, P.red_blocks, kRedThreads, 0, s, k);
+  launch(k_gs4, P.red_blocks, kRedThreads, 0, s, k);
+  launch(k_gs_scale, gn, 256, 0, s, (int)P.n, P.V, P.n, P.w, P.ctl);
 }
 
 static void cycle_start_launch(Problem& P, const KrylovArgs& k, cudaStream_t s) {
-  k_fullmv<double, double, double><<<P.op64.gU + P.op64.gP + P.op64.gS, 128, 0, s>>>(P.op64, P.x, P.w, P.b, -1.0, 1.0);
-  k_cycle_start<<<P.red_blocks, kRedThreads, 0, s>>>(k);
-  k_scale0<<<nblk(P.n, 256), 256, 0, s>>>((int)P.n, P.V, P.w, P.ctl);
+  launch(k_fullmv<double, double, double>, P.op64.gU + P.op64.gP + P.op64.gS, 128, 0, s, P.op64, P.x, P.w, P.b, -1.0, 1.0);
+  launch(k_cycle_start, P.red_blocks, kRedThreads, 0, s, k);
+  launch(k_scale0, nblk(P.n, 256), 256, 0, s, (int)P.n, P.V, P.w, P.ctl);
 }
 
 template <class T>
 static void cycle_end_launch(Problem& P, cudaStream_t s) {
-  k_lsq<<<1, 32, 0, s>>>(P.H, P.g, P.y, P.ctl);
-  k_xupdate<T><<<nblk(P.n, 256), 256, 0, s>>>((int)P.n, P.x, (const T*)P.Z, P.n, P.y, P.ctl);
+  launch(k_lsq, 1, 32, 0, s, P.H, P.g, P.y, P.ctl);
+  launch(k_xupdate<T>, nblk(P.n, 256), 256, 0, s, (int)P.n, P.x, (const T*)P.Z, P.n, P.y, P.ctl);
 }
 
 static int count_kernel_nodes(cudaGraph_t g) {
@@ -942,35 +994,55 @@ static int count_kernel_nodes(cudaGraph_t g) {
   return k;
 }
 
+// The whole solve as one graph: an outer WHILE node over restart/refinement
+// cycles whose body computes the true FP64 residual (k_cycle_start sets both
+// conditions), runs the Arnoldi loop as an inner WHILE node (k_gs2/k_gs4 set
+// its condition) and updates x.  No host round trip inside a solve.
 template <class T>
 static void build_cycle_graph(Problem& P, Prec<T>& pr) {
-  cudaStream_t s = P.stream;
-  CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-  cudaStreamCaptureStatus st;
   cudaGraph_t g = nullptr;
-  CK(cudaStreamGetCaptureInfo(s, &st, nullptr, &g, nullptr, nullptr, nullptr));
-  cudaGraphConditionalHandle h;
-  CK(cudaGraphConditionalHandleCreate(&h, g, 0, 0));
-  KrylovArgs k = krylov_args(P, h);
+  CK(cudaGraphCreate(&g, 0));
+  cudaGraphConditionalHandle h_out;
+  CK(cudaGraphConditionalHandleCreate(&h_out, g, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams op = {};
+  op.type = cudaGraphNodeTypeConditional;
+  op.conditional.handle = h_out;
+  op.conditional.type = cudaGraphCondTypeWhile;
+  op.conditional.size = 1;
+  cudaGraphNode_t onode;
+  CK(cudaGraphAddNode(&onode, g, nullptr, nullptr, 0, &op));
+  cudaGraph_t obody = op.conditional.phGraph_out[0];
+  cudaStream_t s = P.s2;
+  CK(cudaStreamBeginCaptureToGraph(s, obody, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  cudaGraphConditionalHandle h_in;
+  CK(cudaGraphConditionalHandleCreate(&h_in, obody, 0, 0));
+  KrylovArgs k = krylov_args(P, h_in);
+  k.cond_outer = h_out;
   cycle_start_launch(P, k, s);
+  cudaStreamCaptureStatus st;
+  cudaGraph_t cg = nullptr;
   const cudaGraphNode_t* deps = nullptr;
   size_t ndeps = 0;
-  CK(cudaStreamGetCaptureInfo(s, &st, nullptr, &g, &deps, nullptr, &ndeps));
-  cudaGraphNodeParams cp = {};
-  cp.type = cudaGraphNodeTypeConditional;
-  cp.conditional.handle = h;
-  cp.conditional.type = cudaGraphCondTypeWhile;
-  cp.conditional.size = 1;
-  cudaGraphNode_t wnode;
-  CK(cudaGraphAddNode(&wnode, g, deps, nullptr, ndeps, &cp));
-  CK(cudaStreamUpdateCaptureDependencies(s, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies));
-  cudaGraph_t body = cp.conditional.phGraph_out[0];
-  CK(cudaStreamBeginCaptureToGraph(P.s2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-  iteration_launch(P, pr, k, P.s2);
-  CK(cudaStreamEndCapture(P.s2, &body));
-  P.kn_body = count_kernel_nodes(body);
+  CK(cudaStreamGetCaptureInfo(s, &st, nullptr, &cg, &deps, nullptr, &ndeps));
+  cudaGraphNodeParams ip = {};
+  ip.type = cudaGraphNodeTypeConditional;
+  ip.conditional.handle = h_in;
+  ip.conditional.type = cudaGraphCondTypeWhile;
+  ip.conditional.size = 1;
+  cudaGraphNode_t inode;
+  CK(cudaGraphAddNode(&inode, cg, deps, nullptr, ndeps, &ip));
+  CK(cudaStreamUpdateCaptureDependencies(s, &inode, nullptr, 1, cudaStreamSetCaptureDependencies));
+  cudaGraph_t ibody = ip.conditional.phGraph_out[0];
+  CK(cudaStreamBeginCaptureToGraph(P.s5, ibody, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  KrylovArgs ki = k;
+  ki.cond_outer = 0;
+  iteration_launch(P, pr, ki, P.s5);
+  CK(cudaStreamEndCapture(P.s5, &ibody));
+  P.kn_body = count_kernel_nodes(ibody);
   cycle_end_launch<T>(P, s);
-  CK(cudaStreamEndCapture(s, &P.gr_cycle));
+  CK(cudaStreamEndCapture(s, &obody));
+  P.kn_cycle = count_kernel_nodes(obody);
+  P.gr_cycle = g;
   CK(cudaGraphInstantiate(&P.g_cycle, P.gr_cycle, 0));
 }
 
@@ -1005,7 +1077,8 @@ static void build_graphs(Problem& P) {
   {
     KrylovArgs k = krylov_args(P, 0);
     const double inner = (P.prm.precision == 1) ? P.prm.inner_rtol : 0.0;
-    k_solve_begin<<<P.red_blocks, kRedThreads, 0, s>>>(k, P.b, P.prm.rtol, inner, P.prm.max_it, P.m);
+    const int max_cycles = (P.prm.precision == 1) ? P.prm.max_refine + 1 : (1 << 30);
+    launch(k_solve_begin, P.red_blocks, kRedThreads, 0, s, k, P.b, P.prm.rtol, inner, P.prm.max_it, P.m, max_cycles);
   }
   CK(cudaStreamEndCapture(s, &P.gr_begin));
   CK(cudaGraphInstantiate(&P.g_begin, P.gr_begin, 0));
@@ -1021,14 +1094,13 @@ static void build_graphs(Problem& P) {
   }
   // finish: zero-mean pressure
   CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-  k_pmean<<<std::min(64, (int)nblk(P.nP, kRedThreads)), kRedThreads, 0, s>>>(P.nP, P.x + P.offP, P.part, P.ctl);
-  k_psub<<<nblk(P.nP, 256), 256, 0, s>>>(P.nP, P.x + P.offP, P.ctl);
+  launch(k_pmean, std::min(64, (int)nblk(P.nP, kRedThreads)), kRedThreads, 0, s, P.nP, P.x + P.offP, P.part, P.ctl);
+  launch(k_psub, nblk(P.nP, 256), 256, 0, s, P.nP, P.x + P.offP, P.ctl);
   CK(cudaStreamEndCapture(s, &P.gr_finish));
   CK(cudaGraphInstantiate(&P.g_finish, P.gr_finish, 0));
   P.kn_assemble = count_kernel_nodes(P.gr_assemble);
   P.kn_begin = count_kernel_nodes(P.gr_begin);
-  P.kn_cycle = P.host_loop ? count_kernel_nodes(P.gr_cstart) + count_kernel_nodes(P.gr_cend)
-                           : count_kernel_nodes(P.gr_cycle);
+  if (P.host_loop) P.kn_cycle = count_kernel_nodes(P.gr_cstart) + count_kernel_nodes(P.gr_cend);
   P.kn_finish = count_kernel_nodes(P.gr_finish);
 }
 
@@ -1104,6 +1176,7 @@ static double fullop_bytes(Problem& P, double cfnnz, size_t xbytes, size_t ybyte
 }
 
 __global__ void k_flush(size_t n, uint4* __restrict__ buf, unsigned v) {
+  pdl_begin();
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
     buf[i] = make_uint4(v, v, v, v);
 }
@@ -1228,6 +1301,7 @@ int fsi_create_problem_budget(const fsi_params* params, const fsi_solid_mesh* me
     CK(cudaStreamCreateWithFlags(&P.s2, cudaStreamNonBlocking));
     CK(cudaStreamCreateWithFlags(&P.s3, cudaStreamNonBlocking));
     CK(cudaStreamCreateWithFlags(&P.s4, cudaStreamNonBlocking));
+    CK(cudaStreamCreateWithFlags(&P.s5, cudaStreamNonBlocking));
     CK(cudaEventCreateWithFlags(&P.ev_join2, cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&P.ev_fork2, cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&P.ev_fork, cudaEventDisableTiming));
@@ -1294,29 +1368,59 @@ static int status_from_ctl(const Ctl& c) {
   return FSI_OK;
 }
 
+static int fill_info(const Problem& P, fsi_solve_info* info) {
+  const Ctl& c = *P.ctl_host;
+  const int st = status_from_ctl(c);
+  if (info) {
+    info->iterations = c.its;
+    info->restarts = std::max(0, c.cycles - 2);
+    info->refinements = (P.prm.precision == 1) ? std::max(0, c.cycles - 1) : 0;
+    info->status = st;
+    info->rel_residual = c.last_true;
+    info->rel_residual_est = (c.bnorm > 0) ? c.res / c.bnorm : c.res;
+  }
+  return st;
+}
+
+// queue S5-S8 (and the pressure normalisation) without waiting
+static void enqueue_solve(Problem& P) {
+  if (!P.assembled) CK(cudaGraphLaunch(P.g_assemble, P.stream));
+  P.assembled = false;
+  CK(cudaGraphLaunch(P.g_begin, P.stream));
+  CK(cudaGraphLaunch(P.g_cycle, P.stream));
+  CK(cudaGraphLaunch(P.g_finish, P.stream));
+  CK(cudaMemcpyAsync(P.ctl_host, P.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, P.stream));
+}
+
+static void enqueue_advance(Problem& P) {
+  CK(cudaMemcpyAsync(P.uold, P.x, 2 * (size_t)P.nU * 8, cudaMemcpyDeviceToDevice, P.stream));
+  CK(cudaMemcpyAsync(P.Xold, P.x + P.offX, 2 * (size_t)P.nS * 8, cudaMemcpyDeviceToDevice, P.stream));
+}
+
 int fsi_solve_step(fsi_problem* h, fsi_solve_info* info) {
   if (!h) return FSI_ERR_INVALID;
   Problem& P = h->P;
   try {
+    if (!P.host_loop) {
+      enqueue_solve(P);
+      CK(cudaStreamSynchronize(P.stream));
+      return fill_info(P, info);
+    }
     if (!P.assembled) CK(cudaGraphLaunch(P.g_assemble, P.stream));
     P.assembled = false;
     CK(cudaGraphLaunch(P.g_begin, P.stream));
     const int max_cycles = (P.prm.precision == 1) ? P.prm.max_refine + 1 : 1000000;
     Ctl& c = *P.ctl_host;
     for (int cyc = 0; cyc < max_cycles; ++cyc) {
-      if (P.host_loop) {
-        CK(cudaGraphLaunch(P.g_cstart, P.stream));
+      CK(cudaGraphLaunch(P.g_cstart, P.stream));
+      CK(cudaMemcpyAsync(P.ctl_host, P.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, P.stream));
+      CK(cudaStreamSynchronize(P.stream));
+      while (c.cyc_active) {
+        CK(cudaGraphLaunch(P.g_body, P.stream));
         CK(cudaMemcpyAsync(P.ctl_host, P.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, P.stream));
         CK(cudaStreamSynchronize(P.stream));
-        while (c.cyc_active) {
-          CK(cudaGraphLaunch(P.g_body, P.stream));
-          CK(cudaMemcpyAsync(P.ctl_host, P.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, P.stream));
-          CK(cudaStreamSynchronize(P.stream));
-        }
-        CK(cudaGraphLaunch(P.g_cend, P.stream));
-      } else {
-        CK(cudaGraphLaunch(P.g_cycle, P.stream));
       }
+      CK(cudaGraphLaunch(P.g_cend, P.stream));
       CK(cudaMemcpyAsync(P.ctl_host, P.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, P.stream));
       CK(cudaStreamSynchronize(P.stream));
       if (c.stop || c.aflags) break;
@@ -1324,16 +1428,32 @@ int fsi_solve_step(fsi_problem* h, fsi_solve_info* info) {
     CK(cudaGraphLaunch(P.g_finish, P.stream));
     CK(cudaMemcpyAsync(P.ctl_host, P.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, P.stream));
     CK(cudaStreamSynchronize(P.stream));
-    const int st = status_from_ctl(c);
-    if (info) {
-      info->iterations = c.its;
-      info->restarts = std::max(0, c.cycles - 2);
-      info->refinements = (P.prm.precision == 1) ? std::max(0, c.cycles - 1) : 0;
-      info->status = st;
-      info->rel_residual = c.last_true;
-      info->rel_residual_est = (c.bnorm > 0) ? c.res / c.bnorm : c.res;
+    return fill_info(P, info);
+  } catch (...) {
+    return map_exception();
+  }
+}
+
+int fsi_step_batch(fsi_problem* const* problems, int count, fsi_solve_info* infos) {
+  if (!problems || count < 0) return FSI_ERR_INVALID;
+  for (int i = 0; i < count; ++i)
+    if (!problems[i] || problems[i]->P.host_loop) return FSI_ERR_INVALID;
+  int first_err = FSI_OK;
+  try {
+    // queue every instance's whole step on its own stream, then wait for all
+    for (int i = 0; i < count; ++i) {
+      Problem& P = problems[i]->P;
+      P.assembled = false;
+      enqueue_solve(P);
+      enqueue_advance(P);
     }
-    return st;
+    for (int i = 0; i < count; ++i) {
+      Problem& P = problems[i]->P;
+      CK(cudaStreamSynchronize(P.stream));
+      const int st = fill_info(P, infos ? &infos[i] : nullptr);
+      if (st != FSI_OK && first_err == FSI_OK) first_err = st;
+    }
+    return first_err;
   } catch (...) {
     return map_exception();
   }
@@ -1457,11 +1577,11 @@ int fsi_apply_operator(fsi_problem* h, const double* xh, double* yh, int precisi
     double* tmp = P.V;  // first basis vector as scratch
     CK(cudaMemcpyAsync(tmp, xh, P.n * 8, cudaMemcpyHostToDevice, P.stream));
     if (precision == 1) {
-      k_convert<double, float><<<nblk(P.n, 256), 256, 0, P.stream>>>(P.n, tmp, P.p32.vin);
-      k_fullmv<float, float, double><<<P.op32.gU + P.op32.gP + P.op32.gS, 128, 0, P.stream>>>(P.op32, P.p32.vin, P.w,
+      launch(k_convert<double, float>, nblk(P.n, 256), 256, 0, P.stream, P.n, tmp, P.p32.vin);
+      launch(k_fullmv<float, float, double>, P.op32.gU + P.op32.gP + P.op32.gS, 128, 0, P.stream, P.op32, P.p32.vin, P.w,
                                                                                             nullptr, 1.0, 0.0);
     } else {
-      k_fullmv<double, double, double><<<P.op64.gU + P.op64.gP + P.op64.gS, 128, 0, P.stream>>>(P.op64, tmp, P.w,
+      launch(k_fullmv<double, double, double>, P.op64.gU + P.op64.gP + P.op64.gS, 128, 0, P.stream, P.op64, tmp, P.w,
                                                                                                nullptr, 1.0, 0.0);
     }
     CK(cudaGetLastError());
@@ -1481,13 +1601,13 @@ int fsi_apply_preconditioner(fsi_problem* h, const double* vh, double* zh, int p
     double* tmp = P.V;
     CK(cudaMemcpyAsync(tmp, vh, P.n * 8, cudaMemcpyHostToDevice, P.stream));
     if (precision == 1) {
-      k_convert<double, float><<<nblk(P.n, 256), 256, 0, P.stream>>>(P.n, tmp, P.p32.vin);
+      launch(k_convert<double, float>, nblk(P.n, 256), 256, 0, P.stream, P.n, tmp, P.p32.vin);
       precond_launch(P, P.p32, P.stream);
-      k_convert<float, double><<<nblk(P.n, 256), 256, 0, P.stream>>>(P.n, P.p32.zw, P.w);
+      launch(k_convert<float, double>, nblk(P.n, 256), 256, 0, P.stream, P.n, P.p32.zw, P.w);
     } else {
-      k_copy<double><<<nblk(P.n, 256), 256, 0, P.stream>>>(P.n, tmp, P.p64.vin);
+      launch(k_copy<double>, nblk(P.n, 256), 256, 0, P.stream, P.n, tmp, P.p64.vin);
       precond_launch(P, P.p64, P.stream);
-      k_copy<double><<<nblk(P.n, 256), 256, 0, P.stream>>>(P.n, P.p64.zw, P.w);
+      launch(k_copy<double>, nblk(P.n, 256), 256, 0, P.stream, P.n, P.p64.zw, P.w);
     }
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(zh, P.w, P.n * 8, cudaMemcpyDeviceToHost, P.stream));
@@ -1526,16 +1646,16 @@ int fsi_time_kernel(fsi_problem* h, int which, int reps, double* avg_ms, double*
     cudaStream_t s = P.stream;
     const HostBlockMatrix& A0 = P.hs.levels[0].A;
     for (int r = 0; r < reps + 1; ++r) {
-      k_flush<<<2 * 152, 512, 0, s>>>(flush_n, fl, (unsigned)r);
+      launch(k_flush, 2 * 152, 512, 0, s, flush_n, fl, (unsigned)r);
       CK(cudaEventRecord(e0, s));
       switch (which) {
         case 0:  // full operator, FP32 (mixed inner iteration)
-          k_fullmv<float, float, double><<<P.op32.gU + P.op32.gP + P.op32.gS, 128, 0, s>>>(P.op32, P.p32.zw, P.w,
+          launch(k_fullmv<float, float, double>, P.op32.gU + P.op32.gP + P.op32.gS, 128, 0, s, P.op32, P.p32.zw, P.w,
                                                                                           nullptr, 1.0, 0.0);
           *bytes = fullop_bytes<float>(P, cfnnz, sizeof(float), sizeof(double));
           break;
         case 1:  // full operator, FP64 (residual / FP64 iteration)
-          k_fullmv<double, double, double><<<P.op64.gU + P.op64.gP + P.op64.gS, 128, 0, s>>>(P.op64, P.x, P.w, P.b,
+          launch(k_fullmv<double, double, double>, P.op64.gU + P.op64.gP + P.op64.gS, 128, 0, s, P.op64, P.x, P.w, P.b,
                                                                                             -1.0, 1.0);
           *bytes = fullop_bytes<double>(P, cfnnz, 16, 8);
           break;
@@ -1606,6 +1726,7 @@ void fsi_destroy(fsi_problem* h) {
   if (P.s2) cudaStreamDestroy(P.s2);
   if (P.s3) cudaStreamDestroy(P.s3);
   if (P.s4) cudaStreamDestroy(P.s4);
+  if (P.s5) cudaStreamDestroy(P.s5);
   if (P.ev_join2) cudaEventDestroy(P.ev_join2);
   if (P.ev_fork2) cudaEventDestroy(P.ev_fork2);
   if (P.ev_fork) cudaEventDestroy(P.ev_fork);

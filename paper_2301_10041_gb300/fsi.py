@@ -56,6 +56,7 @@ EXPORTS = {
     "fsi_solve_step": (C.c_int, [C.c_void_p, C.POINTER(fsi_solve_info)]),
     "fsi_advance": (C.c_int, [C.c_void_p]),
     "fsi_step": (C.c_int, [C.c_void_p, C.POINTER(fsi_solve_info)]),
+    "fsi_step_batch": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.POINTER(fsi_solve_info)]),
     "fsi_get_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "fsi_set_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "fsi_sizes": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
@@ -276,6 +277,17 @@ def locate_bin_noalloc(N: int, n_tris: int, tris_ptr: int, X_ptr: int, cell_ptr:
         int(N), int(n_tris), C.c_void_p(tris_ptr), C.c_void_p(X_ptr), C.c_void_p(cell_ptr), C.c_void_p(xi_ptr),
         C.c_void_p(eta_ptr), C.c_void_p(cell_start_ptr), C.c_void_p(cell_points_ptr), C.c_void_p(n_outside_ptr),
         C.c_void_p(stream) if stream else None))
+
+
+def step_batch(problems) -> list:
+    """One time step of every problem, all queued before any is waited for."""
+    n = len(problems)
+    handles = (C.c_void_p * n)(*[p._h for p in problems])
+    infos = (fsi_solve_info * n)()
+    st = load_library().fsi_step_batch(handles, n, infos)
+    out = [SolveInfo(i.iterations, i.refinements, i.restarts, i.status, i.rel_residual, i.rel_residual_est)
+           for i in infos]
+    return st, out
 
 
 def problem_from_case(case, precision: int = 0, precond=None, rtol=None, stream=None, **kw) -> Problem:
