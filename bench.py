@@ -28,6 +28,10 @@ import time
 
 import numpy as np
 
+# many independent instances run on their own streams: give the device enough
+# hardware queues that they are not multiplexed onto a few (set before CUDA starts)
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -372,6 +376,74 @@ def run_profile_step(args):
     prob.close()
 
 
+def run_batch(args):
+    """Batched uneven instances (configs[3] shape): fsi_step_batch over the
+    whole set each tick, every instance on its own stream."""
+    import torch
+    import fsi_inputs as fi
+    from paper_2301_10041_gb300 import build, fsi
+    build.build()
+    n = args.batch_instances
+    cases = [fi.config3_instance(i) for i in range(n)]
+    t0 = time.perf_counter()
+    probs = [fsi.problem_from_case(c, precision=1, precond=PRECOND, restart=60, max_it=6000,
+                                   stokes_its=STOKES_ITS) for c in cases]
+    t_create = time.perf_counter() - t0
+    for _ in range(args.warmup):
+        fsi.step_batch(probs)
+    torch.cuda.synchronize()
+    ticks = []
+    its = []
+    failures = 0
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        st, infos = fsi.step_batch(probs)
+        ticks.append(time.perf_counter() - t)
+        its.append(sum(i.iterations for i in infos))
+        failures += sum(1 for i in infos if i.status != 0)
+    for p in probs:
+        p.close()
+    total = sum(ticks)
+    out = {"metric": METRIC, "workload": "batch", "value": n * args.steps / total, "unit": "time-steps/s",
+           "instances": n, "steps": args.steps, "warmup": args.warmup,
+           "tick_ms": {"p50": float(np.percentile(ticks, 50)) * 1e3, "p99": float(np.percentile(ticks, 99)) * 1e3},
+           "krylov_iterations_per_instance_step": float(np.sum(its)) / (n * args.steps),
+           "create_s": t_create, "failed_instance_steps": failures,
+           "dtype": "f32 operators + f64 refinement", "data": "synthetic",
+           "config": {"workload": "256 cavity instances, N~U{16,32,48,64,96}, R~U[0.1,0.3], kappa log-U[1,1e4], "
+                                  "nu log-U[1e-3,1], m=ceil(2RN), restart 60, block upper-triangular, 8 inner Stokes steps",
+                      "instances": n}}
+    print(json.dumps(out))
+
+
+def run_serve(args):
+    """Served stream (configs[4] shape): Poisson arrivals replayed in wall
+    time, admission by device footprint, continuous batching."""
+    import fsi_inputs as fi
+    from paper_2301_10041_gb300 import build
+    from paper_2301_10041_gb300.serve import Request, Server, gpu_ops
+    build.build()
+    trace = fi.config4_trace(args.serve_requests)
+    reqs = [Request(rid=i, arrival=t, case=fi.config4_case(spec), steps=50) for i, (t, spec) in enumerate(trace)]
+    def largest_body(N):   # R <= 0.3, m = ceil(2 R N): the largest ring mesh for this grid
+        m = int(np.ceil(2 * 0.3 * N))
+        return 1 + 3 * m * (m + 1), 6 * m * m
+
+    ops = gpu_ops(precision=1, restart=60, stokes_its=args.serve_stokes_its, max_solid_nodes=largest_body)
+    srv = Server(ops, budget_bytes=int(args.serve_budget_gb * (1 << 30)), max_resident=args.serve_max_resident,
+                 admit_per_tick=2)
+    wall = srv.run(reqs, realtime=True, max_wall=args.serve_wall)
+    rep = srv.report(wall)
+    offered = sum(r.steps for r in reqs if r.arrival <= wall) / wall
+    out = {"metric": METRIC, "workload": "serve", "value": rep["steps_per_s"], "unit": "time-steps/s",
+           "offered_steps_per_s": offered, "p50_step_ms": rep["step_latency_ms"]["p50"],
+           "p99_step_ms": rep["step_latency_ms"]["p99"], "report": rep,
+           "config": {"workload": "Poisson 200/s, N in {32,64,128,256} p=.4/.3/.2/.1, disk/ellipse, R~U[0.1,0.3], "
+                                  "kappa log-U[1,1e4], 50 steps each", "requests": args.serve_requests,
+                      "budget_gb": args.serve_budget_gb, "wall_cap_s": args.serve_wall}}
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -383,7 +455,19 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=300.0)
     ap.add_argument("--profile-step", action="store_true",
                     help="only build the mixed problem, run --warmup steps and one more (for ncu)")
+    ap.add_argument("--workload", choices=["cavity128", "batch", "serve"], default="cavity128",
+                    help="cavity128 (default, the contract line); batch / serve print their own lines")
+    ap.add_argument("--batch-instances", type=int, default=256)
+    ap.add_argument("--serve-requests", type=int, default=2000)
+    ap.add_argument("--serve-budget-gb", type=float, default=64.0)
+    ap.add_argument("--serve-max-resident", type=int, default=16)
+    ap.add_argument("--serve-wall", type=float, default=60.0)
+    ap.add_argument("--serve-stokes-its", type=int, default=8)
     args = ap.parse_args()
+    if args.workload == "batch":
+        return run_batch(args)
+    if args.workload == "serve":
+        return run_serve(args)
     if args.profile_step:
         return run_profile_step(args)
     if args.warmup < 3 and args.impl == "ours":

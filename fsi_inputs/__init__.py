@@ -204,7 +204,8 @@ def config2(N: int, seed: int = BASE_SEED + 2) -> FsiCase:
 def config3_instance(i: int, seed: int = BASE_SEED + 3) -> FsiCase:
     """Instance i of the batch of uneven problems: N ~ U{16,32,48,64,96},
     R ~ U[0.1,0.3], centre ~ U[0.35,0.65]^2, kappa log-uniform [1,1e4],
-    nu log-uniform [1e-3,1], m = ceil(2 R N), walls at rest, u_0 seeded."""
+    nu log-uniform [1e-3,1], m = ceil(2 R N), walls at rest, u_0 seeded;
+    dt = 1e-3 as in the 128x128 workload (the batch definition leaves it open)."""
     r = uniform01(seed, np.arange(8 * i, 8 * i + 8, dtype=np.uint64))
     N = (16, 32, 48, 64, 96)[min(int(r[0] * 5), 4)]
     R = 0.1 + 0.2 * r[1]
@@ -213,7 +214,7 @@ def config3_instance(i: int, seed: int = BASE_SEED + 3) -> FsiCase:
     nu = 10.0 ** (-3.0 + 3.0 * r[5])
     m = int(math.ceil(2.0 * R * N))
     xy, tris = ring_disk_mesh(m, R, (cx, cy))
-    return FsiCase(N=N, rho_f=1.0, nu=nu, kappa=kappa, dt=0.01, lid_u=0.0,
+    return FsiCase(N=N, rho_f=1.0, nu=nu, kappa=kappa, dt=1e-3, lid_u=0.0,
                    ref_xy=xy, tris=tris, u0=initial_velocity(N, seed * 1000003 + i),
                    X0=xy.copy(), precond=1, rtol=1e-8, steps=50, name=f"batch{i}_N{N}")
 
@@ -244,6 +245,6 @@ def config4_case(spec: dict, seed: int = BASE_SEED + 4) -> FsiCase:
         xy, tris = ellipse_mesh(m, R, 0.5 * R, 30.0)
     else:
         xy, tris = ring_disk_mesh(m, R, (0.5, 0.5))
-    return FsiCase(N=N, rho_f=1.0, nu=0.1, kappa=spec["kappa"], dt=0.01, lid_u=1.0,
+    return FsiCase(N=N, rho_f=1.0, nu=0.1, kappa=spec["kappa"], dt=1e-3, lid_u=1.0,
                    ref_xy=xy, tris=tris, u0=wall_velocity(N, 1.0), X0=xy.copy(),
                    precond=1, rtol=1e-8, steps=50, name=f"req{spec['index']}_N{N}")

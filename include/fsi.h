@@ -155,6 +155,14 @@ int fsi_step(fsi_problem* p, fsi_solve_info* info);
  * rejected (FSI_ERR_INVALID). */
 int fsi_step_batch(fsi_problem* const* problems, int count, fsi_solve_info* infos);
 
+/* Asynchronous step for continuous batching: fsi_step_async queues
+ * assemble + solve + advance on the problem's stream and returns at once;
+ * fsi_step_poll returns 1 while that step is still running and 0 once it has
+ * finished (filling info; info->status is the step's status), or a negative
+ * FSI_ERR_* if the stream failed.  Poll before touching the problem again. */
+int fsi_step_async(fsi_problem* p);
+int fsi_step_poll(fsi_problem* p, fsi_solve_info* info);
+
 /* Host copies of the current solution; any pointer may be NULL.
  * u: 2*(2N+1)^2 (wall values included), pr: 3*N^2, X and lam: 2*n_nodes. */
 int fsi_get_state(fsi_problem* p, double* u, double* pr, double* X, double* lam);

@@ -1434,6 +1434,29 @@ int fsi_solve_step(fsi_problem* h, fsi_solve_info* info) {
   }
 }
 
+int fsi_step_async(fsi_problem* h) {
+  if (!h || h->P.host_loop) return FSI_ERR_INVALID;
+  Problem& P = h->P;
+  try {
+    P.assembled = false;
+    enqueue_solve(P);
+    enqueue_advance(P);
+    return FSI_OK;
+  } catch (...) {
+    return map_exception();
+  }
+}
+
+int fsi_step_poll(fsi_problem* h, fsi_solve_info* info) {
+  if (!h) return FSI_ERR_INVALID;
+  Problem& P = h->P;
+  const cudaError_t q = cudaStreamQuery(P.stream);
+  if (q == cudaErrorNotReady) return 1;
+  if (q != cudaSuccess) return FSI_ERR_CUDA;
+  fill_info(P, info);
+  return 0;
+}
+
 int fsi_step_batch(fsi_problem* const* problems, int count, fsi_solve_info* infos) {
   if (!problems || count < 0) return FSI_ERR_INVALID;
   for (int i = 0; i < count; ++i)

@@ -57,6 +57,8 @@ EXPORTS = {
     "fsi_advance": (C.c_int, [C.c_void_p]),
     "fsi_step": (C.c_int, [C.c_void_p, C.POINTER(fsi_solve_info)]),
     "fsi_step_batch": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.POINTER(fsi_solve_info)]),
+    "fsi_step_async": (C.c_int, [C.c_void_p]),
+    "fsi_step_poll": (C.c_int, [C.c_void_p, C.POINTER(fsi_solve_info)]),
     "fsi_get_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "fsi_set_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "fsi_sizes": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
@@ -192,6 +194,20 @@ class Problem:
         info = self.solve_step()
         self.advance()
         return info
+
+    def step_async(self):
+        self._check(load_library().fsi_step_async(self._h), "fsi_step_async")
+
+    def step_poll(self):
+        """None while the queued step runs, else its SolveInfo."""
+        info = fsi_solve_info()
+        st = load_library().fsi_step_poll(self._h, C.byref(info))
+        if st == 1:
+            return None
+        if st < 0:
+            raise FsiError(st, "fsi_step_poll")
+        return SolveInfo(info.iterations, info.refinements, info.restarts, info.status, info.rel_residual,
+                         info.rel_residual_est)
 
     # -- state
     def get_state(self):
