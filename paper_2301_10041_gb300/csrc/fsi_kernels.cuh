@@ -123,28 +123,50 @@ __device__ __forceinline__ void load_x(const TX* __restrict__ x, int c, TA* xv) 
   }
 }
 
-// accumulate this thread's share of block row `row` of A (BR x BC blocks) times x
+// accumulate this thread's share of block row `row` of A (BR x BC blocks) times x.
+// Entries are taken two at a time: both column indices are loaded first,
+// then both value blocks and gathered x blocks, so that several independent
+// loads are in flight per thread before the first FMA (two, not more, keeps
+// the kernels at 32 registers and full occupancy).
 template <class TA, class TX, int BR, int BC, bool KRON, int NV>
 __device__ __forceinline__ void sell_row(const Sell<TA>& A, int row, int t, const TX* __restrict__ x, TA* acc) {
   const int base = A.soff[row >> 3] + (row & 7);
   const int n = A.len[row];
-#pragma unroll 2
-  for (int k = t; k < n; k += kRowThreads) {
-    const int slot = base + (k << 3);
-    const int c = __ldg(A.col + slot);
-    TA xv[BC];
-    load_x<TX, TA, BC>(x, c, xv);
-    if constexpr (KRON) {
-      const TA v = __ldg(A.val + slot);
+  constexpr int U = 2;
+  for (int k0 = t; k0 < n; k0 += U * kRowThreads) {
+    int c[U];
 #pragma unroll
-      for (int i = 0; i < BR; ++i) acc[i] += v * xv[i];
-    } else {
-      TA v[NV];
-      load_block<TA, NV>(A.val + (size_t)slot * NV, v);
+    for (int u = 0; u < U; ++u) {
+      const int k = k0 + u * kRowThreads;
+      c[u] = (k < n) ? __ldg(A.col + base + (k << 3)) : -1;
+    }
+    TA xv[U][BC];
+    TA v[U][KRON ? 1 : NV];
 #pragma unroll
-      for (int i = 0; i < BR; ++i)
+    for (int u = 0; u < U; ++u) {
+      const int slot = base + ((k0 + u * kRowThreads) << 3);
+      if (c[u] >= 0) {
+        load_x<TX, TA, BC>(x, c[u], xv[u]);
+        if constexpr (KRON) v[u][0] = __ldg(A.val + slot);
+        else load_block<TA, NV>(A.val + (size_t)slot * NV, v[u]);
+      } else {
 #pragma unroll
-        for (int j = 0; j < BC; ++j) acc[i] += v[i * BC + j] * xv[j];
+        for (int j = 0; j < BC; ++j) xv[u][j] = 0;
+#pragma unroll
+        for (int j = 0; j < (KRON ? 1 : NV); ++j) v[u][j] = 0;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if constexpr (KRON) {
+#pragma unroll
+        for (int i = 0; i < BR; ++i) acc[i] += v[u][0] * xv[u][i];
+      } else {
+#pragma unroll
+        for (int i = 0; i < BR; ++i)
+#pragma unroll
+          for (int j = 0; j < BC; ++j) acc[i] += v[u][i * BC + j] * xv[u][j];
+      }
     }
   }
 }
@@ -159,7 +181,7 @@ __device__ __forceinline__ void row_reduce(T* acc) {
 }
 
 template <class T, int BR, int BC, bool KRON, int NV, int MODE>
-__global__ void __launch_bounds__(128) k_sell(Sell<T> A, SpmvArgs<T> a) {
+__global__ void __launch_bounds__(128, 16) k_sell(Sell<T> A, SpmvArgs<T> a) {
   pdl_begin();
   const int lane = threadIdx.x & 31;
   const int row = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * kSliceRows + (lane & 7);
@@ -220,7 +242,7 @@ struct FullOp {
 };
 
 template <class TA, class TX, class TY>
-__global__ void __launch_bounds__(128) k_fullmv(FullOp<TA> op, const TX* __restrict__ x, TY* __restrict__ y,
+__global__ void __launch_bounds__(128, 16) k_fullmv(FullOp<TA> op, const TX* __restrict__ x, TY* __restrict__ y,
                                                 const TY* __restrict__ z, TY alpha, TY beta) {
   pdl_begin();
   const int lane = threadIdx.x & 31, t = lane >> 3;
