@@ -110,19 +110,28 @@ STOKES_ITS = 8   # Richardson steps on the Stokes block per preconditioner appli
 MAX_IT = 6000
 
 
-def time_arm(fsi, torch, case, precision, steps, warmup, stream, flush):
-    prob = fsi.problem_from_case(case, precision=precision, precond=PRECOND, rtol=1e-8, stream=stream.cuda_stream,
-                                 max_it=MAX_IT, restart=RESTART, stokes_its=STOKES_ITS)
+def _step_unchecked(prob):
+    prob.assemble_step()
+    info = prob.solve_step(check=False)
+    prob.advance()
+    return info
+
+
+def time_arm(fsi, torch, case, precision, steps, warmup, stream, flush, precond=PRECOND, stokes_its=STOKES_ITS,
+             max_it=MAX_IT, check=True):
+    prob = fsi.problem_from_case(case, precision=precision, precond=precond, rtol=1e-8, stream=stream.cuda_stream,
+                                 max_it=max_it, restart=RESTART, stokes_its=stokes_its)
+    step = prob.step if check else (lambda: _step_unchecked(prob))
     infos = []
     for _ in range(warmup):
-        prob.step()
+        step()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     torch.cuda.synchronize()
     for k in range(steps):
         with torch.cuda.stream(stream):
             flush.fill_(k & 0xFF)          # evict L2 between timed steps (outside the events)
         ev[k][0].record(stream)
-        infos.append(prob.step())
+        infos.append(step())
         ev[k][1].record(stream)
     torch.cuda.synchronize()
     ms = [a.elapsed_time(b) for a, b in ev]
@@ -133,6 +142,7 @@ def time_arm(fsi, torch, case, precision, steps, warmup, stream, flush):
         launches += int(counts[0] + counts[1] + cycles * counts[2] + inf.iterations * counts[3] + counts[4])
     stats = {
         "ms": ms,
+        "status": [i.status for i in infos],
         "iterations": [i.iterations for i in infos],
         "refinements": [i.refinements for i in infos],
         "rel_residual_max": max(i.rel_residual for i in infos),
@@ -419,6 +429,64 @@ def run_batch(args):
     print(json.dumps(out))
 
 
+# ------------------------------------------------------------ size sweep
+SWEEP_SIZES = (64, 256, 512, 1024)
+# (label, precond, Stokes Richardson steps): the paper's two block
+# preconditioners with one V-cycle pair per inner block, and the bench default
+SWEEP_VARIANTS = (("block-diagonal", 0, 1),
+                  ("block-lower-triangular", 1, 1),
+                  ("block-upper-triangular + 8 Stokes Richardson steps", PRECOND, STOKES_ITS))
+SWEEP_MAX_IT = 2000
+
+
+def run_sweep(args):
+    """Ellipse size sweep (N = 64 .. 1024, m = ceil(0.4 N)): Krylov iterations
+    per step of each preconditioner, time per step, and the roofline of the
+    finest-level kernels at every size (HBM-bound once the matrices leave L2)."""
+    import torch
+    import fsi_inputs as fi
+    from paper_2301_10041_gb300 import build, fsi
+    build.build()
+    fsi.load_library()
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    peak = peaks.get("hbm_gbs", 6800.0)
+    sizes = [int(v) for v in args.sweep_sizes.split(",")]
+    stream = torch.cuda.Stream()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    rows = []
+    for N in sizes:
+        case = fi.config2(N)
+        for label, pc, sits in SWEEP_VARIANTS:
+            t0 = time.perf_counter()
+            prob, st = time_arm(fsi, torch, case, 1, args.sweep_steps, 1, stream, flush, precond=pc,
+                                stokes_its=sits, max_it=args.sweep_max_it, check=False)
+            row = {"N": N, "preconditioner": label, "precond": pc, "stokes_its": sits,
+                   "dofs": int(prob_dofs(case)), "solid_nodes": int(case.ref_xy.shape[0]),
+                   "solid_tris": int(case.tris.shape[0]),
+                   "iterations_per_step": st["iterations"], "status": st["status"],
+                   "converged_steps": sum(1 for v in st["status"] if v == 0),
+                   "ms_per_step": float(np.mean(st["ms"])), "rel_residual_max": st["rel_residual_max"],
+                   "wall_s": time.perf_counter() - t0}
+            if pc == PRECOND and sits == STOKES_ITS:
+                kern = {}
+                for name, which in (("full_operator_f32", 0), ("full_operator_f64", 1),
+                                    ("velocity_chebyshev_f32", 2), ("velocity_chebyshev_f64", 3)):
+                    ms, by = prob.time_kernel(which, reps=20)
+                    kern[name] = {"us": ms * 1e3, "bytes": by, "gbs": by / ms / 1e6, "frac": by / ms / 1e6 / peak}
+                row["kernels"] = kern
+            prob.close()
+            rows.append(row)
+            print(json.dumps({"sweep_row": row}), file=sys.stderr, flush=True)
+    out = {"metric": METRIC, "workload": "sweep", "unit": "time-steps/s",
+           "value": None, "rows": rows, "hbm_peak_gbs": peak,
+           "config": {"workload": "ellipse 0.2/0.1 rotated 30 deg, m=ceil(0.4N), kappa=1e2, nu=1, rho=1, dt=0.01, "
+                                  "walls and fluid at rest, mixed precision, rtol 1e-8, restart %d" % RESTART,
+                      "sizes": sizes, "steps_per_case": args.sweep_steps, "max_it": args.sweep_max_it,
+                      "l2": "flushed between timed steps (512 MiB write)"}}
+    print(json.dumps(out))
+
+
 def run_serve(args):
     """Served stream (configs[4] shape): Poisson arrivals replayed in wall
     time, admission by device footprint, continuous batching."""
@@ -458,19 +526,24 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=300.0)
     ap.add_argument("--profile-step", action="store_true",
                     help="only build the mixed problem, run --warmup steps and one more (for ncu)")
-    ap.add_argument("--workload", choices=["cavity128", "batch", "serve"], default="cavity128",
-                    help="cavity128 (default, the contract line); batch / serve print their own lines")
+    ap.add_argument("--workload", choices=["cavity128", "batch", "serve", "sweep"], default="cavity128",
+                    help="cavity128 (default, the contract line); batch / serve / sweep print their own lines")
     ap.add_argument("--batch-instances", type=int, default=256)
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-budget-gb", type=float, default=64.0)
     ap.add_argument("--serve-max-resident", type=int, default=16)
     ap.add_argument("--serve-wall", type=float, default=60.0)
     ap.add_argument("--serve-stokes-its", type=int, default=8)
+    ap.add_argument("--sweep-sizes", default=",".join(str(v) for v in SWEEP_SIZES))
+    ap.add_argument("--sweep-steps", type=int, default=2)
+    ap.add_argument("--sweep-max-it", type=int, default=SWEEP_MAX_IT)
     args = ap.parse_args()
     if args.workload == "batch":
         return run_batch(args)
     if args.workload == "serve":
         return run_serve(args)
+    if args.workload == "sweep":
+        return run_sweep(args)
     if args.profile_step:
         return run_profile_step(args)
     if args.warmup < 3 and args.impl == "ours":

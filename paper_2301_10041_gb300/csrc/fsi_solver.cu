@@ -1653,6 +1653,7 @@ int fsi_time_kernel(fsi_problem* h, int which, int reps, double* avg_ms, double*
   if (!h || !avg_ms || !bytes || reps <= 0) return FSI_ERR_INVALID;
   Problem& P = h->P;
   if ((which == 0 || which == 2) && P.prm.precision != 1) return FSI_ERR_INVALID;
+  if (which == 3 && P.p64.mgU.lv.empty()) return FSI_ERR_INVALID;  // no FP64 hierarchy in mixed mode
   try {
     // total C_f entries of the last assembly
     std::vector<int> len(P.nS);

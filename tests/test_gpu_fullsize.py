@@ -1,0 +1,162 @@
+"""Parity at the full workload sizes, in the launch configuration the bench
+times (mixed precision, block upper-triangular preconditioner with inner
+Stokes Richardson steps, restart 100).
+
+The oracle's direct solve takes minutes at these sizes, so the solve is
+checked through a property that holds at any size: the GPU solution's
+residual, evaluated in the oracle's own FP64 operator, is below the 1e-8
+tolerance of the time step (Section 5 stopping rule).  Everything before the
+solve is compared entry by entry: point locations bit for bit, C_f, the
+operator and the right-hand side to 1e-13 relative (at N = 1024 on sampled
+points and sampled C_f rows, which the oracle computes one by one).
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import bench
+import fsi_inputs as fi
+from oracle import fsi_oracle as fo
+from tests.gpu_helpers import oracle_to_gpu_perm, rel
+
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-8
+
+
+@pytest.fixture(scope="module")
+def fsi():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2301_10041_gb300 import build, fsi as f
+    build.build()
+    f.load_library()
+    return f
+
+
+def _bench_problem(fsi, case, precond=bench.PRECOND, stokes_its=bench.STOKES_ITS, max_it=bench.MAX_IT):
+    return fsi.problem_from_case(case, precision=1, precond=precond, rtol=RTOL, max_it=max_it,
+                                 restart=bench.RESTART, stokes_its=stokes_its)
+
+
+def _oracle(case):
+    return fo.OracleProblem(case.N, case.rho_f, case.nu, case.kappa, case.dt, case.lid_u, case.ref_xy, case.tris)
+
+
+def _check_location(g, case, sample=None):
+    cell, xi, eta = g.get_points()
+    tris = case.tris.astype(np.int64)
+    if sample is not None:
+        rng = np.random.default_rng(case.N)
+        t = np.sort(rng.choice(tris.shape[0], size=min(sample, tris.shape[0]), replace=False))
+        pid = (6 * t[:, None] + np.arange(6)[None, :]).ravel()
+        x = fo.quadrature_points(case.X0, tris[t])
+    else:
+        pid = np.arange(cell.size)
+        x = fo.quadrature_points(case.X0, tris)
+    ocell, oxi, oeta = fo.locate_brute_force(x, case.N)
+    assert np.array_equal(cell[pid], ocell)
+    assert np.array_equal(xi[pid], oxi) and np.array_equal(eta[pid], oeta)
+
+
+def _check_coupling(g, case, n_rows=None):
+    """C_f rows against the oracle; with n_rows, only that many sampled solid
+    nodes, each assembled from every triangle that contains it."""
+    rows, cols, vals = g.get_coupling()
+    grid = fo.FluidGrid(case.N)
+    tris = case.tris.astype(np.int64)
+    ns = case.ref_xy.shape[0]
+    if n_rows is None:
+        pick = np.arange(ns)
+        sub = tris
+    else:
+        rng = np.random.default_rng(case.N + 1)
+        pick = np.sort(rng.choice(ns, size=n_rows, replace=False))
+        mask = np.zeros(ns, dtype=bool)
+        mask[pick] = True
+        sub = tris[mask[tris].any(axis=1)]
+    C, _ = fo.assemble_coupling(grid, case.ref_xy, sub, case.X0)
+    C = C.tocsc()[:, grid.interior_nodes].tocsr()[pick]
+    keep = np.isin(rows, pick)
+    G = sp.coo_matrix((vals[keep], (np.searchsorted(pick, rows[keep]), np.searchsorted(grid.interior_nodes,
+                                                                                      cols[keep]))),
+                      shape=C.shape).tocsr()
+    assert abs(G - C).max() <= 1e-13 * abs(C).max()
+    # partition of unity: every rule point sees a full Q2 partition of unity,
+    # so a row of C_f sums to the row of the P1 mass matrix, |T|/3 per triangle
+    Cs, _ = fo.assemble_solid(case.ref_xy, tris, case.kappa)
+    row_sum = np.bincount(rows, weights=vals, minlength=ns)[pick]
+    mass = np.asarray(Cs.sum(axis=1)).ravel()[pick]
+    assert np.max(np.abs(row_sum - mass)) <= 1e-12 * np.max(mass)
+
+
+def _check_operator_rhs(g, case, o):
+    K, rhs, _ = o.system(case.u0, case.X0)
+    q = oracle_to_gpu_perm(o, g)
+    rng = np.random.default_rng(5)
+    x = rng.standard_normal(K.shape[0])
+    y_ref = (K @ x)[q]
+    assert rel(g.apply_operator(x[q], precision=0), y_ref) < 1e-13
+    assert rel(g.apply_operator(x[q], precision=1), y_ref) < 1e-5
+    assert rel(g.get_rhs(), rhs[q]) < 1e-13
+
+
+def _check_step(g, case, o):
+    info = g.step()
+    assert info.status == 0 and info.rel_residual <= RTOL
+    u, p, X, lam = g.get_state()
+    assert o.relative_residual(case.u0, case.X0, u, p, X, lam) <= RTOL * (1 + 1e-6)
+    return info
+
+
+def test_cavity128_bench_configuration(fsi):
+    """The bench workload itself: N = 128 lid-driven cavity, disk of 7776
+    triangles, kappa = 1e3, nu = 0.01, dt = 1e-3."""
+    case = fi.config1()
+    g = _bench_problem(fsi, case)
+    g.assemble_step()
+    _check_location(g, case)
+    _check_coupling(g, case)
+    o = _oracle(case)
+    _check_operator_rhs(g, case, o)
+    _check_step(g, case, o)
+    g.close()
+
+
+@pytest.mark.parametrize("N", [64, 256, 512])
+def test_ellipse_sweep_size(fsi, N):
+    """Size sweep members (ellipse, m = ceil(0.4 N)) with the bench
+    preconditioner; full comparison of everything before the solve."""
+    case = fi.config2(N)
+    g = _bench_problem(fsi, case)
+    g.assemble_step()
+    _check_location(g, case, sample=None if N <= 256 else 40000)
+    _check_coupling(g, case, n_rows=None if N <= 256 else 4000)
+    o = _oracle(case)
+    _check_operator_rhs(g, case, o)
+    _check_step(g, case, o)
+    g.close()
+
+
+@pytest.mark.parametrize("label,precond,stokes_its", bench.SWEEP_VARIANTS)
+def test_ellipse64_every_sweep_preconditioner(fsi, label, precond, stokes_its):
+    """Each preconditioner the sweep times reaches the tolerance in the
+    oracle's operator."""
+    case = fi.config2(64)
+    g = _bench_problem(fsi, case, precond=precond, stokes_its=stokes_its, max_it=bench.SWEEP_MAX_IT)
+    _check_step(g, case, _oracle(case))
+    g.close()
+
+
+def test_ellipse1024_sampled(fsi):
+    """The largest sweep size (11.6 M unknowns, 1 M solid triangles): sampled
+    point locations and C_f rows against the oracle, and a converged step."""
+    case = fi.config2(1024)
+    g = _bench_problem(fsi, case)
+    g.assemble_step()
+    _check_location(g, case, sample=40000)
+    _check_coupling(g, case, n_rows=4000)
+    info = g.solve_step()
+    assert info.status == 0 and info.rel_residual <= RTOL
+    g.close()

@@ -94,11 +94,14 @@ def test_operator_and_rhs(fsi, name):
         g.close()
 
 
-@pytest.mark.parametrize("precond", [0, 1])
+@pytest.mark.parametrize("precond,stokes_its", [(0, 1), (1, 1), (2, 1), (1, 4), (2, 8)])
 @pytest.mark.parametrize("name", list(CASES))
-def test_one_step_fp64_matches_oracle(fsi, name, precond):
+def test_one_step_fp64_matches_oracle(fsi, name, precond, stokes_its):
+    """Every preconditioner (block-diagonal, lower and upper block-triangular,
+    with one V-cycle pair or inner Richardson steps on the Stokes block)
+    gives the oracle's solution of Eq. (matrix)."""
     case = CASES[name]()
-    g = fsi.problem_from_case(case, precision=0, precond=precond, rtol=1e-12)
+    g = fsi.problem_from_case(case, precision=0, precond=precond, rtol=1e-12, stokes_its=stokes_its)
     info = g.step()
     assert info.rel_residual <= 1e-12
     u, p, X, lam = g.get_state()
@@ -112,12 +115,13 @@ def test_one_step_fp64_matches_oracle(fsi, name, precond):
     g.close()
 
 
+@pytest.mark.parametrize("precond,stokes_its", [(1, 1), (2, 8)])
 @pytest.mark.parametrize("name", list(CASES))
-def test_one_step_mixed_precision(fsi, name):
+def test_one_step_mixed_precision(fsi, name, precond, stokes_its):
     """FP32 operators and preconditioner inside FP64 refinement reach the
     same 1e-8 residual; the error against the FP64 oracle is reported."""
     case = CASES[name]()
-    g = fsi.problem_from_case(case, precision=1, rtol=1e-8)
+    g = fsi.problem_from_case(case, precision=1, rtol=1e-8, precond=precond, stokes_its=stokes_its)
     info = g.step()
     assert info.rel_residual <= 1e-8
     u, p, X, lam = g.get_state()
