@@ -92,6 +92,10 @@ typedef struct fsi_params {
                           preconditioner application, each one V-cycle pair;
                           0 = 1 (the one-shot approximation) */
     double stokes_omega; /* damping of the Richardson corrections after the first; 0 = 1 */
+    int    mg_cluster; /* 0: the coarse multigrid levels whose operators fit in the
+                          shared memory of one thread-block cluster run as one
+                          cluster launch per V-cycle (same arithmetic); -1: one
+                          kernel launch per phase on every level */
 } fsi_params;
 
 /* Solid reference mesh (the body at t = 0, P1 triangles, counter-clockwise). */

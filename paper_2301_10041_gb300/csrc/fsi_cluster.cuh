@@ -1,0 +1,292 @@
+// Cluster-resident coarse levels of the geometric multigrid V-cycle.
+//
+// The coarse part of a V-cycle (Section 5: one V-cycle with Chebyshev-Jacobi
+// smoothing approximates each inner fluid solve) is a chain of tiny,
+// dependent sparse products; as separate launches each one costs a kernel
+// node and three dependent memory round trips.  Here the levels whose
+// operators fit in the shared memory of one thread-block cluster run as ONE
+// launch: every CTA of the cluster copies its slice of the level operators
+// (sliced ELL, its own block rows) into shared memory once, keeps its part of
+// every level vector in shared memory, gathers the vector entries of other
+// CTAs through distributed shared memory, and separates dependent phases by
+// hardware cluster barriers.  The arithmetic of each phase is the same as in
+// the per-level kernels (k_sell modes CHEB, CHEB0, AXPBY, INIT).
+#pragma once
+#include <cooperative_groups.h>
+
+#include "fsi_kernels.cuh"
+
+namespace fsi {
+
+namespace cg = cooperative_groups;
+
+constexpr int kClMaxLevels = 6;
+constexpr int kClMaxDeg = 8;
+constexpr int kClThreads = 1024;
+constexpr int kClColBits = 20;   // packed column: (owner CTA << 20) | block row inside the owner
+constexpr int kClColMask = (1 << kClColBits) - 1;
+
+// One sliced-ELL matrix as held by one CTA: byte offsets of its arrays in the
+// CTA's shared memory.  Slot (s, k, r) = soff[s] + 8k + r over the CTA's own
+// slices; len per own block row; col packed as above.
+struct ClMat {
+  int soff = -1, len = -1, col = -1, val = -1;
+};
+
+template <class T>
+struct ClLevel {
+  int nrows = 0, nsl = 0;  // block rows and 8-row slices of the whole level
+  ClMat A;                 // level operator (absent on the coarsest level)
+  ClMat P;                 // prolongation from the next coarser level (rows here)
+  ClMat R;                 // restriction from the next finer level (rows here)
+  int dinv = -1;           // byte offsets of per-unknown arrays over the CTA's rows
+  int x = -1, x2 = -1, b = -1, r = -1, d = -1;
+  T c0 = 0, c1[kClMaxDeg] = {}, c2[kClMaxDeg] = {};
+};
+
+template <class T>
+struct ClArgs {
+  int nlev = 0;            // cluster levels; the last one is solved by the dense inverse
+  int degree = 2;          // Chebyshev steps per smoothing
+  int csize = 16;          // CTAs per cluster
+  int blob_bytes = 0;      // bytes of operator data per CTA (multiple of 16)
+  size_t blob_stride = 0;  // in uint4 between consecutive CTAs' data
+  const uint4* blob = nullptr;
+  int gmap = -1;           // coarsest level: packed owner of every block row
+  int gbuf = -1;           // coarsest level: gathered right-hand side
+  const T* dense_inv = nullptr;
+  int dense_n = 0;
+  const T* in_b = nullptr; // right-hand side of the top cluster level (global)
+  T* out_x = nullptr;      // its V-cycle result (global)
+  ClLevel<T> lv[kClMaxLevels];
+};
+
+// slices [s0, s1) of a level owned by CTA `rank` (the host packs columns with
+// the same rule)
+__host__ __device__ inline void cl_own(int nsl, int rank, int csize, int& s0, int& s1) {
+  s0 = (int)(((long long)nsl * rank) / csize);
+  s1 = (int)(((long long)nsl * (rank + 1)) / csize);
+}
+
+template <class T>
+__device__ __forceinline__ T* cl_ptr(unsigned char* sm, int off) {
+  return reinterpret_cast<T*>(sm + off);
+}
+
+// One phase: for every own block row of M, acc = M x (x gathered from the
+// owners' shared memory), then the epilogue of MODE on own rows:
+//   AXPBY: y = alpha acc + beta z          CHEB : d = c1 d + c2 dinv (z - acc); y = xown + d
+//   CHEB0: d = c2 dinv (z - acc); y = xown + d
+//   INIT : y = alpha acc + beta z; d = xo = c2 dinv y
+// Vector arguments are byte offsets (-1 = absent); they are the same in
+// every CTA of the cluster.
+template <class T, int BR, int BC, bool KRON, int NV, int MODE>
+__device__ __forceinline__ void cl_phase(unsigned char* sm, const cg::cluster_group& cl, const ClMat& M, int nrows,
+                                         int nsl, int rank, int csize, int xsrc, int xown, int y, int z, int d,
+                                         int dinv, int xo, T alpha, T beta, T c1, T c2) {
+  int s0, s1;
+  cl_own(nsl, rank, csize, s0, s1);
+  const int nloc = s1 - s0;
+  const int* __restrict__ soff = cl_ptr<const int>(sm, M.soff);
+  const int* __restrict__ len = cl_ptr<const int>(sm, M.len);
+  const int* __restrict__ col = cl_ptr<const int>(sm, M.col);
+  const T* __restrict__ val = cl_ptr<const T>(sm, M.val);
+  T* xs = cl_ptr<T>(sm, xsrc);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int t = lane >> 3;
+  for (int sl = warp; sl < nloc; sl += nw) {
+    const int rl = sl * kSliceRows + (lane & 7);
+    const bool live = s0 * kSliceRows + rl < nrows;
+    T acc[BR];
+#pragma unroll
+    for (int i = 0; i < BR; ++i) acc[i] = 0;
+    if (live) {
+      const int base = soff[sl] + (lane & 7);
+      const int n = len[rl];
+      for (int k0 = t; k0 < n; k0 += 2 * kRowThreads) {
+        int c[2];
+        const T* xr[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const int k = k0 + u * kRowThreads;
+          c[u] = (k < n) ? col[base + (k << 3)] : -1;
+          xr[u] = (c[u] >= 0) ? cl.map_shared_rank(xs, (unsigned)(c[u] >> kClColBits)) + (size_t)(c[u] & kClColMask) * BC
+                              : nullptr;
+        }
+        T xv[2][BC];
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+#pragma unroll
+          for (int j = 0; j < BC; ++j) xv[u][j] = xr[u] ? xr[u][j] : (T)0;
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          if (c[u] < 0) continue;
+          const int slot = base + ((k0 + u * kRowThreads) << 3);
+          if constexpr (KRON) {
+            const T v = val[slot];
+#pragma unroll
+            for (int i = 0; i < BR; ++i) acc[i] += v * xv[u][i];
+          } else {
+#pragma unroll
+            for (int i = 0; i < BR; ++i)
+#pragma unroll
+              for (int j = 0; j < BC; ++j) acc[i] += val[(size_t)slot * NV + i * BC + j] * xv[u][j];
+          }
+        }
+      }
+    }
+    row_reduce<T, BR>(acc);
+    if (!live || t != 0) continue;
+#pragma unroll
+    for (int i = 0; i < BR; ++i) {
+      const int q = rl * BR + i;
+      if (MODE == MODE_AXPBY) {
+        T out = alpha * acc[i];
+        if (z >= 0) out += beta * cl_ptr<T>(sm, z)[q];
+        cl_ptr<T>(sm, y)[q] = out;
+      } else if (MODE == MODE_CHEB || MODE == MODE_CHEB0) {
+        const T res = cl_ptr<T>(sm, z)[q] - acc[i];
+        T dn = c2 * cl_ptr<T>(sm, dinv)[q] * res;
+        if (MODE == MODE_CHEB) dn = c1 * cl_ptr<T>(sm, d)[q] + dn;
+        cl_ptr<T>(sm, d)[q] = dn;
+        cl_ptr<T>(sm, y)[q] = cl_ptr<T>(sm, xown)[q] + dn;
+      } else {  // MODE_INIT
+        T tt = alpha * acc[i];
+        if (z >= 0) tt += beta * cl_ptr<T>(sm, z)[q];
+        cl_ptr<T>(sm, y)[q] = tt;
+        const T dn = c2 * cl_ptr<T>(sm, dinv)[q] * tt;
+        cl_ptr<T>(sm, d)[q] = dn;
+        cl_ptr<T>(sm, xo)[q] = dn;
+      }
+    }
+  }
+}
+
+// The V-cycle from the top cluster level down to the dense coarsest level and
+// back, in the order of the per-level host code: on each level (degree - 1)
+// Chebyshev steps from x = d = c0 D^-1 b, residual, restriction (which
+// initialises the coarser smoother), the coarser cycle, prolongation and
+// correction, then `degree` Chebyshev steps.  B: unknowns per block row (2
+// velocity, 3 pressure); TKRON: transfers act on components alike (Q2
+// velocity) instead of as full B x B blocks (P1disc pressure).
+template <class T, int B, bool TKRON>
+__global__ void __launch_bounds__(kClThreads, 1) k_vcycle_cluster(const __grid_constant__ ClArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  const cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank();
+  const int cs = a.csize;
+  constexpr int TNV = TKRON ? 1 : B * B;
+  {  // stage this CTA's operators
+    const uint4* __restrict__ src = a.blob + (size_t)rank * a.blob_stride;
+    uint4* dst = reinterpret_cast<uint4*>(sm);
+    const int n16 = a.blob_bytes >> 4;
+    for (int i = threadIdx.x; i < n16; i += blockDim.x) dst[i] = src[i];
+  }
+  __syncthreads();
+  {  // top level: own part of b, x = d = c0 D^-1 b
+    const ClLevel<T>& L = a.lv[0];
+    int s0, s1;
+    cl_own(L.nsl, rank, cs, s0, s1);
+    const int r0 = s0 * kSliceRows, r1 = min(s1 * kSliceRows, L.nrows);
+    const int n = max(r1 - r0, 0) * B;
+    T* b = cl_ptr<T>(sm, L.b);
+    T* x = cl_ptr<T>(sm, L.x);
+    T* d = cl_ptr<T>(sm, L.d);
+    const T* dinv = cl_ptr<const T>(sm, L.dinv);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const T v = a.in_b[(size_t)r0 * B + i];
+      b[i] = v;
+      const T tv = L.c0 * dinv[i] * v;
+      x[i] = tv;
+      d[i] = tv;
+    }
+  }
+  cl.sync();
+  int cur[kClMaxLevels], oth[kClMaxLevels];
+  const int last = a.nlev - 1;
+  for (int l = 0; l < last; ++l) {
+    const ClLevel<T>& L = a.lv[l];
+    cur[l] = L.x;
+    oth[l] = L.x2;
+    for (int i = 1; i < a.degree; ++i) {
+      cl_phase<T, B, B, false, B * B, MODE_CHEB>(sm, cl, L.A, L.nrows, L.nsl, rank, cs, cur[l], cur[l], oth[l], L.b,
+                                                   L.d, L.dinv, -1, T(0), T(0), L.c1[i - 1], L.c2[i - 1]);
+      const int tmp = cur[l]; cur[l] = oth[l]; oth[l] = tmp;
+      cl.sync();
+    }
+    cl_phase<T, B, B, false, B * B, MODE_AXPBY>(sm, cl, L.A, L.nrows, L.nsl, rank, cs, cur[l], -1, L.r, L.b, -1, -1,
+                                                  -1, T(-1), T(1), T(0), T(0));
+    cl.sync();
+    const ClLevel<T>& C = a.lv[l + 1];
+    if (l + 1 < last)
+      cl_phase<T, B, B, TKRON, TNV, MODE_INIT>(sm, cl, C.R, C.nrows, C.nsl, rank, cs, L.r, -1, C.b, -1, C.d, C.dinv,
+                                               C.x, T(1), T(0), T(0), C.c0);
+    else
+      cl_phase<T, B, B, TKRON, TNV, MODE_AXPBY>(sm, cl, C.R, C.nrows, C.nsl, rank, cs, L.r, -1, C.b, -1, -1, -1, -1,
+                                                T(1), T(0), T(0), T(0));
+    cl.sync();
+  }
+  {  // coarsest level: gather its right-hand side, own rows of (dense inverse) b
+    const ClLevel<T>& C = a.lv[last];
+    const int n = a.dense_n;
+    const int* __restrict__ gmap = cl_ptr<const int>(sm, a.gmap);
+    T* g = cl_ptr<T>(sm, a.gbuf);
+    T* cb = cl_ptr<T>(sm, C.b);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const int row = i / B, comp = i - row * B;
+      const int c = gmap[row];
+      const T* src = cl.map_shared_rank(cb, (unsigned)(c >> kClColBits));
+      g[i] = src[(size_t)(c & kClColMask) * B + comp];
+    }
+    __syncthreads();
+    int s0, s1;
+    cl_own(C.nsl, rank, cs, s0, s1);
+    const int r0 = s0 * kSliceRows, r1 = min(s1 * kSliceRows, C.nrows);
+    const int nown = max(r1 - r0, 0) * B;
+    T* x = cl_ptr<T>(sm, C.x);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int i = warp; i < nown; i += nw) {
+      const T* __restrict__ arow = a.dense_inv + (size_t)(r0 * B + i) * n;
+      T s0a = 0, s1a = 0;
+      int j = lane;
+      for (; j + 32 < n; j += 64) {
+        s0a += arow[j] * g[j];
+        s1a += arow[j + 32] * g[j + 32];
+      }
+      if (j < n) s0a += arow[j] * g[j];
+      T sum = s0a + s1a;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o);
+      if (lane == 0) x[i] = sum;
+    }
+    cur[last] = C.x;
+  }
+  cl.sync();
+  for (int l = last - 1; l >= 0; --l) {
+    const ClLevel<T>& L = a.lv[l];
+    cl_phase<T, B, B, TKRON, TNV, MODE_AXPBY>(sm, cl, L.P, L.nrows, L.nsl, rank, cs, cur[l + 1], -1, cur[l], cur[l], -1,
+                                              -1, -1, T(1), T(1), T(0), T(0));
+    cl.sync();
+    for (int i = 0; i < a.degree; ++i) {
+      if (i == 0)
+        cl_phase<T, B, B, false, B * B, MODE_CHEB0>(sm, cl, L.A, L.nrows, L.nsl, rank, cs, cur[l], cur[l], oth[l],
+                                                      L.b, L.d, L.dinv, -1, T(0), T(0), T(0), L.c0);
+      else
+        cl_phase<T, B, B, false, B * B, MODE_CHEB>(sm, cl, L.A, L.nrows, L.nsl, rank, cs, cur[l], cur[l], oth[l], L.b,
+                                                     L.d, L.dinv, -1, T(0), T(0), L.c1[i - 1], L.c2[i - 1]);
+      const int tmp = cur[l]; cur[l] = oth[l]; oth[l] = tmp;
+      cl.sync();
+    }
+  }
+  {  // the top level's result to global memory (no remote access follows the last barrier)
+    const ClLevel<T>& L = a.lv[0];
+    int s0, s1;
+    cl_own(L.nsl, rank, cs, s0, s1);
+    const int r0 = s0 * kSliceRows, r1 = min(s1 * kSliceRows, L.nrows);
+    const int n = max(r1 - r0, 0) * B;
+    const T* x = cl_ptr<const T>(sm, cur[0]);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) a.out_x[(size_t)r0 * B + i] = x[i];
+  }
+}
+
+}  // namespace fsi

@@ -23,6 +23,8 @@
 #include <vector>
 
 #include "../../include/fsi.h"
+#include "fsi_cluster.cuh"
+#include "fsi_cluster_host.h"
 #include "fsi_coupling.cuh"
 #include "fsi_internal.h"
 #include "fsi_kernels.cuh"
@@ -177,12 +179,24 @@ struct MGLevel {
   Cheb ch;
 };
 
+// Coarse levels run as one thread-block-cluster launch per V-cycle
+// (fsi_cluster.cuh): levels lc .. last.
+template <class T>
+struct ClusterMG {
+  bool on = false;
+  int lc = 0;
+  size_t smem = 0;
+  ClArgs<T> args;
+};
+
 template <class T>
 struct MG {
   std::vector<MGLevel<T>> lv;
   T* coarse_inv = nullptr;
   int coarse_n = 0;
   int degree = 2;
+  bool pressure = false;
+  ClusterMG<T> cl;
 };
 
 constexpr double kChebRatioU = 6.0;   // smoothing interval [hi/ratio, hi]
@@ -192,6 +206,7 @@ template <class T>
 static void build_mg(Arena& ar, const HostSetup& hs, bool pressure, int degree, MG<T>& mg) {
   const int nl = (int)hs.levels.size();
   mg.degree = degree;
+  mg.pressure = pressure;
   mg.lv.resize(nl);
   for (int l = 0; l < nl; ++l) {
     const FluidLevelHost& H = hs.levels[l];
@@ -213,12 +228,91 @@ static void build_mg(Arena& ar, const HostSetup& hs, bool pressure, int degree, 
   mg.coarse_inv = upload_as<T>(ar, pressure ? hs.coarseLinv : hs.coarseAinv);  // row-major
 }
 
+// ------------------------------------------- cluster-resident coarse levels
+constexpr size_t kClSmemCap = 227 * 1024;   // dynamic shared memory per CTA
+
+// The shared-memory limit is a property of the kernel, shared by every
+// problem alive in the process: always raise it to the cap.
+template <class T, int B, bool TKRON>
+static void cluster_kernel_setup() {
+  auto kern = k_vcycle_cluster<T, B, TKRON>;
+  CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kClSmemCap));
+  CK(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+}
+
+template <class T, int B, bool TKRON>
+static int cluster_fits(size_t smem, int csize) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(csize);
+  cfg.blockDim = dim3(kClThreads);
+  cfg.dynamicSmemBytes = smem;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = csize;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, k_vcycle_cluster<T, B, TKRON>, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
+
+// Cluster of 16 CTAs (non-portable size) when the device schedules one,
+// else 8; nothing when neither fits (the per-level kernels run instead).
+template <class T>
+static void setup_cluster(Arena& ar, const HostSetup& hs, MG<T>& mg, bool pressure) {
+  for (int cs : {16, 8}) {
+    auto viable = [&](size_t smem) {
+      if (ar.count_only) return true;
+      if (pressure) {
+        cluster_kernel_setup<T, 3, false>();
+        return cluster_fits<T, 3, false>(smem, cs) > 0;
+      }
+      cluster_kernel_setup<T, 2, true>();
+      return cluster_fits<T, 2, true>(smem, cs) > 0;
+    };
+    if (build_cluster<T>(ar, hs, pressure, mg, cs, kClSmemCap, viable)) return;
+  }
+}
+
+template <class T>
+static void cluster_launch(MG<T>& mg, const T* in_b, T* out_x, cudaStream_t s) {
+  ClArgs<T> a = mg.cl.args;
+  a.in_b = in_b;
+  a.out_x = out_x;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(a.csize);
+  cfg.blockDim = dim3(kClThreads);
+  cfg.dynamicSmemBytes = mg.cl.smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = a.csize;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  const cudaError_t e = mg.pressure ? cudaLaunchKernelEx(&cfg, k_vcycle_cluster<T, 3, false>, a)
+                                    : cudaLaunchKernelEx(&cfg, k_vcycle_cluster<T, 2, true>, a);
+  if (e != cudaSuccess) throw CudaError(e, "cudaLaunchKernelEx (cluster V-cycle)");
+}
+
 // Level l input: L.b, with L.x = L.d = c0 dinv b already set (l < last).
-// Result of the level is written to `out` (if given) or returned.
+// Result of the level is written to `out` (if given) or returned.  Levels
+// from mg.cl.lc down run as one cluster launch when mg.cl.on.
 template <class T>
 static T* vcycle(MG<T>& mg, int l, cudaStream_t s, T* out) {
   const int last = (int)mg.lv.size() - 1;
   MGLevel<T>& L = mg.lv[l];
+  if (mg.cl.on && l == mg.cl.lc) {
+    T* dst = out ? out : L.x;
+    cluster_launch<T>(mg, L.b, dst, s);
+    return dst;
+  }
   if (l == last) {
     launch(k_dense_mv<T>, nblk(mg.coarse_n, 8), 256, 0, s, mg.coarse_n, mg.coarse_inv, L.b, out ? out : L.x);
     return out ? out : L.x;
@@ -235,7 +329,7 @@ static T* vcycle(MG<T>& mg, int l, cudaStream_t s, T* out) {
   }
   sell_launch(L.A, MODE_AXPBY, axpby<T>(xc, L.r, L.b, (T)-1, (T)1), s);
   MGLevel<T>& C = mg.lv[l + 1];
-  if (l + 1 == last) {
+  if (l + 1 == last || (mg.cl.on && l + 1 == mg.cl.lc)) {  // the coarser cycle initialises itself
     sell_launch(L.R, MODE_AXPBY, axpby<T>(L.r, C.b, nullptr, (T)1, (T)0), s);
   } else {
     SpmvArgs<T> a = axpby<T>(L.r, C.b, nullptr, (T)1, (T)0);
@@ -858,6 +952,7 @@ static void check_params(const fsi_params& p, int n_nodes, int n_tris) {
   if (p.precond < 0 || p.precond > 3) throw std::invalid_argument("precond");
   if (p.precision != 0 && p.precision != 1) throw std::invalid_argument("precision");
   if (n_nodes < 3 || n_tris < 1) throw std::invalid_argument("solid mesh");
+  if (p.mg_cluster != 0 && p.mg_cluster != -1) throw std::invalid_argument("mg_cluster");
 }
 
 static fsi_params with_defaults(fsi_params p) {
@@ -881,6 +976,10 @@ static void build_prec(Problem& P, Prec<T>& pr, const FullOp<T>& op, bool alloc_
   Arena& ar = P.ar;
   build_mg<T>(ar, P.hs, false, P.prm.mg_degree, pr.mgU);
   build_mg<T>(ar, P.hs, true, P.prm.mg_degree, pr.mgP);
+  if (P.prm.mg_cluster == 0) {
+    setup_cluster<T>(ar, P.hs, pr.mgU, false);
+    setup_cluster<T>(ar, P.hs, pr.mgP, true);
+  }
   pr.op = op;
   pr.Cs = upload_sell<T>(ar, to_sell(P.hs.Cs));
   pr.As = upload_sell<T>(ar, to_sell(P.hs.As));
