@@ -215,8 +215,11 @@ int fsi_graph_kernel_counts(const fsi_problem* p, int* counts);
  * L2, on the current data of the problem.  which: 0 full operator in FP32
  * (precision 1 only), 1 full operator in FP64 (residual form), 2 finest
  * velocity Chebyshev smoothing step in FP32 (precision 1 only), 3 the same in
- * FP64.  avg_ms: mean launch time; bytes: algorithmic bytes of one launch
- * (stored blocks and indices without padding, each vector once).  Allocates
+ * FP64; 4 and 5 (precision 1 only): one whole V-cycle on the velocity /
+ * pressure-Laplacian hierarchy in FP32, with L2 left warm as inside a solve
+ * (bytes = 0: a latency figure).  avg_ms: mean launch time; bytes:
+ * algorithmic bytes of one launch (stored blocks and indices without
+ * padding, each vector once).  Allocates
  * and frees a 256 MiB scratch buffer. */
 int fsi_time_kernel(fsi_problem* p, int which, int reps, double* avg_ms, double* bytes);
 

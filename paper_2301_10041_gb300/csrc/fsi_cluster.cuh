@@ -73,6 +73,53 @@ __device__ __forceinline__ T* cl_ptr(unsigned char* sm, int off) {
   return reinterpret_cast<T*>(sm + off);
 }
 
+// address of the same shared-memory location in CTA `rank` of the cluster
+__device__ __forceinline__ unsigned cl_map(unsigned saddr, unsigned rank) {
+  unsigned r;
+  asm("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
+  return r;
+}
+
+// BC consecutive values at a shared::cluster address (ordered after the
+// preceding cluster barrier, which is itself a volatile asm with a memory
+// clobber)
+template <class T, int BC>
+__device__ __forceinline__ void cl_load(unsigned addr, T* v) {
+  if constexpr (sizeof(T) == 4 && BC == 2) {
+    float a, b;
+    asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(a), "=f"(b) : "r"(addr));
+    v[0] = a; v[1] = b;
+  } else if constexpr (sizeof(T) == 8 && BC == 2) {
+    double a, b;
+    asm volatile("ld.shared::cluster.v2.f64 {%0, %1}, [%2];" : "=d"(a), "=d"(b) : "r"(addr));
+    v[0] = a; v[1] = b;
+  } else {
+#pragma unroll
+    for (int j = 0; j < BC; ++j) {
+      if constexpr (sizeof(T) == 4) {
+        float a;
+        asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(a) : "r"(addr + 4u * j));
+        v[j] = a;
+      } else {
+        double a;
+        asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(a) : "r"(addr + 8u * j));
+        v[j] = a;
+      }
+    }
+  }
+}
+
+template <class T, int NV>
+__device__ __forceinline__ void cl_block(const T* __restrict__ p, T* v) {
+  if constexpr (NV == 4 && sizeof(T) == 4) {
+    const float4 q = *reinterpret_cast<const float4*>(p);
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+  } else {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) v[i] = p[i];
+  }
+}
+
 // One phase: for every own block row of M, acc = M x (x gathered from the
 // owners' shared memory), then the epilogue of MODE on own rows:
 //   AXPBY: y = alpha acc + beta z          CHEB : d = c1 d + c2 dinv (z - acc); y = xown + d
@@ -91,9 +138,10 @@ __device__ __forceinline__ void cl_phase(unsigned char* sm, const cg::cluster_gr
   const int* __restrict__ len = cl_ptr<const int>(sm, M.len);
   const int* __restrict__ col = cl_ptr<const int>(sm, M.col);
   const T* __restrict__ val = cl_ptr<const T>(sm, M.val);
-  T* xs = cl_ptr<T>(sm, xsrc);
+  const unsigned xs = (unsigned)__cvta_generic_to_shared(sm + xsrc);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int t = lane >> 3;
+  constexpr int U = 4;   // entries in flight per thread (one round for most rows)
   for (int sl = warp; sl < nloc; sl += nw) {
     const int rl = sl * kSliceRows + (lane & 7);
     const bool live = s0 * kSliceRows + rl < nrows;
@@ -103,23 +151,27 @@ __device__ __forceinline__ void cl_phase(unsigned char* sm, const cg::cluster_gr
     if (live) {
       const int base = soff[sl] + (lane & 7);
       const int n = len[rl];
-      for (int k0 = t; k0 < n; k0 += 2 * kRowThreads) {
-        int c[2];
-        const T* xr[2];
+      for (int k0 = t; k0 < n; k0 += U * kRowThreads) {
+        int c[U];
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
+        for (int u = 0; u < U; ++u) {
           const int k = k0 + u * kRowThreads;
           c[u] = (k < n) ? col[base + (k << 3)] : -1;
-          xr[u] = (c[u] >= 0) ? cl.map_shared_rank(xs, (unsigned)(c[u] >> kClColBits)) + (size_t)(c[u] & kClColMask) * BC
-                              : nullptr;
         }
-        T xv[2][BC];
+        T xv[U][BC];
 #pragma unroll
-        for (int u = 0; u < 2; ++u)
+        for (int u = 0; u < U; ++u) {
+          if (c[u] >= 0) {
+            const unsigned addr = cl_map(xs + (unsigned)((c[u] & kClColMask) * BC * (int)sizeof(T)),
+                                         (unsigned)(c[u] >> kClColBits));
+            cl_load<T, BC>(addr, xv[u]);
+          } else {
 #pragma unroll
-          for (int j = 0; j < BC; ++j) xv[u][j] = xr[u] ? xr[u][j] : (T)0;
+            for (int j = 0; j < BC; ++j) xv[u][j] = 0;
+          }
+        }
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
+        for (int u = 0; u < U; ++u) {
           if (c[u] < 0) continue;
           const int slot = base + ((k0 + u * kRowThreads) << 3);
           if constexpr (KRON) {
@@ -127,10 +179,12 @@ __device__ __forceinline__ void cl_phase(unsigned char* sm, const cg::cluster_gr
 #pragma unroll
             for (int i = 0; i < BR; ++i) acc[i] += v * xv[u][i];
           } else {
+            T v[NV];
+            cl_block<T, NV>(val + (size_t)slot * NV, v);
 #pragma unroll
             for (int i = 0; i < BR; ++i)
 #pragma unroll
-              for (int j = 0; j < BC; ++j) acc[i] += val[(size_t)slot * NV + i * BC + j] * xv[u][j];
+              for (int j = 0; j < BC; ++j) acc[i] += v[i * BC + j] * xv[u][j];
           }
         }
       }
@@ -176,11 +230,15 @@ __global__ void __launch_bounds__(kClThreads, 1) k_vcycle_cluster(const __grid_c
   const int rank = (int)cl.block_rank();
   const int cs = a.csize;
   constexpr int TNV = TKRON ? 1 : B * B;
-  {  // stage this CTA's operators
+  {  // stage this CTA's operators: every 16-byte copy is issued before the
+     // single wait, so the whole image is in flight at once
     const uint4* __restrict__ src = a.blob + (size_t)rank * a.blob_stride;
-    uint4* dst = reinterpret_cast<uint4*>(sm);
+    const unsigned dst = (unsigned)__cvta_generic_to_shared(sm);
     const int n16 = a.blob_bytes >> 4;
-    for (int i = threadIdx.x; i < n16; i += blockDim.x) dst[i] = src[i];
+    for (int i = threadIdx.x; i < n16; i += blockDim.x)
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst + 16u * (unsigned)i), "l"(src + i) : "memory");
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
   }
   __syncthreads();
   {  // top level: own part of b, x = d = c0 D^-1 b

@@ -464,12 +464,6 @@ static void solid_launch(Problem& P, Prec<T>& pr, cudaStream_t s) {
   cheb_rest(zL);
 }
 
-// One application z = P^-1 v of the block preconditioner (Section 5), input
-// pr.vin, output pr.zw.  A_11^-1 is approximated by the upper block-
-// triangular Stokes preconditioner: p = -S^-1 v_p with the Cahouet-Chabard
-// Schur approximation S^-1 ~ nu M_p^-1 + (rho/dt) L_p^-1 (one V-cycle on the
-// pressure Laplacian L_p = B diag(M_f)^-1 B^T), then u = A_f^-1 (v_u + B^T p)
-// by one V-cycle with Chebyshev-Jacobi smoothing on the Q2 hierarchy.
 // C_f^T applied to the multiplier part: y_u = z_u - C_f^T lambda (CSR over interior nodes)
 template <class T>
 __global__ void k_cft_sub(int nU, const int* __restrict__ ptr, const int* __restrict__ col, const T* __restrict__ val,
@@ -488,50 +482,54 @@ __global__ void k_cft_sub(int nU, const int* __restrict__ ptr, const int* __rest
   y[2 * r + 1] = a1;
 }
 
-// One application z = P^-1 v of the block preconditioner (Section 5), input
-// pr.vin, output pr.zw.  A_11^-1 is approximated by the upper block-
-// triangular Stokes preconditioner: p = -S^-1 v_p with the Cahouet-Chabard
-// Schur approximation S^-1 ~ nu M_p^-1 + (rho/dt) L_p^-1 (one V-cycle on the
-// pressure Laplacian L_p = B diag(M_f)^-1 B^T), then u = A_f^-1 (v_u + B^T p)
-// by one V-cycle with Chebyshev-Jacobi smoothing on the Q2 hierarchy.
-//   precond 0: diag(A_11, A_22)                      (block-diagonal)
-//   precond 1: [[A_11, 0], [A_21, A_22]]             (block lower-triangular)
-//   precond 2: [[A_11, A_12], [0, A_22]]             (block upper-triangular:
-//              the solid block first, then the fluid with v_u - C_f^T z_l)
-// One application of the upper block-triangular Stokes approximation
-// [[A_f, -B^T], [0, -S]]^-1 to (in_u, in_p): p = -S^-1 in_p with the
+// Pressure part of one application of the upper block-triangular Stokes
+// approximation [[A_f, -B^T], [0, -S]]^-1: p = -S^-1 in_p with the
 // Cahouet-Chabard Schur approximation S^-1 ~ nu M_p^-1 + (rho/dt) L_p^-1
-// (one V-cycle on the pressure Laplacian L_p = B diag(M_f)^-1 B^T), then
-// u = A_f^-1 (in_u + B^T p) by one V-cycle with Chebyshev-Jacobi smoothing on
-// the Q2 hierarchy.  With split = true the pressure part runs on stream s4
-// beside the velocity part and the B^T p term is dropped (block-diagonal).
+// (one V-cycle on the pressure Laplacian L_p = B diag(M_f)^-1 B^T).
+template <class T>
+static void stokes_pressure(Problem& P, Prec<T>& pr, const T* in_p, T* out_p, cudaStream_t s) {
+  const int n3 = 3 * P.nP;
+  MGLevel<T>& L0p = pr.mgP.lv[0];
+  launch(k_cheb_first<T>, nblk(n3, 256), 256, 0, s, n3, in_p, L0p.dinv, (T)L0p.ch.c0, L0p.d, L0p.x, (T)1, L0p.b);
+  T* sp = vcycle<T>(pr.mgP, 0, s, (T*)nullptr);
+  launch(k_schur<T>, nblk(n3, 256), 256, 0, s, n3, in_p, sp, pr.mpinv, (T)P.prm.nu, (T)(P.prm.rho_f / P.prm.dt), out_p);
+}
+
+// Velocity part: u = A_f^-1 (in_u + B^T p) by one V-cycle with
+// Chebyshev-Jacobi smoothing on the Q2 hierarchy (p = nullptr: u = A_f^-1 in_u).
+template <class T>
+static void stokes_velocity(Problem& P, Prec<T>& pr, const T* in_u, const T* p, T* out_u, cudaStream_t s) {
+  MGLevel<T>& L0u = pr.mgU.lv[0];
+  if (p) {
+    SpmvArgs<T> a;
+    a.x = p; a.y = L0u.b; a.z = in_u; a.alpha = -1; a.beta = 1;
+    a.d = L0u.d; a.dinv = L0u.dinv; a.xo = L0u.x; a.c2 = (T)L0u.ch.c0;
+    sell_launch(pr.op.Bt, MODE_INIT, a, s);
+  } else {
+    const int n2 = 2 * P.nU;
+    launch(k_cheb_first<T>, nblk(n2, 256), 256, 0, s, n2, in_u, L0u.dinv, (T)L0u.ch.c0, L0u.d, L0u.x, (T)1, L0u.b);
+  }
+  vcycle(pr.mgU, 0, s, out_u);
+}
+
+// One application of the Stokes approximation to (in_u, in_p): the pressure
+// part, then the velocity part with B^T p.  With split = true the pressure
+// part runs on stream s4 beside the velocity part and the B^T p term is
+// dropped (block-diagonal).
 template <class T>
 static void stokes_apply(Problem& P, Prec<T>& pr, const T* in_u, const T* in_p, T* out_u, T* out_p, cudaStream_t s,
                          bool split) {
-  const int n3 = 3 * P.nP;
-  MGLevel<T>& L0p = pr.mgP.lv[0];
-  MGLevel<T>& L0u = pr.mgU.lv[0];
-  cudaStream_t sp_stream = split ? P.s4 : s;
   if (split) {
     CK(cudaEventRecord(P.ev_fork2, s));
     CK(cudaStreamWaitEvent(P.s4, P.ev_fork2, 0));
-  }
-  launch(k_cheb_first<T>, nblk(n3, 256), 256, 0, sp_stream, n3, in_p, L0p.dinv, (T)L0p.ch.c0, L0p.d, L0p.x, (T)1, L0p.b);
-  T* sp = vcycle<T>(pr.mgP, 0, sp_stream, (T*)nullptr);
-  launch(k_schur<T>, nblk(n3, 256), 256, 0, sp_stream, n3, in_p, sp, pr.mpinv, (T)P.prm.nu, (T)(P.prm.rho_f / P.prm.dt),
-                                                   out_p);
-  if (split) {
+    stokes_pressure(P, pr, in_p, out_p, P.s4);
     CK(cudaEventRecord(P.ev_join2, P.s4));
-    const int n2 = 2 * P.nU;
-    launch(k_cheb_first<T>, nblk(n2, 256), 256, 0, s, n2, in_u, L0u.dinv, (T)L0u.ch.c0, L0u.d, L0u.x, (T)1, L0u.b);
+    stokes_velocity(P, pr, in_u, (const T*)nullptr, out_u, s);
+    CK(cudaStreamWaitEvent(s, P.ev_join2, 0));
   } else {
-    SpmvArgs<T> a;
-    a.x = out_p; a.y = L0u.b; a.z = in_u; a.alpha = -1; a.beta = 1;
-    a.d = L0u.d; a.dinv = L0u.dinv; a.xo = L0u.x; a.c2 = (T)L0u.ch.c0;
-    sell_launch(pr.op.Bt, MODE_INIT, a, s);
+    stokes_pressure(P, pr, in_p, out_p, s);
+    stokes_velocity(P, pr, in_u, (const T*)out_p, out_u, s);
   }
-  vcycle(pr.mgU, 0, s, out_u);
-  if (split) CK(cudaStreamWaitEvent(s, P.ev_join2, 0));
 }
 
 // One application z = P^-1 v of the block preconditioner (Section 5), input
@@ -558,13 +556,24 @@ static void precond_launch(Problem& P, Prec<T>& pr, cudaStream_t s) {
     CK(cudaEventRecord(P.ev_join, P.s3));
   }
   const T* vu = pr.vin;
-  if (pc == 2 || pc == 3) {
+  if (pc == 2) {
+    // the pressure part of the first Stokes application needs only v_p: it
+    // runs beside the solid branch, and only the velocity part waits for z_l
+    stokes_pressure(P, pr, vp, zp, s);
     CK(cudaStreamWaitEvent(s, P.ev_join, 0));
     launch(k_cft_sub<T>, nblk(P.nU, 128), 128, 0, s, P.nU, P.cft_ptr, P.cft_col, pr.op.cft_val, pr.zw + P.offL, pr.vin,
                                                   pr.ru);
     vu = pr.ru;
+    stokes_velocity(P, pr, vu, (const T*)zp, pr.zw, s);
+  } else {
+    if (pc == 3) {
+      CK(cudaStreamWaitEvent(s, P.ev_join, 0));
+      launch(k_cft_sub<T>, nblk(P.nU, 128), 128, 0, s, P.nU, P.cft_ptr, P.cft_col, pr.op.cft_val, pr.zw + P.offL,
+             pr.vin, pr.ru);
+      vu = pr.ru;
+    }
+    stokes_apply(P, pr, vu, vp, pr.zw, zp, s, split);
   }
-  stokes_apply(P, pr, vu, vp, pr.zw, zp, s, split);
   const size_t nf = 2 * (size_t)P.nU + 3 * (size_t)P.nP;
   for (int it = 1; it < pr.stokes_its; ++it) {
     launch(k_stokes_res<T>, pr.op.gU + pr.op.gP, 128, 0, s, pr.op, pr.zw, vu, vp, pr.t);
@@ -1751,7 +1760,7 @@ int fsi_graph_kernel_counts(const fsi_problem* h, int* counts) {
 int fsi_time_kernel(fsi_problem* h, int which, int reps, double* avg_ms, double* bytes) {
   if (!h || !avg_ms || !bytes || reps <= 0) return FSI_ERR_INVALID;
   Problem& P = h->P;
-  if ((which == 0 || which == 2) && P.prm.precision != 1) return FSI_ERR_INVALID;
+  if ((which == 0 || which == 2 || which == 4 || which == 5) && P.prm.precision != 1) return FSI_ERR_INVALID;
   if (which == 3 && P.p64.mgU.lv.empty()) return FSI_ERR_INVALID;  // no FP64 hierarchy in mixed mode
   try {
     // total C_f entries of the last assembly
@@ -1769,7 +1778,7 @@ int fsi_time_kernel(fsi_problem* h, int which, int reps, double* avg_ms, double*
     cudaStream_t s = P.stream;
     const HostBlockMatrix& A0 = P.hs.levels[0].A;
     for (int r = 0; r < reps + 1; ++r) {
-      launch(k_flush, 2 * 152, 512, 0, s, flush_n, fl, (unsigned)r);
+      if (which < 4) launch(k_flush, 2 * 152, 512, 0, s, flush_n, fl, (unsigned)r);
       CK(cudaEventRecord(e0, s));
       switch (which) {
         case 0:  // full operator, FP32 (mixed inner iteration)
@@ -1796,6 +1805,13 @@ int fsi_time_kernel(fsi_problem* h, int which, int reps, double* avg_ms, double*
           a.x = L.x; a.y = L.x2; a.z = L.b; a.d = L.d; a.dinv = L.dinv; a.c1 = 0.5; a.c2 = 0.5;
           sell_launch(L.A, MODE_CHEB, a, s);
           *bytes = sell_bytes<double>(A0) + 6.0 * L.n * sizeof(double);
+          break;
+        }
+        case 4:    // one V-cycle on the Q2 velocity hierarchy, FP32
+        case 5: {  // one V-cycle on the pressure Laplacian hierarchy, FP32
+          MG<float>& mg = (which == 4) ? P.p32.mgU : P.p32.mgP;
+          vcycle<float>(mg, 0, s, mg.lv[0].x2);
+          *bytes = 0;
           break;
         }
         default:
