@@ -76,6 +76,16 @@ struct SpmvArgs {
   const T* dinv = nullptr;
   T* xo = nullptr;
   T c1 = 0, c2 = 0;
+  // MODE_CHEB / MODE_CHEB0 extras (the last smoothing step of a V-cycle):
+  // with sout, s = -(snu * smp * sv + srdt * y) is written to sout (the
+  // Cahouet-Chabard combination of the Schur approximation); with acc,
+  // acc += omega * (s if sout else y) (a Richardson update)
+  const T* sv = nullptr;
+  const T* smp = nullptr;
+  T* sout = nullptr;
+  T snu = 0, srdt = 0;
+  T* acc = nullptr;
+  T omega = 1;
 };
 
 // Sliced ELL with slice height 8 ("SELL-8"): slot(s, k, r) = soff[s] + 8k + r.
@@ -201,16 +211,18 @@ __global__ void __launch_bounds__(128, 16) k_sell(Sell<T> A, SpmvArgs<T> a) {
       T out = a.alpha * acc[i];
       if (a.z) out += a.beta * a.z[r];
       a.y[r] = out;
-    } else if (MODE == MODE_CHEB) {
+    } else if (MODE == MODE_CHEB || MODE == MODE_CHEB0) {
       const T res = a.z[r] - acc[i];
-      const T dn = a.c1 * a.d[r] + a.c2 * a.dinv[r] * res;
+      const T dn = (MODE == MODE_CHEB) ? a.c1 * a.d[r] + a.c2 * a.dinv[r] * res : a.c2 * a.dinv[r] * res;
       a.d[r] = dn;
-      a.y[r] = x[r] + dn;
-    } else if (MODE == MODE_CHEB0) {
-      const T res = a.z[r] - acc[i];
-      const T dn = a.c2 * a.dinv[r] * res;
-      a.d[r] = dn;
-      a.y[r] = x[r] + dn;
+      const T yv = x[r] + dn;
+      a.y[r] = yv;
+      T ov = yv;
+      if (a.sout) {
+        ov = -(a.snu * a.smp[r] * a.sv[r] + a.srdt * yv);
+        a.sout[r] = ov;
+      }
+      if (a.acc) a.acc[r] += a.omega * ov;
     } else {  // MODE_INIT
       T tt = a.alpha * acc[i];
       if (a.z) tt += a.beta * a.z[r];
@@ -329,10 +341,13 @@ __global__ void __launch_bounds__(128, 16) k_fullmv(FullOp<TA> op, const TX* __r
 // Residual of the fluid (Stokes) block A_11 = [[A_f, -B^T], [-B, 0]]:
 // t_u = r_u - (A_f z_u - B^T z_p), t_p = r_p + B z_u.  Vectors hold
 // [u (2 nU) | p (3 nP)] at offset 0; same CTA layout as k_fullmv's first two
-// segments.
+// segments.  With pd given, the pressure rows also start the pressure
+// V-cycle on t_p: pb = t_p, pd = px = pc0 pdinv t_p.
 template <class T>
 __global__ void __launch_bounds__(128) k_stokes_res(FullOp<T> op, const T* __restrict__ z, const T* __restrict__ ru,
-                                                    const T* __restrict__ rp, T* __restrict__ t) {
+                                                    const T* __restrict__ rp, T* __restrict__ t,
+                                                    const T* __restrict__ pdinv, T pc0, T* __restrict__ pb,
+                                                    T* __restrict__ pd, T* __restrict__ px) {
   pdl_begin();
   const int lane = threadIdx.x & 31, tt = lane >> 3;
   const int b = blockIdx.x;
@@ -358,7 +373,16 @@ __global__ void __launch_bounds__(128) k_stokes_res(FullOp<T> op, const T* __res
     row_reduce<T, 3>(a);
     if (!live || tt != 0) return;
 #pragma unroll
-    for (int i = 0; i < 3; ++i) t[offP + 3 * r + i] = rp[3 * r + i] - a[i];
+    for (int i = 0; i < 3; ++i) {
+      const T tv = rp[3 * r + i] - a[i];
+      t[offP + 3 * r + i] = tv;
+      if (pd) {  // first Chebyshev step of the pressure V-cycle on this residual
+        pb[3 * r + i] = tv;
+        const T v = pc0 * pdinv[3 * r + i] * tv;
+        pd[3 * r + i] = v;
+        px[3 * r + i] = v;
+      }
+    }
   }
 }
 

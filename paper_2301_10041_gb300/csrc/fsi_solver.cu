@@ -304,10 +304,14 @@ static void cluster_launch(MG<T>& mg, const T* in_b, T* out_x, cudaStream_t s) {
 // Level l input: L.b, with L.x = L.d = c0 dinv b already set (l < last).
 // Result of the level is written to `out` (if given) or returned.  Levels
 // from mg.cl.lc down run as one cluster launch when mg.cl.on.
+// `fin`, when given, adds its Schur / accumulate epilogue (SpmvArgs sv ..
+// omega) to the last smoothing step of level l; *fused tells whether it was
+// applied (not when level l is solved by the cluster launch or densely).
 template <class T>
-static T* vcycle(MG<T>& mg, int l, cudaStream_t s, T* out) {
+static T* vcycle(MG<T>& mg, int l, cudaStream_t s, T* out, const SpmvArgs<T>* fin = nullptr, bool* fused = nullptr) {
   const int last = (int)mg.lv.size() - 1;
   MGLevel<T>& L = mg.lv[l];
+  if (fused) *fused = false;
   if (mg.cl.on && l == mg.cl.lc) {
     T* dst = out ? out : L.x;
     cluster_launch<T>(mg, L.b, dst, s);
@@ -341,6 +345,11 @@ static T* vcycle(MG<T>& mg, int l, cudaStream_t s, T* out) {
   for (int i = 0; i < k; ++i) {  // post-smoothing
     SpmvArgs<T> a;
     T* dst = (i == k - 1 && out) ? out : xn;
+    if (i == k - 1 && fin) {
+      a.sv = fin->sv; a.smp = fin->smp; a.sout = fin->sout; a.snu = fin->snu; a.srdt = fin->srdt;
+      a.acc = fin->acc; a.omega = fin->omega;
+      if (fused) *fused = true;
+    }
     a.x = xc; a.y = dst; a.z = L.b; a.d = L.d; a.dinv = L.dinv;
     if (i == 0) { a.c2 = (T)L.ch.c0; sell_launch(L.A, MODE_CHEB0, a, s); }
     else { a.c1 = (T)L.ch.c1[i - 1]; a.c2 = (T)L.ch.c2[i - 1]; sell_launch(L.A, MODE_CHEB, a, s); }
@@ -486,19 +495,39 @@ __global__ void k_cft_sub(int nU, const int* __restrict__ ptr, const int* __rest
 // approximation [[A_f, -B^T], [0, -S]]^-1: p = -S^-1 in_p with the
 // Cahouet-Chabard Schur approximation S^-1 ~ nu M_p^-1 + (rho/dt) L_p^-1
 // (one V-cycle on the pressure Laplacian L_p = B diag(M_f)^-1 B^T).
+//
+// With started = true the caller has already set L0.b = in_p and
+// L0.x = L0.d = c0 D^-1 in_p (k_stokes_res does it); with acc, also
+// acc += omega * out_p.  Both the Schur combination and the update ride on
+// the last smoothing kernel of the finest pressure level when it is a
+// per-level kernel.
 template <class T>
-static void stokes_pressure(Problem& P, Prec<T>& pr, const T* in_p, T* out_p, cudaStream_t s) {
+static void stokes_pressure(Problem& P, Prec<T>& pr, const T* in_p, T* out_p, cudaStream_t s, bool started = false,
+                            T* acc = nullptr, T omega = 1) {
   const int n3 = 3 * P.nP;
   MGLevel<T>& L0p = pr.mgP.lv[0];
-  launch(k_cheb_first<T>, nblk(n3, 256), 256, 0, s, n3, in_p, L0p.dinv, (T)L0p.ch.c0, L0p.d, L0p.x, (T)1, L0p.b);
-  T* sp = vcycle<T>(pr.mgP, 0, s, (T*)nullptr);
-  launch(k_schur<T>, nblk(n3, 256), 256, 0, s, n3, in_p, sp, pr.mpinv, (T)P.prm.nu, (T)(P.prm.rho_f / P.prm.dt), out_p);
+  if (!started)
+    launch(k_cheb_first<T>, nblk(n3, 256), 256, 0, s, n3, in_p, L0p.dinv, (T)L0p.ch.c0, L0p.d, L0p.x, (T)1, L0p.b);
+  SpmvArgs<T> fin;
+  fin.sv = in_p; fin.smp = pr.mpinv; fin.sout = out_p;
+  fin.snu = (T)P.prm.nu; fin.srdt = (T)(P.prm.rho_f / P.prm.dt);
+  fin.acc = acc; fin.omega = omega;
+  bool fused = false;
+  T* sp = vcycle<T>(pr.mgP, 0, s, (T*)nullptr, &fin, &fused);
+  if (!fused) {
+    launch(k_schur<T>, nblk(n3, 256), 256, 0, s, n3, in_p, sp, pr.mpinv, (T)P.prm.nu, (T)(P.prm.rho_f / P.prm.dt),
+           out_p);
+    if (acc) launch(k_axpy<T>, nblk(n3, 256), 256, 0, s, (size_t)n3, omega, (const T*)out_p, acc);
+  }
 }
 
 // Velocity part: u = A_f^-1 (in_u + B^T p) by one V-cycle with
 // Chebyshev-Jacobi smoothing on the Q2 hierarchy (p = nullptr: u = A_f^-1 in_u).
+// With acc, also acc += omega * out_u (on the last smoothing kernel when the
+// finest level is a per-level kernel).
 template <class T>
-static void stokes_velocity(Problem& P, Prec<T>& pr, const T* in_u, const T* p, T* out_u, cudaStream_t s) {
+static void stokes_velocity(Problem& P, Prec<T>& pr, const T* in_u, const T* p, T* out_u, cudaStream_t s,
+                            T* acc = nullptr, T omega = 1) {
   MGLevel<T>& L0u = pr.mgU.lv[0];
   if (p) {
     SpmvArgs<T> a;
@@ -509,7 +538,14 @@ static void stokes_velocity(Problem& P, Prec<T>& pr, const T* in_u, const T* p, 
     const int n2 = 2 * P.nU;
     launch(k_cheb_first<T>, nblk(n2, 256), 256, 0, s, n2, in_u, L0u.dinv, (T)L0u.ch.c0, L0u.d, L0u.x, (T)1, L0u.b);
   }
-  vcycle(pr.mgU, 0, s, out_u);
+  SpmvArgs<T> fin;
+  fin.acc = acc; fin.omega = omega;
+  bool fused = false;
+  vcycle(pr.mgU, 0, s, out_u, acc ? &fin : (const SpmvArgs<T>*)nullptr, &fused);
+  if (acc && !fused) {
+    const size_t n2 = 2 * (size_t)P.nU;
+    launch(k_axpy<T>, nblk(n2, 256), 256, 0, s, n2, omega, (const T*)out_u, acc);
+  }
 }
 
 // One application of the Stokes approximation to (in_u, in_p): the pressure
@@ -575,10 +611,21 @@ static void precond_launch(Problem& P, Prec<T>& pr, cudaStream_t s) {
     stokes_apply(P, pr, vu, vp, pr.zw, zp, s, split);
   }
   const size_t nf = 2 * (size_t)P.nU + 3 * (size_t)P.nP;
+  MGLevel<T>& L0p = pr.mgP.lv[0];
   for (int it = 1; it < pr.stokes_its; ++it) {
-    launch(k_stokes_res<T>, pr.op.gU + pr.op.gP, 128, 0, s, pr.op, pr.zw, vu, vp, pr.t);
-    stokes_apply(P, pr, pr.t, pr.t + P.offP, pr.dz, pr.dz + P.offP, s, split);
-    launch(k_axpy<T>, nblk(nf, 256), 256, 0, s, nf, pr.stokes_omega, pr.dz, pr.zw);
+    if (split) {
+      launch(k_stokes_res<T>, pr.op.gU + pr.op.gP, 128, 0, s, pr.op, pr.zw, vu, vp, pr.t, (const T*)nullptr, (T)0,
+             (T*)nullptr, (T*)nullptr, (T*)nullptr);
+      stokes_apply(P, pr, pr.t, pr.t + P.offP, pr.dz, pr.dz + P.offP, s, split);
+      launch(k_axpy<T>, nblk(nf, 256), 256, 0, s, nf, pr.stokes_omega, pr.dz, pr.zw);
+    } else {
+      // residual (starting the pressure smoother), then the pressure and
+      // velocity corrections, each added to z by its own last kernel
+      launch(k_stokes_res<T>, pr.op.gU + pr.op.gP, 128, 0, s, pr.op, pr.zw, vu, vp, pr.t, (const T*)L0p.dinv,
+             (T)L0p.ch.c0, L0p.b, L0p.d, L0p.x);
+      stokes_pressure(P, pr, pr.t + P.offP, pr.dz + P.offP, s, true, pr.zw + P.offP, pr.stokes_omega);
+      stokes_velocity(P, pr, pr.t, (const T*)(pr.dz + P.offP), pr.dz, s, pr.zw, pr.stokes_omega);
+    }
   }
   if (pc == 1) solid_launch(P, pr, s);
   if (pc == 0) CK(cudaStreamWaitEvent(s, P.ev_join, 0));
