@@ -48,7 +48,7 @@ def workload_config(case):
     return {"workload": "cavity128_lid_disk7776: N=128 Q2/P1disc fluid, disk R=0.2 m=36 (3997 nodes, 7776 P1 "
                         "triangles), kappa=1e3, nu=0.01, rho=1, dt=1e-3, lid 1, rtol 1e-8",
             "preconditioner": "block upper-triangular; Stokes block by 8 Richardson steps of a V-cycle pair",
-            "restart": RESTART,
+            "restart": {"mixed": RESTART_MIXED, "fp64": RESTART}, "inner_rtol": INNER_RTOL,
             "N": case.N, "solid_nodes": int(case.ref_xy.shape[0]), "solid_tris": int(case.tris.shape[0]),
             "dofs": None, "l2": "flushed between timed steps (512 MiB write)"}
 
@@ -105,7 +105,9 @@ class ClockSampler:
 
 # ------------------------------------------------------------ our GPU arm
 PRECOND = 2      # block upper-triangular [[A11, A12], [0, A22]]
-RESTART = 100    # FGMRES restart (the library default is the paper's 200)
+RESTART = 100    # FGMRES restart of the FP64 arm and the size sweep (the library default is the paper's 200)
+RESTART_MIXED = 30   # restart inside each refinement cycle of the mixed arm (cheaper Gram-Schmidt, same iterations)
+INNER_RTOL = 1e-4    # relative tolerance of each refinement cycle of the mixed arm
 STOKES_ITS = 8   # Richardson steps on the Stokes block per preconditioner application
 MAX_IT = 6000
 
@@ -117,10 +119,17 @@ def _step_unchecked(prob):
     return info
 
 
+def arm_settings(precision):
+    """FGMRES restart and inner tolerance of one arm."""
+    if precision == 1:
+        return dict(restart=RESTART_MIXED, inner_rtol=INNER_RTOL)
+    return dict(restart=RESTART)
+
+
 def time_arm(fsi, torch, case, precision, steps, warmup, stream, flush, precond=PRECOND, stokes_its=STOKES_ITS,
-             max_it=MAX_IT, check=True):
+             max_it=MAX_IT, check=True, settings=None):
     prob = fsi.problem_from_case(case, precision=precision, precond=precond, rtol=1e-8, stream=stream.cuda_stream,
-                                 max_it=max_it, restart=RESTART, stokes_its=stokes_its)
+                                 max_it=max_it, stokes_its=stokes_its, **(settings or arm_settings(precision)))
     step = prob.step if check else (lambda: _step_unchecked(prob))
     infos = []
     for _ in range(warmup):
@@ -154,7 +163,7 @@ def time_arm(fsi, torch, case, precision, steps, warmup, stream, flush, precond=
 def time_e2e(fsi, case, precision, steps, stream):
     """Through the C ABI with host buffers: set_state (H2D) + step + get_state (D2H)."""
     prob = fsi.problem_from_case(case, precision=precision, precond=PRECOND, rtol=1e-8, stream=stream.cuda_stream,
-                                 max_it=MAX_IT, restart=RESTART, stokes_its=STOKES_ITS)
+                                 max_it=MAX_IT, stokes_its=STOKES_ITS, **arm_settings(precision))
     u, p, X, lam = prob.get_state()
     prob.step()
     u, p, X, lam = prob.get_state()
@@ -380,7 +389,8 @@ def run_profile_step(args):
     from paper_2301_10041_gb300 import build, fsi
     build.build()
     case = workload()
-    prob = fsi.problem_from_case(case, precision=1, precond=PRECOND, rtol=1e-8, max_it=MAX_IT, restart=RESTART, stokes_its=STOKES_ITS)
+    prob = fsi.problem_from_case(case, precision=1, precond=PRECOND, rtol=1e-8, max_it=MAX_IT, stokes_its=STOKES_ITS,
+                                 **arm_settings(1))
     for _ in range(args.warmup):
         prob.step()
     info = prob.step()
@@ -460,7 +470,8 @@ def run_sweep(args):
         for label, pc, sits in SWEEP_VARIANTS:
             t0 = time.perf_counter()
             prob, st = time_arm(fsi, torch, case, 1, args.sweep_steps, 1, stream, flush, precond=pc,
-                                stokes_its=sits, max_it=args.sweep_max_it, check=False)
+                                stokes_its=sits, max_it=args.sweep_max_it, check=False,
+                                settings=dict(restart=RESTART))
             row = {"N": N, "preconditioner": label, "precond": pc, "stokes_its": sits,
                    "dofs": int(prob_dofs(case)), "solid_nodes": int(case.ref_xy.shape[0]),
                    "solid_tris": int(case.tris.shape[0]),

@@ -9,13 +9,18 @@
 namespace fsi {
 
 // Programmatic dependent launch: kernels are launched so that the next one
-// may be scheduled while the previous one finishes.  Every kernel first lets
-// its dependents launch, then waits until all the grids it depends on have
-// completed and their writes are visible, before it reads anything.  Launched
-// without the attribute, both instructions are no-ops.
+// may be scheduled while the previous one finishes.  Every kernel first waits
+// until all the grids it depends on have completed and their writes are
+// visible, before it reads anything (pdl_begin); the SpMV kernels let their
+// dependents launch once their loads are done (pdl_trigger), so that the
+// next kernel's CTAs arrive during the tail rather than competing for the SMs
+// from the start.  Launched without the attribute, both are no-ops.
 __device__ __forceinline__ void pdl_begin() {
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
 // device error flags (OR-ed into Ctl::flags)
@@ -202,6 +207,7 @@ __global__ void __launch_bounds__(128, 16) k_sell(Sell<T> A, SpmvArgs<T> a) {
   for (int i = 0; i < BR; ++i) acc[i] = 0;
   if (live) sell_row<T, T, BR, BC, KRON, NV>(A, row, t, a.x, acc);
   row_reduce<T, BR>(acc);
+  pdl_trigger();
   if (!live || t != 0) return;
   const T* __restrict__ x = a.x;
 #pragma unroll
@@ -362,6 +368,7 @@ __global__ void __launch_bounds__(128) k_stokes_res(FullOp<T> op, const T* __res
       sell_row<T, T, 2, 3, false, 6>(op.Bt, r, tt, z + offP, a);
     }
     row_reduce<T, 2>(a);
+    pdl_trigger();
     if (!live || tt != 0) return;
     t[2 * r] = ru[2 * r] - a[0];
     t[2 * r + 1] = ru[2 * r + 1] - a[1];
@@ -371,6 +378,7 @@ __global__ void __launch_bounds__(128) k_stokes_res(FullOp<T> op, const T* __res
     T a[3] = {0, 0, 0};
     if (live) sell_row<T, T, 3, 2, false, 6>(op.Bneg, r, tt, z, a);
     row_reduce<T, 3>(a);
+    pdl_trigger();
     if (!live || tt != 0) return;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {

@@ -1,6 +1,6 @@
 """Parity at the full workload sizes, in the launch configuration the bench
 times (mixed precision, block upper-triangular preconditioner with inner
-Stokes Richardson steps, restart 100).
+Stokes Richardson steps, the mixed arm's restart and inner tolerance).
 
 The oracle's direct solve takes minutes at these sizes, so the solve is
 checked through a property that holds at any size: the GPU solution's
@@ -37,7 +37,7 @@ def fsi():
 
 def _bench_problem(fsi, case, precond=bench.PRECOND, stokes_its=bench.STOKES_ITS, max_it=bench.MAX_IT):
     return fsi.problem_from_case(case, precision=1, precond=precond, rtol=RTOL, max_it=max_it,
-                                 restart=bench.RESTART, stokes_its=stokes_its)
+                                 stokes_its=stokes_its, **bench.arm_settings(1))
 
 
 def _oracle(case):
