@@ -80,13 +80,23 @@ void triangle_rule(double lam[6][3], double w[6]);
 // ------------------------------------------------------------- device side
 template <class T>
 struct Sell {            // sliced ELL of block rows, slice height 8
+  static constexpr int kMaxRuns = 16;
   int nrows = 0;         // block rows
   int BR = 1, BC = 1, NV = 1;
   bool kron = false;
   const int* soff = nullptr;  // per slice: first slot
   const int* len = nullptr;   // per block row
-  const int* col = nullptr;   // per slot
+  const int* col = nullptr;   // per slot (-1 in padding slots when nrun > 0)
   const T* val = nullptr;     // NV per slot
+  // Slices of equal width come in a few runs on the structured fluid grid
+  // (node types x wall rows).  With nrun > 0 a kernel computes the first slot
+  // of slice s as run_off[k] + 8 (s - run_s[k]) run_w[k] for the run k that
+  // holds s and scans run_w[k] slots, skipping column -1, so it reads neither
+  // soff nor len (one dependent memory round trip less per launch).
+  int nrun = 0;
+  int run_s[kMaxRuns] = {};    // first slice of each run
+  int run_w[kMaxRuns] = {};    // slots per row in the run
+  int run_off[kMaxRuns] = {};  // first slot of the run
 };
 
 struct SellHost {        // SELL arrays before upload

@@ -145,8 +145,19 @@ __device__ __forceinline__ void load_x(const TX* __restrict__ x, int c, TA* xv) 
 // the kernels at 32 registers and full occupancy).
 template <class TA, class TX, int BR, int BC, bool KRON, int NV>
 __device__ __forceinline__ void sell_row(const Sell<TA>& A, int row, int t, const TX* __restrict__ x, TA* acc) {
-  const int base = A.soff[row >> 3] + (row & 7);
-  const int n = A.len[row];
+  int base, n;
+  if (A.nrun > 0) {  // slice offset from the run table (kernel parameters, no memory load)
+    const int s = row >> 3;
+    int k = 0;
+#pragma unroll
+    for (int q = 1; q < Sell<TA>::kMaxRuns; ++q)
+      if (q < A.nrun && s >= A.run_s[q]) k = q;
+    n = A.run_w[k];
+    base = A.run_off[k] + (s - A.run_s[k]) * kSliceRows * n + (row & 7);
+  } else {
+    base = A.soff[row >> 3] + (row & 7);
+    n = A.len[row];
+  }
   constexpr int U = 2;
   for (int k0 = t; k0 < n; k0 += U * kRowThreads) {
     int c[U];
@@ -196,7 +207,7 @@ __device__ __forceinline__ void row_reduce(T* acc) {
 }
 
 template <class T, int BR, int BC, bool KRON, int NV, int MODE>
-__global__ void __launch_bounds__(128, 16) k_sell(Sell<T> A, SpmvArgs<T> a) {
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 16 : 8) k_sell(Sell<T> A, SpmvArgs<T> a) {
   pdl_begin();
   const int lane = threadIdx.x & 31;
   const int row = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * kSliceRows + (lane & 7);
@@ -260,7 +271,7 @@ struct FullOp {
 };
 
 template <class TA, class TX, class TY>
-__global__ void __launch_bounds__(128, 16) k_fullmv(FullOp<TA> op, const TX* __restrict__ x, TY* __restrict__ y,
+__global__ void __launch_bounds__(128, sizeof(TA) == 4 ? 16 : 8) k_fullmv(FullOp<TA> op, const TX* __restrict__ x, TY* __restrict__ y,
                                                 const TY* __restrict__ z, TY alpha, TY beta) {
   pdl_begin();
   const int lane = threadIdx.x & 31, t = lane >> 3;

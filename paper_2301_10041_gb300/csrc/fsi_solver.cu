@@ -108,7 +108,31 @@ static Sell<T> upload_sell(Arena& ar, const SellHost& s) {
   d.nrows = s.nrows; d.BR = s.BR; d.BC = s.BC; d.NV = s.NV; d.kron = s.kron;
   d.soff = ar.upload(s.soff);
   d.len = ar.upload(s.len);
-  d.col = ar.upload(s.col);
+  // runs of equal slice width (structured-grid matrices have at most 15)
+  std::vector<int> rs, rw, ro;
+  for (int sl = 0; sl < s.nslices; ++sl) {
+    const int w = (s.soff[sl + 1] - s.soff[sl]) / kSliceRows;
+    if (rw.empty() || w != rw.back()) {
+      rs.push_back(sl);
+      rw.push_back(w);
+      ro.push_back(s.soff[sl]);
+    }
+  }
+  std::vector<int> col = s.col;
+  if (!rs.empty() && rs.size() <= (size_t)Sell<T>::kMaxRuns) {
+    d.nrun = (int)rs.size();
+    for (int k = 0; k < d.nrun; ++k) {
+      d.run_s[k] = rs[k];
+      d.run_w[k] = rw[k];
+      d.run_off[k] = ro[k];
+    }
+    for (int r = 0; r < s.nrows; ++r) {  // mark the padding slots
+      const int sl = r / kSliceRows, lane = r % kSliceRows;
+      const int w = (s.soff[sl + 1] - s.soff[sl]) / kSliceRows;
+      for (int k = s.len[r]; k < w; ++k) col[(size_t)s.soff[sl] + (size_t)k * kSliceRows + lane] = -1;
+    }
+  }
+  d.col = ar.upload(col);
   std::vector<T> v(s.val.begin(), s.val.end());
   d.val = ar.upload(v);
   return d;
@@ -1318,7 +1342,7 @@ static void allocate_problem(Problem& P, const double* ref_xy, const int* tris_h
 // ----------------------------------------------------------- timing hook
 template <class T>
 static double sell_bytes(const HostBlockMatrix& A) {
-  return (double)A.nnzb() * (A.NV * sizeof(T) + sizeof(int)) + (double)A.nrows * sizeof(int);
+  return (double)A.nnzb() * (A.NV * sizeof(T) + sizeof(int));  // stored blocks: values + column index
 }
 
 template <class T>
