@@ -280,11 +280,13 @@ def prob_dofs(case):
 
 
 def roofline(prob, args):
-    """Roofline of the dominant kernel of the mixed path: the Chebyshev
+    """Roofline of the dominant HBM kernel of the mixed path: the Chebyshev
     smoothing step on the finest Q2 velocity level (k_sell, 2x2 blocks, the
-    largest share of the launch list in profiles/), timed live on the
-    library's stream with CUDA events, L2 evicted before every launch.  The
-    FP32 full-system operator is reported beside it."""
+    largest per-level kernel of the launch list in profiles/), timed live on
+    the library's stream with CUDA events, L2 evicted before every launch.
+    The FP32 full-system operator is reported beside it, and the
+    cluster-resident coarse V-cycle launches (the largest share of the step,
+    latency-bound, no HBM roofline) as launch times."""
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     peak = peaks.get("hbm_gbs", 6800.0)
@@ -292,6 +294,15 @@ def roofline(prob, args):
     for name, which in (("full_operator_f32", 0), ("velocity_chebyshev_f32", 2)):
         ms, by = prob.time_kernel(which, reps=30)
         out[name] = {"ms": ms, "bytes": by, "gbs": by / ms / 1e6}
+    # the largest-share launches are the cluster-resident coarse V-cycle
+    # levels: latency-bound, reported as launch times (L2 warm)
+    for name, which in (("vcycle_cluster_velocity_f32", 6), ("vcycle_cluster_pressure_f32", 7),
+                        ("vcycle_velocity_f32", 4), ("vcycle_pressure_f32", 5)):
+        try:
+            ms, _ = prob.time_kernel(which, reps=30)
+            out[name] = {"us": ms * 1e3}
+        except Exception:
+            pass
     dom = out["velocity_chebyshev_f32"]
     traffic = None   # DRAM bytes per launch from the committed ncu summary of this kernel
     prof = os.path.join(ROOT, "profiles", "ncu_velocity_chebyshev_f32_cavity128.md")

@@ -217,7 +217,9 @@ int fsi_graph_kernel_counts(const fsi_problem* p, int* counts);
  * velocity Chebyshev smoothing step in FP32 (precision 1 only), 3 the same in
  * FP64; 4 and 5 (precision 1 only): one whole V-cycle on the velocity /
  * pressure-Laplacian hierarchy in FP32, with L2 left warm as inside a solve
- * (bytes = 0: a latency figure).  avg_ms: mean launch time; bytes:
+ * (bytes = 0: a latency figure); 6 and 7: the cluster launch of that
+ * hierarchy's coarse levels alone (FSI_ERR_INVALID when they run as
+ * per-level kernels).  avg_ms: mean launch time; bytes:
  * algorithmic bytes of one launch (stored blocks and indices without
  * padding, each vector once).  Allocates
  * and frees a 256 MiB scratch buffer. */

@@ -1831,7 +1831,7 @@ int fsi_graph_kernel_counts(const fsi_problem* h, int* counts) {
 int fsi_time_kernel(fsi_problem* h, int which, int reps, double* avg_ms, double* bytes) {
   if (!h || !avg_ms || !bytes || reps <= 0) return FSI_ERR_INVALID;
   Problem& P = h->P;
-  if ((which == 0 || which == 2 || which == 4 || which == 5) && P.prm.precision != 1) return FSI_ERR_INVALID;
+  if ((which == 0 || which == 2 || which >= 4) && P.prm.precision != 1) return FSI_ERR_INVALID;
   if (which == 3 && P.p64.mgU.lv.empty()) return FSI_ERR_INVALID;  // no FP64 hierarchy in mixed mode
   try {
     // total C_f entries of the last assembly
@@ -1882,6 +1882,18 @@ int fsi_time_kernel(fsi_problem* h, int which, int reps, double* avg_ms, double*
         case 5: {  // one V-cycle on the pressure Laplacian hierarchy, FP32
           MG<float>& mg = (which == 4) ? P.p32.mgU : P.p32.mgP;
           vcycle<float>(mg, 0, s, mg.lv[0].x2);
+          *bytes = 0;
+          break;
+        }
+        case 6:    // the cluster launch of the velocity coarse levels alone, FP32
+        case 7: {  // the same for the pressure Laplacian
+          MG<float>& mg = (which == 6) ? P.p32.mgU : P.p32.mgP;
+          if (!mg.cl.on) {
+            cudaFree(fl);
+            return FSI_ERR_INVALID;
+          }
+          MGLevel<float>& L = mg.lv[mg.cl.lc];
+          cluster_launch<float>(mg, L.b, L.x, s);
           *bytes = 0;
           break;
         }
