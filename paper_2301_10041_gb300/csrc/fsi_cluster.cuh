@@ -230,31 +230,34 @@ __global__ void __launch_bounds__(kClThreads, 1) k_vcycle_cluster(const __grid_c
   const int rank = (int)cl.block_rank();
   const int cs = a.csize;
   constexpr int TNV = TKRON ? 1 : B * B;
-  {  // stage this CTA's operators: every 16-byte copy is issued before the
-     // single wait, so the whole image is in flight at once
+  const ClLevel<T>& L0 = a.lv[0];
+  int t0, t1;
+  cl_own(L0.nsl, rank, cs, t0, t1);
+  const int r0 = t0 * kSliceRows, r1 = min(t1 * kSliceRows, L0.nrows);
+  const int n0 = max(r1 - r0, 0) * B;  // own unknowns of the top level
+  {  // stage this CTA's operators and its part of the top-level right-hand
+     // side: every copy is issued before the single wait, so all are in flight
     const uint4* __restrict__ src = a.blob + (size_t)rank * a.blob_stride;
     const unsigned dst = (unsigned)__cvta_generic_to_shared(sm);
     const int n16 = a.blob_bytes >> 4;
     for (int i = threadIdx.x; i < n16; i += blockDim.x)
       asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst + 16u * (unsigned)i), "l"(src + i) : "memory");
+    const unsigned bdst = (unsigned)__cvta_generic_to_shared(sm + L0.b);
+    const T* bsrc = a.in_b + (size_t)r0 * B;
+    for (int i = threadIdx.x; i < n0; i += blockDim.x)
+      asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(bdst + (unsigned)(i * sizeof(T))), "l"(bsrc + i),
+                   "n"(sizeof(T)) : "memory");
     asm volatile("cp.async.commit_group;" ::: "memory");
     asm volatile("cp.async.wait_group 0;" ::: "memory");
   }
   __syncthreads();
-  {  // top level: own part of b, x = d = c0 D^-1 b
-    const ClLevel<T>& L = a.lv[0];
-    int s0, s1;
-    cl_own(L.nsl, rank, cs, s0, s1);
-    const int r0 = s0 * kSliceRows, r1 = min(s1 * kSliceRows, L.nrows);
-    const int n = max(r1 - r0, 0) * B;
-    T* b = cl_ptr<T>(sm, L.b);
-    T* x = cl_ptr<T>(sm, L.x);
-    T* d = cl_ptr<T>(sm, L.d);
-    const T* dinv = cl_ptr<const T>(sm, L.dinv);
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      const T v = a.in_b[(size_t)r0 * B + i];
-      b[i] = v;
-      const T tv = L.c0 * dinv[i] * v;
+  {  // top level: x = d = c0 D^-1 b on own rows
+    const T* b = cl_ptr<const T>(sm, L0.b);
+    T* x = cl_ptr<T>(sm, L0.x);
+    T* d = cl_ptr<T>(sm, L0.d);
+    const T* dinv = cl_ptr<const T>(sm, L0.dinv);
+    for (int i = threadIdx.x; i < n0; i += blockDim.x) {
+      const T tv = L0.c0 * dinv[i] * b[i];
       x[i] = tv;
       d[i] = tv;
     }
@@ -299,20 +302,26 @@ __global__ void __launch_bounds__(kClThreads, 1) k_vcycle_cluster(const __grid_c
     __syncthreads();
     int s0, s1;
     cl_own(C.nsl, rank, cs, s0, s1);
-    const int r0 = s0 * kSliceRows, r1 = min(s1 * kSliceRows, C.nrows);
-    const int nown = max(r1 - r0, 0) * B;
+    const int rc0 = s0 * kSliceRows, rc1 = min(s1 * kSliceRows, C.nrows);
+    const int nown = max(rc1 - rc0, 0) * B;
     T* x = cl_ptr<T>(sm, C.x);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int i = warp; i < nown; i += nw) {
-      const T* __restrict__ arow = a.dense_inv + (size_t)(r0 * B + i) * n;
-      T s0a = 0, s1a = 0;
-      int j = lane;
-      for (; j + 32 < n; j += 64) {
-        s0a += arow[j] * g[j];
-        s1a += arow[j + 32] * g[j + 32];
+      const T* __restrict__ arow = a.dense_inv + (size_t)(rc0 * B + i) * n;
+      // eight independent loads in flight per lane, one L2 round trip for
+      // rows of up to 256 entries
+      T acc8[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) acc8[u] = 0;
+      for (int j0 = lane; j0 < n; j0 += 256) {
+        T av[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) av[u] = (j0 + 32 * u < n) ? __ldg(arow + j0 + 32 * u) : (T)0;
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if (j0 + 32 * u < n) acc8[u] += av[u] * g[j0 + 32 * u];
       }
-      if (j < n) s0a += arow[j] * g[j];
-      T sum = s0a + s1a;
+      T sum = ((acc8[0] + acc8[1]) + (acc8[2] + acc8[3])) + ((acc8[4] + acc8[5]) + (acc8[6] + acc8[7]));
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o);
       if (lane == 0) x[i] = sum;
@@ -337,13 +346,8 @@ __global__ void __launch_bounds__(kClThreads, 1) k_vcycle_cluster(const __grid_c
     }
   }
   {  // the top level's result to global memory (no remote access follows the last barrier)
-    const ClLevel<T>& L = a.lv[0];
-    int s0, s1;
-    cl_own(L.nsl, rank, cs, s0, s1);
-    const int r0 = s0 * kSliceRows, r1 = min(s1 * kSliceRows, L.nrows);
-    const int n = max(r1 - r0, 0) * B;
     const T* x = cl_ptr<const T>(sm, cur[0]);
-    for (int i = threadIdx.x; i < n; i += blockDim.x) a.out_x[(size_t)r0 * B + i] = x[i];
+    for (int i = threadIdx.x; i < n0; i += blockDim.x) a.out_x[(size_t)r0 * B + i] = x[i];
   }
 }
 
