@@ -21,11 +21,13 @@ fictitious domain approach", arXiv:2301.10041):
   so the duality pairing is the L2(B) product and C_s is the P1 mass matrix.
 * P(F) = kappa F (Section 4, before Eq. (matrix)): A_s = kappa (grad chi_j,
   grad chi_i)_B per component.
-* C_f(X^n)_{l j} = (chi_l, phi_j(X^n))_B is computed by locating every solid
-  quadrature point in the fluid grid (brute force over all cells) and
-  evaluating the Q2 basis there, with a 6-point degree-4 symmetric triangle
-  rule (Dunavant 1985).  The paper instead integrates exactly over
-  mesh intersections (Section 4); point location is the rule built here.
+* C_f(X^n)_{l j} = (chi_l, phi_j(X^n))_B is computed in one of two ways:
+  by locating every solid quadrature point in the fluid grid (brute force
+  over all cells) and evaluating the Q2 basis there, with a 6-point degree-4
+  symmetric triangle rule (Dunavant 1985); or exactly, as the paper does
+  (Section 4), by intersecting each mapped solid triangle with the fluid
+  cells (Sutherland-Hodgman) and integrating on the pieces with a degree-5
+  rule (``assemble_coupling_exact``).
 * The block system of Eq. (matrix) is solved by a sparse direct solve with a
   bordering row that fixes the pressure mean (p in L^2_0, Problem 2).
 
@@ -313,6 +315,111 @@ def assemble_coupling(grid: FluidGrid, ref_xy: np.ndarray, tris: np.ndarray, X: 
     return C, (x, cell, xi, eta)
 
 
+# --------------------------------------------------------------------------
+# Exact coupling by mesh intersection (Section 4: the paper's own rule)
+# --------------------------------------------------------------------------
+
+
+def radon_rule():
+    """Radon's 7-point symmetric rule on a triangle, exact for degree 5
+    (Radon 1948; Stroud's T2:5-1), from its closed form: the centroid with
+    weight 9/40 and the orbits (a, a, 1-2a), a = (6 -/+ sqrt 15)/21, with
+    weights (155 -/+ sqrt 15)/1200.  Barycentric points, weights summing to 1."""
+    r = np.sqrt(15.0)
+    pts = [(1.0 / 3.0, 1.0 / 3.0, 1.0 / 3.0)]
+    wts = [9.0 / 40.0]
+    for a, w in (((6.0 - r) / 21.0, (155.0 - r) / 1200.0), ((6.0 + r) / 21.0, (155.0 + r) / 1200.0)):
+        b = 1.0 - 2.0 * a
+        pts += [(b, a, a), (a, b, a), (a, a, b)]
+        wts += [w, w, w]
+    return np.array(pts), np.array(wts)
+
+
+def clip_half_plane(poly, axis: int, value: float, keep_below: bool):
+    """One Sutherland-Hodgman pass: the part of a convex polygon (list of
+    2-vectors, in order) with x[axis] <= value (keep_below) or >= value.
+    A crossing edge contributes its intersection point, whose clipped
+    coordinate is set to `value` exactly."""
+    out = []
+    n = len(poly)
+    for i in range(n):
+        P, Q = poly[i], poly[(i + 1) % n]
+        inP = P[axis] <= value if keep_below else P[axis] >= value
+        inQ = Q[axis] <= value if keep_below else Q[axis] >= value
+        if inP:
+            out.append(P)
+        if inP != inQ:
+            t = (value - P[axis]) / (Q[axis] - P[axis])
+            R = P + t * (Q - P)
+            R[axis] = value
+            out.append(R)
+    return out
+
+
+def clip_to_cell(P: np.ndarray, x0: float, x1: float, y0: float, y1: float):
+    """Intersection of the triangle P (3 x 2) with the square [x0,x1] x
+    [y0,y1] by four Sutherland-Hodgman passes (Section 4); [] if empty."""
+    poly = [P[0].copy(), P[1].copy(), P[2].copy()]
+    for axis, value, below in ((0, x0, False), (0, x1, True), (1, y0, False), (1, y1, True)):
+        poly = clip_half_plane(poly, axis, value, below)
+        if len(poly) < 3:
+            return []
+    return poly
+
+
+def assemble_coupling_exact(grid: FluidGrid, ref_xy: np.ndarray, tris: np.ndarray, X: np.ndarray):
+    """Scalar coupling matrix C (n_s x n_nodes), C_{l j} = (chi_l, phi_j(X^n))_B,
+    integrated exactly as in Section 4.  On a solid triangle E the map X^n is
+    affine, so the integral over E equals (|E| / |X(E)|) times the integral
+    over the mapped triangle X(E) of lambda_l(x) phi_j(x), lambda_l the
+    barycentric coordinate of X(E).  X(E) is intersected with every fluid cell
+    its bounding box touches (Sutherland-Hodgman), each intersection polygon
+    is split into triangles from its first vertex, and the integrand (linear
+    times biquadratic: degree 5) is integrated by Radon's degree-5 rule.
+    Raises on a vertex outside the fluid domain or a degenerate image."""
+    N, h = grid.N, grid.h
+    lam_q, w_q = radon_rule()
+    area_ref, _ = p1_geometry(ref_xy, tris)
+    rows, cols, vals = [], [], []
+    for t in range(tris.shape[0]):
+        P = np.asarray(X[tris[t]], dtype=np.float64)
+        if np.any(P < 0.0) or np.any(P > 1.0):
+            raise ValueError("mapped solid vertex outside the fluid domain")
+        d1, d2 = P[1] - P[0], P[2] - P[0]
+        det = d1[0] * d2[1] - d1[1] * d2[0]
+        if det == 0.0:
+            raise ValueError("degenerate mapped solid triangle")
+        scale = area_ref[t] / (0.5 * abs(det))
+        lo = np.minimum(np.floor(P.min(axis=0) * N).astype(np.int64), N - 1)
+        hi = np.minimum(np.floor(P.max(axis=0) * N).astype(np.int64), N - 1)
+        for cy in range(lo[1], hi[1] + 1):
+            for cx in range(lo[0], hi[0] + 1):
+                poly = clip_to_cell(P, cx * h, (cx + 1) * h, cy * h, (cy + 1) * h)
+                acc = np.zeros((3, 9))
+                for i in range(1, len(poly) - 1):
+                    S = np.array([poly[0], poly[i], poly[i + 1]])
+                    e1, e2 = S[1] - S[0], S[2] - S[0]
+                    a_sub = 0.5 * abs(e1[0] * e2[1] - e1[1] * e2[0])
+                    if a_sub == 0.0:
+                        continue
+                    xq = lam_q @ S                                   # 7 x 2 points
+                    r = xq - P[0]
+                    l1 = (r[:, 0] * d2[1] - r[:, 1] * d2[0]) / det
+                    l2 = (d1[0] * r[:, 1] - d1[1] * r[:, 0]) / det
+                    lam = np.stack([1.0 - l1 - l2, l1, l2], axis=1)  # 7 x 3
+                    phi = (q2_1d((xq[:, 1] - cy * h) / h)[:, :, None]
+                           * q2_1d((xq[:, 0] - cx * h) / h)[:, None, :]).reshape(-1, 9)  # local id 3b + a
+                    acc += a_sub * np.einsum("q,qa,qj->aj", w_q, lam, phi)
+                if not acc.any():
+                    continue
+                rows.append(np.repeat(tris[t], 9))
+                cols.append(np.tile(grid.cell_nodes[cy * N + cx], 3))
+                vals.append((scale * acc).ravel())
+    C = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                      shape=(ref_xy.shape[0], grid.n_nodes)).tocsr()
+    return C
+
+
 def kron2(A):
     """Scalar operator acting on both components of interleaved 2-vectors."""
     return sp.kron(A, sp.identity(2), format="csr")
@@ -356,8 +463,13 @@ def nested_dissection(G, xy, leaf: int = 64):
 class OracleProblem:
     """Constant matrices of one FSI instance (the paper's T_ass work)."""
 
-    def __init__(self, N, rho_f, nu, kappa, dt, lid_u, ref_xy, tris):
+    def __init__(self, N, rho_f, nu, kappa, dt, lid_u, ref_xy, tris, coupling: str = "point"):
+        """coupling: "point" (the degree-4 point rule with point location) or
+        "exact" (mesh intersection, the paper's rule of Section 4)."""
         self.N, self.rho, self.nu, self.kappa, self.dt, self.lid_u = N, rho_f, nu, kappa, dt, lid_u
+        if coupling not in ("point", "exact"):
+            raise ValueError("coupling")
+        self.coupling = coupling
         self.grid = FluidGrid(N)
         self.ref_xy = np.asarray(ref_xy, dtype=np.float64)
         self.tris = np.asarray(tris, dtype=np.int64)
@@ -391,7 +503,10 @@ class OracleProblem:
         both use u^{n+1}).
         """
         I, D = self.I, self.D
-        Cscal, loc = assemble_coupling(self.grid, self.ref_xy, self.tris, X)
+        if self.coupling == "exact":
+            Cscal, loc = assemble_coupling_exact(self.grid, self.ref_xy, self.tris, X), None
+        else:
+            Cscal, loc = assemble_coupling(self.grid, self.ref_xy, self.tris, X)
         Cf = kron2(Cscal)
         uD = self.u_wall.reshape(-1)[D]
         un = np.asarray(u_nodal, dtype=np.float64).reshape(-1)

@@ -342,3 +342,125 @@ def test_lid_driven_cavity_conserves_no_mass_through_walls():
     assert np.abs(prob.B @ u.reshape(-1)).max() < 1e-11 * np.abs(prob.B).max()
     top = (prob.grid.n1 - 1) * prob.grid.n1 + np.arange(1, prob.grid.n1 - 1)
     assert np.all(u[top, 0] == 1.0)
+
+
+# ------------------------------------------- exact coupling (mesh intersection)
+
+def _duffy_rule(n: int):
+    """Gauss product rule on the reference triangle {s1, s2 >= 0, s1 + s2 <= 1}
+    through the collapsed map s = (u, v (1 - u)) with Jacobian (1 - u): an
+    independent rule, exact for polynomials of degree <= 2n - 2 in s."""
+    g, w = fo.gauss01(n)
+    U, V = np.meshgrid(g, g, indexing="ij")
+    W = np.outer(w, w) * (1.0 - U)
+    return np.stack([U.ravel(), (V * (1.0 - U)).ravel()], 1), W.ravel()   # weights sum to 1/2
+
+
+def test_radon_rule_exact_to_degree_5():
+    """Integrals of s1^a s2^b over the reference triangle: a! b! / (a+b+2)!,
+    exact for a + b <= 5 and not for every monomial of degree 6."""
+    lam, w = fo.radon_rule()
+    assert abs(w.sum() - 1.0) < 1e-15
+    s1, s2 = lam[:, 1], lam[:, 2]
+    for a in range(6):
+        for b in range(6 - a):
+            exact = math.factorial(a) * math.factorial(b) / math.factorial(a + b + 2)
+            assert abs(0.5 * np.dot(w, s1 ** a * s2 ** b) - exact) < 1e-15
+    errs = [abs(0.5 * np.dot(w, s1 ** a * s2 ** (6 - a))
+                - math.factorial(a) * math.factorial(6 - a) / math.factorial(8)) for a in range(7)]
+    assert max(errs) > 1e-6
+
+
+def test_clipping_conserves_area_and_covers_the_triangle():
+    """The pieces of a triangle cut by every cell of its bounding box
+    (Sutherland-Hodgman) have areas that add up to the triangle's, for
+    triangles with vertices on grid lines, inside one cell and across many."""
+    rng = np.random.default_rng(4)
+    N = 8
+    h = 1.0 / N
+    tris = [np.array([[0.1, 0.1], [0.9, 0.2], [0.3, 0.8]]),
+            np.array([[0.25, 0.25], [0.5, 0.25], [0.25, 0.5]]),          # vertices on grid lines
+            np.array([[0.51, 0.52], [0.56, 0.53], [0.52, 0.6]])]          # inside one cell
+    tris += [rng.uniform(0.0, 1.0, (3, 2)) for _ in range(20)]
+    for P in tris:
+        d1, d2 = P[1] - P[0], P[2] - P[0]
+        area = 0.5 * abs(d1[0] * d2[1] - d1[1] * d2[0])
+        lo = np.minimum(np.floor(P.min(0) * N).astype(int), N - 1)
+        hi = np.minimum(np.floor(P.max(0) * N).astype(int), N - 1)
+        tot = 0.0
+        for cy in range(lo[1], hi[1] + 1):
+            for cx in range(lo[0], hi[0] + 1):
+                poly = fo.clip_to_cell(P, cx * h, (cx + 1) * h, cy * h, (cy + 1) * h)
+                for q in poly:   # every piece lies in its cell
+                    assert cx * h - 1e-15 <= q[0] <= (cx + 1) * h + 1e-15
+                    assert cy * h - 1e-15 <= q[1] <= (cy + 1) * h + 1e-15
+                for i in range(1, len(poly) - 1):
+                    e1, e2 = poly[i] - poly[0], poly[i + 1] - poly[0]
+                    tot += 0.5 * abs(e1[0] * e2[1] - e1[1] * e2[0])
+        assert abs(tot - area) <= 1e-14 * max(area, 1e-3)
+
+
+def _sheared_body(m=4, R=0.23, c=(0.47, 0.52)):
+    xy, tris = fi.ring_disk_mesh(m, R, c)
+    d = xy - np.array(c)
+    co, si = np.cos(0.4), np.sin(0.4)
+    X = np.stack([co * d[:, 0] - si * d[:, 1] + 0.3 * d[:, 1], si * d[:, 0] + co * d[:, 1]], 1) + np.array(c)
+    return xy, tris.astype(np.int64), X
+
+
+def test_exact_coupling_reproduces_biquadratic_fields():
+    """For a biquadratic field p, the Q2 interpolant is p itself on every
+    cell, so (C p_nodal)_l must equal the integral over B of chi_l p(X(s)),
+    computed here on whole solid triangles by an independent product rule.
+    The integrand has degree 5 (x^2 y^2 times a linear chi), so the exact
+    rule passes and the degree-4 point rule does not."""
+    xy, tris, X = _sheared_body(m=2)                      # large triangles across many cells
+    rng = np.random.default_rng(9)
+    c = rng.standard_normal((3, 3))                      # p = sum c_ab x^a y^b, a, b <= 2
+
+    def p(pts):
+        return sum(c[a, b] * pts[:, 0] ** a * pts[:, 1] ** b for a in range(3) for b in range(3))
+
+    s, w = _duffy_rule(5)
+    ref = np.zeros(xy.shape[0])
+    for t in range(tris.shape[0]):
+        A, Bv, Cv = xy[tris[t]]
+        jac = abs((Bv - A)[0] * (Cv - A)[1] - (Bv - A)[1] * (Cv - A)[0])
+        lam = np.stack([1.0 - s[:, 0] - s[:, 1], s[:, 0], s[:, 1]], 1)
+        Xq = lam @ X[tris[t]]
+        for k in range(3):
+            ref[tris[t, k]] += jac * np.dot(w, lam[:, k] * p(Xq))
+    for N in (6, 8, 16):
+        grid = fo.FluidGrid(N)
+        pn = p(grid.node_xy)
+        Cx = fo.assemble_coupling_exact(grid, xy, tris, X)
+        assert np.max(np.abs(Cx @ pn - ref)) <= 1e-13 * np.max(np.abs(ref))
+        Cp, _ = fo.assemble_coupling(grid, xy, tris, X)
+        assert np.max(np.abs(Cp @ pn - ref)) > 1e-10 * np.max(np.abs(ref))
+
+
+def test_exact_coupling_partition_of_unity_and_agreement_with_point_rule():
+    """Rows of the exact C sum to the rows of the solid mass matrix (the Q2
+    basis sums to one); and as the solid mesh is refined on a fixed fluid
+    grid (triangles ever more often inside a single cell, where the integrand
+    is one polynomial), the point rule approaches the exact rule."""
+    grid = fo.FluidGrid(8)
+    errs = []
+    for m in (3, 6, 12):
+        xy, tris, X = _sheared_body(m=m)
+        Cs, _ = fo.assemble_solid(xy, tris, 1.0)
+        mass = np.asarray(Cs.sum(axis=1)).ravel()
+        Cx = fo.assemble_coupling_exact(grid, xy, tris, X)
+        assert np.max(np.abs(np.asarray(Cx.sum(axis=1)).ravel() - mass)) <= 1e-13 * mass.max()
+        Cp, _ = fo.assemble_coupling(grid, xy, tris, X)
+        u = np.cos(3.0 * grid.node_xy[:, 0]) * np.sin(2.0 * grid.node_xy[:, 1])   # a smooth nodal field
+        errs.append(np.max(np.abs(Cx @ u - Cp @ u)) / np.max(np.abs(Cx @ u)))
+    assert errs[2] < errs[1] < errs[0]
+
+
+def test_exact_coupling_rejects_vertices_outside():
+    xy, tris, X = _sheared_body()
+    X = X.copy()
+    X[0] = (1.01, 0.5)
+    with pytest.raises(ValueError):
+        fo.assemble_coupling_exact(fo.FluidGrid(8), xy, tris, X)
