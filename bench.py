@@ -304,6 +304,22 @@ def roofline(prob, args):
         except Exception:
             pass
     dom = out["velocity_chebyshev_f32"]
+    # C_f assembly (S2-S4) with the located-point rule of this workload, and
+    # with the paper's exact rule (mesh intersection) on the same X^n
+    try:
+        ms, _ = prob.time_kernel(8, reps=20)
+        out["cf_assembly_point_rule"] = {"us": ms * 1e3}
+        from paper_2301_10041_gb300 import fsi as _f
+        import fsi_inputs as _fi
+        c = _fi.config1()
+        px = _f.problem_from_case(c, precision=1, precond=PRECOND, stokes_its=STOKES_ITS, coupling=1,
+                                  **arm_settings(1))
+        px.assemble_step()
+        ms, _ = px.time_kernel(9, reps=20)
+        out["cf_assembly_exact_rule"] = {"us": ms * 1e3}
+        px.close()
+    except Exception as e:  # report, do not fail the bench line
+        out["cf_assembly_error"] = str(e)
     traffic = None   # DRAM bytes per launch from the committed ncu summary of this kernel
     prof = os.path.join(ROOT, "profiles", "ncu_velocity_chebyshev_f32_cavity128.md")
     if os.path.exists(prof):

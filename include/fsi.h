@@ -96,6 +96,11 @@ typedef struct fsi_params {
                           shared memory of one thread-block cluster run as one
                           cluster launch per V-cycle (same arithmetic); -1: one
                           kernel launch per phase on every level */
+    int    coupling;   /* C_f(X^n) quadrature: 0 = the degree-4 6-point rule at
+                          points located in the fluid grid; 1 = exact, by
+                          intersecting each mapped solid triangle with the
+                          fluid cells (Sutherland-Hodgman) and integrating the
+                          pieces with a degree-5 rule (Section 4) */
 } fsi_params;
 
 /* Solid reference mesh (the body at t = 0, P1 triangles, counter-clockwise). */
@@ -180,7 +185,8 @@ int fsi_sizes(const fsi_problem* p, int* n_u, int* n_p, int* n_x, int* n_total);
 
 /* Test hooks.  Point location of the last fsi_assemble_step: for point
  * id = 6*triangle + q, the fluid cell id (cy*N + cx, or -1 outside) and the
- * local coordinates (xi, eta) in [0,1]^2.  Arrays of 6*n_tris; may be NULL. */
+ * local coordinates (xi, eta) in [0,1]^2.  Arrays of 6*n_tris; may be NULL.
+ * FSI_ERR_INVALID with coupling = 1 (the exact rule locates no points). */
 int fsi_get_points(fsi_problem* p, int* cell, double* xi, double* eta);
 
 /* Test hook: the scalar coupling matrix C of the last fsi_assemble_step in
@@ -219,7 +225,9 @@ int fsi_graph_kernel_counts(const fsi_problem* p, int* counts);
  * pressure-Laplacian hierarchy in FP32, with L2 left warm as inside a solve
  * (bytes = 0: a latency figure); 6 and 7: the cluster launch of that
  * hierarchy's coarse levels alone (FSI_ERR_INVALID when they run as
- * per-level kernels).  avg_ms: mean launch time; bytes:
+ * per-level kernels); 8: the C_f row assembly by located points (coupling
+ * 0 only), 9: by mesh intersection (coupling 1 only), both on the current
+ * X^n (L2 evicted; bytes = 0).  avg_ms: mean launch time; bytes:
  * algorithmic bytes of one launch (stored blocks and indices without
  * padding, each vector once).  Allocates
  * and frees a 256 MiB scratch buffer. */

@@ -1033,6 +1033,7 @@ static void check_params(const fsi_params& p, int n_nodes, int n_tris) {
   if (p.precision != 0 && p.precision != 1) throw std::invalid_argument("precision");
   if (n_nodes < 3 || n_tris < 1) throw std::invalid_argument("solid mesh");
   if (p.mg_cluster != 0 && p.mg_cluster != -1) throw std::invalid_argument("mg_cluster");
+  if (p.coupling != 0 && p.coupling != 1) throw std::invalid_argument("coupling");
 }
 
 static fsi_params with_defaults(fsi_params p) {
@@ -1114,10 +1115,15 @@ static KrylovArgs krylov_args(Problem& P, cudaGraphConditionalHandle h) {
 
 static void assemble_launch(Problem& P, cudaStream_t s) {
   CK(cudaMemsetAsync(&P.ctl->aflags, 0, sizeof(int), s));
-  launch(k_locate, nblk(P.nPts, 256), 256, 0, s, P.nPts, P.N, P.tris, P.Xold, P.cell, P.xi, P.eta, &P.ctl->aflags);
-  launch(k_cf_rows, nblk(P.nS, kCfWarps), 32 * kCfWarps, 0, s, P.nS, P.N, P.ntp, P.nt, P.area, P.cell, P.xi, P.eta,
-                                                          P.l2n, P.wall, P.cf_cap, P.cf_len, P.cf_col, P.cf_val,
-                                                          P.cf_val32, P.cflift, &P.ctl->aflags);
+  if (P.prm.coupling == 1) {  // the paper's exact rule: mesh intersection
+    launch(k_cf_rows_exact, nblk(P.nS, kCfWarps), 32 * kCfWarps, 0, s, P.nS, P.N, P.ntp, P.nt, P.tris, P.Xold, P.area,
+           P.l2n, P.wall, P.cf_cap, P.cf_len, P.cf_col, P.cf_val, P.cf_val32, P.cflift, &P.ctl->aflags);
+  } else {                    // located points of the degree-4 rule
+    launch(k_locate, nblk(P.nPts, 256), 256, 0, s, P.nPts, P.N, P.tris, P.Xold, P.cell, P.xi, P.eta, &P.ctl->aflags);
+    launch(k_cf_rows, nblk(P.nS, kCfWarps), 32 * kCfWarps, 0, s, P.nS, P.N, P.ntp, P.nt, P.area, P.cell, P.xi, P.eta,
+                                                            P.l2n, P.wall, P.cf_cap, P.cf_len, P.cf_col, P.cf_val,
+                                                            P.cf_val32, P.cflift, &P.ctl->aflags);
+  }
   CK(cudaMemsetAsync(P.cft_cnt, 0, sizeof(int) * P.nU, s));
   const size_t nslot = (size_t)P.nS * P.cf_cap;
   launch(k_cft_count, nblk(nslot, 256), 256, 0, s, P.nS, P.cf_cap, P.cf_len, P.cf_col, P.cft_cnt);
@@ -1295,6 +1301,30 @@ static void allocate_problem(Problem& P, const double* ref_xy, const int* tris_h
   P.cell = ar.alloc<int>(P.nPts);
   P.xi = ar.alloc<double>(P.nPts);
   P.eta = ar.alloc<double>(P.nPts);
+  // capacity of a coupling row: the fluid lattice nodes of the cells that the
+  // triangles around one solid node overlap in the reference configuration
+  // (at least 64, at most the assembly window); a row that outgrows it later
+  // raises FSI_ERR_CAPACITY
+  {
+    int need = 64;
+    for (int l = 0; l < P.nS; ++l) {
+      double lo[2] = {1e300, 1e300}, hi[2] = {-1e300, -1e300};
+      for (int k = hs.node_tri_ptr[l]; k < hs.node_tri_ptr[l + 1]; ++k) {
+        const int t = hs.node_tri[k] / 3;
+        for (int v = 0; v < 3; ++v)
+          for (int c = 0; c < 2; ++c) {
+            const double x = ref_xy[2 * (size_t)tris_h[3 * (size_t)t + v] + c];
+            lo[c] = std::min(lo[c], x);
+            hi[c] = std::max(hi[c], x);
+          }
+      }
+      if (hi[0] < lo[0]) continue;
+      const int cw = (int)std::floor(hi[0] * P.N) - (int)std::floor(lo[0] * P.N) + 1;
+      const int ch = (int)std::floor(hi[1] * P.N) - (int)std::floor(lo[1] * P.N) + 1;
+      need = std::max(need, (2 * cw + 1) * (2 * ch + 1));
+    }
+    P.cf_cap = std::min(need, kCfWindow);
+  }
   const size_t cfslots = (size_t)nblk(P.nS, 32) * 32 * P.cf_cap;
   P.cf_len = ar.alloc<int>(P.nS);
   P.cf_col = ar.alloc<int>(cfslots);
@@ -1498,6 +1528,22 @@ int fsi_create_problem_budget(const fsi_params* params, const fsi_solid_mesh* me
       triangle_rule(lam, w);
       CK(cudaMemcpyToSymbol(c_rule_lam, lam, sizeof(lam)));
       CK(cudaMemcpyToSymbol(c_rule_w, w, sizeof(w)));
+      // Radon's 7-point rule (exact to degree 5) from its closed form: the
+      // centroid, weight 9/40; orbits (a, a, 1-2a), a = (6 -/+ sqrt 15)/21,
+      // weights (155 -/+ sqrt 15)/1200
+      double rl[7][3], rw[7];
+      const double r15 = std::sqrt(15.0);
+      rl[0][0] = rl[0][1] = rl[0][2] = 1.0 / 3.0;
+      rw[0] = 9.0 / 40.0;
+      const double oa[2] = {(6.0 - r15) / 21.0, (6.0 + r15) / 21.0};
+      const double ow[2] = {(155.0 - r15) / 1200.0, (155.0 + r15) / 1200.0};
+      for (int o = 0; o < 2; ++o)
+        for (int k = 0; k < 3; ++k) {
+          for (int c = 0; c < 3; ++c) rl[1 + 3 * o + k][c] = (c == k) ? 1.0 - 2.0 * oa[o] : oa[o];
+          rw[1 + 3 * o + k] = ow[o];
+        }
+      CK(cudaMemcpyToSymbol(c_radon_lam, rl, sizeof(rl)));
+      CK(cudaMemcpyToSymbol(c_radon_w, rw, sizeof(rw)));
     }
     allocate_problem(P, mesh->ref_xy, mesh->tris);
     CK(cudaMemset(P.ctl, 0, sizeof(Ctl)));
@@ -1729,6 +1775,7 @@ int fsi_sizes(const fsi_problem* h, int* n_u, int* n_p, int* n_x, int* n_total) 
 int fsi_get_points(fsi_problem* h, int* cell, double* xi, double* eta) {
   if (!h) return FSI_ERR_INVALID;
   Problem& P = h->P;
+  if (P.prm.coupling != 0) return FSI_ERR_INVALID;  // the exact rule locates no points
   try {
     if (cell) CK(cudaMemcpyAsync(cell, P.cell, (size_t)P.nPts * 4, cudaMemcpyDeviceToHost, P.stream));
     if (xi) CK(cudaMemcpyAsync(xi, P.xi, (size_t)P.nPts * 8, cudaMemcpyDeviceToHost, P.stream));
@@ -1831,7 +1878,9 @@ int fsi_graph_kernel_counts(const fsi_problem* h, int* counts) {
 int fsi_time_kernel(fsi_problem* h, int which, int reps, double* avg_ms, double* bytes) {
   if (!h || !avg_ms || !bytes || reps <= 0) return FSI_ERR_INVALID;
   Problem& P = h->P;
-  if ((which == 0 || which == 2 || which >= 4) && P.prm.precision != 1) return FSI_ERR_INVALID;
+  if ((which == 0 || which == 2 || (which >= 4 && which <= 7)) && P.prm.precision != 1) return FSI_ERR_INVALID;
+  if (which == 8 && P.prm.coupling != 0) return FSI_ERR_INVALID;  // would overwrite the exact rows
+  if (which == 9 && P.prm.coupling != 1) return FSI_ERR_INVALID;
   if (which == 3 && P.p64.mgU.lv.empty()) return FSI_ERR_INVALID;  // no FP64 hierarchy in mixed mode
   try {
     // total C_f entries of the last assembly
@@ -1885,6 +1934,18 @@ int fsi_time_kernel(fsi_problem* h, int which, int reps, double* avg_ms, double*
           *bytes = 0;
           break;
         }
+        case 8:    // C_f rows by the degree-4 rule at located points (S2 + S4)
+          launch(k_locate, nblk(P.nPts, 256), 256, 0, s, P.nPts, P.N, P.tris, P.Xold, P.cell, P.xi, P.eta,
+                 &P.ctl->aflags);
+          launch(k_cf_rows, nblk(P.nS, kCfWarps), 32 * kCfWarps, 0, s, P.nS, P.N, P.ntp, P.nt, P.area, P.cell, P.xi,
+                 P.eta, P.l2n, P.wall, P.cf_cap, P.cf_len, P.cf_col, P.cf_val, P.cf_val32, P.cflift, &P.ctl->aflags);
+          *bytes = 0;
+          break;
+        case 9:    // C_f rows by the exact rule (mesh intersection)
+          launch(k_cf_rows_exact, nblk(P.nS, kCfWarps), 32 * kCfWarps, 0, s, P.nS, P.N, P.ntp, P.nt, P.tris, P.Xold,
+                 P.area, P.l2n, P.wall, P.cf_cap, P.cf_len, P.cf_col, P.cf_val, P.cf_val32, P.cflift, &P.ctl->aflags);
+          *bytes = 0;
+          break;
         case 6:    // the cluster launch of the velocity coarse levels alone, FP32
         case 7: {  // the same for the pressure Laplacian
           MG<float>& mg = (which == 6) ? P.p32.mgU : P.p32.mgP;
