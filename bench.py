@@ -417,7 +417,7 @@ def run_profile_step(args):
     build.build()
     case = workload()
     prob = fsi.problem_from_case(case, precision=1, precond=PRECOND, rtol=1e-8, max_it=MAX_IT, stokes_its=STOKES_ITS,
-                                 **arm_settings(1))
+                                 coupling=1 if args.coupling == "exact" else 0, **arm_settings(1))
     for _ in range(args.warmup):
         prob.step()
     info = prob.step()
@@ -572,6 +572,8 @@ def main():
     ap.add_argument("--serve-max-resident", type=int, default=16)
     ap.add_argument("--serve-wall", type=float, default=60.0)
     ap.add_argument("--serve-stokes-its", type=int, default=8)
+    ap.add_argument("--coupling", choices=["point", "exact"], default="point",
+                    help="C_f rule of --profile-step (the bench line always uses the point rule)")
     ap.add_argument("--sweep-sizes", default=",".join(str(v) for v in SWEEP_SIZES))
     ap.add_argument("--sweep-steps", type=int, default=2)
     ap.add_argument("--sweep-max-it", type=int, default=SWEEP_MAX_IT)

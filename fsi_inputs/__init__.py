@@ -109,6 +109,38 @@ def ellipse_mesh(m: int, a: float, b: float, angle_deg: float, center=(0.5, 0.5)
     return out, tris
 
 
+def bar_mesh(nx: int, ny: int, x0: float = 0.0, x1: float = 0.4, y0: float = 0.45, y1: float = 0.55):
+    """Structured P1 triangulation of the rectangle [x0,x1] x [y0,y1]
+    ((nx+1)(ny+1) nodes, row-major from the bottom left; each grid square cut
+    by the diagonal from its bottom-left corner, counter-clockwise)."""
+    xs = np.linspace(x0, x1, nx + 1)
+    ys = np.linspace(y0, y1, ny + 1)
+    X, Y = np.meshgrid(xs, ys)
+    xy = np.stack([X.ravel(), Y.ravel()], 1)
+    tris = []
+    for j in range(ny):
+        for i in range(nx):
+            a = j * (nx + 1) + i
+            b, c, d = a + 1, a + nx + 2, a + nx + 1
+            tris += [(a, b, c), (a, c, d)]
+    return xy, np.array(tris, dtype=np.int32)
+
+
+def config5_bar(N: int = 32, nx: int = 16, ny: int = 4, bend: float = 0.05) -> FsiCase:
+    """Nonlinear solid (the bar test of Section 6): the bar [0,0.4] x
+    [0.45,0.55] with W(F) = (gamma/(2 eta)) exp(eta (tr F^T F - 2)),
+    gamma = 1.333, eta = 9.242, rho = 1, nu = 0.2, dt = 0.002, walls and
+    fluid at rest.  The paper pulls the bar down by a force of unstated size
+    and releases it; here the bar starts bent down (X0 = s - bend (s_x/0.4)^2
+    e_y, clamped at the left wall) and relaxes, which is the released phase."""
+    xy, tris = bar_mesh(nx, ny)
+    X0 = xy.copy()
+    X0[:, 1] -= bend * (xy[:, 0] / 0.4) ** 2
+    return FsiCase(N=N, rho_f=1.0, nu=0.2, kappa=0.0, dt=0.002, lid_u=0.0, ref_xy=xy, tris=tris,
+                   u0=wall_velocity(N, 0.0), X0=X0, precond=1, rtol=1e-8, steps=1, name=f"bar_N{N}",
+                   extra={"solid_law": "exp", "gamma": 1.333, "eta": 9.242})
+
+
 def node_grid_shape(N: int) -> int:
     """Number of Q2 nodes per side of the N x N cell grid."""
     return 2 * N + 1

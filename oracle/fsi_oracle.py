@@ -420,6 +420,55 @@ def assemble_coupling_exact(grid: FluidGrid, ref_xy: np.ndarray, tris: np.ndarra
     return C
 
 
+# --------------------------------------------------------------------------
+# Nonlinear solid (Section 6, bar test): exponential strain energy
+# --------------------------------------------------------------------------
+
+
+def exp_law_energy(F, gamma: float, eta: float):
+    """W(F) = (gamma / (2 eta)) exp(eta (tr(F^T F) - 2)) per element, F [t, 2, 2]."""
+    n2 = np.einsum("tck,tck->t", F, F)
+    return (gamma / (2.0 * eta)) * np.exp(eta * (n2 - 2.0))
+
+
+def deformation_gradients(ref_xy: np.ndarray, tris: np.ndarray, X: np.ndarray):
+    """F_E = dX/ds on every P1 triangle (constant): F[t, c, k] = sum_v X_{v,c} d chi_v / d s_k."""
+    _, grads = p1_geometry(ref_xy, tris)                     # [t, 3, 2]
+    return np.einsum("tvc,tvk->tck", X[tris], grads)
+
+
+def solid_nonlinear(ref_xy: np.ndarray, tris: np.ndarray, X: np.ndarray, gamma: float, eta: float):
+    """The solid term (P(F), grad Y)_B of Problem 3 for P = dW/dF =
+    gamma exp(eta (|F|^2 - 2)) F, and its derivative in X.
+
+    Returns S [n_s, 2] with S_i = sum_E |E| P(F_E) grad chi_i, and the
+    tangent K_T = dS/dX as a sparse (2 n_s x 2 n_s) matrix in the order
+    2*node + component:
+      K_T[(i,d),(j,c)] = sum_E |E| e (delta_dc grad chi_j . grad chi_i
+                                      + 2 eta (F grad chi_j)_c (F grad chi_i)_d),
+    e = gamma exp(eta (|F|^2 - 2))."""
+    area, grads = p1_geometry(ref_xy, tris)
+    F = deformation_gradients(ref_xy, tris, X)
+    e = gamma * np.exp(eta * (np.einsum("tck,tck->t", F, F) - 2.0))
+    ns = ref_xy.shape[0]
+    S = np.zeros((ns, 2))
+    FG = np.einsum("tck,tvk->tvc", F, grads)                  # (F grad chi_v)_c
+    np.add.at(S, tris, (area * e)[:, None, None] * FG)
+    rows, cols, vals = [], [], []
+    for v in range(3):
+        for w in range(3):
+            gg = np.einsum("tk,tk->t", grads[:, v], grads[:, w])
+            for d in range(2):
+                for c in range(2):
+                    val = area * e * ((1.0 if d == c else 0.0) * gg + 2.0 * eta * FG[:, w, c] * FG[:, v, d])
+                    rows.append(2 * tris[:, v] + d)
+                    cols.append(2 * tris[:, w] + c)
+                    vals.append(val)
+    K = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                      shape=(2 * ns, 2 * ns)).tocsr()
+    return S, K
+
+
 def kron2(A):
     """Scalar operator acting on both components of interleaved 2-vectors."""
     return sp.kron(A, sp.identity(2), format="csr")
@@ -463,13 +512,22 @@ def nested_dissection(G, xy, leaf: int = 64):
 class OracleProblem:
     """Constant matrices of one FSI instance (the paper's T_ass work)."""
 
-    def __init__(self, N, rho_f, nu, kappa, dt, lid_u, ref_xy, tris, coupling: str = "point"):
+    def __init__(self, N, rho_f, nu, kappa, dt, lid_u, ref_xy, tris, coupling: str = "point",
+                 solid_law: str = "linear", gamma: float = 0.0, eta: float = 0.0, newton_tol: float = 1e-6,
+                 newton_max: int = 30):
         """coupling: "point" (the degree-4 point rule with point location) or
-        "exact" (mesh intersection, the paper's rule of Section 4)."""
+        "exact" (mesh intersection, the paper's rule of Section 4).
+        solid_law: "linear" (P = kappa F) or "exp" (the exponential strain
+        energy of the bar test, Section 6, solved by Newton's method)."""
         self.N, self.rho, self.nu, self.kappa, self.dt, self.lid_u = N, rho_f, nu, kappa, dt, lid_u
         if coupling not in ("point", "exact"):
             raise ValueError("coupling")
+        if solid_law not in ("linear", "exp"):
+            raise ValueError("solid_law")
         self.coupling = coupling
+        self.solid_law, self.gamma, self.eta = solid_law, gamma, eta
+        self.newton_tol, self.newton_max = newton_tol, newton_max
+        self.newton_history = []
         self.grid = FluidGrid(N)
         self.ref_xy = np.asarray(ref_xy, dtype=np.float64)
         self.tris = np.asarray(tris, dtype=np.int64)
@@ -489,7 +547,7 @@ class OracleProblem:
             uD[top, 0] = lid_u
         self.u_wall = uD
 
-    def system(self, u_nodal, X):
+    def system(self, u_nodal, X, X_iter=None):
         """Block matrix of Eq. (matrix) on interior velocity dofs and its
         right-hand side, for the state (u^n, X^n).
 
@@ -518,13 +576,22 @@ class OracleProblem:
         C_I = Cf[:, I]
         C_D = Cf[:, D]
         Z = None
+        # solid row: linear law A_s X; exponential law linearised at the
+        # Newton iterate X_k: K_T(X_k) X = K_T(X_k) X_k - S(X_k) + ...
+        if self.solid_law == "exp":
+            Xk = np.asarray(X if X_iter is None else X_iter, dtype=np.float64)
+            S, KT = solid_nonlinear(self.ref_xy, self.tris, Xk, self.gamma, self.eta)
+            Asolid = KT
+            g3 = KT @ Xk.reshape(-1) - S.reshape(-1)
+        else:
+            Asolid = self.As
+            g3 = np.zeros(Xn.size)
         Kmat = sp.bmat([[A_II, -B_I.T, Z, C_I.T],
                         [-B_I, Z, Z, Z],
-                        [Z, Z, self.As, -self.Cs],
+                        [Z, Z, Asolid, -self.Cs],
                         [C_I, Z, -(1.0 / self.dt) * self.Cs, Z]], format="csr")
         g1 = (self.rho / self.dt) * (self.M[I] @ un) - A_ID @ uD
         g2 = B_D @ uD
-        g3 = np.zeros(Xn.size)
         g4 = -(1.0 / self.dt) * (self.Cs @ Xn) - C_D @ uD
         rhs = np.concatenate([g1, g2, g3, g4])
         return Kmat, rhs, loc
@@ -611,13 +678,32 @@ class OracleProblem:
     def step(self, u_nodal, X):
         """One backward-Euler step (Section 4): returns u^{n+1} (nodal, with
         wall values), p^{n+1} [N^2, 3], X^{n+1} [n_s, 2], lambda^{n+1} [n_s, 2]."""
-        Kmat, rhs, _ = self.system(u_nodal, X)
-        x = self.solve_system(Kmat, rhs, X)
-        return self.split(x)
+        if self.solid_law == "linear":
+            Kmat, rhs, _ = self.system(u_nodal, X)
+            x = self.solve_system(Kmat, rhs, X)
+            return self.split(x)
+        # Newton's method on the nonlinear solid row (Section 4): each iterate
+        # solves the block system linearised at X_k; stop when the change of X
+        # is below newton_tol times the step's displacement (absolute floor
+        # 1e-13)
+        Xk = np.asarray(X, dtype=np.float64)
+        self.newton_history = []
+        for _ in range(self.newton_max):
+            Kmat, rhs, _ = self.system(u_nodal, X, Xk)
+            out = self.split(self.solve_system(Kmat, rhs, X))
+            Xn1 = out[2]
+            dX = np.max(np.abs(Xn1 - Xk))
+            self.newton_history.append(dX)
+            Xk = Xn1
+            if dX <= max(self.newton_tol * np.max(np.abs(Xn1 - X)), 1e-13):
+                return out
+        raise RuntimeError("Newton did not converge")
 
     def relative_residual(self, u_nodal_old, X_old, u_new, p, X_new, lam):
-        """||b - K x|| / ||b|| of a candidate solution in the oracle's operator."""
-        Kmat, rhs, _ = self.system(u_nodal_old, X_old)
+        """||b - K x|| / ||b|| of a candidate solution in the oracle's operator
+        (for the exponential law the system linearised at X_new, whose
+        residual is the nonlinear one: S(X_new) - C_s lambda in the solid rows)."""
+        Kmat, rhs, _ = self.system(u_nodal_old, X_old, X_new if self.solid_law == "exp" else None)
         x = self.pack(u_new, p, X_new, lam)
         return float(np.linalg.norm(rhs - Kmat @ x) / np.linalg.norm(rhs))
 

@@ -222,6 +222,8 @@ __device__ __forceinline__ void exact_pair(const double (*P)[2], double det, dou
   if (n < 3) return;
   const double d1x = P[1][0] - P[0][0], d1y = P[1][1] - P[0][1];
   const double d2x = P[2][0] - P[0][0], d2y = P[2][1] - P[0][1];
+  const double idet = 1.0 / det;       // one division per pair: the FP64 pipe is the bound
+  const double fN = (double)N;
   for (int i = 1; i + 1 < n; ++i) {
     const double e1x = b0[i][0] - b0[0][0], e1y = b0[i][1] - b0[0][1];
     const double e2x = b0[i + 1][0] - b0[0][0], e2y = b0[i + 1][1] - b0[0][1];
@@ -231,10 +233,10 @@ __device__ __forceinline__ void exact_pair(const double (*P)[2], double det, dou
       const double xq = c_radon_lam[q][0] * b0[0][0] + c_radon_lam[q][1] * b0[i][0] + c_radon_lam[q][2] * b0[i + 1][0];
       const double yq = c_radon_lam[q][0] * b0[0][1] + c_radon_lam[q][1] * b0[i][1] + c_radon_lam[q][2] * b0[i + 1][1];
       const double rx = xq - P[0][0], ry = yq - P[0][1];
-      const double l1 = (rx * d2y - ry * d2x) / det;
-      const double l2 = (d1x * ry - d1y * rx) / det;
+      const double l1 = (rx * d2y - ry * d2x) * idet;
+      const double l2 = (d1x * ry - d1y * rx) * idet;
       const double la = (a == 0) ? 1.0 - l1 - l2 : (a == 1 ? l1 : l2);
-      const double xi = (xq - cx * h) / h, eta = (yq - cy * h) / h;
+      const double xi = xq * fN - cx, eta = yq * fN - cy;
       const double wq = asub * c_radon_w[q] * la;
       double bx[3], by[3];
 #pragma unroll

@@ -464,3 +464,74 @@ def test_exact_coupling_rejects_vertices_outside():
     X[0] = (1.01, 0.5)
     with pytest.raises(ValueError):
         fo.assemble_coupling_exact(fo.FluidGrid(8), xy, tris, X)
+
+
+# ------------------------------------------------------- nonlinear solid law
+
+def _bent_bar():
+    case = fi.config5_bar(N=16, nx=8, ny=2)
+    return case, case.ref_xy, case.tris.astype(np.int64), case.X0
+
+
+def test_exp_law_stress_is_the_energy_gradient():
+    """S = d/dX of sum_E |E| W(F_E), by central differences of the energy."""
+    _, xy, tris, X = _bent_bar()
+    g, e = 1.333, 9.242
+    area, _ = fo.p1_geometry(xy, tris)
+
+    def energy(Xv):
+        return float(np.dot(area, fo.exp_law_energy(fo.deformation_gradients(xy, tris, Xv), g, e)))
+
+    S, _ = fo.solid_nonlinear(xy, tris, X, g, e)
+    rng = np.random.default_rng(1)
+    for _ in range(6):
+        i, c = int(rng.integers(xy.shape[0])), int(rng.integers(2))
+        hstep = 1e-6
+        Xp, Xm = X.copy(), X.copy()
+        Xp[i, c] += hstep
+        Xm[i, c] -= hstep
+        fd = (energy(Xp) - energy(Xm)) / (2 * hstep)
+        assert abs(fd - S[i, c]) <= 1e-6 * max(1.0, abs(S[i, c]))
+
+
+def test_exp_law_tangent_is_the_stress_derivative():
+    """K_T = dS/dX, column by column by central differences of S."""
+    _, xy, tris, X = _bent_bar()
+    g, e = 1.333, 9.242
+    _, K = fo.solid_nonlinear(xy, tris, X, g, e)
+    K = K.toarray()
+    for j in (0, 5, 11, 20):
+        for c in range(2):
+            hstep = 1e-6
+            Xp, Xm = X.copy(), X.copy()
+            Xp[j, c] += hstep
+            Xm[j, c] -= hstep
+            Sp, _ = fo.solid_nonlinear(xy, tris, Xp, g, e)
+            Sm, _ = fo.solid_nonlinear(xy, tris, Xm, g, e)
+            fd = ((Sp - Sm) / (2 * hstep)).reshape(-1)
+            assert np.max(np.abs(fd - K[:, 2 * j + c])) <= 1e-5 * max(1.0, np.max(np.abs(K)))
+
+
+def test_exp_law_tends_to_the_linear_law():
+    """As eta -> 0, W -> gamma/(2 eta) + (gamma/2)(|F|^2 - 2): P -> gamma F,
+    so S -> A_s X with kappa = gamma (the linear law of Eq. (matrix))."""
+    _, xy, tris, X = _bent_bar()
+    S, K = fo.solid_nonlinear(xy, tris, X, 1.333, 1e-9)
+    _, As = fo.assemble_solid(xy, tris, 1.333)
+    assert np.max(np.abs(S - As @ X)) <= 1e-7 * np.max(np.abs(S))
+    assert abs(K - fo.kron2(As)).max() <= 1e-7 * abs(K).max()
+
+
+def test_newton_converges_quadratically_on_the_bar():
+    """Newton on the linearised block systems: the change of X falls at
+    least quadratically until it reaches rounding, and the converged state
+    has a small nonlinear residual in the oracle's operator."""
+    case, xy, tris, X = _bent_bar()
+    o = fo.OracleProblem(case.N, case.rho_f, case.nu, case.kappa, case.dt, case.lid_u, xy, tris,
+                         solid_law="exp", gamma=1.333, eta=9.242, newton_tol=1e-12)
+    u, p, Xn, lam = o.step(case.u0, case.X0)
+    h = o.newton_history
+    assert len(h) >= 3
+    for a, b in zip(h[:-2], h[1:-1]):
+        assert b <= 100.0 * a * a or b <= 1e-11
+    assert o.relative_residual(case.u0, case.X0, u, p, Xn, lam) < 1e-10
