@@ -101,6 +101,16 @@ typedef struct fsi_params {
                           intersecting each mapped solid triangle with the
                           fluid cells (Sutherland-Hodgman) and integrating the
                           pieces with a degree-5 rule (Section 4) */
+    int    solid_law;  /* 0: P(F) = kappa F (the linear law of Eq. (matrix));
+                          1: the exponential strain energy of the bar test
+                          (Section 6), W(F) = (gamma/(2 eta)) exp(eta (tr F^T F
+                          - 2)), each time step solved by Newton's method */
+    double gamma;      /* solid_law 1: gamma of W (the paper's test: 1.333) */
+    double eta;        /* solid_law 1: eta of W (the paper's test: 9.242) */
+    double newton_tol; /* solid_law 1: stop when max |X_{k+1} - X_k| <=
+                          newton_tol * max |X_{k+1} - X^n| (floor 1e-13);
+                          0 = 1e-6 */
+    int    newton_max; /* solid_law 1: Newton iteration cap; 0 = 20 */
 } fsi_params;
 
 /* Solid reference mesh (the body at t = 0, P1 triangles, counter-clockwise). */
@@ -119,6 +129,9 @@ typedef struct fsi_solve_info {
     int    status;           /* same as the return value */
     double rel_residual;     /* true ||b - A x|| / ||b|| in FP64 at exit */
     double rel_residual_est; /* last Krylov estimate */
+    int    newton_iterations; /* solid_law 1: Newton iterations of the step (each
+                                 one linear solve; iterations above sum over
+                                 them); 0 for the linear law */
 } fsi_solve_info;
 
 typedef struct fsi_problem fsi_problem;  /* opaque; owns all device memory */

@@ -268,6 +268,7 @@ struct FullOp {
   const TA* cf_val = nullptr;
   int cf_cap = 0;
   TA inv_dt = 0;
+  const TA* kt = nullptr;             // nonlinear solid: 2x2 tangent blocks in the Ssol slots
 };
 
 template <class TA, class TX, class TY>
@@ -326,8 +327,14 @@ __global__ void __launch_bounds__(128, sizeof(TA) == 4 ? 16 : 8) k_fullmv(FullOp
         TA Xv[2], Lv[2];
         load_x<TX, TA, 2>(x + offX, c, Xv);
         load_x<TX, TA, 2>(x + offL, c, Lv);
-        a[0] += as * Xv[0] - cs * Lv[0];
-        a[1] += as * Xv[1] - cs * Lv[1];
+        if (op.kt) {  // tangent of the nonlinear law: a 2x2 block per slot
+          const TA* kb = op.kt + 4 * (size_t)slot;
+          a[0] += kb[0] * Xv[0] + kb[1] * Xv[1] - cs * Lv[0];
+          a[1] += kb[2] * Xv[0] + kb[3] * Xv[1] - cs * Lv[1];
+        } else {
+          a[0] += as * Xv[0] - cs * Lv[0];
+          a[1] += as * Xv[1] - cs * Lv[1];
+        }
         a[2] -= op.inv_dt * cs * Xv[0];
         a[3] -= op.inv_dt * cs * Xv[1];
       }

@@ -28,6 +28,7 @@
 #include "fsi_coupling.cuh"
 #include "fsi_internal.h"
 #include "fsi_kernels.cuh"
+#include "fsi_solid.cuh"
 
 namespace fsi {
 
@@ -401,6 +402,7 @@ struct Prec {
   T *ru = nullptr, *t = nullptr, *dz = nullptr;
   int stokes_its = 1;
   T stokes_omega = 1;
+  Sell<T> KT;            // nonlinear solid: the tangent as 2x2 blocks (pattern of the solid pair matrix)
 };
 
 struct Problem;
@@ -426,6 +428,11 @@ struct Problem {
   int* l2n = nullptr; double* wall = nullptr;
   int* cell = nullptr; double* xi = nullptr; double* eta = nullptr;
   int cf_cap = 64;
+  // nonlinear solid: reference gradients of the P1 basis per triangle (3 x 2),
+  // tangent blocks in the slots of the solid pair matrix (4 per slot)
+  double* tgrad = nullptr;
+  double* kt64 = nullptr;
+  float* kt32 = nullptr;
   int* cf_len = nullptr; int* cf_col = nullptr; double* cf_val = nullptr; float* cf_val32 = nullptr;
   double* cflift = nullptr;
   int* cft_ptr = nullptr; int* cft_col = nullptr; double* cft_val = nullptr; float* cft_val32 = nullptr;
@@ -493,7 +500,7 @@ static void solid_launch(Problem& P, Prec<T>& pr, cudaStream_t s) {
   SpmvArgs<T> a2;
   a2.x = zX; a2.y = pr.sb; a2.z = vX; a2.alpha = 1; a2.beta = -1;
   a2.d = pr.sd; a2.dinv = pr.csdinv; a2.xo = pr.sx; a2.c2 = (T)pr.chs.c0;
-  sell_launch(pr.As, MODE_INIT, a2, s);
+  sell_launch(P.prm.solid_law == 1 ? pr.KT : pr.As, MODE_INIT, a2, s);
   cheb_rest(zL);
 }
 
@@ -1034,6 +1041,8 @@ static void check_params(const fsi_params& p, int n_nodes, int n_tris) {
   if (n_nodes < 3 || n_tris < 1) throw std::invalid_argument("solid mesh");
   if (p.mg_cluster != 0 && p.mg_cluster != -1) throw std::invalid_argument("mg_cluster");
   if (p.coupling != 0 && p.coupling != 1) throw std::invalid_argument("coupling");
+  if (p.solid_law != 0 && p.solid_law != 1) throw std::invalid_argument("solid_law");
+  if (p.solid_law == 1 && !(p.gamma > 0 && p.eta > 0)) throw std::invalid_argument("gamma, eta");
 }
 
 static fsi_params with_defaults(fsi_params p) {
@@ -1048,6 +1057,8 @@ static fsi_params with_defaults(fsi_params p) {
   if (p.stokes_its <= 0) p.stokes_its = 1;
   if (p.stokes_its > 16) p.stokes_its = 16;
   if (!(p.stokes_omega > 0)) p.stokes_omega = 1.0;
+  if (!(p.newton_tol > 0)) p.newton_tol = 1e-6;
+  if (p.newton_max <= 0) p.newton_max = 20;
   return p;
 }
 
@@ -1064,6 +1075,12 @@ static void build_prec(Problem& P, Prec<T>& pr, const FullOp<T>& op, bool alloc_
   pr.op = op;
   pr.Cs = upload_sell<T>(ar, to_sell(P.hs.Cs));
   pr.As = upload_sell<T>(ar, to_sell(P.hs.As));
+  if (P.prm.solid_law == 1) {
+    pr.KT.nrows = P.nS; pr.KT.BR = 2; pr.KT.BC = 2; pr.KT.NV = 4; pr.KT.kron = false;
+    pr.KT.soff = op.Ssol.soff; pr.KT.len = op.Ssol.len; pr.KT.col = op.Ssol.col;
+    if constexpr (std::is_same<T, double>::value) pr.KT.val = P.kt64;
+    else pr.KT.val = P.kt32;
+  }
   pr.mpinv = upload_as<T>(ar, P.hs.mp_inv);
   pr.csdinv = upload_as<T>(ar, P.hs.cs_dinv);
   pr.vin = ar.alloc<T>(P.n);
@@ -1093,6 +1110,10 @@ static FullOp<T> make_op(Problem& P, const T* cfv, const T* cftv) {
   op.cft_ptr = P.cft_ptr; op.cft_col = P.cft_col; op.cft_val = cftv;
   op.cf_len = P.cf_len; op.cf_col = P.cf_col; op.cf_val = cfv; op.cf_cap = P.cf_cap;
   op.inv_dt = (T)(1.0 / P.prm.dt);
+  if (P.prm.solid_law == 1) {
+    if constexpr (std::is_same<T, double>::value) op.kt = P.kt64;
+    else op.kt = P.kt32;
+  }
   return op;
 }
 
@@ -1324,6 +1345,24 @@ static void allocate_problem(Problem& P, const double* ref_xy, const int* tris_h
       need = std::max(need, (2 * cw + 1) * (2 * ch + 1));
     }
     P.cf_cap = std::min(need, kCfWindow);
+  }
+  if (P.prm.solid_law == 1) {
+    std::vector<double> tg(6 * (size_t)P.nTri);
+    for (int t = 0; t < P.nTri; ++t) {
+      const double* p0 = ref_xy + 2 * (size_t)tris_h[3 * t];
+      const double* p1 = ref_xy + 2 * (size_t)tris_h[3 * t + 1];
+      const double* p2 = ref_xy + 2 * (size_t)tris_h[3 * t + 2];
+      const double d1x = p1[0] - p0[0], d1y = p1[1] - p0[1], d2x = p2[0] - p0[0], d2y = p2[1] - p0[1];
+      const double det = d1x * d2y - d1y * d2x;
+      const double g1x = d2y / det, g1y = -d2x / det, g2x = -d1y / det, g2y = d1x / det;
+      const double v[6] = {-(g1x + g2x), -(g1y + g2y), g1x, g1y, g2x, g2y};
+      for (int q = 0; q < 6; ++q) tg[6 * (size_t)t + q] = v[q];
+    }
+    P.tgrad = ar.upload(tg);
+    const SellHost ss = to_sell(hs.Ssol);
+    const size_t nslot = (size_t)ss.soff[ss.nslices];
+    P.kt64 = ar.alloc<double>(4 * nslot);
+    P.kt32 = ar.alloc<float>(4 * nslot);
   }
   const size_t cfslots = (size_t)nblk(P.nS, 32) * 32 * P.cf_cap;
   P.cf_len = ar.alloc<int>(P.nS);
@@ -1622,10 +1661,10 @@ static void enqueue_advance(Problem& P) {
   CK(cudaMemcpyAsync(P.Xold, P.x + P.offX, 2 * (size_t)P.nS * 8, cudaMemcpyDeviceToDevice, P.stream));
 }
 
-int fsi_solve_step(fsi_problem* h, fsi_solve_info* info) {
-  if (!h) return FSI_ERR_INVALID;
-  Problem& P = h->P;
-  try {
+// One linear solve of the assembled block system (S5-S8) from the current
+// iterate P.x.
+static int solve_linear(Problem& P, fsi_solve_info* info) {
+  {
     if (!P.host_loop) {
       enqueue_solve(P);
       CK(cudaStreamSynchronize(P.stream));
@@ -1654,13 +1693,65 @@ int fsi_solve_step(fsi_problem* h, fsi_solve_info* info) {
     CK(cudaMemcpyAsync(P.ctl_host, P.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, P.stream));
     CK(cudaStreamSynchronize(P.stream));
     return fill_info(P, info);
+  }
+}
+
+// Newton's method for the nonlinear solid law (Section 4: a nonlinear P(F)
+// is handled by a Newton iteration): from X_0 = X^n, each iteration puts the
+// tangent K_T(X_k) in place of A_s and K_T X_k - S(X_k) in the solid rows of
+// the right-hand side, and solves the block system from the current iterate.
+// Stops when max |X_{k+1} - X_k| <= newton_tol * max |X_{k+1} - X^n| (floor
+// 1e-13).
+static int solve_newton(Problem& P, fsi_solve_info* info) {
+  const size_t n2 = 2 * (size_t)P.nS;
+  std::vector<double> xk(n2), xn(n2), xo(n2);
+  CK(cudaMemcpyAsync(P.x + P.offX, P.Xold, n2 * 8, cudaMemcpyDeviceToDevice, P.stream));
+  CK(cudaMemcpyAsync(xo.data(), P.Xold, n2 * 8, cudaMemcpyDeviceToHost, P.stream));
+  CK(cudaStreamSynchronize(P.stream));
+  xk = xo;
+  int total_its = 0, st = FSI_OK;
+  fsi_solve_info last{};
+  for (int it = 0; it < P.prm.newton_max; ++it) {
+    launch(k_solid_tangent, nblk(P.nS, 128), 128, 0, P.stream, P.nS, P.ntp, P.nt, P.tris, P.area, P.tgrad,
+           (const double*)(P.x + P.offX), P.prm.gamma, P.prm.eta, P.op64.Ssol.soff, P.op64.Ssol.len,
+           P.op64.Ssol.col, P.kt64, P.kt32, P.b + P.offX, &P.ctl->aflags);
+    st = solve_linear(P, &last);
+    total_its += last.iterations;
+    if (st != FSI_OK) break;
+    CK(cudaMemcpyAsync(xn.data(), P.x + P.offX, n2 * 8, cudaMemcpyDeviceToHost, P.stream));
+    CK(cudaStreamSynchronize(P.stream));
+    double dx = 0.0, disp = 0.0;
+    for (size_t i = 0; i < n2; ++i) {
+      dx = std::max(dx, std::fabs(xn[i] - xk[i]));
+      disp = std::max(disp, std::fabs(xn[i] - xo[i]));
+    }
+    xk.swap(xn);
+    last.newton_iterations = it + 1;
+    if (dx <= std::max(P.prm.newton_tol * disp, 1e-13)) break;
+    if (it + 1 == P.prm.newton_max) st = FSI_ERR_NOT_CONVERGED;
+    P.assembled = true;  // C_f(X^n) and the linear right-hand side stay as assembled
+  }
+  P.assembled = false;
+  last.iterations = total_its;
+  last.status = st;
+  if (info) *info = last;
+  return st;
+}
+
+int fsi_solve_step(fsi_problem* h, fsi_solve_info* info) {
+  if (!h) return FSI_ERR_INVALID;
+  Problem& P = h->P;
+  try {
+    if (info) info->newton_iterations = 0;
+    if (P.prm.solid_law == 1) return solve_newton(P, info);
+    return solve_linear(P, info);
   } catch (...) {
     return map_exception();
   }
 }
 
 int fsi_step_async(fsi_problem* h) {
-  if (!h || h->P.host_loop) return FSI_ERR_INVALID;
+  if (!h || h->P.host_loop || h->P.prm.solid_law != 0) return FSI_ERR_INVALID;
   Problem& P = h->P;
   try {
     P.assembled = false;
@@ -1685,7 +1776,7 @@ int fsi_step_poll(fsi_problem* h, fsi_solve_info* info) {
 int fsi_step_batch(fsi_problem* const* problems, int count, fsi_solve_info* infos) {
   if (!problems || count < 0) return FSI_ERR_INVALID;
   for (int i = 0; i < count; ++i)
-    if (!problems[i] || problems[i]->P.host_loop) return FSI_ERR_INVALID;
+    if (!problems[i] || problems[i]->P.host_loop || problems[i]->P.prm.solid_law != 0) return FSI_ERR_INVALID;
   int first_err = FSI_OK;
   try {
     // queue every instance's whole step on its own stream, then wait for all

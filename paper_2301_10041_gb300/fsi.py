@@ -34,7 +34,8 @@ class fsi_params(C.Structure):
                 ("restart", C.c_int), ("rtol", C.c_double), ("max_it", C.c_int), ("mg_degree", C.c_int),
                 ("cs_degree", C.c_int), ("inner_rtol", C.c_double), ("max_refine", C.c_int),
                 ("stokes_its", C.c_int), ("stokes_omega", C.c_double), ("mg_cluster", C.c_int),
-                ("coupling", C.c_int)]
+                ("coupling", C.c_int), ("solid_law", C.c_int), ("gamma", C.c_double), ("eta", C.c_double),
+                ("newton_tol", C.c_double), ("newton_max", C.c_int)]
 
 
 class fsi_solid_mesh(C.Structure):
@@ -44,7 +45,7 @@ class fsi_solid_mesh(C.Structure):
 
 class fsi_solve_info(C.Structure):
     _fields_ = [("iterations", C.c_int), ("refinements", C.c_int), ("restarts", C.c_int), ("status", C.c_int),
-                ("rel_residual", C.c_double), ("rel_residual_est", C.c_double)]
+                ("rel_residual", C.c_double), ("rel_residual_est", C.c_double), ("newton_iterations", C.c_int)]
 
 
 EXPORTS = {
@@ -113,11 +114,12 @@ def _f64(a) -> np.ndarray:
 
 def make_params(N, rho_f, nu, kappa, dt, lid_u=0.0, precond=1, precision=0, restart=0, rtol=0.0, max_it=0,
                 mg_degree=0, cs_degree=0, inner_rtol=0.0, max_refine=0, stokes_its=0,
-                stokes_omega=0.0, mg_cluster=0, coupling=0) -> fsi_params:
+                stokes_omega=0.0, mg_cluster=0, coupling=0, solid_law=0, gamma=0.0, eta=0.0, newton_tol=0.0,
+                newton_max=0) -> fsi_params:
     return fsi_params(int(N), float(rho_f), float(nu), float(kappa), float(dt), float(lid_u), int(precond),
                       int(precision), int(restart), float(rtol), int(max_it), int(mg_degree), int(cs_degree),
                       float(inner_rtol), int(max_refine), int(stokes_its), float(stokes_omega), int(mg_cluster),
-                      int(coupling))
+                      int(coupling), int(solid_law), float(gamma), float(eta), float(newton_tol), int(newton_max))
 
 
 def footprint_bytes(params: fsi_params, n_nodes: int, n_tris: int) -> int:
@@ -132,6 +134,7 @@ class SolveInfo:
     status: int
     rel_residual: float
     rel_residual_est: float
+    newton_iterations: int = 0
 
 
 class Problem:
@@ -186,7 +189,7 @@ class Problem:
         if check:
             self._check(st, "fsi_solve_step")
         return SolveInfo(info.iterations, info.refinements, info.restarts, info.status, info.rel_residual,
-                         info.rel_residual_est)
+                         info.rel_residual_est, info.newton_iterations)
 
     def advance(self):
         self._check(load_library().fsi_advance(self._h), "fsi_advance")
@@ -209,7 +212,7 @@ class Problem:
         if st < 0:
             raise FsiError(st, "fsi_step_poll")
         return SolveInfo(info.iterations, info.refinements, info.restarts, info.status, info.rel_residual,
-                         info.rel_residual_est)
+                         info.rel_residual_est, info.newton_iterations)
 
     # -- state
     def get_state(self):
@@ -309,7 +312,13 @@ def step_batch(problems) -> list:
 
 
 def problem_from_case(case, precision: int = 0, precond=None, rtol=None, stream=None, **kw) -> Problem:
-    """Build a Problem from an ``fsi_inputs.FsiCase``."""
+    """Build a Problem from an ``fsi_inputs.FsiCase`` (its ``extra`` may name
+    the exponential solid law with gamma and eta)."""
+    extra = getattr(case, "extra", None) or {}
+    if extra.get("solid_law") == "exp":
+        kw.setdefault("solid_law", 1)
+        kw.setdefault("gamma", extra["gamma"])
+        kw.setdefault("eta", extra["eta"])
     prm = make_params(case.N, case.rho_f, case.nu, case.kappa, case.dt, case.lid_u,
                       precond=case.precond if precond is None else precond, precision=precision,
                       rtol=case.rtol if rtol is None else rtol, **kw)
