@@ -525,6 +525,57 @@ def run_sweep(args):
     print(json.dumps(out))
 
 
+# ------------------------------------------------------- nonlinear solid (bar)
+BAR_SIZES = (32, 64, 128)
+
+
+def run_bar(args):
+    """The nonlinear bar (Section 6: exponential strain energy, Newton's
+    method) at growing fluid grids with the solid mesh refined alongside:
+    Newton iterations per step, Krylov iterations per Newton iteration and
+    time per step for the block-diagonal and block-triangular preconditioners
+    (the quantities of the paper's nonlinear table)."""
+    import torch
+    import fsi_inputs as fi
+    from paper_2301_10041_gb300 import build, fsi
+    build.build()
+    fsi.load_library()
+    stream = torch.cuda.Stream()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    rows = []
+    for N in [int(v) for v in args.bar_sizes.split(",")]:
+        case = fi.config5_bar(N=N, nx=N // 2, ny=max(2, N // 8))
+        for label, pc in (("block-diagonal", 0), ("block-lower-triangular", 1)):
+            prob = fsi.problem_from_case(case, precision=1, precond=pc, rtol=1e-8, stream=stream.cuda_stream,
+                                         max_it=MAX_IT, restart=60, stokes_its=1)
+            for _ in range(1):
+                prob.step()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(args.bar_steps)]
+            infos = []
+            torch.cuda.synchronize()
+            for k in range(args.bar_steps):
+                with torch.cuda.stream(stream):
+                    flush.fill_(k & 0xFF)
+                ev[k][0].record(stream)
+                infos.append(prob.step())
+                ev[k][1].record(stream)
+            torch.cuda.synchronize()
+            ms = [a.elapsed_time(b) for a, b in ev]
+            newton = [i.newton_iterations for i in infos]
+            rows.append({"N": N, "preconditioner": label, "dofs": int(prob_dofs(case)),
+                         "solid_nodes": int(case.ref_xy.shape[0]), "newton_per_step": newton,
+                         "krylov_per_newton": [round(i.iterations / max(1, i.newton_iterations), 1) for i in infos],
+                         "ms_per_step": float(np.mean(ms)), "status": [i.status for i in infos]})
+            print(json.dumps({"bar_row": rows[-1]}), file=sys.stderr, flush=True)
+            prob.close()
+    print(json.dumps({"metric": METRIC, "workload": "bar", "unit": "time-steps/s", "value": None, "rows": rows,
+                      "config": {"workload": "bar [0,0.4]x[0.45,0.55], W = (gamma/2eta) exp(eta(tr F^T F - 2)), "
+                                             "gamma 1.333, eta 9.242, rho 1, nu 0.2, dt 0.002, bent start, mixed "
+                                             "precision, rtol 1e-8, Newton 1e-6, one V-cycle pair per Stokes "
+                                             "application", "steps": args.bar_steps}}))
+
+
 def run_serve(args):
     """Served stream (configs[4] shape): Poisson arrivals replayed in wall
     time, admission by device footprint, continuous batching."""
@@ -564,8 +615,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=300.0)
     ap.add_argument("--profile-step", action="store_true",
                     help="only build the mixed problem, run --warmup steps and one more (for ncu)")
-    ap.add_argument("--workload", choices=["cavity128", "batch", "serve", "sweep"], default="cavity128",
-                    help="cavity128 (default, the contract line); batch / serve / sweep print their own lines")
+    ap.add_argument("--workload", choices=["cavity128", "batch", "serve", "sweep", "bar"], default="cavity128",
+                    help="cavity128 (default, the contract line); batch / serve / sweep / bar print their own lines")
     ap.add_argument("--batch-instances", type=int, default=256)
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-budget-gb", type=float, default=64.0)
@@ -575,6 +626,8 @@ def main():
     ap.add_argument("--coupling", choices=["point", "exact"], default="point",
                     help="C_f rule of --profile-step (the bench line always uses the point rule)")
     ap.add_argument("--sweep-sizes", default=",".join(str(v) for v in SWEEP_SIZES))
+    ap.add_argument("--bar-sizes", default=",".join(str(v) for v in BAR_SIZES))
+    ap.add_argument("--bar-steps", type=int, default=5)
     ap.add_argument("--sweep-steps", type=int, default=2)
     ap.add_argument("--sweep-max-it", type=int, default=SWEEP_MAX_IT)
     args = ap.parse_args()
@@ -584,6 +637,8 @@ def main():
         return run_serve(args)
     if args.workload == "sweep":
         return run_sweep(args)
+    if args.workload == "bar":
+        return run_bar(args)
     if args.profile_step:
         return run_profile_step(args)
     if args.warmup < 3 and args.impl == "ours":
