@@ -143,7 +143,7 @@ __device__ __forceinline__ void load_x(const TX* __restrict__ x, int c, TA* xv) 
 // then both value blocks and gathered x blocks, so that several independent
 // loads are in flight per thread before the first FMA (two, not more, keeps
 // the kernels at 32 registers and full occupancy).
-template <class TA, class TX, int BR, int BC, bool KRON, int NV>
+template <class TA, class TX, int BR, int BC, bool KRON, int NV, int TPR = kRowThreads>
 __device__ __forceinline__ void sell_row(const Sell<TA>& A, int row, int t, const TX* __restrict__ x, TA* acc) {
   int base, n;
   if (A.nrun > 0) {  // slice offset from the run table (kernel parameters, no memory load)
@@ -159,18 +159,18 @@ __device__ __forceinline__ void sell_row(const Sell<TA>& A, int row, int t, cons
     n = A.len[row];
   }
   constexpr int U = 2;
-  for (int k0 = t; k0 < n; k0 += U * kRowThreads) {
+  for (int k0 = t; k0 < n; k0 += U * TPR) {
     int c[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const int k = k0 + u * kRowThreads;
+      const int k = k0 + u * TPR;
       c[u] = (k < n) ? __ldg(A.col + base + (k << 3)) : -1;
     }
     TA xv[U][BC];
     TA v[U][KRON ? 1 : NV];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const int slot = base + ((k0 + u * kRowThreads) << 3);
+      const int slot = base + ((k0 + u * TPR) << 3);
       if (c[u] >= 0) {
         load_x<TX, TA, BC>(x, c[u], xv[u]);
         if constexpr (KRON) v[u][0] = __ldg(A.val + slot);
@@ -197,27 +197,33 @@ __device__ __forceinline__ void sell_row(const Sell<TA>& A, int row, int t, cons
   }
 }
 
-template <class T, int BR>
+// sum of a row's partial sums over its TPR threads (lane = (32/TPR) t + r)
+template <class T, int BR, int TPR = kRowThreads>
 __device__ __forceinline__ void row_reduce(T* acc) {
 #pragma unroll
   for (int i = 0; i < BR; ++i) {
-    acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], 8);
-    acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], 16);
+#pragma unroll
+    for (int o = 32 / TPR; o < 32; o <<= 1) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], o);
   }
 }
+
+// Threads per block row in the per-level SpMV kernels (k_sell): a warp holds
+// 32 / kSellTPR block rows.
+constexpr int kSellTPR = 4;
 
 template <class T, int BR, int BC, bool KRON, int NV, int MODE>
 __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 16 : 8) k_sell(Sell<T> A, SpmvArgs<T> a) {
   pdl_begin();
+  constexpr int RPW = 32 / kSellTPR;  // block rows per warp
   const int lane = threadIdx.x & 31;
-  const int row = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * kSliceRows + (lane & 7);
-  const int t = lane >> 3;
+  const int row = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * RPW + (lane % RPW);
+  const int t = lane / RPW;
   const bool live = row < A.nrows;
   T acc[BR];
 #pragma unroll
   for (int i = 0; i < BR; ++i) acc[i] = 0;
-  if (live) sell_row<T, T, BR, BC, KRON, NV>(A, row, t, a.x, acc);
-  row_reduce<T, BR>(acc);
+  if (live) sell_row<T, T, BR, BC, KRON, NV, kSellTPR>(A, row, t, a.x, acc);
+  row_reduce<T, BR, kSellTPR>(acc);
   pdl_trigger();
   if (!live || t != 0) return;
   const T* __restrict__ x = a.x;

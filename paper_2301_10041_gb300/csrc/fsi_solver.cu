@@ -148,7 +148,7 @@ static T* upload_as(Arena& ar, const std::vector<double>& h) {
 // ------------------------------------------------------------- SpMV launch
 template <class T, int BR, int BC, bool KRON, int NV>
 static void sell_launch_shape(const Sell<T>& A, int mode, const SpmvArgs<T>& a, cudaStream_t s) {
-  const unsigned g = nblk(A.nrows, 32);  // 4 warps x 8 block rows
+  const unsigned g = nblk(A.nrows, 4 * (32 / kSellTPR));  // 4 warps x 32/kSellTPR block rows
   switch (mode) {
     case MODE_AXPBY: launch(k_sell<T, BR, BC, KRON, NV, MODE_AXPBY>, g, 128, 0, s, A, a); break;
     case MODE_CHEB: launch(k_sell<T, BR, BC, KRON, NV, MODE_CHEB>, g, 128, 0, s, A, a); break;
