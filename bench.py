@@ -587,6 +587,41 @@ def run_bar(args):
                                              "application", "steps": args.bar_steps}}))
 
 
+# ----------------------------------------------- quarter annulus (Table 1)
+ANNULUS_SIZES = (48, 96, 192, 384)
+
+
+def run_annulus(args):
+    """The linear-solid refinement test of Section 6 (the paper's Table 1:
+    quarter annulus released from a stretched state, kappa = 10, nu = 0.1,
+    dt = 0.01): Krylov iterations per step of the block-diagonal and
+    block-lower-triangular preconditioners (one V-cycle pair per Stokes
+    application) as the fluid grid and the solid mesh are refined together."""
+    import torch
+    import fsi_inputs as fi
+    from paper_2301_10041_gb300 import build, fsi
+    build.build()
+    fsi.load_library()
+    stream = torch.cuda.Stream()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    rows = []
+    for N in [int(v) for v in args.annulus_sizes.split(",")]:
+        case = fi.config6_annulus(N)
+        for label, pc in (("block-diagonal", 0), ("block-lower-triangular", 1)):
+            prob, st = time_arm(fsi, torch, case, 1, args.annulus_steps, 1, stream, flush, precond=pc, stokes_its=1,
+                                max_it=SWEEP_MAX_IT, check=False, settings=dict(restart=RESTART))
+            rows.append({"N": N, "preconditioner": label, "dofs": int(prob_dofs(case)),
+                         "solid_nodes": int(case.ref_xy.shape[0]), "iterations_per_step": st["iterations"],
+                         "status": st["status"], "ms_per_step": float(np.mean(st["ms"]))})
+            print(json.dumps({"annulus_row": rows[-1]}), file=sys.stderr, flush=True)
+            prob.close()
+    print(json.dumps({"metric": METRIC, "workload": "annulus", "unit": "time-steps/s", "value": None, "rows": rows,
+                      "config": {"workload": "quarter annulus 0.3<=|s|<=0.5 released from X = (s1/1.4, 1.4 s2), "
+                                             "kappa 10, rho 1, nu 0.1, dt 0.01, no-slip walls, mixed precision, rtol "
+                                             "1e-8, restart %d, one V-cycle pair per Stokes application" % RESTART,
+                                 "steps": args.annulus_steps}}))
+
+
 def run_serve(args):
     """Served stream (configs[4] shape): Poisson arrivals replayed in wall
     time, admission by device footprint, continuous batching."""
@@ -626,8 +661,9 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=300.0)
     ap.add_argument("--profile-step", action="store_true",
                     help="only build the mixed problem, run --warmup steps and one more (for ncu)")
-    ap.add_argument("--workload", choices=["cavity128", "batch", "serve", "sweep", "bar"], default="cavity128",
-                    help="cavity128 (default, the contract line); batch / serve / sweep / bar print their own lines")
+    ap.add_argument("--workload", choices=["cavity128", "batch", "serve", "sweep", "bar", "annulus"],
+                    default="cavity128",
+                    help="cavity128 (default, the contract line); the others print their own lines")
     ap.add_argument("--batch-instances", type=int, default=256)
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-budget-gb", type=float, default=64.0)
@@ -639,6 +675,8 @@ def main():
     ap.add_argument("--sweep-sizes", default=",".join(str(v) for v in SWEEP_SIZES))
     ap.add_argument("--bar-sizes", default=",".join(str(v) for v in BAR_SIZES))
     ap.add_argument("--bar-steps", type=int, default=5)
+    ap.add_argument("--annulus-sizes", default=",".join(str(v) for v in ANNULUS_SIZES))
+    ap.add_argument("--annulus-steps", type=int, default=2)
     ap.add_argument("--sweep-steps", type=int, default=2)
     ap.add_argument("--sweep-max-it", type=int, default=SWEEP_MAX_IT)
     args = ap.parse_args()
@@ -650,6 +688,8 @@ def main():
         return run_sweep(args)
     if args.workload == "bar":
         return run_bar(args)
+    if args.workload == "annulus":
+        return run_annulus(args)
     if args.profile_step:
         return run_profile_step(args)
     if args.warmup < 3 and args.impl == "ours":

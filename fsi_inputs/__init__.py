@@ -141,6 +141,42 @@ def config5_bar(N: int = 32, nx: int = 16, ny: int = 4, bend: float = 0.05) -> F
                    extra={"solid_law": "exp", "gamma": 1.333, "eta": 9.242})
 
 
+def annulus_mesh(nr: int, nt: int, r0: float = 0.3, r1: float = 0.5):
+    """Structured P1 triangulation of the quarter annulus {x, y >= 0,
+    r0 <= |x| <= r1}: nodes (r_i cos t_j, r_i sin t_j) on nr radial and nt
+    angular intervals, node id = j (nr+1) + i; each (r, t) cell cut by a
+    diagonal, counter-clockwise.  The edges t = 0 and t = pi/2 lie exactly on
+    y = 0 and x = 0."""
+    r = np.linspace(r0, r1, nr + 1)
+    t = np.linspace(0.0, 0.5 * np.pi, nt + 1)
+    R, T = np.meshgrid(r, t)
+    xy = np.stack([R * np.cos(T), R * np.sin(T)], -1).reshape(-1, 2)
+    xy[-(nr + 1):, 0] = 0.0          # t = pi/2 on the wall x = 0
+    xy[:nr + 1, 1] = 0.0             # t = 0 on the wall y = 0
+    tris = []
+    for j in range(nt):
+        for i in range(nr):
+            a = j * (nr + 1) + i
+            b, c, d = a + 1, a + nr + 2, a + nr + 1
+            tris += [(a, b, c), (a, c, d)]
+    return xy, np.array(tris, dtype=np.int32)
+
+
+def config6_annulus(N: int = 48) -> FsiCase:
+    """The linear-solid test of Section 6 (Table 1): the quarter annulus
+    0.3 <= |s| <= 0.5 in the first quadrant, kappa = 10, rho = 1, nu = 0.1,
+    dt = 0.01, fluid at rest, released from the stretched state
+    X(s, 0) = (s1 / 1.4, 1.4 s2).  Solid mesh refined with the fluid grid
+    (about one solid interval per fluid cell).  The paper lets fluid and body
+    slide along the walls x = 0 and y = 0; here every wall is no-slip."""
+    nr = max(2, int(np.ceil(0.2 * N)))
+    nt = max(4, int(np.ceil(0.2 * np.pi * N)))
+    xy, tris = annulus_mesh(nr, nt)
+    X0 = np.stack([xy[:, 0] / 1.4, 1.4 * xy[:, 1]], 1)
+    return FsiCase(N=N, rho_f=1.0, nu=0.1, kappa=10.0, dt=0.01, lid_u=0.0, ref_xy=xy, tris=tris,
+                   u0=wall_velocity(N, 0.0), X0=X0, precond=1, rtol=1e-8, steps=1, name=f"annulus_N{N}")
+
+
 def node_grid_shape(N: int) -> int:
     """Number of Q2 nodes per side of the N x N cell grid."""
     return 2 * N + 1

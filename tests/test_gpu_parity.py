@@ -146,3 +146,19 @@ def test_five_step_trajectory(fsi):
     assert rel(Xg - case.X0, X - case.X0) < 1e-7
     assert rel(lamg, lam) < 1e-7
     g.close()
+
+
+@pytest.mark.parametrize("precond", [0, 1])
+def test_quarter_annulus_one_step(fsi, precond):
+    """The linear-solid test geometry of Section 6 (quarter annulus released
+    from its stretched state; edges on the walls x = 0 and y = 0)."""
+    case = fi.config6_annulus(16)
+    g = fsi.problem_from_case(case, precision=0, precond=precond, rtol=1e-12)
+    info = g.step()
+    assert info.rel_residual <= 1e-12
+    u, p, X, lam = g.get_state()
+    uo, po, Xo, lamo = _oracle(case).step(case.u0, case.X0)
+    assert rel(u, uo) < 1e-7
+    assert rel(X - case.X0, Xo - case.X0) < 1e-7
+    assert rel(lam, lamo) < 1e-7
+    g.close()
