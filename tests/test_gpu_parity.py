@@ -162,3 +162,21 @@ def test_quarter_annulus_one_step(fsi, precond):
     assert rel(X - case.X0, Xo - case.X0) < 1e-7
     assert rel(lam, lamo) < 1e-7
     g.close()
+
+
+@pytest.mark.parametrize("N", [4, 6, 8, 12])
+def test_tiny_grids(fsi, N):
+    """Degenerate hierarchies: N <= 8 has a single level (the V-cycle is the
+    dense inverse, no cluster suffix); N = 12 coarsens once to an odd grid."""
+    xy, tris = fi.ring_disk_mesh(3, 0.2, (0.5, 0.5))
+    case = fi.FsiCase(N=N, rho_f=1.0, nu=0.5, kappa=10.0, dt=0.01, lid_u=1.0, ref_xy=xy, tris=tris,
+                      u0=fi.initial_velocity(N, 11, lid_u=1.0), X0=xy.copy(), precond=1, rtol=1e-12)
+    for precision, tol in ((0, 1e-7), (1, 1e-5)):
+        g = fsi.problem_from_case(case, precision=precision, rtol=1e-12 if precision == 0 else 1e-9)
+        info = g.step()
+        assert info.status == 0
+        u, p, X, lam = g.get_state()
+        uo, po, Xo, lamo = _oracle(case).step(case.u0, case.X0)
+        assert rel(u, uo) < tol
+        assert rel(lam, lamo) < tol
+        g.close()
