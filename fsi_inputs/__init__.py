@@ -177,6 +177,49 @@ def config6_annulus(N: int = 48) -> FsiCase:
                    u0=wall_velocity(N, 0.0), X0=X0, precond=1, rtol=1e-8, steps=1, name=f"annulus_N{N}")
 
 
+def mirrored_annulus_mesh(nr: int, nt: int, r0: float = 0.3, r1: float = 0.5):
+    """The full annulus r0 <= |x| <= r1 as the quarter mesh of annulus_mesh
+    and its mirror images in x = 0 and y = 0 (orientation restored in the
+    mirrored quadrants; nodes on the mirror lines shared), so that the mesh is
+    exactly symmetric under both reflections."""
+    qxy, qtris = annulus_mesh(nr, nt, r0, r1)
+    index: dict = {}
+    xy: list = []
+    tris: list = []
+    for sx, sy in ((1.0, 1.0), (-1.0, 1.0), (-1.0, -1.0), (1.0, -1.0)):
+        ids = []
+        for p in qxy:
+            key = (sx * p[0] + 0.0, sy * p[1] + 0.0)   # + 0.0: one key for -0.0 and 0.0
+            if key not in index:
+                index[key] = len(xy)
+                xy.append(key)
+            ids.append(index[key])
+        for a, b, c in qtris:
+            t = (ids[a], ids[b], ids[c])
+            tris.append(t if sx * sy > 0 else (t[0], t[2], t[1]))
+    return np.array(xy), np.array(tris, dtype=np.int32)
+
+
+def config7_symmetric_annulus(Nq: int = 24) -> FsiCase:
+    """The Table 1 test (see config6_annulus) with the paper's free-slip walls
+    x = 0 and y = 0, obtained by symmetry: the quarter problem on [0,1]^2 with
+    free slip on x = 0, y = 0 and no slip on x = 1, y = 1 is the restriction
+    of the full-annulus problem on [-1,1]^2 with no slip everywhere.  That
+    problem, scaled into the unit square (x' = (x + 1)/2, so u' = u/2), is
+    the same dynamics with nu' = nu/4 and kappa' = kappa/4 (pressure /4),
+    rho and dt unchanged.  Nq is the quarter problem's grid; this grid is
+    N = 2 Nq, with the solid mesh mirrored from the quarter mesh."""
+    nr = max(2, int(np.ceil(0.2 * Nq)))
+    nt = max(4, int(np.ceil(0.2 * np.pi * Nq)))
+    xy, tris = mirrored_annulus_mesh(nr, nt)
+    X = np.stack([xy[:, 0] / 1.4, 1.4 * xy[:, 1]], 1)
+    ref = 0.5 + 0.5 * xy
+    X0 = 0.5 + 0.5 * X
+    N = 2 * Nq
+    return FsiCase(N=N, rho_f=1.0, nu=0.1 / 4.0, kappa=10.0 / 4.0, dt=0.01, lid_u=0.0, ref_xy=ref, tris=tris,
+                   u0=wall_velocity(N, 0.0), X0=X0, precond=1, rtol=1e-8, steps=1, name=f"annulus_sym_Nq{Nq}")
+
+
 def node_grid_shape(N: int) -> int:
     """Number of Q2 nodes per side of the N x N cell grid."""
     return 2 * N + 1

@@ -180,3 +180,23 @@ def test_tiny_grids(fsi, N):
         assert rel(u, uo) < tol
         assert rel(lam, lamo) < tol
         g.close()
+
+
+def test_symmetric_annulus_one_step_is_mirror_symmetric(fsi):
+    """The full annulus that carries the quarter problem's free-slip walls by
+    symmetry: the GPU step matches the oracle and is mirror-symmetric."""
+    from scipy.spatial import cKDTree
+    case = fi.config7_symmetric_annulus(8)
+    g = fsi.problem_from_case(case, precision=0, precond=1, rtol=1e-12)
+    g.step()
+    u, p, X, lam = g.get_state()
+    uo, po, Xo, lamo = _oracle(case).step(case.u0, case.X0)
+    assert rel(X - case.X0, Xo - case.X0) < 1e-7
+    assert rel(lam, lamo) < 1e-7
+    mirror = case.ref_xy.copy()
+    mirror[:, 0] = 1.0 - mirror[:, 0]
+    idx = cKDTree(case.ref_xy).query(mirror)[1]
+    D = X - case.X0
+    assert np.max(np.abs(D[idx, 0] + D[:, 0])) <= 1e-8 * np.max(np.abs(D))
+    assert np.max(np.abs(D[idx, 1] - D[:, 1])) <= 1e-8 * np.max(np.abs(D))
+    g.close()
