@@ -160,12 +160,14 @@ def time_arm(fsi, torch, case, precision, steps, warmup, stream, flush, precond=
     return prob, stats
 
 
-def time_e2e(fsi, case, precision, steps, stream):
-    """Through the C ABI with host buffers: set_state (H2D) + step + get_state (D2H)."""
+def time_e2e(fsi, case, precision, steps, warmup, stream):
+    """Through the C ABI with host buffers: set_state (H2D) + step + get_state
+    (D2H), over the same time steps as the device-timed arm (after the same
+    warm-up steps: the first steps of the trajectory need more iterations)."""
     prob = fsi.problem_from_case(case, precision=precision, precond=PRECOND, rtol=1e-8, stream=stream.cuda_stream,
                                  max_it=MAX_IT, stokes_its=STOKES_ITS, **arm_settings(precision))
-    u, p, X, lam = prob.get_state()
-    prob.step()
+    for _ in range(warmup):
+        prob.step()
     u, p, X, lam = prob.get_state()
     t = []
     for _ in range(steps):
@@ -233,7 +235,7 @@ def run_ours(args):
     clk = clocks.stop()
     prob_d, fp64 = time_arm(fsi, torch, case, 0, args.steps, args.warmup, stream, flush)
     roof = roofline(prob_m, args)
-    e2e_t, h2d, d2h = time_e2e(fsi, case, 1, max(3, min(args.steps, 10)), stream)
+    e2e_t, h2d, d2h = time_e2e(fsi, case, 1, max(3, min(args.steps, 10)), args.warmup, stream)
     prob_m.close()
     prob_d.close()
 
