@@ -41,7 +41,7 @@ L2_FLUSH_BYTES = 512 << 20
 
 def workload():
     import fsi_inputs as fi
-    return fi.config1()
+    return fi.cavity128_case()
 
 
 def workload_config(case):
@@ -324,7 +324,7 @@ def roofline(prob, args):
         out["cf_assembly_point_rule"] = {"us": ms * 1e3}
         from paper_2301_10041_gb300 import fsi as _f
         import fsi_inputs as _fi
-        c = _fi.config1()
+        c = _fi.cavity128_case()
         px = _f.problem_from_case(c, precision=1, precond=PRECOND, stokes_its=STOKES_ITS, coupling=1,
                                   **arm_settings(1))
         px.assemble_step()
@@ -354,7 +354,7 @@ import numpy as np
 import fsi_inputs as fi
 from oracle import fsi_oracle as fo
 steps = int(sys.argv[2]); budget = float(sys.argv[3])
-case = fi.config1()
+case = fi.cavity128_case()
 t0 = time.perf_counter()
 prob = fo.OracleProblem(case.N, case.rho_f, case.nu, case.kappa, case.dt, case.lid_u, case.ref_xy, case.tris)
 setup = time.perf_counter() - t0
@@ -440,14 +440,14 @@ def run_profile_step(args):
 
 
 def run_batch(args):
-    """Batched uneven instances (configs[3] shape): fsi_step_batch over the
+    """Batched uneven instances (256 cavity instances of uneven size): fsi_step_batch over the
     whole set each tick, every instance on its own stream."""
     import torch
     import fsi_inputs as fi
     from paper_2301_10041_gb300 import build, fsi
     build.build()
     n = args.batch_instances
-    cases = [fi.config3_instance(i) for i in range(n)]
+    cases = [fi.batch_instance(i) for i in range(n)]
     t0 = time.perf_counter()
     probs = [fsi.problem_from_case(c, precision=1, precond=PRECOND, restart=60, max_it=6000,
                                    stokes_its=STOKES_ITS) for c in cases]
@@ -506,7 +506,7 @@ def run_sweep(args):
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     rows = []
     for N in sizes:
-        case = fi.config2(N)
+        case = fi.ellipse_case(N)
         for label, pc, sits in SWEEP_VARIANTS:
             t0 = time.perf_counter()
             prob, st = time_arm(fsi, torch, case, 1, args.sweep_steps, 1, stream, flush, precond=pc,
@@ -557,7 +557,7 @@ def run_bar(args):
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     rows = []
     for N in [int(v) for v in args.bar_sizes.split(",")]:
-        case = fi.config5_bar(N=N, nx=N // 2, ny=max(2, N // 8))
+        case = fi.bar_case(N=N, nx=N // 2, ny=max(2, N // 8))
         for label, pc in (("block-diagonal", 0), ("block-lower-triangular", 1)):
             prob = fsi.problem_from_case(case, precision=1, precond=pc, rtol=1e-8, stream=stream.cuda_stream,
                                          max_it=MAX_IT, restart=60, stokes_its=1)
@@ -612,7 +612,7 @@ def run_annulus(args):
     for N in [int(v) for v in args.annulus_sizes.split(",")]:
         # --annulus-symmetric: the paper's free-slip walls by symmetry (the
         # full annulus on an N grid, equivalent to the quarter on N/2)
-        case = fi.config7_symmetric_annulus(N // 2) if args.annulus_symmetric else fi.config6_annulus(N)
+        case = fi.symmetric_annulus_case(N // 2) if args.annulus_symmetric else fi.annulus_case(N)
         variants = [(lab, pc, int(si)) for si in args.annulus_stokes_its.split(",")
                     for lab, pc in (("block-diagonal", 0), ("block-lower-triangular", 1))]
         for label, pc, sits in variants:
@@ -633,14 +633,14 @@ def run_annulus(args):
 
 
 def run_serve(args):
-    """Served stream (configs[4] shape): Poisson arrivals replayed in wall
+    """Served stream (Poisson arrivals of cavity requests): Poisson arrivals replayed in wall
     time, admission by device footprint, continuous batching."""
     import fsi_inputs as fi
     from paper_2301_10041_gb300 import build
     from paper_2301_10041_gb300.serve import Request, Server, gpu_ops
     build.build()
-    trace = fi.config4_trace(args.serve_requests)
-    reqs = [Request(rid=i, arrival=t, case=fi.config4_case(spec), steps=50) for i, (t, spec) in enumerate(trace)]
+    trace = fi.serve_trace(args.serve_requests)
+    reqs = [Request(rid=i, arrival=t, case=fi.serve_case(spec), steps=50) for i, (t, spec) in enumerate(trace)]
     def largest_body(N):   # R <= 0.3, m = ceil(2 R N): the largest ring mesh for this grid
         m = int(np.ceil(2 * 0.3 * N))
         return 1 + 3 * m * (m + 1), 6 * m * m

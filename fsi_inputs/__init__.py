@@ -126,7 +126,7 @@ def bar_mesh(nx: int, ny: int, x0: float = 0.0, x1: float = 0.4, y0: float = 0.4
     return xy, np.array(tris, dtype=np.int32)
 
 
-def config5_bar(N: int = 32, nx: int = 16, ny: int = 4, bend: float = 0.05) -> FsiCase:
+def bar_case(N: int = 32, nx: int = 16, ny: int = 4, bend: float = 0.05) -> FsiCase:
     """Nonlinear solid (the bar test of Section 6): the bar [0,0.4] x
     [0.45,0.55] with W(F) = (gamma/(2 eta)) exp(eta (tr F^T F - 2)),
     gamma = 1.333, eta = 9.242, rho = 1, nu = 0.2, dt = 0.002, walls and
@@ -162,7 +162,7 @@ def annulus_mesh(nr: int, nt: int, r0: float = 0.3, r1: float = 0.5):
     return xy, np.array(tris, dtype=np.int32)
 
 
-def config6_annulus(N: int = 48) -> FsiCase:
+def annulus_case(N: int = 48) -> FsiCase:
     """The linear-solid test of Section 6 (Table 1): the quarter annulus
     0.3 <= |s| <= 0.5 in the first quadrant, kappa = 10, rho = 1, nu = 0.1,
     dt = 0.01, fluid at rest, released from the stretched state
@@ -200,8 +200,8 @@ def mirrored_annulus_mesh(nr: int, nt: int, r0: float = 0.3, r1: float = 0.5):
     return np.array(xy), np.array(tris, dtype=np.int32)
 
 
-def config7_symmetric_annulus(Nq: int = 24) -> FsiCase:
-    """The Table 1 test (see config6_annulus) with the paper's free-slip walls
+def symmetric_annulus_case(Nq: int = 24) -> FsiCase:
+    """The Table 1 test (see annulus_case) with the paper's free-slip walls
     x = 0 and y = 0, obtained by symmetry: the quarter problem on [0,1]^2 with
     free slip on x = 0, y = 0 and no slip on x = 1, y = 1 is the restriction
     of the full-annulus problem on [-1,1]^2 with no slip everywhere.  That
@@ -282,7 +282,7 @@ class FsiCase:
 BASE_SEED = 2301
 
 
-def config0(seed: int = BASE_SEED + 0) -> FsiCase:
+def disk16_case(seed: int = BASE_SEED + 0) -> FsiCase:
     """Plain FP64 single step: N=16, nu=1, rho=1, kappa=10, dt=0.01, disk
     R=0.2 at (0.5, 0.5) with m=6 (216 triangles), u_0 uniform[-1,1]."""
     N = 16
@@ -292,7 +292,7 @@ def config0(seed: int = BASE_SEED + 0) -> FsiCase:
                    precond=0, rtol=1e-10, steps=1, name="cavity16_disk216_fp64")
 
 
-def config1(seed: int = BASE_SEED + 1, N: int = 128, m: int = 36) -> FsiCase:
+def cavity128_case(seed: int = BASE_SEED + 1, N: int = 128, m: int = 36) -> FsiCase:
     """Plain vs mixed precision: N=128, nu=0.01, kappa=1e3, dt=1e-3, lid 1,
     disk R=0.2 with m=36 (7776 triangles), body at rest, fluid at rest."""
     xy, tris = ring_disk_mesh(m, 0.2, (0.5, 0.5))
@@ -302,7 +302,7 @@ def config1(seed: int = BASE_SEED + 1, N: int = 128, m: int = 36) -> FsiCase:
                    name=f"cavity{N}_lid_disk{len(tris)}")
 
 
-def config2(N: int, seed: int = BASE_SEED + 2) -> FsiCase:
+def ellipse_case(N: int, seed: int = BASE_SEED + 2) -> FsiCase:
     """Size sweep member: ellipse 0.2/0.1 rotated 30 degrees, m = ceil(0.4 N),
     kappa=1e2, nu=1, rho=1, dt=0.01, walls at rest, fluid at rest."""
     m = int(math.ceil(0.4 * N))
@@ -312,7 +312,7 @@ def config2(N: int, seed: int = BASE_SEED + 2) -> FsiCase:
                    precond=1, rtol=1e-8, steps=20, name=f"ellipse_N{N}")
 
 
-def config3_instance(i: int, seed: int = BASE_SEED + 3) -> FsiCase:
+def batch_instance(i: int, seed: int = BASE_SEED + 3) -> FsiCase:
     """Instance i of the batch of uneven problems: N ~ U{16,32,48,64,96},
     R ~ U[0.1,0.3], centre ~ U[0.35,0.65]^2, kappa log-uniform [1,1e4],
     nu log-uniform [1e-3,1], m = ceil(2 R N), walls at rest, u_0 seeded;
@@ -330,7 +330,7 @@ def config3_instance(i: int, seed: int = BASE_SEED + 3) -> FsiCase:
                    X0=xy.copy(), precond=1, rtol=1e-8, steps=50, name=f"batch{i}_N{N}")
 
 
-def config4_trace(n_requests: int = 2000, rate: float = 200.0, seed: int = BASE_SEED + 4):
+def serve_trace(n_requests: int = 2000, rate: float = 200.0, seed: int = BASE_SEED + 4):
     """Served stream: Poisson arrivals (exponential gaps at ``rate``/s); each
     request is 50 steps of a cavity problem with N in {32,64,128,256}
     (p = .4/.3/.2/.1), disk or ellipse (p = 1/2), R ~ U[0.1,0.3],
@@ -348,7 +348,7 @@ def config4_trace(n_requests: int = 2000, rate: float = 200.0, seed: int = BASE_
     return out
 
 
-def config4_case(spec: dict, seed: int = BASE_SEED + 4) -> FsiCase:
+def serve_case(spec: dict, seed: int = BASE_SEED + 4) -> FsiCase:
     N = spec["N"]
     R = spec["R"]
     m = int(math.ceil(2.0 * R * N))

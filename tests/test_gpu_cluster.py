@@ -32,7 +32,7 @@ def _ragged():
                       u0=fi.initial_velocity(24, 7, lid_u=1.0), X0=xy.copy(), precond=2, rtol=1e-12)
 
 
-CASES = {"cfg0": fi.config0, "ragged24": _ragged, "cavity128": fi.config1, "ellipse256": lambda: fi.config2(256)}
+CASES = {"disk16": fi.disk16_case, "ragged24": _ragged, "cavity128": fi.cavity128_case, "ellipse256": lambda: fi.ellipse_case(256)}
 
 
 def _pair(fsi, case, precision, precond, stokes_its):

@@ -26,7 +26,7 @@ def fsi():
 
 
 def test_invalid_parameters_and_empty_mesh_are_refused(fsi):
-    case = fi.config0()
+    case = fi.disk16_case()
     for kw in (dict(N=15), dict(N=18), dict(N=0)):          # odd, c > 8, empty grid
         prm = fsi.make_params(kw["N"], 1.0, 1.0, 10.0, 0.01)
         with pytest.raises(fsi.FsiError) as e:
@@ -42,7 +42,7 @@ def test_invalid_parameters_and_empty_mesh_are_refused(fsi):
 
 
 def test_budget_refusal_allocates_nothing(fsi):
-    case = fi.config1()
+    case = fi.cavity128_case()
     prm = fsi.make_params(case.N, case.rho_f, case.nu, case.kappa, case.dt, case.lid_u, precision=1)
     need = fsi.footprint_bytes(prm, case.ref_xy.shape[0], case.tris.shape[0])
     assert need > 0
@@ -53,7 +53,7 @@ def test_budget_refusal_allocates_nothing(fsi):
 
 @pytest.mark.parametrize("coupling", [0, 1])
 def test_body_outside_the_domain_reports_out_of_domain(fsi, coupling):
-    case = fi.config0()
+    case = fi.disk16_case()
     X0 = case.X0.copy()
     X0[:, 0] += 0.45                                        # the disk crosses x = 1
     g = fsi.Problem(fsi.make_params(case.N, 1.0, 1.0, 10.0, 0.01, coupling=coupling), case.ref_xy, case.tris,
@@ -65,7 +65,7 @@ def test_body_outside_the_domain_reports_out_of_domain(fsi, coupling):
 
 
 def test_nan_velocity_reports_nan(fsi):
-    case = fi.config0()
+    case = fi.disk16_case()
     u0 = case.u0.copy()
     u0[len(u0) // 2] = np.nan
     g = fsi.Problem(fsi.make_params(case.N, 1.0, 1.0, 10.0, 0.01, precond=1), case.ref_xy, case.tris, u0=u0,

@@ -48,7 +48,7 @@ def _coarse_body():
                       u0=fi.initial_velocity(32, 3), X0=X0, precond=1, rtol=1e-12)
 
 
-CASES = {"cfg0": fi.config0, "ragged24": _ragged, "coarse_body32": _coarse_body}
+CASES = {"disk16": fi.disk16_case, "ragged24": _ragged, "coarse_body32": _coarse_body}
 
 
 def _oracle(case):
@@ -96,7 +96,7 @@ def test_exact_coupling_bench_workload(fsi):
     """The N = 128 cavity in the bench's mixed configuration with the exact
     rule: C_f entry by entry, the operator and right-hand side, and a step
     whose residual in the oracle's operator meets 1e-8."""
-    case = fi.config1()
+    case = fi.cavity128_case()
     g = fsi.problem_from_case(case, precision=1, precond=bench.PRECOND, rtol=1e-8, max_it=bench.MAX_IT,
                               stokes_its=bench.STOKES_ITS, coupling=1, **bench.arm_settings(1))
     g.assemble_step()

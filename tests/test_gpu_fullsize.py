@@ -113,7 +113,7 @@ def _check_step(g, case, o):
 def test_cavity128_bench_configuration(fsi):
     """The bench workload itself: N = 128 lid-driven cavity, disk of 7776
     triangles, kappa = 1e3, nu = 0.01, dt = 1e-3."""
-    case = fi.config1()
+    case = fi.cavity128_case()
     g = _bench_problem(fsi, case)
     g.assemble_step()
     _check_location(g, case)
@@ -128,7 +128,7 @@ def test_cavity128_bench_configuration(fsi):
 def test_ellipse_sweep_size(fsi, N):
     """Size sweep members (ellipse, m = ceil(0.4 N)) with the bench
     preconditioner; full comparison of everything before the solve."""
-    case = fi.config2(N)
+    case = fi.ellipse_case(N)
     g = _bench_problem(fsi, case)
     g.assemble_step()
     _check_location(g, case, sample=None if N <= 256 else 40000)
@@ -143,7 +143,7 @@ def test_ellipse_sweep_size(fsi, N):
 def test_ellipse64_every_sweep_preconditioner(fsi, label, precond, stokes_its):
     """Each preconditioner the sweep times reaches the tolerance in the
     oracle's operator."""
-    case = fi.config2(64)
+    case = fi.ellipse_case(64)
     g = _bench_problem(fsi, case, precond=precond, stokes_its=stokes_its, max_it=bench.SWEEP_MAX_IT)
     _check_step(g, case, _oracle(case))
     g.close()
@@ -152,7 +152,7 @@ def test_ellipse64_every_sweep_preconditioner(fsi, label, precond, stokes_its):
 def test_ellipse1024_sampled(fsi):
     """The largest sweep size (11.6 M unknowns, 1 M solid triangles): sampled
     point locations and C_f rows against the oracle, and a converged step."""
-    case = fi.config2(1024)
+    case = fi.ellipse_case(1024)
     g = _bench_problem(fsi, case)
     g.assemble_step()
     _check_location(g, case, sample=40000)

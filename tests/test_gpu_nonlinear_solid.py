@@ -36,7 +36,7 @@ def _oracle(case, tol=1e-12):
 
 @pytest.mark.parametrize("precond", [0, 1, 2])
 def test_bar_one_step_fp64_matches_oracle(fsi, precond):
-    case = fi.config5_bar(N=16, nx=8, ny=2)
+    case = fi.bar_case(N=16, nx=8, ny=2)
     g = fsi.problem_from_case(case, precision=0, precond=precond, rtol=1e-12, newton_tol=1e-12, stokes_its=4)
     info = g.step()
     assert info.status == 0 and info.newton_iterations >= 2
@@ -51,7 +51,7 @@ def test_bar_one_step_fp64_matches_oracle(fsi, precond):
 
 
 def test_bar_three_step_trajectory(fsi):
-    case = fi.config5_bar(N=16, nx=8, ny=2)
+    case = fi.bar_case(N=16, nx=8, ny=2)
     g = fsi.problem_from_case(case, precision=0, precond=1, rtol=1e-12, newton_tol=1e-12)
     o = _oracle(case)
     u, X = case.u0, case.X0
@@ -68,7 +68,7 @@ def test_bar_three_step_trajectory(fsi):
 def test_bar_mixed_precision(fsi):
     """FP32 operators inside FP64 refinement, Newton to the default 1e-6: the
     state is a converged nonlinear solution to the solve's tolerance."""
-    case = fi.config5_bar(N=32, nx=16, ny=4)
+    case = fi.bar_case(N=32, nx=16, ny=4)
     g = fsi.problem_from_case(case, precision=1, precond=2, rtol=1e-10, stokes_its=4, restart=60)
     info = g.step()
     assert info.status == 0 and 2 <= info.newton_iterations <= 6
@@ -81,7 +81,7 @@ def test_bar_mixed_precision(fsi):
 
 
 def test_nonlinear_law_rejects_unsupported_paths(fsi):
-    case = fi.config5_bar(N=16, nx=8, ny=2)
+    case = fi.bar_case(N=16, nx=8, ny=2)
     g = fsi.problem_from_case(case, precision=0)
     with pytest.raises(fsi.FsiError):      # Newton needs the host between solves
         g.step_async()

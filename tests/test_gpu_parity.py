@@ -42,7 +42,7 @@ def _deformed_case(N=24, m=9, seed=7):
                       u0=fi.initial_velocity(N, seed, lid_u=1.0), X0=X0, precond=1, rtol=1e-12)
 
 
-CASES = {"cfg0": fi.config0, "ragged24": _deformed_case}
+CASES = {"disk16": fi.disk16_case, "ragged24": _deformed_case}
 
 
 @pytest.mark.parametrize("name", list(CASES))
@@ -134,7 +134,7 @@ def test_one_step_mixed_precision(fsi, name, precond, stokes_its):
 
 
 def test_five_step_trajectory(fsi):
-    case = fi.config0()
+    case = fi.disk16_case()
     g = fsi.problem_from_case(case, precision=0, precond=1, rtol=1e-12)
     o = _oracle(case)
     u, X = case.u0, case.X0
@@ -152,7 +152,7 @@ def test_five_step_trajectory(fsi):
 def test_quarter_annulus_one_step(fsi, precond):
     """The linear-solid test geometry of Section 6 (quarter annulus released
     from its stretched state; edges on the walls x = 0 and y = 0)."""
-    case = fi.config6_annulus(16)
+    case = fi.annulus_case(16)
     g = fsi.problem_from_case(case, precision=0, precond=precond, rtol=1e-12)
     info = g.step()
     assert info.rel_residual <= 1e-12
@@ -186,7 +186,7 @@ def test_symmetric_annulus_one_step_is_mirror_symmetric(fsi):
     """The full annulus that carries the quarter problem's free-slip walls by
     symmetry: the GPU step matches the oracle and is mirror-symmetric."""
     from scipy.spatial import cKDTree
-    case = fi.config7_symmetric_annulus(8)
+    case = fi.symmetric_annulus_case(8)
     g = fsi.problem_from_case(case, precision=0, precond=1, rtol=1e-12)
     g.step()
     u, p, X, lam = g.get_state()

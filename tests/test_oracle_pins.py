@@ -279,7 +279,7 @@ def test_coupling_rejects_points_outside():
 # ------------------------------------------------------------------- one step
 
 def test_step_residual_and_scipy_agreement():
-    c = fi.config0()
+    c = fi.disk16_case()
     prob = fo.OracleProblem(c.N, c.rho_f, c.nu, c.kappa, c.dt, c.lid_u, c.ref_xy, c.tris)
     Kmat, rhs, _ = prob.system(c.u0, c.X0)
     x = prob.solve_system(Kmat, rhs, c.X0)
@@ -296,7 +296,7 @@ def test_step_residual_and_scipy_agreement():
 
 
 def test_pressure_has_zero_mean_and_velocity_is_discretely_solenoidal():
-    c = fi.config0()
+    c = fi.disk16_case()
     prob, u, p, X, lam = fo.run_steps(c, 1)
     assert abs(p[:, 0].sum()) < 1e-10 * np.abs(p[:, 0]).max()
     div = prob.B @ u.reshape(-1)
@@ -308,7 +308,7 @@ def test_discrete_energy_identity():
     rho/(2dt)(|u1|_M^2 - |u0|_M^2 + |u1-u0|_M^2) + a(u1, u1)
       + kappa/(2dt)(|grad X1|^2 - |grad X0|^2 + |grad(X1-X0)|^2) = 0
     with walls at rest: the coupling and pressure terms cancel in pairs."""
-    c = fi.config0()
+    c = fi.disk16_case()
     prob, u1, p, X1, lam = fo.run_steps(c, 1)
     u0 = c.u0.reshape(-1)
     u1 = u1.reshape(-1)
@@ -469,7 +469,7 @@ def test_exact_coupling_rejects_vertices_outside():
 # ------------------------------------------------------- nonlinear solid law
 
 def _bent_bar():
-    case = fi.config5_bar(N=16, nx=8, ny=2)
+    case = fi.bar_case(N=16, nx=8, ny=2)
     return case, case.ref_xy, case.tris.astype(np.int64), case.X0
 
 

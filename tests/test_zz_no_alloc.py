@@ -28,7 +28,7 @@ def env():
 
 
 def _cases():
-    c0 = fi.config0()
+    c0 = fi.disk16_case()
     xy, tris = fi.ring_disk_mesh(9, 0.23, (0.47, 0.52))
     d = xy - np.array([0.47, 0.52])
     X = np.stack([0.9 * d[:, 0] - 0.3 * d[:, 1], 0.3 * d[:, 0] + 0.9 * d[:, 1]], 1) + np.array([0.47, 0.52])
