@@ -119,11 +119,14 @@ def _step_unchecked(prob):
     return info
 
 
+AUTOTUNE = 0     # 0: one fixed SpMV tile shape (faster inside a step); 1: the library's autotuner
+
+
 def arm_settings(precision):
-    """FGMRES restart and inner tolerance of one arm."""
+    """FGMRES restart, inner tolerance and tile-shape tuning of one arm."""
     if precision == 1:
-        return dict(restart=RESTART_MIXED, inner_rtol=INNER_RTOL)
-    return dict(restart=RESTART)
+        return dict(restart=RESTART_MIXED, inner_rtol=INNER_RTOL, autotune=AUTOTUNE)
+    return dict(restart=RESTART, autotune=AUTOTUNE)
 
 
 def time_arm(fsi, torch, case, precision, steps, warmup, stream, flush, precond=PRECOND, stokes_its=STOKES_ITS,
@@ -680,6 +683,8 @@ def main():
     ap.add_argument("--serve-max-resident", type=int, default=16)
     ap.add_argument("--serve-wall", type=float, default=60.0)
     ap.add_argument("--serve-stokes-its", type=int, default=8)
+    ap.add_argument("--autotune", action="store_true",
+                    help="per-level SpMV tile shapes chosen by the library's autotuner instead of one fixed shape")
     ap.add_argument("--coupling", choices=["point", "exact"], default="point",
                     help="C_f rule of --profile-step (the bench line always uses the point rule)")
     ap.add_argument("--sweep-sizes", default=",".join(str(v) for v in SWEEP_SIZES))
@@ -694,6 +699,9 @@ def main():
     ap.add_argument("--sweep-steps", type=int, default=2)
     ap.add_argument("--sweep-max-it", type=int, default=SWEEP_MAX_IT)
     args = ap.parse_args()
+    global AUTOTUNE
+    if args.autotune:
+        AUTOTUNE = 1
     if args.workload == "batch":
         return run_batch(args)
     if args.workload == "serve":

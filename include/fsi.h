@@ -111,6 +111,12 @@ typedef struct fsi_params {
                           newton_tol * max |X_{k+1} - X^n| (floor 1e-13);
                           0 = 1e-6 */
     int    newton_max; /* solid_law 1: Newton iteration cap; 0 = 20 */
+    int    autotune;   /* 0: one fixed tile shape (4 threads per block row) for
+                          every multigrid level's SpMV; 1: the shape of each
+                          level (4 or 8 threads per block row) is chosen at
+                          creation by timing its Chebyshev smoothing step alone
+                          on the device (cached per matrix shape and size for
+                          the process) */
 } fsi_params;
 
 /* Solid reference mesh (the body at t = 0, P1 triangles, counter-clockwise). */

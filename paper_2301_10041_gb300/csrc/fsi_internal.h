@@ -94,6 +94,7 @@ struct Sell {            // sliced ELL of block rows, slice height 8
   // holds s and scans run_w[k] slots, skipping column -1, so it reads neither
   // soff nor len (one dependent memory round trip less per launch).
   int nrun = 0;
+  int tpr = 4;                 // threads per block row of the per-level SpMV (4 or 8, set by the autotuner)
   int run_s[kMaxRuns] = {};    // first slice of each run
   int run_w[kMaxRuns] = {};    // slots per row in the run
   int run_off[kMaxRuns] = {};  // first slot of the run

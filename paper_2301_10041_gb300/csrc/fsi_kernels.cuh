@@ -207,14 +207,12 @@ __device__ __forceinline__ void row_reduce(T* acc) {
   }
 }
 
-// Threads per block row in the per-level SpMV kernels (k_sell): a warp holds
-// 32 / kSellTPR block rows.
-constexpr int kSellTPR = 4;
-
-template <class T, int BR, int BC, bool KRON, int NV, int MODE>
+// The per-level SpMV (k_sell) takes TPR threads per block row (4 or 8, the
+// tile shape the autotuner picks per matrix): a warp holds 32 / TPR rows.
+template <class T, int BR, int BC, bool KRON, int NV, int MODE, int TPR>
 __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 16 : 8) k_sell(Sell<T> A, SpmvArgs<T> a) {
   pdl_begin();
-  constexpr int RPW = 32 / kSellTPR;  // block rows per warp
+  constexpr int RPW = 32 / TPR;  // block rows per warp
   const int lane = threadIdx.x & 31;
   const int row = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * RPW + (lane % RPW);
   const int t = lane / RPW;
@@ -222,8 +220,8 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 16 : 8) k_sell(Sell<T> A
   T acc[BR];
 #pragma unroll
   for (int i = 0; i < BR; ++i) acc[i] = 0;
-  if (live) sell_row<T, T, BR, BC, KRON, NV, kSellTPR>(A, row, t, a.x, acc);
-  row_reduce<T, BR, kSellTPR>(acc);
+  if (live) sell_row<T, T, BR, BC, KRON, NV, TPR>(A, row, t, a.x, acc);
+  row_reduce<T, BR, TPR>(acc);
   pdl_trigger();
   if (!live || t != 0) return;
   const T* __restrict__ x = a.x;

@@ -15,9 +15,12 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <stdexcept>
 #include <string>
+#include <tuple>
 #include <type_traits>
 #include <utility>
 #include <vector>
@@ -146,15 +149,21 @@ static T* upload_as(Arena& ar, const std::vector<double>& h) {
 }
 
 // ------------------------------------------------------------- SpMV launch
+template <class T, int BR, int BC, bool KRON, int NV, int TPR>
+static void sell_launch_tpr(const Sell<T>& A, int mode, const SpmvArgs<T>& a, cudaStream_t s) {
+  const unsigned g = nblk(A.nrows, 4 * (32 / TPR));  // 4 warps x 32/TPR block rows
+  switch (mode) {
+    case MODE_AXPBY: launch(k_sell<T, BR, BC, KRON, NV, MODE_AXPBY, TPR>, g, 128, 0, s, A, a); break;
+    case MODE_CHEB: launch(k_sell<T, BR, BC, KRON, NV, MODE_CHEB, TPR>, g, 128, 0, s, A, a); break;
+    case MODE_CHEB0: launch(k_sell<T, BR, BC, KRON, NV, MODE_CHEB0, TPR>, g, 128, 0, s, A, a); break;
+    default: launch(k_sell<T, BR, BC, KRON, NV, MODE_INIT, TPR>, g, 128, 0, s, A, a); break;
+  }
+}
+
 template <class T, int BR, int BC, bool KRON, int NV>
 static void sell_launch_shape(const Sell<T>& A, int mode, const SpmvArgs<T>& a, cudaStream_t s) {
-  const unsigned g = nblk(A.nrows, 4 * (32 / kSellTPR));  // 4 warps x 32/kSellTPR block rows
-  switch (mode) {
-    case MODE_AXPBY: launch(k_sell<T, BR, BC, KRON, NV, MODE_AXPBY>, g, 128, 0, s, A, a); break;
-    case MODE_CHEB: launch(k_sell<T, BR, BC, KRON, NV, MODE_CHEB>, g, 128, 0, s, A, a); break;
-    case MODE_CHEB0: launch(k_sell<T, BR, BC, KRON, NV, MODE_CHEB0>, g, 128, 0, s, A, a); break;
-    default: launch(k_sell<T, BR, BC, KRON, NV, MODE_INIT>, g, 128, 0, s, A, a); break;
-  }
+  if (A.tpr == 8) return sell_launch_tpr<T, BR, BC, KRON, NV, 8>(A, mode, a, s);
+  sell_launch_tpr<T, BR, BC, KRON, NV, 4>(A, mode, a, s);
 }
 
 template <class T>
@@ -173,6 +182,81 @@ static SpmvArgs<T> axpby(const T* x, T* y, const T* z, T alpha, T beta) {
   SpmvArgs<T> a;
   a.x = x; a.y = y; a.z = z; a.alpha = alpha; a.beta = beta;
   return a;
+}
+
+// ------------------------------------------------------------- autotuner
+// Tile shape of the per-level SpMV: 4 or 8 threads per block row, chosen per
+// matrix by timing both on the device in the form a V-cycle runs it (the
+// Chebyshev-Jacobi smoothing step, 20 dependent launches captured in a CUDA
+// graph and replayed once warm: the conditions inside a solve); 8 is kept
+// only when at least 5 % faster.
+// Results are cached per (device, block shape, rows, slots, precision) for
+// the life of the process, so instances of one size tune once and problems
+// created in one process take the same shapes (the same rounding).
+static std::mutex g_tune_mu;
+static std::map<std::tuple<int, int, int, int, int, int, int>, int> g_tune;
+
+template <class T>
+static void autotune_sell(Sell<T>& A, int nslots) {
+  if (A.nrows == 0 || A.BR != A.BC) return;
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  const auto key = std::make_tuple(dev, A.BR, A.BC, (int)A.kron, A.nrows, nslots, (int)sizeof(T));
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    const auto it = g_tune.find(key);
+    if (it != g_tune.end()) {
+      A.tpr = it->second;
+      return;
+    }
+  }
+  const size_t nx = (size_t)A.nrows * A.BR;
+  T* buf = nullptr;   // x, y, b, d, dinv
+  CK(cudaMalloc(&buf, 5 * nx * sizeof(T)));
+  CK(cudaMemset(buf, 0, 5 * nx * sizeof(T)));
+  T* x = buf;
+  T* y = buf + nx;
+  cudaStream_t s;
+  CK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  float t[2] = {0.f, 0.f};
+  SpmvArgs<T> axy;
+  axy.z = buf + 2 * nx; axy.d = buf + 3 * nx; axy.dinv = buf + 4 * nx;
+  axy.c1 = (T)0.5; axy.c2 = (T)0.5;
+  SpmvArgs<T> ayx = axy;
+  axy.x = x; axy.y = y;
+  ayx.x = y; ayx.y = x;
+  for (int v = 0; v < 2; ++v) {
+    // 20 dependent launches (x -> y -> x ...) in a CUDA graph, as in a solve
+    Sell<T> B = A;
+    B.tpr = v == 0 ? 4 : 8;
+    cudaGraph_t gr;
+    cudaGraphExec_t ge;
+    CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    for (int r = 0; r < 20; ++r) sell_launch(B, MODE_CHEB, (r & 1) ? ayx : axy, s);
+    CK(cudaStreamEndCapture(s, &gr));
+    CK(cudaGraphInstantiate(&ge, gr, 0));
+    CK(cudaGraphLaunch(ge, s));
+    CK(cudaEventRecord(e0, s));
+    CK(cudaGraphLaunch(ge, s));
+    CK(cudaEventRecord(e1, s));
+    CK(cudaEventSynchronize(e1));
+    CK(cudaEventElapsedTime(&t[v], e0, e1));
+    cudaGraphExecDestroy(ge);
+    cudaGraphDestroy(gr);
+  }
+  A.tpr = (t[1] < 0.95f * t[0]) ? 8 : 4;
+  if (const char* v = getenv("FSI_TUNE_VERBOSE"); v && v[0] == '1')
+    fprintf(stderr, "fsi autotune: %dx%d blocks, %d rows, %s: 4 threads/row %.2f us, 8 threads/row %.2f us -> %d\n",
+            A.BR, A.BC, A.nrows, sizeof(T) == 4 ? "fp32" : "fp64", t[0] * 50.f, t[1] * 50.f, A.tpr);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamDestroy(s);
+  cudaFree(buf);
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune[key] = A.tpr;
 }
 
 // ---------------------------------------------------------------- multigrid
@@ -228,7 +312,7 @@ constexpr double kChebRatioU = 6.0;   // smoothing interval [hi/ratio, hi]
 constexpr double kChebRatioP = 8.0;
 
 template <class T>
-static void build_mg(Arena& ar, const HostSetup& hs, bool pressure, int degree, MG<T>& mg) {
+static void build_mg(Arena& ar, const HostSetup& hs, bool pressure, int degree, MG<T>& mg, bool tune) {
   const int nl = (int)hs.levels.size();
   mg.degree = degree;
   mg.pressure = pressure;
@@ -237,7 +321,9 @@ static void build_mg(Arena& ar, const HostSetup& hs, bool pressure, int degree, 
     const FluidLevelHost& H = hs.levels[l];
     MGLevel<T>& L = mg.lv[l];
     const HostBlockMatrix& A = pressure ? H.L : H.A;
-    L.A = upload_sell<T>(ar, to_sell(A));
+    const SellHost sa = to_sell(A);
+    L.A = upload_sell<T>(ar, sa);
+    if (tune && !ar.count_only) autotune_sell<T>(L.A, sa.soff[sa.nslices]);
     L.n = A.nrows * A.BR;
     L.dinv = upload_as<T>(ar, pressure ? H.dinvL : H.dinvA);
     if (l + 1 < nl) {
@@ -1042,6 +1128,7 @@ static void check_params(const fsi_params& p, int n_nodes, int n_tris) {
   if (p.mg_cluster != 0 && p.mg_cluster != -1) throw std::invalid_argument("mg_cluster");
   if (p.coupling != 0 && p.coupling != 1) throw std::invalid_argument("coupling");
   if (p.solid_law != 0 && p.solid_law != 1) throw std::invalid_argument("solid_law");
+  if (p.autotune != 0 && p.autotune != 1) throw std::invalid_argument("autotune");
   if (p.solid_law == 1 && !(p.gamma > 0 && p.eta > 0)) throw std::invalid_argument("gamma, eta");
 }
 
@@ -1066,8 +1153,8 @@ template <class T>
 static void build_prec(Problem& P, Prec<T>& pr, const FullOp<T>& op, bool alloc_all) {
   (void)alloc_all;
   Arena& ar = P.ar;
-  build_mg<T>(ar, P.hs, false, P.prm.mg_degree, pr.mgU);
-  build_mg<T>(ar, P.hs, true, P.prm.mg_degree, pr.mgP);
+  build_mg<T>(ar, P.hs, false, P.prm.mg_degree, pr.mgU, P.prm.autotune == 1);
+  build_mg<T>(ar, P.hs, true, P.prm.mg_degree, pr.mgP, P.prm.autotune == 1);
   if (P.prm.mg_cluster == 0) {
     setup_cluster<T>(ar, P.hs, pr.mgU, false);
     setup_cluster<T>(ar, P.hs, pr.mgP, true);

@@ -74,3 +74,23 @@ def test_cluster_solve_meets_oracle(fsi, precond):
     assert rel(u, uo) < 1e-7
     assert rel(lam, lamo) < 1e-7
     g.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("name", ["cavity128", "ellipse256"])
+def test_autotuned_tiles_match_fixed_tiles(fsi, name, precision):
+    """The autotuner only changes how the per-level SpMV splits a row over
+    threads (the summation order): the preconditioner is the same to
+    rounding."""
+    case = CASES[name]()
+    kw = dict(precision=precision, precond=bench.PRECOND, stokes_its=bench.STOKES_ITS, restart=bench.RESTART)
+    tuned = fsi.problem_from_case(case, autotune=1, **kw)
+    fixed = fsi.problem_from_case(case, autotune=0, **kw)
+    tuned.assemble_step()
+    fixed.assemble_step()
+    v = np.random.default_rng(5).standard_normal(tuned.n)
+    for p in sorted({0, precision}):
+        assert rel(tuned.apply_preconditioner(v, precision=p), fixed.apply_preconditioner(v, precision=p)) < (
+            1e-12 if p == 0 else 2e-5)
+    tuned.close()
+    fixed.close()
