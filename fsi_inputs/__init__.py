@@ -141,12 +141,13 @@ def bar_case(N: int = 32, nx: int = 16, ny: int = 4, bend: float = 0.05) -> FsiC
                    extra={"solid_law": "exp", "gamma": 1.333, "eta": 9.242})
 
 
-def annulus_mesh(nr: int, nt: int, r0: float = 0.3, r1: float = 0.5):
-    """Structured P1 triangulation of the quarter annulus {x, y >= 0,
-    r0 <= |x| <= r1}: nodes (r_i cos t_j, r_i sin t_j) on nr radial and nt
-    angular intervals, node id = j (nr+1) + i; each (r, t) cell cut by a
-    diagonal, counter-clockwise.  The edges t = 0 and t = pi/2 lie exactly on
-    y = 0 and x = 0."""
+def annulus_mesh(nr: int, nt: int, r0: float = 0.3, r1: float = 0.5, quads: bool = False):
+    """Structured mesh of the quarter annulus {x, y >= 0, r0 <= |x| <= r1}:
+    nodes (r_i cos t_j, r_i sin t_j) on nr radial and nt angular intervals,
+    node id = j (nr+1) + i.  Each (r, t) cell is one quadrilateral
+    (quads=True, the Q1 solid of the paper's test) or two triangles cut by a
+    diagonal; counter-clockwise either way.  The edges t = 0 and t = pi/2 lie
+    exactly on y = 0 and x = 0."""
     r = np.linspace(r0, r1, nr + 1)
     t = np.linspace(0.0, 0.5 * np.pi, nt + 1)
     R, T = np.meshgrid(r, t)
@@ -158,31 +159,34 @@ def annulus_mesh(nr: int, nt: int, r0: float = 0.3, r1: float = 0.5):
         for i in range(nr):
             a = j * (nr + 1) + i
             b, c, d = a + 1, a + nr + 2, a + nr + 1
-            tris += [(a, b, c), (a, c, d)]
+            tris += [(a, b, c, d)] if quads else [(a, b, c), (a, c, d)]
     return xy, np.array(tris, dtype=np.int32)
 
 
-def annulus_case(N: int = 48) -> FsiCase:
+def annulus_case(N: int = 48, quads: bool = False) -> FsiCase:
     """The linear-solid test of Section 6 (Table 1): the quarter annulus
     0.3 <= |s| <= 0.5 in the first quadrant, kappa = 10, rho = 1, nu = 0.1,
     dt = 0.01, fluid at rest, released from the stretched state
     X(s, 0) = (s1 / 1.4, 1.4 s2).  Solid mesh refined with the fluid grid
     (about one solid interval per fluid cell).  The paper lets fluid and body
-    slide along the walls x = 0 and y = 0; here every wall is no-slip."""
+    slide along the walls x = 0 and y = 0; here every wall is no-slip.
+    quads=True takes the paper's Q1 solid (one quadrilateral per (r, t)
+    cell) instead of P1 triangles."""
     nr = max(2, int(np.ceil(0.2 * N)))
     nt = max(4, int(np.ceil(0.2 * np.pi * N)))
-    xy, tris = annulus_mesh(nr, nt)
+    xy, tris = annulus_mesh(nr, nt, quads=quads)
     X0 = np.stack([xy[:, 0] / 1.4, 1.4 * xy[:, 1]], 1)
     return FsiCase(N=N, rho_f=1.0, nu=0.1, kappa=10.0, dt=0.01, lid_u=0.0, ref_xy=xy, tris=tris,
-                   u0=wall_velocity(N, 0.0), X0=X0, precond=1, rtol=1e-8, steps=1, name=f"annulus_N{N}")
+                   u0=wall_velocity(N, 0.0), X0=X0, precond=1, rtol=1e-8, steps=1,
+                   name=f"annulus_{'q1' if quads else 'p1'}_N{N}")
 
 
-def mirrored_annulus_mesh(nr: int, nt: int, r0: float = 0.3, r1: float = 0.5):
+def mirrored_annulus_mesh(nr: int, nt: int, r0: float = 0.3, r1: float = 0.5, quads: bool = False):
     """The full annulus r0 <= |x| <= r1 as the quarter mesh of annulus_mesh
     and its mirror images in x = 0 and y = 0 (orientation restored in the
     mirrored quadrants; nodes on the mirror lines shared), so that the mesh is
     exactly symmetric under both reflections."""
-    qxy, qtris = annulus_mesh(nr, nt, r0, r1)
+    qxy, qtris = annulus_mesh(nr, nt, r0, r1, quads=quads)
     index: dict = {}
     xy: list = []
     tris: list = []
@@ -194,13 +198,13 @@ def mirrored_annulus_mesh(nr: int, nt: int, r0: float = 0.3, r1: float = 0.5):
                 index[key] = len(xy)
                 xy.append(key)
             ids.append(index[key])
-        for a, b, c in qtris:
-            t = (ids[a], ids[b], ids[c])
-            tris.append(t if sx * sy > 0 else (t[0], t[2], t[1]))
+        for el in qtris:
+            t = tuple(ids[v] for v in el)
+            tris.append(t if sx * sy > 0 else (t[0],) + t[:0:-1])   # reversed after the first vertex
     return np.array(xy), np.array(tris, dtype=np.int32)
 
 
-def symmetric_annulus_case(Nq: int = 24) -> FsiCase:
+def symmetric_annulus_case(Nq: int = 24, quads: bool = False) -> FsiCase:
     """The Table 1 test (see annulus_case) with the paper's free-slip walls
     x = 0 and y = 0, obtained by symmetry: the quarter problem on [0,1]^2 with
     free slip on x = 0, y = 0 and no slip on x = 1, y = 1 is the restriction
@@ -208,16 +212,18 @@ def symmetric_annulus_case(Nq: int = 24) -> FsiCase:
     problem, scaled into the unit square (x' = (x + 1)/2, so u' = u/2), is
     the same dynamics with nu' = nu/4 and kappa' = kappa/4 (pressure /4),
     rho and dt unchanged.  Nq is the quarter problem's grid; this grid is
-    N = 2 Nq, with the solid mesh mirrored from the quarter mesh."""
+    N = 2 Nq, with the solid mesh mirrored from the quarter mesh (Q1
+    quadrilaterals with quads=True, else P1 triangles)."""
     nr = max(2, int(np.ceil(0.2 * Nq)))
     nt = max(4, int(np.ceil(0.2 * np.pi * Nq)))
-    xy, tris = mirrored_annulus_mesh(nr, nt)
+    xy, tris = mirrored_annulus_mesh(nr, nt, quads=quads)
     X = np.stack([xy[:, 0] / 1.4, 1.4 * xy[:, 1]], 1)
     ref = 0.5 + 0.5 * xy
     X0 = 0.5 + 0.5 * X
     N = 2 * Nq
     return FsiCase(N=N, rho_f=1.0, nu=0.1 / 4.0, kappa=10.0 / 4.0, dt=0.01, lid_u=0.0, ref_xy=ref, tris=tris,
-                   u0=wall_velocity(N, 0.0), X0=X0, precond=1, rtol=1e-8, steps=1, name=f"annulus_sym_Nq{Nq}")
+                   u0=wall_velocity(N, 0.0), X0=X0, precond=1, rtol=1e-8, steps=1,
+                   name=f"annulus_sym_{'q1' if quads else 'p1'}_Nq{Nq}")
 
 
 def node_grid_shape(N: int) -> int:
@@ -269,7 +275,7 @@ class FsiCase:
     dt: float
     lid_u: float
     ref_xy: np.ndarray          # [n_s, 2] reference (= initial) solid node positions
-    tris: np.ndarray            # [n_tri, 3] int32, counter-clockwise
+    tris: np.ndarray            # [n_el, 3] P1 triangles or [n_el, 4] Q1 quadrilaterals, int32, counter-clockwise
     u0: np.ndarray              # [(2N+1)^2, 2] nodal velocity
     X0: np.ndarray              # [n_s, 2] initial solid node positions
     precond: int = 0            # 0 block-diagonal, 1 block-triangular

@@ -17,8 +17,10 @@ fictitious domain approach", arXiv:2301.10041):
   position X^n and the new velocity u^{n+1} (the matrix of Eq. (matrix)).
 * Fluid: Q2 velocity / P1-discontinuous pressure on a uniform N x N grid of
   the unit square (Section 4); pressure basis per cell {1, (x-xc)/h, (y-yc)/h}.
-* Solid and multiplier: one P1 space on triangles (S_h = Lambda_h, Section 4),
-  so the duality pairing is the L2(B) product and C_s is the P1 mass matrix.
+* Solid and multiplier: one space S_h = Lambda_h (Section 4), so the duality
+  pairing is the L2(B) product and C_s is its mass matrix: P1 on triangles,
+  or Q1 on quadrilaterals (the annulus test of Section 6), integrated by a
+  3 x 3 Gauss rule.
 * P(F) = kappa F (Section 4, before Eq. (matrix)): A_s = kappa (grad chi_j,
   grad chi_i)_B per component.
 * C_f(X^n)_{l j} = (chi_l, phi_j(X^n))_B is computed in one of two ways:
@@ -232,6 +234,83 @@ def assemble_solid(ref_xy: np.ndarray, tris: np.ndarray, kappa: float):
 
 
 # --------------------------------------------------------------------------
+# Solid: Q1 matrices (the quadrilateral solid of the annulus test, Section 6)
+# --------------------------------------------------------------------------
+
+
+def q1_rule():
+    """3 x 3 Gauss-Legendre rule on the unit square [0,1]^2 from its closed
+    form: 1-D nodes 1/2 and 1/2 -/+ sqrt(3/5)/2 with weights 4/9 and 5/18.
+    Point q = 3 j + i sits at (s_i, t_j); returns (s, t, s*t, weight) per
+    point, the product s*t rounded once in FP64 (the mapped-point formula of
+    ``quadrature_points_q1`` uses it)."""
+    r = 0.5 * np.sqrt(0.6)
+    g = np.array([0.5 - r, 0.5, 0.5 + r])
+    w1 = np.array([5.0 / 18.0, 8.0 / 18.0, 5.0 / 18.0])
+    s = np.tile(g, 3)
+    t = np.repeat(g, 3)
+    w = np.tile(w1, 3) * np.repeat(w1, 3)
+    return s, t, s * t, w
+
+
+def q1_shape(s, t):
+    """Bilinear shape functions of the vertices (0,0), (1,0), (1,1), (0,1)
+    of the unit square, and their derivatives d/ds, d/dt; each [..., 4]."""
+    s = np.asarray(s, dtype=np.float64)
+    t = np.asarray(t, dtype=np.float64)
+    chi = np.stack([(1 - s) * (1 - t), s * (1 - t), s * t, (1 - s) * t], -1)
+    ds = np.stack([-(1 - t), 1 - t, t, -t], -1)
+    dt = np.stack([-(1 - s), -s, s, 1 - s], -1)
+    return chi, ds, dt
+
+
+def q1_geometry(xy: np.ndarray, quads: np.ndarray):
+    """Jacobian determinant and physical shape-function gradients at the 9
+    rule points of every quadrilateral (vertices counter-clockwise, the
+    bilinear map of the unit square).  Returns det [n_el, 9] and grads
+    [n_el, 9, 4, 2]."""
+    s, t, _, _ = q1_rule()
+    _, ds, dt = q1_shape(s, t)                              # [9, 4]
+    P = xy[quads]                                           # [n_el, 4, 2]
+    Js = np.einsum("qa,ead->eqd", ds, P)                    # dx/ds  [n_el, 9, 2]
+    Jt = np.einsum("qa,ead->eqd", dt, P)                    # dx/dt
+    det = Js[..., 0] * Jt[..., 1] - Js[..., 1] * Jt[..., 0]
+    # grad chi = J^-T (dchi/ds, dchi/dt), J = [[Js_x, Jt_x], [Js_y, Jt_y]]
+    gx = (Jt[..., 1, None] * ds[None] - Js[..., 1, None] * dt[None]) / det[..., None]
+    gy = (-Jt[..., 0, None] * ds[None] + Js[..., 0, None] * dt[None]) / det[..., None]
+    return det, np.stack([gx, gy], -1)
+
+
+def assemble_solid_q1(ref_xy: np.ndarray, quads: np.ndarray, kappa: float):
+    """Scalar Q1 mass C and kappa * stiffness A on the reference
+    configuration, by the 3 x 3 Gauss rule on each quadrilateral.  The mass
+    integrand (bilinear x bilinear x the bilinear |det J|) is integrated
+    exactly; the stiffness integrand is rational on a general quadrilateral
+    and the rule is the stated reading (exact on parallelograms)."""
+    ns = ref_xy.shape[0]
+    s, t, _, w = q1_rule()
+    chi, _, _ = q1_shape(s, t)
+    det, grads = q1_geometry(ref_xy, quads)
+    if np.any(det <= 0):
+        raise ValueError("solid quadrilaterals must be counter-clockwise and non-degenerate")
+    wd = w[None, :] * det                                   # [n_el, 9]
+    mass_e = np.einsum("eq,qa,qb->eab", wd, chi, chi)
+    stiff_e = kappa * np.einsum("eq,eqad,eqbd->eab", wd, grads, grads)
+    rows = np.repeat(quads, 4, axis=1).ravel()
+    cols = np.tile(quads, (1, 4)).ravel()
+    C = sp.coo_matrix((mass_e.ravel(), (rows, cols)), shape=(ns, ns)).tocsr()
+    A = sp.coo_matrix((stiff_e.ravel(), (rows, cols)), shape=(ns, ns)).tocsr()
+    return C, A
+
+
+def solid_matrices(ref_xy: np.ndarray, elems: np.ndarray, kappa: float):
+    """(C, A) of the solid space: P1 for triangles, Q1 for quadrilaterals."""
+    if elems.shape[1] == 4:
+        return assemble_solid_q1(ref_xy, elems, kappa)
+    return assemble_solid(ref_xy, elems, kappa)
+
+
+# --------------------------------------------------------------------------
 # Coupling: point location and C_f(X^n) (Section 4, "coupling matrix")
 # --------------------------------------------------------------------------
 
@@ -258,6 +337,31 @@ def quadrature_points(X: np.ndarray, tris: np.ndarray):
     t1 = xi1 * d1
     t2 = xi2 * d2
     x = (P0 + t1) + t2
+    return x.reshape(-1, 2)
+
+
+def quadrature_points_q1(X: np.ndarray, quads: np.ndarray):
+    """Physical positions X^n(s_q) of the 9 rule points of every
+    quadrilateral, shape [n_el*9, 2], point id = 9 * element + q.
+
+    Reading (the paper does not fix it): with d1 = P1 - P0, d3 = P3 - P0 and
+    e = (P2 - P3) - d1, the bilinear map is evaluated as
+    x = ((P0 + s d1) + t d3) + (s t) e, left to right in round-to-nearest FP64
+    with no fused multiply-add, so that any implementation reproduces it bit
+    for bit.
+    """
+    s, t, st, _ = q1_rule()
+    P0 = X[quads[:, 0]][:, None, :]
+    P1 = X[quads[:, 1]][:, None, :]
+    P2 = X[quads[:, 2]][:, None, :]
+    P3 = X[quads[:, 3]][:, None, :]
+    d1 = P1 - P0
+    d3 = P3 - P0
+    e = (P2 - P3) - d1
+    a = s[None, :, None] * d1
+    b = t[None, :, None] * d3
+    c = st[None, :, None] * e
+    x = ((P0 + a) + b) + c
     return x.reshape(-1, 2)
 
 
@@ -292,7 +396,12 @@ def assemble_coupling(grid: FluidGrid, ref_xy: np.ndarray, tris: np.ndarray, X: 
     C_{l j} = sum_T sum_q |T| w_q chi_l(s_q) phi_j(X^n(s_q))  ~  (chi_l, phi_j(X^n))_B,
     where |T| is the reference-triangle area (the integral is over B).
     C_f = C acting on each velocity component.  Raises on a point outside
-    the fluid domain.  Also returns the point locations."""
+    the fluid domain.  Also returns the point locations.
+    With quadrilaterals (4 node ids per element) the solid space is Q1 and
+    the rule is the 3 x 3 Gauss rule of ``q1_rule``:
+    C_{l j} = sum_E sum_q w_q |det J_E(s_q)| chi_l(s_q) phi_j(X^n(s_q))."""
+    if tris.shape[1] == 4:
+        return assemble_coupling_q1(grid, ref_xy, tris, X)
     lam, w = triangle_rule()
     area, _ = p1_geometry(ref_xy, tris)
     x = quadrature_points(X, tris)
@@ -310,6 +419,32 @@ def assemble_coupling(grid: FluidGrid, ref_xy: np.ndarray, tris: np.ndarray, X: 
     vals = wq[:, None, None] * chi[:, :, None] * phi[:, None, :]
     rows = np.repeat(solid_nodes[:, :, None], 9, axis=2)
     cols = np.repeat(fluid_nodes[:, None, :], 3, axis=1)
+    C = sp.coo_matrix((vals.ravel(), (rows.ravel(), cols.ravel())),
+                      shape=(ref_xy.shape[0], grid.n_nodes)).tocsr()
+    return C, (x, cell, xi, eta)
+
+
+def assemble_coupling_q1(grid: FluidGrid, ref_xy: np.ndarray, quads: np.ndarray, X: np.ndarray):
+    """C_f for a Q1 solid (see ``assemble_coupling``): the reference-element
+    weights w_q |det J_E(s_q)| come from the reference configuration B."""
+    s, t, _, w = q1_rule()
+    chi, _, _ = q1_shape(s, t)                               # [9, 4]
+    det, _ = q1_geometry(ref_xy, quads)
+    x = quadrature_points_q1(X, quads)
+    cell, xi, eta = locate_brute_force(x, grid.N)
+    if np.any(cell < 0):
+        raise ValueError("solid quadrature point outside the fluid domain")
+    nel = quads.shape[0]
+    Lx = q2_1d(xi)
+    Ly = q2_1d(eta)
+    phi = (Ly[:, :, None] * Lx[:, None, :]).reshape(-1, 9)
+    fluid_nodes = grid.cell_nodes[cell]
+    wq = (w[None, :] * det).ravel()
+    chis = np.tile(chi, (nel, 1))                            # [npts, 4]
+    solid_nodes = np.repeat(quads, 9, axis=0)                # [npts, 4]
+    vals = wq[:, None, None] * chis[:, :, None] * phi[:, None, :]
+    rows = np.repeat(solid_nodes[:, :, None], 9, axis=2)
+    cols = np.repeat(fluid_nodes[:, None, :], 4, axis=1)
     C = sp.coo_matrix((vals.ravel(), (rows.ravel(), cols.ravel())),
                       shape=(ref_xy.shape[0], grid.n_nodes)).tocsr()
     return C, (x, cell, xi, eta)
@@ -531,9 +666,11 @@ class OracleProblem:
         self.grid = FluidGrid(N)
         self.ref_xy = np.asarray(ref_xy, dtype=np.float64)
         self.tris = np.asarray(tris, dtype=np.int64)
+        if self.tris.shape[1] == 4 and (coupling != "point" or solid_law != "linear"):
+            raise ValueError("the Q1 solid takes the point rule and the linear law only")
         self.M, self.K, self.B = assemble_fluid(self.grid, nu)
         self.A = (rho_f / dt) * self.M + self.K
-        Cs, As = assemble_solid(self.ref_xy, self.tris, kappa)
+        Cs, As = solid_matrices(self.ref_xy, self.tris, kappa)
         self.Cs_scalar, self.As_scalar = Cs, As
         self.Cs = kron2(Cs)
         self.As = kron2(As)

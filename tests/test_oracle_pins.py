@@ -535,3 +535,145 @@ def test_newton_converges_quadratically_on_the_bar():
     for a, b in zip(h[:-2], h[1:-1]):
         assert b <= 100.0 * a * a or b <= 1e-11
     assert o.relative_residual(case.u0, case.X0, u, p, Xn, lam) < 1e-10
+
+
+# ------------------------------------------------- Q1 solid (annulus test)
+
+def _quad_areas(xy, quads):
+    P = xy[quads]
+    x, y = P[..., 0], P[..., 1]
+    return 0.5 * np.sum(x * np.roll(y, -1, axis=1) - np.roll(x, -1, axis=1) * y, axis=1)
+
+
+def test_q1_rule_is_the_gauss_legendre_product_rule():
+    """Nodes and weights equal the library Gauss-Legendre rule mapped to
+    [0,1]; the product rule integrates s^i t^j exactly for i, j <= 5."""
+    s, t, st, w = fo.q1_rule()
+    x, wx = np.polynomial.legendre.leggauss(3)
+    g, wg = 0.5 * (x + 1.0), 0.5 * wx
+    assert np.allclose(s, np.tile(g, 3), atol=1e-16, rtol=0)
+    assert np.allclose(t, np.repeat(g, 3), atol=1e-16, rtol=0)
+    assert np.allclose(w, np.tile(wg, 3) * np.repeat(wg, 3), atol=1e-16, rtol=0)
+    assert np.array_equal(st, s * t)
+    for i in range(6):
+        for j in range(6):
+            assert abs(np.sum(w * s ** i * t ** j) - 1.0 / ((i + 1) * (j + 1))) < 1e-15
+
+
+def test_q1_element_matrices_on_a_square_match_closed_forms():
+    """Square of side h: mass h^2/36 [4 2 1 2; 2 4 2 1; 1 2 4 2; 2 1 2 4],
+    stiffness kappa/6 [4 -1 -2 -1; -1 4 -1 -2; -2 -1 4 -1; -1 -2 -1 4]."""
+    h, kappa = 0.125, 2.5
+    xy = np.array([[0.3, 0.4], [0.3 + h, 0.4], [0.3 + h, 0.4 + h], [0.3, 0.4 + h]])
+    quads = np.array([[0, 1, 2, 3]])
+    C, A = fo.assemble_solid_q1(xy, quads, kappa)
+    circ = lambda r: np.array([np.roll(r, k) for k in range(4)])
+    assert np.abs(C.toarray() - h * h / 36.0 * circ([4.0, 2.0, 1.0, 2.0])).max() < 1e-17
+    assert np.abs(A.toarray() - kappa / 6.0 * circ([4.0, -1.0, -2.0, -1.0])).max() < 1e-14
+
+
+def test_q1_solid_matrices_on_curved_quadrilaterals():
+    """Annulus quadrilaterals (no two edges parallel): total mass = polygon
+    area, constants have no gradient, kappa int |grad f|^2 = kappa |G|^2 area
+    for a linear f (its Q1 interpolant is f itself), and the mass entries
+    equal an independent 6 x 6 Gauss product rule (the integrand is a
+    polynomial of degree 3 in each reference variable)."""
+    xy, quads = fi.annulus_mesh(3, 5, quads=True)
+    kappa = 3.0
+    C, A = fo.assemble_solid_q1(xy, quads, kappa)
+    one = np.ones(xy.shape[0])
+    area = _quad_areas(xy, quads).sum()
+    assert abs(one @ C @ one - area) < 1e-15
+    assert np.abs(A @ one).max() < 1e-13
+    f = 0.7 * xy[:, 0] - 1.3 * xy[:, 1]
+    assert abs(f @ A @ f - kappa * (0.7 ** 2 + 1.3 ** 2) * area) < 1e-13
+    x6, w6 = np.polynomial.legendre.leggauss(6)
+    g6, v6 = 0.5 * (x6 + 1), 0.5 * w6
+    S, T = np.meshgrid(g6, g6, indexing="ij")
+    W = np.outer(v6, v6)
+    chi = np.stack([(1 - S) * (1 - T), S * (1 - T), S * T, (1 - S) * T])
+    Cq = np.zeros((xy.shape[0],) * 2)
+    for q in quads:
+        P = xy[q]
+        xs = (-(1 - T) * P[0, 0] + (1 - T) * P[1, 0] + T * P[2, 0] - T * P[3, 0])
+        ys = (-(1 - T) * P[0, 1] + (1 - T) * P[1, 1] + T * P[2, 1] - T * P[3, 1])
+        xt = (-(1 - S) * P[0, 0] - S * P[1, 0] + S * P[2, 0] + (1 - S) * P[3, 0])
+        yt = (-(1 - S) * P[0, 1] - S * P[1, 1] + S * P[2, 1] + (1 - S) * P[3, 1])
+        J = xs * yt - ys * xt
+        for a in range(4):
+            for b in range(4):
+                Cq[q[a], q[b]] += np.sum(W * J * chi[a] * chi[b])
+    assert np.abs(C.toarray() - Cq).max() < 1e-16
+
+
+def test_q1_mapped_points_are_the_bilinear_map():
+    """The rounding-fixed point formula is the bilinear map sum_a chi_a(s) P_a
+    (to rounding), and the mirrored quadrilaterals keep a positive Jacobian."""
+    xy, quads = fi.annulus_mesh(2, 4, quads=True)
+    X = _deformed(xy)
+    x = fo.quadrature_points_q1(X, quads).reshape(-1, 9, 2)
+    s, t, _, _ = fo.q1_rule()
+    chi, _, _ = fo.q1_shape(s, t)
+    ref = np.einsum("qa,ead->eqd", chi, X[quads])
+    assert np.abs(x - ref).max() < 4e-16
+    mxy, mquads = fi.mirrored_annulus_mesh(2, 4, quads=True)
+    det, _ = fo.q1_geometry(mxy, mquads)
+    assert (det > 0).all()
+
+
+def test_q1_coupling_partition_of_unity_and_reproduction():
+    """C_f 1 = C_s 1; C_f reproduces linear fields (f o X is bilinear, equal
+    to the Q1 interpolant of f at the moved nodes); for x^2 the integrand
+    chi_l (X_x)^2 |det J| is of degree 4 in each reference variable, so the
+    3 x 3 rule is exact: compare with an independent 6 x 6 Gauss rule."""
+    N = 12
+    g = fo.FluidGrid(N)
+    xy, quads = fi.annulus_mesh(3, 6, quads=True)
+    xy = 0.1 + 0.9 * xy
+    X = _deformed(xy, center=(0.45, 0.45))
+    C, (xq, cell, xi, eta) = fo.assemble_coupling(g, xy, quads, X)
+    Cs, _ = fo.assemble_solid_q1(xy, quads, 1.0)
+    rs = C @ np.ones(g.n_nodes)
+    assert np.abs(rs - Cs @ np.ones(xy.shape[0])).max() < 1e-13 * np.abs(rs).max()
+    for comp in range(2):
+        assert np.abs(C @ g.node_xy[:, comp] - Cs @ X[:, comp]).max() < 1e-14
+    x6, w6 = np.polynomial.legendre.leggauss(6)
+    g6, v6 = 0.5 * (x6 + 1), 0.5 * w6
+    S, T = np.meshgrid(g6, g6, indexing="ij")
+    W = np.outer(v6, v6)
+    chi = np.stack([(1 - S) * (1 - T), S * (1 - T), S * T, (1 - S) * T])
+    ref = np.zeros(xy.shape[0])
+    for q in quads:
+        P = xy[q]
+        xs = -(1 - T) * P[0, 0] + (1 - T) * P[1, 0] + T * P[2, 0] - T * P[3, 0]
+        ys = -(1 - T) * P[0, 1] + (1 - T) * P[1, 1] + T * P[2, 1] - T * P[3, 1]
+        xt = -(1 - S) * P[0, 0] - S * P[1, 0] + S * P[2, 0] + (1 - S) * P[3, 0]
+        yt = -(1 - S) * P[0, 1] - S * P[1, 1] + S * P[2, 1] + (1 - S) * P[3, 1]
+        Xx = sum(chi[a] * X[q[a], 0] for a in range(4))
+        for a in range(4):
+            ref[q[a]] += np.sum(W * (xs * yt - ys * xt) * chi[a] * Xx ** 2)
+    assert np.abs(C @ g.node_xy[:, 0] ** 2 - ref).max() < 1e-14
+
+
+def test_q1_step_residual_and_body_at_rest():
+    """One step with a Q1 solid: the direct solve meets its residual and
+    agrees with an unscaled library solve; with kappa = 0, u_0 = 0 and no
+    lid the body at rest stays at rest."""
+    c = fi.annulus_case(12, quads=True)
+    prob = fo.OracleProblem(c.N, c.rho_f, c.nu, c.kappa, c.dt, c.lid_u, c.ref_xy, c.tris)
+    Kmat, rhs, _ = prob.system(c.u0, c.X0)
+    x = prob.solve_system(Kmat, rhs, c.X0)
+    assert np.linalg.norm(rhs - Kmat @ x) / np.linalg.norm(rhs) < 1e-12
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spla
+    n_u, n_p, n_x = prob.sizes()
+    e = np.zeros(Kmat.shape[0])
+    e[n_u:n_u + n_p:3] = 1.0
+    big = sp.bmat([[Kmat, sp.csr_matrix(e[:, None])], [sp.csr_matrix(e[None, :]), None]], format="csc")
+    x2 = spla.spsolve(big, np.concatenate([rhs, [0.0]]))[:-1]
+    assert np.linalg.norm(x - x2) / np.linalg.norm(x2) < 1e-9
+    rest = fo.OracleProblem(c.N, 1.0, 0.1, 0.0, 0.01, 0.0, c.ref_xy, c.tris)
+    u, p, X, lam = rest.step(np.zeros_like(c.u0), c.ref_xy)
+    assert np.abs(u).max() < 1e-13 and np.abs(X - c.ref_xy).max() < 1e-15
+    with pytest.raises(ValueError):
+        fo.OracleProblem(c.N, 1.0, 0.1, 1.0, 0.01, 0.0, c.ref_xy, c.tris, coupling="exact")
