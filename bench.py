@@ -615,7 +615,10 @@ def run_annulus(args):
     for N in [int(v) for v in args.annulus_sizes.split(",")]:
         # --annulus-symmetric: the paper's free-slip walls by symmetry (the
         # full annulus on an N grid, equivalent to the quarter on N/2)
-        case = fi.symmetric_annulus_case(N // 2) if args.annulus_symmetric else fi.annulus_case(N)
+        # --annulus-q1: the paper's Q1 solid (one quadrilateral per (r, t) cell)
+        q1 = args.annulus_q1
+        case = (fi.symmetric_annulus_case(N // 2, quads=q1) if args.annulus_symmetric
+                else fi.annulus_case(N, quads=q1))
         variants = [(lab, pc, int(si)) for si in args.annulus_stokes_its.split(",")
                     for lab, pc in (("block-diagonal", 0), ("block-lower-triangular", 1))]
         for label, pc, sits in variants:
@@ -630,8 +633,9 @@ def run_annulus(args):
              if args.annulus_symmetric else "no-slip walls")
     print(json.dumps({"metric": METRIC, "workload": "annulus", "unit": "time-steps/s", "value": None, "rows": rows,
                       "config": {"workload": "quarter annulus 0.3<=|s|<=0.5 released from X = (s1/1.4, 1.4 s2), "
-                                             "kappa 10, rho 1, nu 0.1, dt 0.01, %s, mixed precision, rtol 1e-8, "
-                                             "restart %d" % (walls, RESTART),
+                                             "kappa 10, rho 1, nu 0.1, dt 0.01, %s, %s solid, mixed precision, "
+                                             "rtol 1e-8, restart %d"
+                                             % (walls, "Q1" if args.annulus_q1 else "P1", RESTART),
                                  "steps": args.annulus_steps, "stokes_its": args.annulus_stokes_its}}))
 
 
@@ -694,6 +698,8 @@ def main():
     ap.add_argument("--annulus-steps", type=int, default=2)
     ap.add_argument("--annulus-symmetric", action="store_true",
                     help="free-slip walls x = 0, y = 0 by symmetry (full annulus, nu and kappa scaled)")
+    ap.add_argument("--annulus-q1", action="store_true",
+                    help="Q1 quadrilateral solid (the paper's element) instead of P1 triangles")
     ap.add_argument("--annulus-stokes-its", default="1,16",
                     help="Richardson steps on the Stokes block: 1 = one V-cycle pair, 16 = nearly exact")
     ap.add_argument("--sweep-steps", type=int, default=2)

@@ -117,14 +117,22 @@ typedef struct fsi_params {
                           creation by timing its Chebyshev smoothing step alone
                           on the device (cached per matrix shape and size for
                           the process) */
+    int    solid_elem; /* solid (and multiplier) element: 0 = P1 triangles, 3
+                          node ids per element; 1 = Q1 quadrilaterals (the
+                          annulus test of Section 6), 4 node ids per element,
+                          with A_s, C_s and the C_f point rule by the 3 x 3
+                          Gauss rule on each element.  Q1 takes coupling 0 and
+                          solid_law 0 only */
 } fsi_params;
 
-/* Solid reference mesh (the body at t = 0, P1 triangles, counter-clockwise). */
+/* Solid reference mesh (the body at t = 0): P1 triangles, or Q1
+ * quadrilaterals with fsi_params.solid_elem = 1; vertices counter-clockwise. */
 typedef struct fsi_solid_mesh {
     int           n_nodes;
-    int           n_tris;
+    int           n_tris;  /* elements (triangles or quadrilaterals) */
     const double* ref_xy;  /* host, 2*n_nodes, interleaved (x, y) */
-    const int*    tris;    /* host, 3*n_tris node ids */
+    const int*    tris;    /* host, 3*n_tris (triangles) or 4*n_tris
+                              (quadrilaterals) node ids */
 } fsi_solid_mesh;
 
 /* Per-step report (the paper's its / T_coup / T_sol, Tables 1-4). */
@@ -150,7 +158,9 @@ int fsi_create_problem(const fsi_params* params, const fsi_solid_mesh* mesh,
                        const double* u0, const double* X0, void* cuda_stream,
                        fsi_problem** out);
 
-/* Bytes of device memory fsi_create_problem would allocate for these sizes. */
+/* Bytes of device memory fsi_create_problem would allocate for these sizes
+ * (n_tris: solid elements of the kind params->solid_elem names); 0 when the
+ * parameters are invalid. */
 size_t fsi_footprint_bytes(const fsi_params* params, int n_solid_nodes, int n_tris);
 
 /* Same as fsi_create_problem, but fails with FSI_ERR_BUDGET (allocating
@@ -203,8 +213,10 @@ int fsi_set_state(fsi_problem* p, const double* u, const double* X);
 int fsi_sizes(const fsi_problem* p, int* n_u, int* n_p, int* n_x, int* n_total);
 
 /* Test hooks.  Point location of the last fsi_assemble_step: for point
- * id = 6*triangle + q, the fluid cell id (cy*N + cx, or -1 outside) and the
- * local coordinates (xi, eta) in [0,1]^2.  Arrays of 6*n_tris; may be NULL.
+ * id = 6*triangle + q (P1; 9*quadrilateral + q with a Q1 solid, q = 3 j + i
+ * at Gauss nodes (s_i, t_j)), the fluid cell id (cy*N + cx, or -1 outside)
+ * and the local coordinates (xi, eta) in [0,1]^2.  Arrays of 6*n_tris
+ * (9*n_tris for Q1); may be NULL.
  * FSI_ERR_INVALID with coupling = 1 (the exact rule locates no points). */
 int fsi_get_points(fsi_problem* p, int* cell, double* xi, double* eta);
 

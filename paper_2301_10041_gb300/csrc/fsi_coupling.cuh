@@ -8,28 +8,52 @@ namespace fsi {
 
 __constant__ double c_rule_lam[6][3];  // barycentric points of the degree-4 rule
 __constant__ double c_rule_w[6];       // weights, summing to 1
+__constant__ double c_q1_pt[9][3];     // Q1: (s, t, s t) of the 3 x 3 Gauss points
+__constant__ double c_q1_chi[9][4];    // Q1: the four bilinear shape functions there
 
-// S2: x_q = P0 + xi1 (P1 - P0) + xi2 (P2 - P0), evaluated left to right with
-// explicitly rounded FP64 operations (no contraction), then the cell by the
-// half-open rule on t = x * N (the last cell is closed at x = 1).
+// Rule points per solid element: the 6-point triangle rule (P1) or the 3 x 3
+// Gauss rule (Q1 quadrilaterals).
+template <int NPE>
+__host__ __device__ constexpr int rule_points() { return NPE == 3 ? 6 : 9; }
+
+// S2: the mapped point, evaluated left to right with explicitly rounded FP64
+// operations (no contraction):
+//   P1: x_q = P0 + xi1 (P1 - P0) + xi2 (P2 - P0);
+//   Q1: x_q = ((P0 + s d1) + t d3) + (s t) e with d1 = P1 - P0,
+//       d3 = P3 - P0, e = (P2 - P3) - d1 (the bilinear map of the square);
+// then the cell by the half-open rule on t = x * N (the last cell is closed
+// at x = 1).
+template <int NPE>
 __global__ void k_locate(int n_pts, int N, const int* __restrict__ tris, const double* __restrict__ X,
                          int* __restrict__ cell, double* __restrict__ xi, double* __restrict__ eta,
                          int* __restrict__ flags) {
   pdl_begin();
+  constexpr int NQ = rule_points<NPE>();
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n_pts) return;
-  const int t = p / 6, q = p - 6 * (p / 6);
-  const int v0 = tris[3 * t], v1 = tris[3 * t + 1], v2 = tris[3 * t + 2];
-  const double l1 = c_rule_lam[q][1], l2 = c_rule_lam[q][2];
+  const int t = p / NQ, q = p - NQ * (p / NQ);
+  int v[NPE];
+#pragma unroll
+  for (int a = 0; a < NPE; ++a) v[a] = tris[NPE * t + a];
   const double fN = (double)N;
   double loc[2];
   int idx[2];
   bool ok = true;
 #pragma unroll
   for (int c = 0; c < 2; ++c) {
-    const double P0 = X[2 * v0 + c], P1 = X[2 * v1 + c], P2 = X[2 * v2 + c];
-    const double d1 = __dsub_rn(P1, P0), d2 = __dsub_rn(P2, P0);
-    const double xc = __dadd_rn(__dadd_rn(P0, __dmul_rn(l1, d1)), __dmul_rn(l2, d2));
+    double xc;
+    if constexpr (NPE == 3) {
+      const double l1 = c_rule_lam[q][1], l2 = c_rule_lam[q][2];
+      const double P0 = X[2 * v[0] + c], P1 = X[2 * v[1] + c], P2 = X[2 * v[2] + c];
+      const double d1 = __dsub_rn(P1, P0), d2 = __dsub_rn(P2, P0);
+      xc = __dadd_rn(__dadd_rn(P0, __dmul_rn(l1, d1)), __dmul_rn(l2, d2));
+    } else {
+      const double P0 = X[2 * v[0] + c], P1 = X[2 * v[1] + c], P2 = X[2 * v[2] + c], P3 = X[2 * v[3] + c];
+      const double d1 = __dsub_rn(P1, P0), d3 = __dsub_rn(P3, P0);
+      const double e = __dsub_rn(__dsub_rn(P2, P3), d1);
+      xc = __dadd_rn(__dadd_rn(__dadd_rn(P0, __dmul_rn(c_q1_pt[q][0], d1)), __dmul_rn(c_q1_pt[q][1], d3)),
+                     __dmul_rn(c_q1_pt[q][2], e));
+    }
     if (!(xc >= 0.0 && xc <= 1.0)) { ok = false; idx[c] = 0; loc[c] = 0.0; continue; }
     const double tc = __dmul_rn(xc, fN);
     int i = (int)floor(tc);
@@ -100,11 +124,15 @@ __device__ __forceinline__ double q2b(int a, double t) {
 }
 
 // S4: one warp per solid node l.  Row l of the scalar coupling matrix,
-//   C_{l j} = sum_{T ni l} sum_q |T| w_q lam_l(q) phi_j(x_q),
-// is accumulated in a shared-memory window over the fluid lattice nodes of
-// the cells hit by the row's points, points taken in a fixed order (no
-// atomics, deterministic); then the window is compacted into the ELL row.
-// Columns on the wall go to the right-hand side (times the wall velocity).
+//   C_{l j} = sum_{E ni l} sum_q omega_{E,q} chi_l(q) phi_j(x_q),
+// with omega = |T| w_q for a P1 triangle (area: one per triangle) and
+// omega = w_q |det J_E(s_q)| for a Q1 quadrilateral (area: one per point, from
+// the reference configuration), is accumulated in a shared-memory window
+// over the fluid lattice nodes of the cells hit by the row's points, points
+// taken in a fixed order (no atomics, deterministic); then the window is
+// compacted into the ELL row.  Columns on the wall go to the right-hand side
+// (times the wall velocity).
+template <int NPE>
 __global__ void __launch_bounds__(32 * kCfWarps) k_cf_rows(
     int nS, int N, const int* __restrict__ ntp, const int* __restrict__ nt, const double* __restrict__ area,
     const int* __restrict__ cell, const double* __restrict__ xi, const double* __restrict__ eta,
@@ -117,14 +145,15 @@ __global__ void __launch_bounds__(32 * kCfWarps) k_cf_rows(
   const int l = blockIdx.x * kCfWarps + warp;
   if (l >= nS) return;
   double* W = win[warp];
+  constexpr int NQ = rule_points<NPE>();
   const int e0 = ntp[l], e1 = ntp[l + 1];
-  const int npt = 6 * (e1 - e0);
+  const int npt = NQ * (e1 - e0);
   // bounding box of the cells of the row's points
   int x0 = 1 << 30, y0 = 1 << 30, x1 = -1, y1 = -1;
   bool bad = false;
   for (int k = lane; k < npt; k += 32) {
-    const int e = nt[e0 + k / 6];
-    const int p = 6 * (e / 3) + (k % 6);
+    const int e = nt[e0 + k / NQ];
+    const int p = NQ * (e / NPE) + (k % NQ);
     const int c = cell[p];
     if (c < 0) { bad = true; continue; }
     const int cx = c % N, cy = c / N;
@@ -150,14 +179,14 @@ __global__ void __launch_bounds__(32 * kCfWarps) k_cf_rows(
   for (int k = lane; k < wn * hn; k += 32) W[k] = 0.0;
   __syncwarp();
   for (int k = 0; k < npt; ++k) {
-    const int e = nt[e0 + k / 6];
-    const int t = e / 3, a = e - 3 * (e / 3), q = k % 6;
-    const int p = 6 * t + q;
+    const int e = nt[e0 + k / NQ];
+    const int t = e / NPE, a = e - NPE * (e / NPE), q = k % NQ;
+    const int p = NQ * t + q;
     const int c = cell[p];
     const int cx = c % N, cy = c / N;
     if (lane < 9) {
       const int aa = lane % 3, bb = lane / 3;
-      const double wq = area[t] * c_rule_w[q] * c_rule_lam[q][a];
+      const double wq = (NPE == 3) ? area[t] * c_rule_w[q] * c_rule_lam[q][a] : area[p] * c_q1_chi[q][a];
       const double phi = q2b(aa, xi[p]) * q2b(bb, eta[p]);
       W[(2 * (cy - y0) + bb) * wn + 2 * (cx - x0) + aa] += wq * phi;
     }

@@ -43,6 +43,7 @@ struct FluidLevelHost {
 
 struct SetupParams {
   int N; double rho, nu, kappa, dt, lid;
+  int npe = 3;            // solid element: 3 = P1 triangle, 4 = Q1 quadrilateral
 };
 
 struct HostSetup {
@@ -65,8 +66,10 @@ struct HostSetup {
   std::vector<int> lattice_to_node;    // lattice id -> internal node or -1
   std::vector<double> wall_u;          // lattice nodal wall data, 2 per node
   // solid mesh data for the coupling assembly
-  std::vector<double> tri_area;        // reference areas
-  std::vector<int> node_tri_ptr, node_tri;  // node -> (triangle*3 + local vertex)
+  std::vector<double> tri_area;        // P1: reference areas
+  std::vector<double> pt_w;            // Q1: w_q |det J_E(s_q)| per rule point (9 per element)
+  std::vector<int> node_tri_ptr, node_tri;  // node -> (element*npe + local vertex)
+  double cs_lo = 0.5, cs_hi = 2.0;     // an interval holding the spectrum of D^-1 C_s
 };
 
 void build_setup(const SetupParams& sp, int n_s, int n_tri, const double* ref_xy,
@@ -76,6 +79,14 @@ void build_setup(const SetupParams& sp, int n_s, int n_tri, const double* ref_xy
 // (lam0, lam1, lam2) and weights summing to 1, in the order used by the
 // point-location kernel (point id = 6*triangle + q).
 void triangle_rule(double lam[6][3], double w[6]);
+
+// 3 x 3 Gauss-Legendre rule on the unit square: point q = 3 j + i at
+// (s_i, t_j), its rounded product s t, and weights summing to 1.
+void quad_rule(double s[9], double t[9], double st[9], double w[9]);
+
+// Bilinear shape functions of the unit square's vertices (0,0), (1,0),
+// (1,1), (0,1) at (s, t).
+void q1_shape(double s, double t, double chi[4]);
 
 // ------------------------------------------------------------- device side
 template <class T>

@@ -457,6 +457,60 @@ void triangle_rule(double lam[6][3], double w[6]) {
   }
 }
 
+void quad_rule(double s[9], double t[9], double st[9], double w[9]) {
+  // 1-D Gauss-Legendre on [0,1]: 1/2 and 1/2 -/+ sqrt(3/5)/2, weights 4/9, 5/18
+  const double r = 0.5 * std::sqrt(0.6);
+  const double g[3] = {0.5 - r, 0.5, 0.5 + r};
+  const double w1[3] = {5.0 / 18.0, 8.0 / 18.0, 5.0 / 18.0};
+  for (int j = 0; j < 3; ++j)
+    for (int i = 0; i < 3; ++i) {
+      const int q = 3 * j + i;
+      s[q] = g[i];
+      t[q] = g[j];
+      st[q] = g[i] * g[j];
+      w[q] = w1[i] * w1[j];
+    }
+}
+
+void q1_shape(double s, double t, double chi[4]) {
+  chi[0] = (1.0 - s) * (1.0 - t);
+  chi[1] = s * (1.0 - t);
+  chi[2] = s * t;
+  chi[3] = (1.0 - s) * t;
+}
+
+// Extreme eigenvalues of a symmetric 4 x 4 matrix by cyclic Jacobi rotations.
+static void sym4_eig_range(double a[4][4], double& lo, double& hi) {
+  for (int sweep = 0; sweep < 50; ++sweep) {
+    double off = 0.0;
+    for (int p = 0; p < 4; ++p)
+      for (int q = p + 1; q < 4; ++q) off += a[p][q] * a[p][q];
+    if (off < 1e-30) break;
+    for (int p = 0; p < 4; ++p)
+      for (int q = p + 1; q < 4; ++q) {
+        if (a[p][q] == 0.0) continue;
+        const double th = 0.5 * (a[q][q] - a[p][p]) / a[p][q];
+        const double t = (th >= 0 ? 1.0 : -1.0) / (std::fabs(th) + std::sqrt(th * th + 1.0));
+        const double c = 1.0 / std::sqrt(t * t + 1.0), sn = t * c;
+        for (int k = 0; k < 4; ++k) {  // columns p, q
+          const double akp = a[k][p], akq = a[k][q];
+          a[k][p] = c * akp - sn * akq;
+          a[k][q] = sn * akp + c * akq;
+        }
+        for (int k = 0; k < 4; ++k) {  // rows p, q
+          const double apk = a[p][k], aqk = a[q][k];
+          a[p][k] = c * apk - sn * aqk;
+          a[q][k] = sn * apk + c * aqk;
+        }
+      }
+  }
+  lo = hi = a[0][0];
+  for (int k = 1; k < 4; ++k) {
+    lo = std::min(lo, a[k][k]);
+    hi = std::max(hi, a[k][k]);
+  }
+}
+
 void build_setup(const SetupParams& sp, int n_s, int n_tri, const double* ref_xy, const int* tris,
                  HostSetup& out) {
   const int N = sp.N;
@@ -536,24 +590,78 @@ void build_setup(const SetupParams& sp, int n_s, int n_tri, const double* ref_xy
       out.mp_inv[3 * c + 2] = 12.0 / h2;
     }
   }
-  // ---- solid P1 operators on the reference configuration
-  out.tri_area.resize(n_tri);
-  std::vector<std::vector<std::pair<int, double>>> rowsA(n_s), rowsC(n_s);
+  // ---- solid operators on the reference configuration (P1 or Q1)
+  const int npe = sp.npe;
   out.node_tri_ptr.assign(n_s + 1, 0);
   for (int t = 0; t < n_tri; ++t)
-    for (int a = 0; a < 3; ++a) out.node_tri_ptr[tris[3 * t + a] + 1]++;
+    for (int a = 0; a < npe; ++a) out.node_tri_ptr[tris[npe * t + a] + 1]++;
   for (int i = 0; i < n_s; ++i) out.node_tri_ptr[i + 1] += out.node_tri_ptr[i];
-  out.node_tri.assign(3 * (size_t)n_tri, 0);
+  out.node_tri.assign(npe * (size_t)n_tri, 0);
   {
     std::vector<int> pos(out.node_tri_ptr.begin(), out.node_tri_ptr.end() - 1);
     for (int t = 0; t < n_tri; ++t)
-      for (int a = 0; a < 3; ++a) out.node_tri[pos[tris[3 * t + a]]++] = 3 * t + a;
+      for (int a = 0; a < npe; ++a) out.node_tri[pos[tris[npe * t + a]]++] = npe * t + a;
   }
   HostBlockMatrix S;
   init_matrix(S, 2, 2, true, n_s, n_s);
   S.NV = 2;  // (A_s, C_s) per block
   std::vector<RowAcc> acc(n_s, RowAcc(2));
-  for (int t = 0; t < n_tri; ++t) {
+  if (npe == 4) {
+    // Q1: 3 x 3 Gauss on each element, J = [dx/ds dx/dt] of the bilinear map;
+    // the interval for D^-1 C_s from the element mass matrices (Wathen: the
+    // Rayleigh quotient of (C_s, D) lies between the extreme eigenvalues of
+    // the element pairs (M_E, diag M_E))
+    double qs[9], qt[9], qst[9], qw[9];
+    quad_rule(qs, qt, qst, qw);
+    out.pt_w.resize(9 * (size_t)n_tri);
+    out.cs_lo = 1e300;
+    out.cs_hi = 0.0;
+    for (int e = 0; e < n_tri; ++e) {
+      const int* v = tris + 4 * (size_t)e;
+      double P[4][2];
+      for (int a = 0; a < 4; ++a) { P[a][0] = ref_xy[2 * v[a]]; P[a][1] = ref_xy[2 * v[a] + 1]; }
+      double Me[4][4] = {};
+      for (int q = 0; q < 9; ++q) {
+        const double s_ = qs[q], t_ = qt[q];
+        double chi[4];
+        q1_shape(s_, t_, chi);
+        const double ds[4] = {-(1.0 - t_), 1.0 - t_, t_, -t_};
+        const double dt[4] = {-(1.0 - s_), -s_, s_, 1.0 - s_};
+        double xs = 0, ys = 0, xt = 0, yt = 0;
+        for (int a = 0; a < 4; ++a) {
+          xs += ds[a] * P[a][0]; ys += ds[a] * P[a][1];
+          xt += dt[a] * P[a][0]; yt += dt[a] * P[a][1];
+        }
+        const double det = xs * yt - ys * xt;
+        if (!(det > 0)) throw std::invalid_argument("solid quadrilateral not counter-clockwise");
+        const double wd = qw[q] * det;
+        out.pt_w[9 * (size_t)e + q] = wd;
+        double g[4][2];
+        for (int a = 0; a < 4; ++a) {
+          g[a][0] = (yt * ds[a] - ys * dt[a]) / det;
+          g[a][1] = (-xt * ds[a] + xs * dt[a]) / det;
+        }
+        for (int a = 0; a < 4; ++a)
+          for (int b = 0; b < 4; ++b) {
+            double* sl = acc[v[a]].slot(v[b]);
+            sl[0] += sp.kappa * wd * (g[a][0] * g[b][0] + g[a][1] * g[b][1]);
+            sl[1] += wd * chi[a] * chi[b];
+            Me[a][b] += wd * chi[a] * chi[b];
+          }
+      }
+      double Ds[4];
+      for (int a = 0; a < 4; ++a) Ds[a] = 1.0 / std::sqrt(Me[a][a]);
+      for (int a = 0; a < 4; ++a)
+        for (int b = 0; b < 4; ++b) Me[a][b] *= Ds[a] * Ds[b];
+      double lo, hi;
+      sym4_eig_range(Me, lo, hi);
+      out.cs_lo = std::min(out.cs_lo, lo);
+      out.cs_hi = std::max(out.cs_hi, hi);
+    }
+    for (int i = 0; i < n_s; ++i) acc[i].flush(S);
+  }
+  if (npe == 3) out.tri_area.resize(n_tri);
+  for (int t = 0; t < (npe == 3 ? n_tri : 0); ++t) {
     const int v[3] = {tris[3 * t], tris[3 * t + 1], tris[3 * t + 2]};
     const double x0 = ref_xy[2 * v[0]], y0 = ref_xy[2 * v[0] + 1];
     const double d1x = ref_xy[2 * v[1]] - x0, d1y = ref_xy[2 * v[1] + 1] - y0;
@@ -573,7 +681,8 @@ void build_setup(const SetupParams& sp, int n_s, int n_tri, const double* ref_xy
         s[1] += area / 12.0 * (a == b ? 2.0 : 1.0);
       }
   }
-  for (int i = 0; i < n_s; ++i) acc[i].flush(S);
+  if (npe == 3)
+    for (int i = 0; i < n_s; ++i) acc[i].flush(S);
   out.Ssol = S;
   out.Cs = S; out.Cs.NV = 1; out.Cs.val.resize(S.nnzb());
   out.As = S; out.As.NV = 1; out.As.val.resize(S.nnzb());

@@ -481,7 +481,7 @@ struct Prec {
   T* vin = nullptr;      // preconditioner input (n)
   T* zw = nullptr;       // preconditioner output (n)
   T *sb = nullptr, *sx = nullptr, *sx2 = nullptr, *sd = nullptr;  // solid work (2 nS)
-  Cheb chs;              // Chebyshev on [1/2, 2] for D^-1 C_s (Wathen's bounds for P1)
+  Cheb chs;              // Chebyshev for D^-1 C_s on Wathen's interval ([1/2, 2] for P1)
   int cs_k = 16;
   // inner Richardson on the Stokes block: velocity right-hand side, residual
   // and correction, each [u (2 nU) | p (3 nP)]
@@ -1124,7 +1124,10 @@ static void check_params(const fsi_params& p, int n_nodes, int n_tris) {
   if (!(p.dt > 0) || !(p.rho_f > 0) || !(p.nu > 0) || !(p.kappa >= 0)) throw std::invalid_argument("bad material");
   if (p.precond < 0 || p.precond > 3) throw std::invalid_argument("precond");
   if (p.precision != 0 && p.precision != 1) throw std::invalid_argument("precision");
-  if (n_nodes < 3 || n_tris < 1) throw std::invalid_argument("solid mesh");
+  if (p.solid_elem != 0 && p.solid_elem != 1) throw std::invalid_argument("solid_elem");
+  if (n_nodes < (p.solid_elem == 1 ? 4 : 3) || n_tris < 1) throw std::invalid_argument("solid mesh");
+  if (p.solid_elem == 1 && (p.coupling != 0 || p.solid_law != 0))
+    throw std::invalid_argument("the Q1 solid takes the point rule and the linear law");
   if (p.mg_cluster != 0 && p.mg_cluster != -1) throw std::invalid_argument("mg_cluster");
   if (p.coupling != 0 && p.coupling != 1) throw std::invalid_argument("coupling");
   if (p.solid_law != 0 && p.solid_law != 1) throw std::invalid_argument("solid_law");
@@ -1132,13 +1135,20 @@ static void check_params(const fsi_params& p, int n_nodes, int n_tris) {
   if (p.solid_law == 1 && !(p.gamma > 0 && p.eta > 0)) throw std::invalid_argument("gamma, eta");
 }
 
+// Node ids per solid element and rule points per element (P1: the 6-point
+// triangle rule; Q1: 3 x 3 Gauss).
+static int elem_nodes(const fsi_params& p) { return p.solid_elem == 1 ? 4 : 3; }
+static int elem_points(const fsi_params& p) { return p.solid_elem == 1 ? 9 : 6; }
+
 static fsi_params with_defaults(fsi_params p) {
   if (p.restart <= 0) p.restart = 200;
   if (p.restart > 250) p.restart = 250;
   if (!(p.rtol > 0)) p.rtol = 1e-8;
   if (p.max_it <= 0) p.max_it = 1000;
   if (p.mg_degree <= 0) p.mg_degree = 2;
-  if (p.cs_degree <= 0) p.cs_degree = (p.precision == 1) ? 12 : 16;
+  // Q1: D^-1 C_s has a wider interval ([1/4, 9/4] on squares against [1/2, 2]
+  // for P1), so about 1.6 x the Chebyshev steps for the same reduction
+  if (p.cs_degree <= 0) p.cs_degree = (p.precision == 1) ? (p.solid_elem == 1 ? 20 : 12) : (p.solid_elem == 1 ? 26 : 16);
   if (!(p.inner_rtol > 0)) p.inner_rtol = 1e-5;
   if (p.max_refine <= 0) p.max_refine = 30;
   if (p.stokes_its <= 0) p.stokes_its = 1;
@@ -1175,7 +1185,7 @@ static void build_prec(Problem& P, Prec<T>& pr, const FullOp<T>& op, bool alloc_
   const size_t n2 = 2 * (size_t)P.nS;
   pr.sb = ar.alloc<T>(n2); pr.sx = ar.alloc<T>(n2); pr.sx2 = ar.alloc<T>(n2); pr.sd = ar.alloc<T>(n2);
   pr.cs_k = P.prm.cs_degree;
-  pr.chs = cheb_coeffs(0.5, 2.0, pr.cs_k);
+  pr.chs = cheb_coeffs(P.hs.cs_lo, P.hs.cs_hi, pr.cs_k);
   const size_t nf = 2 * (size_t)P.nU + 3 * (size_t)P.nP;
   pr.ru = ar.alloc<T>(2 * (size_t)P.nU);
   pr.t = ar.alloc<T>(nf);
@@ -1221,16 +1231,28 @@ static KrylovArgs krylov_args(Problem& P, cudaGraphConditionalHandle h) {
   return k;
 }
 
+// S2 + S4 by the point rule: locate the rule points, then the C_f rows.
+static void point_rule_launch(Problem& P, cudaStream_t s) {
+  if (elem_nodes(P.prm) == 4) {
+    launch(k_locate<4>, nblk(P.nPts, 256), 256, 0, s, P.nPts, P.N, P.tris, P.Xold, P.cell, P.xi, P.eta,
+           &P.ctl->aflags);
+    launch(k_cf_rows<4>, nblk(P.nS, kCfWarps), 32 * kCfWarps, 0, s, P.nS, P.N, P.ntp, P.nt, P.area, P.cell, P.xi,
+           P.eta, P.l2n, P.wall, P.cf_cap, P.cf_len, P.cf_col, P.cf_val, P.cf_val32, P.cflift, &P.ctl->aflags);
+  } else {
+    launch(k_locate<3>, nblk(P.nPts, 256), 256, 0, s, P.nPts, P.N, P.tris, P.Xold, P.cell, P.xi, P.eta,
+           &P.ctl->aflags);
+    launch(k_cf_rows<3>, nblk(P.nS, kCfWarps), 32 * kCfWarps, 0, s, P.nS, P.N, P.ntp, P.nt, P.area, P.cell, P.xi,
+           P.eta, P.l2n, P.wall, P.cf_cap, P.cf_len, P.cf_col, P.cf_val, P.cf_val32, P.cflift, &P.ctl->aflags);
+  }
+}
+
 static void assemble_launch(Problem& P, cudaStream_t s) {
   CK(cudaMemsetAsync(&P.ctl->aflags, 0, sizeof(int), s));
   if (P.prm.coupling == 1) {  // the paper's exact rule: mesh intersection
     launch(k_cf_rows_exact, nblk(P.nS, kCfWarps), 32 * kCfWarps, 0, s, P.nS, P.N, P.ntp, P.nt, P.tris, P.Xold, P.area,
            P.l2n, P.wall, P.cf_cap, P.cf_len, P.cf_col, P.cf_val, P.cf_val32, P.cflift, &P.ctl->aflags);
-  } else {                    // located points of the degree-4 rule
-    launch(k_locate, nblk(P.nPts, 256), 256, 0, s, P.nPts, P.N, P.tris, P.Xold, P.cell, P.xi, P.eta, &P.ctl->aflags);
-    launch(k_cf_rows, nblk(P.nS, kCfWarps), 32 * kCfWarps, 0, s, P.nS, P.N, P.ntp, P.nt, P.area, P.cell, P.xi, P.eta,
-                                                            P.l2n, P.wall, P.cf_cap, P.cf_len, P.cf_col, P.cf_val,
-                                                            P.cf_val32, P.cflift, &P.ctl->aflags);
+  } else {                    // located points of the point rule
+    point_rule_launch(P, s);
   }
   CK(cudaMemsetAsync(P.cft_cnt, 0, sizeof(int) * P.nU, s));
   const size_t nslot = (size_t)P.nS * P.cf_cap;
@@ -1400,8 +1422,9 @@ static void build_graphs(Problem& P) {
 static void allocate_problem(Problem& P, const double* ref_xy, const int* tris_h) {
   Arena& ar = P.ar;
   const HostSetup& hs = P.hs;
-  P.tris = ar.upload(std::vector<int>(tris_h, tris_h + 3 * (size_t)P.nTri));
-  P.area = ar.upload(hs.tri_area);
+  const int npe = elem_nodes(P.prm);
+  P.tris = ar.upload(std::vector<int>(tris_h, tris_h + npe * (size_t)P.nTri));
+  P.area = ar.upload(npe == 4 ? hs.pt_w : hs.tri_area);
   P.ntp = ar.upload(hs.node_tri_ptr);
   P.nt = ar.upload(hs.node_tri);
   P.l2n = ar.upload(hs.lattice_to_node);
@@ -1418,10 +1441,10 @@ static void allocate_problem(Problem& P, const double* ref_xy, const int* tris_h
     for (int l = 0; l < P.nS; ++l) {
       double lo[2] = {1e300, 1e300}, hi[2] = {-1e300, -1e300};
       for (int k = hs.node_tri_ptr[l]; k < hs.node_tri_ptr[l + 1]; ++k) {
-        const int t = hs.node_tri[k] / 3;
-        for (int v = 0; v < 3; ++v)
+        const int t = hs.node_tri[k] / npe;
+        for (int v = 0; v < npe; ++v)
           for (int c = 0; c < 2; ++c) {
-            const double x = ref_xy[2 * (size_t)tris_h[3 * (size_t)t + v] + c];
+            const double x = ref_xy[2 * (size_t)tris_h[npe * (size_t)t + v] + c];
             lo[c] = std::min(lo[c], x);
             hi[c] = std::max(hi[c], x);
           }
@@ -1570,11 +1593,12 @@ static size_t footprint_impl(const fsi_params& prm0, int n_nodes, int n_tris, co
   P.ar.count_only = true;
   P.N = prm.N;
   VNum vn(prm.N);
-  P.nU = vn.n; P.nP = prm.N * prm.N; P.nS = n_nodes; P.nTri = n_tris; P.nPts = 6 * n_tris;
+  P.nU = vn.n; P.nP = prm.N * prm.N; P.nS = n_nodes; P.nTri = n_tris; P.nPts = elem_points(prm) * n_tris;
   P.offP = 2 * (size_t)P.nU; P.offX = P.offP + 3 * (size_t)P.nP; P.offL = P.offX + 2 * (size_t)P.nS;
   P.n = P.offL + 2 * (size_t)P.nS;
   P.m = prm.restart;
   SetupParams sp{prm.N, prm.rho_f, prm.nu, prm.kappa, prm.dt, prm.lid_u};
+  sp.npe = elem_nodes(prm);
   build_setup(sp, n_nodes, n_tris, ref_xy, tris, P.hs);
   allocate_problem(P, ref_xy, tris);
   return P.ar.bytes;
@@ -1598,6 +1622,19 @@ size_t fsi_footprint_bytes(const fsi_params* params, int n_solid_nodes, int n_tr
       xy[2 * i + 1] = 0.5 + 0.1 * std::sin(a);
     }
     xy[0] = 0.5; xy[1] = 0.5;
+    if (params->solid_elem == 1) {
+      // quadrilaterals (centre, three consecutive ring nodes): convex and
+      // counter-clockwise while three ring steps span less than half a turn
+      if (n_solid_nodes < 8) return 0;
+      tr.assign(4 * (size_t)n_tris, 0);
+      for (int t = 0; t < n_tris; ++t) {
+        const int a = 1 + t % (n_solid_nodes - 1);
+        const int b = 1 + (a % (n_solid_nodes - 1));
+        const int c = 1 + (b % (n_solid_nodes - 1));
+        tr[4 * t] = 0; tr[4 * t + 1] = a; tr[4 * t + 2] = b; tr[4 * t + 3] = c;
+      }
+      return footprint_impl(*params, n_solid_nodes, n_tris, xy.data(), tr.data());
+    }
     for (int t = 0; t < n_tris; ++t) {
       const int a = 1 + t % (n_solid_nodes - 1);
       const int b = 1 + (a % (n_solid_nodes - 1));
@@ -1617,7 +1654,7 @@ int fsi_create_problem_budget(const fsi_params* params, const fsi_solid_mesh* me
   try {
     fsi_params prm = with_defaults(*params);
     check_params(prm, mesh->n_nodes, mesh->n_tris);
-    for (int i = 0; i < 3 * mesh->n_tris; ++i)
+    for (size_t i = 0; i < (size_t)elem_nodes(prm) * mesh->n_tris; ++i)
       if (mesh->tris[i] < 0 || mesh->tris[i] >= mesh->n_nodes) return FSI_ERR_INVALID;
     if (budget_bytes > 0) {
       const size_t need = footprint_impl(prm, mesh->n_nodes, mesh->n_tris, mesh->ref_xy, mesh->tris);
@@ -1643,11 +1680,12 @@ int fsi_create_problem_budget(const fsi_params* params, const fsi_solid_mesh* me
     CK(cudaEventCreateWithFlags(&P.ev_join, cudaEventDisableTiming));
     P.N = prm.N;
     VNum vn(prm.N);
-    P.nU = vn.n; P.nP = prm.N * prm.N; P.nS = mesh->n_nodes; P.nTri = mesh->n_tris; P.nPts = 6 * mesh->n_tris;
+    P.nU = vn.n; P.nP = prm.N * prm.N; P.nS = mesh->n_nodes; P.nTri = mesh->n_tris; P.nPts = elem_points(prm) * mesh->n_tris;
     P.offP = 2 * (size_t)P.nU; P.offX = P.offP + 3 * (size_t)P.nP; P.offL = P.offX + 2 * (size_t)P.nS;
     P.n = P.offL + 2 * (size_t)P.nS;
     P.m = prm.restart;
     SetupParams sp{prm.N, prm.rho_f, prm.nu, prm.kappa, prm.dt, prm.lid_u};
+    sp.npe = elem_nodes(prm);
     build_setup(sp, P.nS, P.nTri, mesh->ref_xy, mesh->tris, P.hs);
     {
       double lam[6][3], w[6];
@@ -1670,6 +1708,15 @@ int fsi_create_problem_budget(const fsi_params* params, const fsi_solid_mesh* me
         }
       CK(cudaMemcpyToSymbol(c_radon_lam, rl, sizeof(rl)));
       CK(cudaMemcpyToSymbol(c_radon_w, rw, sizeof(rw)));
+      // Q1: (s, t, s t) of the 3 x 3 Gauss points and the shape functions there
+      double qs[9], qt[9], qst[9], qw[9], qp[9][3], qc[9][4];
+      quad_rule(qs, qt, qst, qw);
+      for (int q = 0; q < 9; ++q) {
+        qp[q][0] = qs[q]; qp[q][1] = qt[q]; qp[q][2] = qst[q];
+        q1_shape(qs[q], qt[q], qc[q]);
+      }
+      CK(cudaMemcpyToSymbol(c_q1_pt, qp, sizeof(qp)));
+      CK(cudaMemcpyToSymbol(c_q1_chi, qc, sizeof(qc)));
     }
     allocate_problem(P, mesh->ref_xy, mesh->tris);
     CK(cudaMemset(P.ctl, 0, sizeof(Ctl)));
@@ -2112,11 +2159,8 @@ int fsi_time_kernel(fsi_problem* h, int which, int reps, double* avg_ms, double*
           *bytes = 0;
           break;
         }
-        case 8:    // C_f rows by the degree-4 rule at located points (S2 + S4)
-          launch(k_locate, nblk(P.nPts, 256), 256, 0, s, P.nPts, P.N, P.tris, P.Xold, P.cell, P.xi, P.eta,
-                 &P.ctl->aflags);
-          launch(k_cf_rows, nblk(P.nS, kCfWarps), 32 * kCfWarps, 0, s, P.nS, P.N, P.ntp, P.nt, P.area, P.cell, P.xi,
-                 P.eta, P.l2n, P.wall, P.cf_cap, P.cf_len, P.cf_col, P.cf_val, P.cf_val32, P.cflift, &P.ctl->aflags);
+        case 8:    // C_f rows by the point rule at located points (S2 + S4)
+          point_rule_launch(P, s);
           *bytes = 0;
           break;
         case 9:    // C_f rows by the exact rule (mesh intersection)

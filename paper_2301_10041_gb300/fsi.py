@@ -35,7 +35,8 @@ class fsi_params(C.Structure):
                 ("cs_degree", C.c_int), ("inner_rtol", C.c_double), ("max_refine", C.c_int),
                 ("stokes_its", C.c_int), ("stokes_omega", C.c_double), ("mg_cluster", C.c_int),
                 ("coupling", C.c_int), ("solid_law", C.c_int), ("gamma", C.c_double), ("eta", C.c_double),
-                ("newton_tol", C.c_double), ("newton_max", C.c_int), ("autotune", C.c_int)]
+                ("newton_tol", C.c_double), ("newton_max", C.c_int), ("autotune", C.c_int),
+                ("solid_elem", C.c_int)]
 
 
 class fsi_solid_mesh(C.Structure):
@@ -115,12 +116,12 @@ def _f64(a) -> np.ndarray:
 def make_params(N, rho_f, nu, kappa, dt, lid_u=0.0, precond=1, precision=0, restart=0, rtol=0.0, max_it=0,
                 mg_degree=0, cs_degree=0, inner_rtol=0.0, max_refine=0, stokes_its=0,
                 stokes_omega=0.0, mg_cluster=0, coupling=0, solid_law=0, gamma=0.0, eta=0.0, newton_tol=0.0,
-                newton_max=0, autotune=0) -> fsi_params:
+                newton_max=0, autotune=0, solid_elem=0) -> fsi_params:
     return fsi_params(int(N), float(rho_f), float(nu), float(kappa), float(dt), float(lid_u), int(precond),
                       int(precision), int(restart), float(rtol), int(max_it), int(mg_degree), int(cs_degree),
                       float(inner_rtol), int(max_refine), int(stokes_its), float(stokes_omega), int(mg_cluster),
                       int(coupling), int(solid_law), float(gamma), float(eta), float(newton_tol), int(newton_max),
-                      int(autotune))
+                      int(autotune), int(solid_elem))
 
 
 def footprint_bytes(params: fsi_params, n_nodes: int, n_tris: int) -> int:
@@ -145,7 +146,7 @@ class Problem:
         lib = load_library()
         self.params = params
         self.ref_xy = _f64(ref_xy).reshape(-1, 2)
-        self.tris = np.ascontiguousarray(tris, dtype=np.int32).reshape(-1, 3)
+        self.tris = np.ascontiguousarray(tris, dtype=np.int32).reshape(-1, 4 if params.solid_elem == 1 else 3)
         mesh = fsi_solid_mesh(self.ref_xy.shape[0], self.tris.shape[0],
                               self.ref_xy.ctypes.data_as(C.POINTER(C.c_double)),
                               self.tris.ctypes.data_as(C.POINTER(C.c_int)))
@@ -232,7 +233,7 @@ class Problem:
 
     # -- test hooks
     def get_points(self):
-        npts = 6 * self.tris.shape[0]
+        npts = (9 if self.params.solid_elem == 1 else 6) * self.tris.shape[0]
         cell = np.empty(npts, dtype=np.int32)
         xi = np.empty(npts)
         eta = np.empty(npts)
@@ -314,8 +315,11 @@ def step_batch(problems) -> list:
 
 def problem_from_case(case, precision: int = 0, precond=None, rtol=None, stream=None, **kw) -> Problem:
     """Build a Problem from an ``fsi_inputs.FsiCase`` (its ``extra`` may name
-    the exponential solid law with gamma and eta)."""
+    the exponential solid law with gamma and eta; a mesh of quadrilaterals
+    takes the Q1 solid)."""
     extra = getattr(case, "extra", None) or {}
+    if np.asarray(case.tris).shape[1] == 4:
+        kw.setdefault("solid_elem", 1)
     if extra.get("solid_law") == "exp":
         kw.setdefault("solid_law", 1)
         kw.setdefault("gamma", extra["gamma"])

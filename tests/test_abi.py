@@ -35,3 +35,44 @@ def test_library_exports_every_declared_symbol():
     assert sorted(fsi.EXPORTS) == declared()
     fsi.load_library(path)
     assert fsi.load_library().fsi_status_str(-4) == b"solid point outside the fluid domain"
+
+
+def test_ctypes_structs_match_the_header_layout(tmp_path):
+    """Offsets and sizes of the ctypes mirrors of fsi_params, fsi_solid_mesh
+    and fsi_solve_info equal those a C compiler gives the header."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    from paper_2301_10041_gb300 import fsi
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "fsi.h"', "int main(void) {"]
+    structs = {"fsi_params": fsi.fsi_params, "fsi_solid_mesh": fsi.fsi_solid_mesh,
+               "fsi_solve_info": fsi.fsi_solve_info}
+    for cname, cls in structs.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in cls._fields_:
+            lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, cls in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(cls), cname
+        for f, _ in cls._fields_:
+            assert got[(cname, f)] == getattr(cls, f).offset, (cname, f)
+
+
+def test_ctypes_structs_list_every_header_field_in_order():
+    """A field missing from a ctypes mirror could hide in tail padding: the
+    member names of each header struct equal the mirror's, in order."""
+    from paper_2301_10041_gb300 import fsi
+    src = open(os.path.join(ROOT, "include", "fsi.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    for cname, cls in (("fsi_params", fsi.fsi_params), ("fsi_solid_mesh", fsi.fsi_solid_mesh),
+                       ("fsi_solve_info", fsi.fsi_solve_info)):
+        body = re.search(r"typedef struct " + cname + r"\s*\{(.*?)\}\s*" + cname + ";", src, flags=re.S).group(1)
+        names = [re.findall(r"(\w+)\s*$", d.strip())[0] for d in body.split(";") if d.strip()]
+        assert names == [f for f, _ in cls._fields_], cname
