@@ -217,26 +217,62 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 16 : 8) k_sell(Sell<T> A
   const int row = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * RPW + (lane % RPW);
   const int t = lane / RPW;
   const bool live = row < A.nrows;
+  // The row's epilogue operands (z, d, dinv, x) do not depend on A x.  For
+  // square blocks (the multigrid level operators) thread t of the row loads
+  // one of them (t = 0: z, 1: d, 2: dinv, 3: x) before the product, so that
+  // their memory latency overlaps it, and they reach thread 0 by shuffles
+  // after the reduction; other shapes load them after it (more registers
+  // would spill).  Only thread 0 of the row writes y[r] and d[r], and x is not
+  // written in these modes, so the early reads see the same values.
+  constexpr bool PRE = (BR == BC);
+  const T* pre_src = nullptr;
+  if (t == 0) pre_src = a.z;
+  else if (t == 1 && MODE == MODE_CHEB) pre_src = a.d;
+  else if (t == 2 && MODE != MODE_AXPBY) pre_src = a.dinv;
+  else if (t == 3 && (MODE == MODE_CHEB || MODE == MODE_CHEB0)) pre_src = a.x;
+  T pre[BR];
+#pragma unroll
+  for (int i = 0; i < BR; ++i) pre[i] = (PRE && live && pre_src) ? pre_src[row * BR + i] : (T)0;
   T acc[BR];
 #pragma unroll
   for (int i = 0; i < BR; ++i) acc[i] = 0;
   if (live) sell_row<T, T, BR, BC, KRON, NV, TPR>(A, row, t, a.x, acc);
   row_reduce<T, BR, TPR>(acc);
   pdl_trigger();
+  T zr[BR], dr[BR], vr[BR], xr[BR];
+  if constexpr (PRE) {
+    const int r0 = lane % RPW;  // lane of the row's thread 0; thread k is at r0 + k RPW
+#pragma unroll
+    for (int i = 0; i < BR; ++i) {
+      zr[i] = __shfl_sync(0xffffffffu, pre[i], r0);
+      dr[i] = __shfl_sync(0xffffffffu, pre[i], r0 + RPW);
+      vr[i] = __shfl_sync(0xffffffffu, pre[i], r0 + 2 * RPW);
+      xr[i] = __shfl_sync(0xffffffffu, pre[i], r0 + 3 * RPW);
+    }
+  }
   if (!live || t != 0) return;
-  const T* __restrict__ x = a.x;
+  if constexpr (!PRE) {
+#pragma unroll
+    for (int i = 0; i < BR; ++i) {
+      const int r = row * BR + i;
+      zr[i] = a.z ? a.z[r] : (T)0;
+      dr[i] = (MODE == MODE_CHEB) ? a.d[r] : (T)0;
+      vr[i] = (MODE != MODE_AXPBY) ? a.dinv[r] : (T)0;
+      xr[i] = (MODE == MODE_CHEB || MODE == MODE_CHEB0) ? a.x[r] : (T)0;
+    }
+  }
 #pragma unroll
   for (int i = 0; i < BR; ++i) {
     const int r = row * BR + i;
     if (MODE == MODE_AXPBY) {
       T out = a.alpha * acc[i];
-      if (a.z) out += a.beta * a.z[r];
+      if (a.z) out += a.beta * zr[i];
       a.y[r] = out;
     } else if (MODE == MODE_CHEB || MODE == MODE_CHEB0) {
-      const T res = a.z[r] - acc[i];
-      const T dn = (MODE == MODE_CHEB) ? a.c1 * a.d[r] + a.c2 * a.dinv[r] * res : a.c2 * a.dinv[r] * res;
+      const T res = zr[i] - acc[i];
+      const T dn = (MODE == MODE_CHEB) ? a.c1 * dr[i] + a.c2 * vr[i] * res : a.c2 * vr[i] * res;
       a.d[r] = dn;
-      const T yv = x[r] + dn;
+      const T yv = xr[i] + dn;
       a.y[r] = yv;
       T ov = yv;
       if (a.sout) {
@@ -246,9 +282,9 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 16 : 8) k_sell(Sell<T> A
       if (a.acc) a.acc[r] += a.omega * ov;
     } else {  // MODE_INIT
       T tt = a.alpha * acc[i];
-      if (a.z) tt += a.beta * a.z[r];
+      if (a.z) tt += a.beta * zr[i];
       a.y[r] = tt;
-      const T dn = a.c2 * a.dinv[r] * tt;
+      const T dn = a.c2 * vr[i] * tt;
       a.d[r] = dn;
       a.xo[r] = dn;
     }
