@@ -37,6 +37,8 @@ struct FluidLevelHost {
   HostBlockMatrix L;      // pressure Laplacian B diag(M)^-1 B^T, 3x3 cell blocks
   HostBlockMatrix Pu, Ru; // velocity prolongation from / restriction to the coarser level (kron 2)
   HostBlockMatrix Pp, Rp; // pressure prolongation / restriction (3x3)
+  HostBlockMatrix RAp;    // Rp L (coarse rows x fine columns, full blocks): the restricted
+                          // pressure residual R (b - L x) = R b - (R L) x in one pass
   std::vector<double> dinvA, dinvL;  // Jacobi inverses (per scalar dof)
   double lmaxA = 0, lmaxL = 0;       // lambda_max of D^-1 A and D^-1 L
 };

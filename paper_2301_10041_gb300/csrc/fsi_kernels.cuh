@@ -291,6 +291,43 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 16 : 8) k_sell(Sell<T> A
   }
 }
 
+// Fused residual and restriction of one multigrid level, on the coarse rows:
+//   y = R b - (R A) x  (= R (b - A x); R A is formed once on the host),
+// so the fine residual is neither launched nor stored.  MODE_INIT also starts
+// the coarse level's smoother: d = xo = c2 dinv y.  Used on the pressure
+// levels, whose R A is small (16 blocks per coarse row).
+template <class T, int B, bool RKRON, int RNV, int MODE, int TPR>
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 16 : 8) k_resrestrict(Sell<T> R, Sell<T> RA, SpmvArgs<T> a) {
+  pdl_begin();
+  constexpr int RPW = 32 / TPR;
+  const int lane = threadIdx.x & 31;
+  const int row = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * RPW + (lane % RPW);
+  const int t = lane / RPW;
+  const bool live = row < R.nrows;
+  T acc[B];
+#pragma unroll
+  for (int i = 0; i < B; ++i) acc[i] = 0;
+  if (live) {
+    sell_row<T, T, B, B, false, B * B, TPR>(RA, row, t, a.x, acc);  // (R A) x
+#pragma unroll
+    for (int i = 0; i < B; ++i) acc[i] = -acc[i];
+    sell_row<T, T, B, B, RKRON, RNV, TPR>(R, row, t, a.z, acc);     // + R b
+  }
+  row_reduce<T, B, TPR>(acc);
+  pdl_trigger();
+  if (!live || t != 0) return;
+#pragma unroll
+  for (int i = 0; i < B; ++i) {
+    const int r = row * B + i;
+    a.y[r] = acc[i];
+    if (MODE == MODE_INIT) {
+      const T dn = a.c2 * a.dinv[r] * acc[i];
+      a.d[r] = dn;
+      a.xo[r] = dn;
+    }
+  }
+}
+
 // --------------------------------------------------- full-system operator
 // y = alpha * A x + beta * z for the block operator of Eq. (matrix) in the
 // layout [u (2 nU) | p (3 nP) | X (2 nS) | lambda (2 nS)].  One launch covers

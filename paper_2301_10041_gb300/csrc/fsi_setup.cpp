@@ -346,6 +346,56 @@ static HostBlockMatrix transpose(const HostBlockMatrix& A) {
   return T;
 }
 
+// C = R A for a block matrix R (B x B blocks, kron or full) and a square-block
+// matrix A (B x B, full): full B x B blocks, rows sorted by column.
+static HostBlockMatrix block_product(const HostBlockMatrix& R, const HostBlockMatrix& A) {
+  const int B = A.BR;
+  if (A.BC != B || A.kron || R.BR != B || R.BC != B || R.ncols != A.nrows)
+    throw std::logic_error("block_product: shapes");
+  HostBlockMatrix C;
+  init_matrix(C, B, B, false, R.nrows, A.ncols);
+  const int BB = B * B;
+  std::vector<int> slot(A.ncols, -1), cols, order;
+  std::vector<double> acc;
+  for (int r = 0; r < R.nrows; ++r) {
+    cols.clear();
+    acc.clear();
+    for (int j = R.ptr[r]; j < R.ptr[r + 1]; ++j) {
+      const int k = R.col[j];
+      for (int m = A.ptr[k]; m < A.ptr[k + 1]; ++m) {
+        const int c = A.col[m];
+        if (slot[c] < 0) {
+          slot[c] = (int)cols.size();
+          cols.push_back(c);
+          acc.resize(acc.size() + BB, 0.0);
+        }
+        double* dst = &acc[(size_t)slot[c] * BB];
+        const double* a = &A.val[(size_t)m * BB];
+        for (int i = 0; i < B; ++i)
+          for (int jj = 0; jj < B; ++jj) {
+            double sum = 0.0;
+            if (R.kron) {
+              sum = R.val[j] * a[i * B + jj];
+            } else {
+              for (int q = 0; q < B; ++q) sum += R.val[(size_t)j * BB + i * B + q] * a[q * B + jj];
+            }
+            dst[i * B + jj] += sum;
+          }
+      }
+    }
+    order.resize(cols.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+    std::sort(order.begin(), order.end(), [&](int x, int y) { return cols[x] < cols[y]; });
+    for (int i : order) {
+      C.col.push_back(cols[i]);
+      for (int v = 0; v < BB; ++v) C.val.push_back(acc[(size_t)i * BB + v]);
+      slot[cols[i]] = -1;
+    }
+    C.ptr.push_back((int)C.col.size());
+  }
+  return C;
+}
+
 static std::vector<double> block_diag_inverse_scalar(const HostBlockMatrix& A) {
   // inverse of the scalar diagonal (per dof) of a square block matrix
   std::vector<double> d((size_t)A.nrows * A.BR, 0.0);
@@ -552,6 +602,7 @@ void build_setup(const SetupParams& sp, int n_s, int n_tri, const double* ref_xy
       L.Ru = transpose(L.Pu);
       assemble_prolong_p(Ns[l + 1], L.Pp);
       L.Rp = transpose(L.Pp);
+      L.RAp = block_product(L.Rp, L.L);
     }
     // lambda_max on a proxy grid of at most 24 cells with the same cell size
     const int Np = std::min(L.N, 24);

@@ -166,6 +166,22 @@ static void sell_launch_shape(const Sell<T>& A, int mode, const SpmvArgs<T>& a, 
   sell_launch_tpr<T, BR, BC, KRON, NV, 4>(A, mode, a, s);
 }
 
+// Fused residual + restriction (k_resrestrict) of the pressure levels: full
+// 3x3 restriction blocks, R L with full blocks.
+template <class T, int B, bool RKRON, int RNV, int TPR>
+static void resrestrict_shape(const Sell<T>& R, const Sell<T>& RA, int mode, const SpmvArgs<T>& a, cudaStream_t s) {
+  const unsigned g = nblk(R.nrows, 4 * (32 / TPR));
+  if (mode == MODE_INIT) launch(k_resrestrict<T, B, RKRON, RNV, MODE_INIT, TPR>, g, 128, 0, s, R, RA, a);
+  else launch(k_resrestrict<T, B, RKRON, RNV, MODE_AXPBY, TPR>, g, 128, 0, s, R, RA, a);
+}
+
+template <class T>
+static void resrestrict_launch(const Sell<T>& R, const Sell<T>& RA, int mode, const SpmvArgs<T>& a, cudaStream_t s) {
+  if (R.nrows == 0) return;
+  if (!R.kron && R.BR == 3 && RA.BR == 3) return resrestrict_shape<T, 3, false, 9, 4>(R, RA, mode, a, s);
+  throw std::logic_error("unsupported restriction shape");
+}
+
 template <class T>
 static void sell_launch(const Sell<T>& A, int mode, const SpmvArgs<T>& a, cudaStream_t s) {
   if (A.nrows == 0) return;
@@ -282,6 +298,7 @@ static Cheb cheb_coeffs(double lo, double hi, int k) {
 template <class T>
 struct MGLevel {
   Sell<T> A, P, R;  // P: prolongation from the next coarser level, R: restriction to it
+  Sell<T> RA;       // pressure levels: R L, so that R (b - L x) = R b - (R L) x takes one pass
   T* dinv = nullptr;
   T *x = nullptr, *x2 = nullptr, *b = nullptr, *r = nullptr, *d = nullptr;
   int n = 0;        // scalar unknowns
@@ -329,9 +346,11 @@ static void build_mg(Arena& ar, const HostSetup& hs, bool pressure, int degree, 
     if (l + 1 < nl) {
       L.P = upload_sell<T>(ar, to_sell(pressure ? H.Pp : H.Pu));
       L.R = upload_sell<T>(ar, to_sell(pressure ? H.Rp : H.Ru));
+      if (pressure) L.RA = upload_sell<T>(ar, to_sell(H.RAp));
     }
     L.x = ar.alloc<T>(L.n); L.x2 = ar.alloc<T>(L.n); L.b = ar.alloc<T>(L.n);
-    L.r = ar.alloc<T>(L.n); L.d = ar.alloc<T>(L.n);
+    if (!pressure) L.r = ar.alloc<T>(L.n);
+    L.d = ar.alloc<T>(L.n);
     const double hi = 1.05 * (pressure ? H.lmaxL : H.lmaxA);
     L.ch = cheb_coeffs(hi / (pressure ? kChebRatioP : kChebRatioU), hi, degree);
   }
@@ -442,14 +461,25 @@ static T* vcycle(MG<T>& mg, int l, cudaStream_t s, T* out, const SpmvArgs<T>* fi
     sell_launch(L.A, MODE_CHEB, a, s);
     std::swap(xc, xn);
   }
-  sell_launch(L.A, MODE_AXPBY, axpby<T>(xc, L.r, L.b, (T)-1, (T)1), s);
   MGLevel<T>& C = mg.lv[l + 1];
-  if (l + 1 == last || (mg.cl.on && l + 1 == mg.cl.lc)) {  // the coarser cycle initialises itself
-    sell_launch(L.R, MODE_AXPBY, axpby<T>(L.r, C.b, nullptr, (T)1, (T)0), s);
-  } else {
-    SpmvArgs<T> a = axpby<T>(L.r, C.b, nullptr, (T)1, (T)0);
-    a.d = C.d; a.dinv = C.dinv; a.xo = C.x; a.c2 = (T)C.ch.c0;
-    sell_launch(L.R, MODE_INIT, a, s);
+  if (L.RA.nrows == 0) {  // residual, then its restriction
+    sell_launch(L.A, MODE_AXPBY, axpby<T>(xc, L.r, L.b, (T)-1, (T)1), s);
+    if (l + 1 == last || (mg.cl.on && l + 1 == mg.cl.lc)) {
+      sell_launch(L.R, MODE_AXPBY, axpby<T>(L.r, C.b, nullptr, (T)1, (T)0), s);
+    } else {
+      SpmvArgs<T> a = axpby<T>(L.r, C.b, nullptr, (T)1, (T)0);
+      a.d = C.d; a.dinv = C.dinv; a.xo = C.x; a.c2 = (T)C.ch.c0;
+      sell_launch(L.R, MODE_INIT, a, s);
+    }
+  } else {  // the coarse right-hand side R (b - A x) = R b - (R A) x in one launch
+    SpmvArgs<T> ra;
+    ra.x = xc; ra.z = L.b; ra.y = C.b;
+    if (l + 1 == last || (mg.cl.on && l + 1 == mg.cl.lc)) {
+      resrestrict_launch(L.R, L.RA, MODE_AXPBY, ra, s);
+    } else {
+      ra.d = C.d; ra.dinv = C.dinv; ra.xo = C.x; ra.c2 = (T)C.ch.c0;
+      resrestrict_launch(L.R, L.RA, MODE_INIT, ra, s);
+    }
   }
   T* xcoarse = vcycle<T>(mg, l + 1, s, (T*)nullptr);
   sell_launch(L.P, MODE_AXPBY, axpby<T>(xcoarse, xc, xc, (T)1, (T)1), s);
