@@ -179,15 +179,16 @@ def gpu_ops(precision: int = 1, restart: int = 60, stokes_its: int = 8, precond:
     cache: dict = {}
 
     def params(case):
+        # a mesh of quadrilaterals takes the Q1 solid
         return fsi.make_params(case.N, case.rho_f, case.nu, case.kappa, case.dt, case.lid_u,
                                precond=precond, precision=precision, rtol=case.rtol, restart=restart,
-                               max_it=6000, stokes_its=stokes_its)
+                               max_it=6000, stokes_its=stokes_its, solid_elem=int(case.tris.shape[1] == 4))
 
     def footprint(case):
         if max_solid_nodes is not None:
-            key = (case.N,) + tuple(max_solid_nodes(case.N))
+            key = (case.N,) + tuple(max_solid_nodes(case.N)) + (case.tris.shape[1],)
         else:
-            key = (case.N, case.ref_xy.shape[0], case.tris.shape[0])
+            key = (case.N, case.ref_xy.shape[0], case.tris.shape[0], case.tris.shape[1])
         if key not in cache:
             cache[key] = fsi.footprint_bytes(params(case), key[1], key[2])
         return cache[key]

@@ -1,0 +1,102 @@
+// Host-only checks of the library's setup code (fsi_setup.cpp), run by
+// tests/test_setup_host.py without a GPU.
+//
+//   setup_harness products N
+//     for every pressure level with a fused restriction, the product R L
+//     applied to a random vector against R applied to L x (one line per
+//     level: {"level": l, "rel_err": e});
+//   setup_harness solid <mesh file> <kappa>
+//     build the solid operators of a Q1 mesh (file: n_nodes n_el, then x y
+//     per node, then 4 node ids per element) and print C_s and A_s as
+//     triplets and the Chebyshev interval of D^-1 C_s, as one JSON object.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <random>
+#include <string>
+#include <vector>
+
+#include "fsi_internal.h"
+
+using namespace fsi;
+
+static void spmv(const HostBlockMatrix& A, const std::vector<double>& x, std::vector<double>& y) {
+  y.assign((size_t)A.nrows * A.BR, 0.0);
+  for (int r = 0; r < A.nrows; ++r)
+    for (int j = A.ptr[r]; j < A.ptr[r + 1]; ++j) {
+      const int c = A.col[j];
+      for (int i = 0; i < A.BR; ++i)
+        for (int k = 0; k < A.BC; ++k) {
+          const double v = A.kron ? (i == k ? A.val[j] : 0.0) : A.val[(size_t)j * A.NV + i * A.BC + k];
+          y[(size_t)r * A.BR + i] += v * x[(size_t)c * A.BC + k];
+        }
+    }
+}
+
+static int products(int N) {
+  // a small solid inside the domain: the fluid hierarchy does not depend on it
+  const double xy[6] = {0.4, 0.4, 0.6, 0.4, 0.5, 0.6};
+  const int tris[3] = {0, 1, 2};
+  SetupParams sp{N, 1.0, 0.1, 10.0, 0.01, 0.0};
+  HostSetup hs;
+  build_setup(sp, 3, 1, xy, tris, hs);
+  std::mt19937_64 rng(7);
+  std::uniform_real_distribution<double> U(-1.0, 1.0);
+  for (size_t l = 0; l + 1 < hs.levels.size(); ++l) {
+    const FluidLevelHost& L = hs.levels[l];
+    std::vector<double> x((size_t)L.L.ncols * L.L.BC), Lx, RLx, fused;
+    for (double& v : x) v = U(rng);
+    spmv(L.L, x, Lx);
+    spmv(L.Rp, Lx, RLx);
+    spmv(L.RAp, x, fused);
+    double num = 0, den = 0;
+    for (size_t i = 0; i < RLx.size(); ++i) {
+      num += (fused[i] - RLx[i]) * (fused[i] - RLx[i]);
+      den += RLx[i] * RLx[i];
+    }
+    std::printf("{\"level\": %zu, \"rows\": %d, \"rel_err\": %.3e}\n", l, L.RAp.nrows, std::sqrt(num / den));
+  }
+  return 0;
+}
+
+static void triplets(const char* name, const HostBlockMatrix& A) {
+  std::printf("\"%s\": [", name);
+  bool first = true;
+  for (int r = 0; r < A.nrows; ++r)
+    for (int j = A.ptr[r]; j < A.ptr[r + 1]; ++j) {
+      std::printf("%s[%d, %d, %.17g]", first ? "" : ", ", r, A.col[j], A.val[j]);
+      first = false;
+    }
+  std::printf("]");
+}
+
+static int solid(const char* path, double kappa) {
+  FILE* f = std::fopen(path, "r");
+  if (!f) return 2;
+  int ns = 0, ne = 0;
+  if (std::fscanf(f, "%d %d", &ns, &ne) != 2) return 2;
+  std::vector<double> xy(2 * (size_t)ns);
+  std::vector<int> el(4 * (size_t)ne);
+  for (double& v : xy)
+    if (std::fscanf(f, "%lf", &v) != 1) return 2;
+  for (int& v : el)
+    if (std::fscanf(f, "%d", &v) != 1) return 2;
+  std::fclose(f);
+  SetupParams sp{8, 1.0, 0.1, kappa, 0.01, 0.0};
+  sp.npe = 4;
+  HostSetup hs;
+  build_setup(sp, ns, ne, xy.data(), el.data(), hs);
+  std::printf("{");
+  triplets("Cs", hs.Cs);
+  std::printf(", ");
+  triplets("As", hs.As);
+  std::printf(", \"cs_lo\": %.17g, \"cs_hi\": %.17g}\n", hs.cs_lo, hs.cs_hi);
+  return 0;
+}
+
+int main(int argc, char** argv) {
+  if (argc >= 3 && std::string(argv[1]) == "products") return products(std::atoi(argv[2]));
+  if (argc >= 4 && std::string(argv[1]) == "solid") return solid(argv[2], std::atof(argv[3]));
+  std::fprintf(stderr, "usage: setup_harness products N | solid mesh kappa\n");
+  return 1;
+}

@@ -80,3 +80,36 @@ def test_admission_budget_refuses(fsi):
     assert e.value.code == fsi.FSI_ERR_BUDGET
     p = fsi.Problem(prm, c.ref_xy, c.tris, u0=c.u0, X0=c.X0, budget_bytes=need)
     p.close()
+
+
+def _mixed_elements():
+    """A P1 disk and two Q1 annuli (quarter, no-slip; mirrored full annulus)."""
+    return [_cases()[0], fi.annulus_case(16, quads=True), fi.symmetric_annulus_case(8, quads=True)]
+
+
+def test_batch_mixed_elements_equals_alone(fsi):
+    cases = _mixed_elements()
+    probs = [fsi.problem_from_case(c, precision=1) for c in cases]
+    for _ in range(2):
+        st, infos = fsi.step_batch(probs)
+        assert st == 0 and all(i.status == 0 for i in infos)
+    for c, p in zip(cases, probs):
+        ref = _alone(fsi, c, 2)
+        for a, b in zip(p.get_state(), ref):
+            assert np.array_equal(a, b)
+        p.close()
+
+
+def test_served_q1_requests_equal_alone(fsi):
+    from paper_2301_10041_gb300.serve import Request, Server, gpu_ops
+    cases = _mixed_elements()
+    ops = gpu_ops(precision=1, restart=40, stokes_its=1, precond=2)
+    srv = Server(ops, budget_bytes=sum(ops.footprint(c) for c in cases))
+    reqs = [Request(rid=i, arrival=0.0, case=c, steps=2) for i, c in enumerate(cases)]
+    srv.run(reqs, realtime=False)
+    assert len(srv.finished) == 3
+    for r in srv.finished:
+        assert r.error is None
+        ref = _alone(fsi, r.case, r.steps, restart=40, stokes_its=1, precond=2)
+        for a, b in zip(r.result, ref):
+            assert np.array_equal(a, b)
