@@ -1653,15 +1653,52 @@ size_t fsi_footprint_bytes(const fsi_params* params, int n_solid_nodes, int n_tr
     }
     xy[0] = 0.5; xy[1] = 0.5;
     if (params->solid_elem == 1) {
+      if (n_solid_nodes < 4) return 0;  // a quadrilateral needs 4 nodes
+      tr.assign(4 * (size_t)n_tris, 0);
+      if (n_solid_nodes < 8) {
+        // a ladder of m quadrilaterals-wide strip: nodes j (bottom) and m + j (top)
+        const int m = n_solid_nodes / 2;
+        for (int j = 0; j < m; ++j) {
+          xy[2 * j] = xy[2 * (m + j)] = 0.3 + 0.4 * j / (m - 1);
+          xy[2 * j + 1] = 0.45;
+          xy[2 * (m + j) + 1] = 0.55;
+        }
+        for (int t = 0; t < n_tris; ++t) {
+          const int j = t % (m - 1);
+          tr[4 * t] = j; tr[4 * t + 1] = j + 1; tr[4 * t + 2] = m + j + 1; tr[4 * t + 3] = m + j;
+        }
+        return footprint_impl(*params, n_solid_nodes, n_tris, xy.data(), tr.data());
+      }
       // quadrilaterals (centre, three consecutive ring nodes): convex and
       // counter-clockwise while three ring steps span less than half a turn
-      if (n_solid_nodes < 8) return 0;
-      tr.assign(4 * (size_t)n_tris, 0);
       for (int t = 0; t < n_tris; ++t) {
         const int a = 1 + t % (n_solid_nodes - 1);
         const int b = 1 + (a % (n_solid_nodes - 1));
         const int c = 1 + (b % (n_solid_nodes - 1));
         tr[4 * t] = 0; tr[4 * t + 1] = a; tr[4 * t + 2] = b; tr[4 * t + 3] = c;
+      }
+      return footprint_impl(*params, n_solid_nodes, n_tris, xy.data(), tr.data());
+    }
+    if (n_solid_nodes < 5) {
+      // too few ring nodes for a fan (its closing triangle would span half a
+      // turn): one triangle, or a strip of two-triangle cells (nodes j bottom,
+      // m + j top), counter-clockwise
+      const int m = n_solid_nodes / 2;
+      if (n_solid_nodes == 3) {
+        const double p3[6] = {0.45, 0.45, 0.55, 0.45, 0.5, 0.55};
+        for (int i = 0; i < 6; ++i) xy[i] = p3[i];
+      } else {
+        for (int j = 0; j < m; ++j) {
+          xy[2 * j] = xy[2 * (m + j)] = 0.3 + 0.4 * j / (m - 1);
+          xy[2 * j + 1] = 0.45;
+          xy[2 * (m + j) + 1] = 0.55;
+        }
+      }
+      for (int t = 0; t < n_tris; ++t) {
+        if (n_solid_nodes == 3) { tr[3 * t] = 0; tr[3 * t + 1] = 1; tr[3 * t + 2] = 2; continue; }
+        const int c = t % (2 * (m - 1)), j = c / 2;
+        if (c % 2 == 0) { tr[3 * t] = j; tr[3 * t + 1] = j + 1; tr[3 * t + 2] = m + j + 1; }
+        else { tr[3 * t] = j; tr[3 * t + 1] = m + j + 1; tr[3 * t + 2] = m + j; }
       }
       return footprint_impl(*params, n_solid_nodes, n_tris, xy.data(), tr.data());
     }

@@ -76,3 +76,45 @@ def test_ctypes_structs_list_every_header_field_in_order():
         body = re.search(r"typedef struct " + cname + r"\s*\{(.*?)\}\s*" + cname + ";", src, flags=re.S).group(1)
         names = [re.findall(r"(\w+)\s*$", d.strip())[0] for d in body.split(";") if d.strip()]
         assert names == [f for f, _ in cls._fields_], cname
+
+
+FOOTPRINT_SWEEP = r"""
+import sys
+sys.path.insert(0, sys.argv[1])
+from paper_2301_10041_gb300 import fsi
+fsi.load_library()
+bad = []
+for elem in (0, 1):
+    for N in (8, 16):
+        prm = fsi.make_params(N, 1.0, 0.1, 10.0, 0.01, solid_elem=elem)
+        for nn in range(1, 14):
+            for ne in (1, 2, 5, 17, 40):
+                v = fsi.footprint_bytes(prm, nn, ne)
+                valid = nn >= (4 if elem else 3)
+                if (v > 0) != valid:
+                    bad.append((elem, N, nn, ne, v))
+print("bad", bad)
+"""
+
+
+def test_footprint_is_host_logic_and_never_crashes():
+    """fsi_footprint_bytes counts bytes on the host (no device call): it is
+    positive for every valid size, 0 for meshes too small for their element,
+    never faults on tiny meshes (run in a child process), and grows with
+    the grid and the solid."""
+    import subprocess
+    import sys
+    from paper_2301_10041_gb300 import build, fsi
+    try:
+        build.build()
+    except RuntimeError as e:
+        pytest.skip(str(e))
+    r = subprocess.run([sys.executable, "-c", FOOTPRINT_SWEEP, ROOT], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert r.stdout.strip().endswith("bad []"), r.stdout[-2000:]
+    fsi.load_library()
+    for elem in (0, 1):
+        f = lambda N, nn, ne: fsi.footprint_bytes(fsi.make_params(N, 1.0, 0.1, 10.0, 0.01, solid_elem=elem), nn, ne)
+        assert f(16, 60, 44) < f(32, 60, 44) < f(64, 60, 44)
+        assert f(32, 60, 44) < f(32, 600, 440)
+    assert fsi.footprint_bytes(fsi.make_params(15, 1.0, 0.1, 10.0, 0.01), 60, 44) == 0   # odd N
