@@ -78,3 +78,27 @@ def test_budgeted_fifo_admission_and_release():
     rep = srv.report(wall)
     assert rep["steps"] == sum(r.steps for r in reqs if r.rid != 99)
     assert rep["requests_rejected"] == 1
+
+
+def test_admission_footprint_follows_the_solid_element():
+    """The server's footprint (host logic of the library, no device call)
+    takes the element type from the mesh: Q1 quadrilaterals (9 rule points
+    per element) need more coupling storage than the same counts as P1, and
+    P1 and Q1 sizes are cached apart."""
+    import pytest
+    import fsi_inputs as fi
+    from paper_2301_10041_gb300 import build
+    from paper_2301_10041_gb300.serve import gpu_ops
+    try:
+        build.build()
+    except RuntimeError as e:
+        pytest.skip(str(e))
+    ops = gpu_ops(precision=1)
+    q1 = fi.annulus_case(16, quads=True)
+    p1_same_counts = fi.FsiCase(N=q1.N, rho_f=q1.rho_f, nu=q1.nu, kappa=q1.kappa, dt=q1.dt, lid_u=0.0,
+                                ref_xy=q1.ref_xy, tris=np.zeros((q1.tris.shape[0], 3), dtype=np.int32),
+                                u0=q1.u0, X0=q1.X0, rtol=q1.rtol)
+    f_q1 = ops.footprint(q1)
+    f_p1 = ops.footprint(p1_same_counts)
+    assert f_q1 > 0 and f_p1 > 0 and f_q1 != f_p1
+    assert ops.footprint(q1) == f_q1    # cached per (N, nodes, elements, element type)
