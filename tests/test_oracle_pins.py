@@ -677,3 +677,37 @@ def test_q1_step_residual_and_body_at_rest():
     assert np.abs(u).max() < 1e-13 and np.abs(X - c.ref_xy).max() < 1e-15
     with pytest.raises(ValueError):
         fo.OracleProblem(c.N, 1.0, 0.1, 1.0, 0.01, 0.0, c.ref_xy, c.tris, coupling="exact")
+
+
+@pytest.mark.parametrize("quads", [False, True])
+def test_mirrored_annulus_gives_free_slip_quarter(quads):
+    """The reading behind the free-slip walls of the annulus test (Section 6):
+    the full annulus, mirror-symmetric mesh and data, has a mirror-symmetric
+    step, so its velocity has no normal component on the mirror lines x = 1/2
+    and y = 1/2 (the quarter problem's free-slip walls) and the body's
+    displacement is mirror-symmetric."""
+    from scipy.spatial import cKDTree
+    case = fi.symmetric_annulus_case(8, quads=quads)
+    prob = fo.OracleProblem(case.N, case.rho_f, case.nu, case.kappa, case.dt, case.lid_u, case.ref_xy, case.tris)
+    u, p, X, lam = prob.step(case.u0, case.X0)
+    n1 = 2 * case.N + 1
+    U = u.reshape(n1, n1, 2)                        # [iy, ix, comp]
+    scale = np.abs(U).max()
+    assert scale > 0
+    # mirror in x = 1/2: u_x odd, u_y even; in y = 1/2: u_x even, u_y odd
+    assert np.abs(U[:, ::-1, 0] + U[:, :, 0]).max() <= 1e-10 * scale
+    assert np.abs(U[:, ::-1, 1] - U[:, :, 1]).max() <= 1e-10 * scale
+    assert np.abs(U[::-1, :, 0] - U[:, :, 0]).max() <= 1e-10 * scale
+    assert np.abs(U[::-1, :, 1] + U[:, :, 1]).max() <= 1e-10 * scale
+    # no flow through the mirror lines (the quarter's free-slip walls)
+    assert np.abs(U[:, case.N, 0]).max() <= 1e-10 * scale
+    assert np.abs(U[case.N, :, 1]).max() <= 1e-10 * scale
+    D = X - case.X0
+    tree = cKDTree(case.ref_xy)
+    mx = case.ref_xy.copy()
+    mx[:, 0] = 1.0 - mx[:, 0]
+    ix = tree.query(mx)[1]
+    assert np.abs(case.ref_xy[ix] - mx).max() < 1e-12
+    dmax = np.abs(D).max()
+    assert np.abs(D[ix, 0] + D[:, 0]).max() <= 1e-10 * dmax
+    assert np.abs(D[ix, 1] - D[:, 1]).max() <= 1e-10 * dmax
