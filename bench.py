@@ -130,13 +130,17 @@ def arm_settings(precision):
 
 
 def time_arm(fsi, torch, case, precision, steps, warmup, stream, flush, precond=PRECOND, stokes_its=STOKES_ITS,
-             max_it=MAX_IT, check=True, settings=None):
+             max_it=MAX_IT, check=True, settings=None, first_state=None):
+    """Time `steps` time steps after `warmup` untimed ones; with a list
+    `first_state`, the state after the first (untimed) step is appended to it."""
     prob = fsi.problem_from_case(case, precision=precision, precond=precond, rtol=1e-8, stream=stream.cuda_stream,
                                  max_it=max_it, stokes_its=stokes_its, **(settings or arm_settings(precision)))
     step = prob.step if check else (lambda: _step_unchecked(prob))
     infos = []
-    for _ in range(warmup):
+    for k in range(warmup):
         step()
+        if k == 0 and first_state is not None:
+            first_state.append(prob.get_state())
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     torch.cuda.synchronize()
     for k in range(steps):
@@ -222,8 +226,11 @@ def run_ours(args):
     case = workload()
 
     cpu = None
+    oracle_npz = ""
     if rank == 0 and not args.no_cpu_baseline:
-        cpu = start_cpu_baseline(args)
+        import tempfile
+        oracle_npz = os.path.join(tempfile.mkdtemp(prefix="fsi_oracle_"), "step1.npz")
+        cpu = start_cpu_baseline(args, oracle_npz)
 
     stream = torch.cuda.Stream()
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
@@ -233,11 +240,14 @@ def run_ours(args):
     torch.cuda.synchronize()
     clocks.start()
     t_wall0 = time.perf_counter()
-    prob_m, mixed = time_arm(fsi, torch, case, 1, args.steps, args.warmup, stream, flush)
+    first_m, first_d = [], []
+    prob_m, mixed = time_arm(fsi, torch, case, 1, args.steps, args.warmup, stream, flush, first_state=first_m)
     t_wall1 = time.perf_counter()
     clk = clocks.stop()
-    prob_d, fp64 = time_arm(fsi, torch, case, 0, args.steps, args.warmup, stream, flush)
+    prob_d, fp64 = time_arm(fsi, torch, case, 0, args.steps, args.warmup, stream, flush, first_state=first_d)
     roof = roofline(prob_m, args)
+    if not args.no_large_n:
+        roof["large_n"] = large_n_roofline(fsi, stream, local, roof["peak"], args.large_n)
     e2e_t, h2d, d2h = time_e2e(fsi, case, 1, max(3, min(args.steps, 10)), args.warmup, stream)
     prob_m.close()
     prob_d.close()
@@ -285,6 +295,12 @@ def run_ours(args):
     out["config"]["parallelism"] = f"replicas x{world}"
     if cpu is not None:
         out["cpu_baseline"] = finish_cpu_baseline(cpu)
+        if os.path.exists(oracle_npz):
+            out["error_vs_oracle"] = {
+                "what": "relative L2 error per field of time step 1 (from the initial state) against the oracle's "
+                        "direct solve of the same step; X as the displacement X - X^0",
+                "mixed": field_errors(case, first_m[0], oracle_npz),
+                "fp64": field_errors(case, first_d[0], oracle_npz)}
     print(json.dumps(out))
     if dist:
         dist.destroy_process_group()
@@ -349,6 +365,34 @@ def roofline(prob, args):
             "launch_us": dom["ms"] * 1e3, "algorithmic_bytes": dom["bytes"], "others": out}
 
 
+def large_n_roofline(fsi, stream, device_index, peak, N):
+    """The same kernels on the largest sweep member (ellipse, N = 1024 by
+    default: 13.5 M unknowns, matrices of GBs, far larger than L2), where
+    they are bandwidth-bound; clocks sampled over this leg."""
+    import fsi_inputs as fi
+    case = fi.ellipse_case(N)
+    prob = fsi.problem_from_case(case, precision=1, precond=PRECOND, rtol=1e-8, stream=stream.cuda_stream,
+                                 max_it=MAX_IT, stokes_its=STOKES_ITS, **arm_settings(1))
+    prob64 = None
+    prob.assemble_step()
+    clocks = ClockSampler(device_index)
+    clocks.start()
+    out = {"N": N, "dofs": int(prob_dofs(case)), "workload": "ellipse sweep member, m = ceil(0.4 N)"}
+    for name, which in (("full_operator_f32", 0), ("velocity_chebyshev_f32", 2), ("full_operator_f64", 1)):
+        ms, by = prob.time_kernel(which, reps=30)
+        out[name] = {"us": ms * 1e3, "bytes": by, "gbs": by / ms / 1e6, "frac": by / ms / 1e6 / peak}
+    prob.close()
+    prob64 = fsi.problem_from_case(case, precision=0, precond=PRECOND, rtol=1e-8, stream=stream.cuda_stream,
+                                   max_it=MAX_IT, stokes_its=STOKES_ITS, **arm_settings(0))
+    prob64.assemble_step()
+    ms, by = prob64.time_kernel(3, reps=30)
+    out["velocity_chebyshev_f64"] = {"us": ms * 1e3, "bytes": by, "gbs": by / ms / 1e6, "frac": by / ms / 1e6 / peak}
+    prob64.close()
+    out["clocks"] = clocks.stop()
+    out["l2"] = "evicted before every launch (256 MiB write)"
+    return out
+
+
 # ------------------------------------------------------- CPU oracle timing
 CPU_SCRIPT = r"""
 import json, os, sys, time
@@ -357,6 +401,7 @@ import numpy as np
 import fsi_inputs as fi
 from oracle import fsi_oracle as fo
 steps = int(sys.argv[2]); budget = float(sys.argv[3])
+save = sys.argv[4] if len(sys.argv) > 4 else ""
 case = fi.cavity128_case()
 t0 = time.perf_counter()
 prob = fo.OracleProblem(case.N, case.rho_f, case.nu, case.kappa, case.dt, case.lid_u, case.ref_xy, case.tris)
@@ -368,17 +413,36 @@ for k in range(steps):
     t = time.perf_counter()
     u, p, X, lam = prob.step(u, X)
     times.append(time.perf_counter() - t)
+    if k == 0 and save:
+        np.savez(save, u=u, p=p, X=X, lam=lam)
     if time.perf_counter() - start > budget:
         break
 print(json.dumps({"setup_s": setup, "step_s": times}))
 """
 
 
-def start_cpu_baseline(args):
+def start_cpu_baseline(args, save_path=""):
+    """The oracle on the host cores in a child process, beside the GPU arms;
+    with save_path it also writes its first time step's solution there."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     env.pop("CUDA_VISIBLE_DEVICES", None)
-    return subprocess.Popen([sys.executable, "-c", CPU_SCRIPT, ROOT, str(args.cpu_steps), str(args.cpu_budget)],
+    return subprocess.Popen([sys.executable, "-c", CPU_SCRIPT, ROOT, str(args.cpu_steps), str(args.cpu_budget),
+                             save_path],
                             stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True, env=env)
+
+
+def field_errors(case, gpu_state, oracle_npz):
+    """Relative L2 error of each field of the first time step (u with its
+    wall values, p, the displacement X - X^0, lambda) against the oracle's
+    direct solve of the same step."""
+    o = np.load(oracle_npz)
+    u, p, X, lam = gpu_state
+
+    def rel(a, b):
+        return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300))
+
+    return {"u": rel(u, o["u"]), "p": rel(p, o["p"]), "X": rel(X - case.X0, o["X"] - case.X0),
+            "lam": rel(lam, o["lam"])}
 
 
 def finish_cpu_baseline(proc):
@@ -674,6 +738,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-large-n", action="store_true", help="skip the N = 1024 roofline leg")
+    ap.add_argument("--large-n", type=int, default=1024, help="grid of the large-N roofline leg")
     ap.add_argument("--cpu-steps", type=int, default=1)
     ap.add_argument("--cpu-budget", type=float, default=300.0)
     ap.add_argument("--profile-step", action="store_true",

@@ -308,6 +308,17 @@ def cavity128_case(seed: int = BASE_SEED + 1, N: int = 128, m: int = 36) -> FsiC
                    name=f"cavity{N}_lid_disk{len(tris)}")
 
 
+def lid_body_case(N: int = 16, m: int = 5, seed: int = BASE_SEED + 5) -> FsiCase:
+    """A disk (R = 0.07 at (0.43, 0.925), m rings) whose rule points fall in
+    the top row of cells, under a lid moving with velocity 1: the coupling
+    rows see the lid's nodal values.  nu = 0.1, kappa = 30, dt = 0.01,
+    u_0 = half-amplitude seeded field with the wall data."""
+    xy, tris = ring_disk_mesh(m, 0.07, (0.43, 0.925))
+    return FsiCase(N=N, rho_f=1.0, nu=0.1, kappa=30.0, dt=0.01, lid_u=1.0,
+                   ref_xy=xy, tris=tris, u0=initial_velocity(N, seed, lid_u=1.0, amplitude=0.5), X0=xy.copy(),
+                   precond=1, rtol=1e-12, steps=1, name=f"lid_body{N}")
+
+
 def ellipse_case(N: int, seed: int = BASE_SEED + 2) -> FsiCase:
     """Size sweep member: ellipse 0.2/0.1 rotated 30 degrees, m = ceil(0.4 N),
     kappa=1e2, nu=1, rho=1, dt=0.01, walls at rest, fluid at rest."""

@@ -61,7 +61,8 @@ extern "C" {
 #define FSI_ERR_NOT_CONVERGED  -5  /* max_it reached above rtol */
 #define FSI_ERR_BREAKDOWN      -6  /* Krylov breakdown (zero new direction) */
 #define FSI_ERR_NAN            -7  /* NaN/Inf in the residual */
-#define FSI_ERR_TIMEOUT        -8  /* a bounded device wait ran out */
+#define FSI_ERR_TIMEOUT        -8  /* reserved: no call of this version returns it (no
+                                      kernel of the library waits on a flag) */
 #define FSI_ERR_CAPACITY       -9  /* a coupling row exceeded its storage */
 #define FSI_ERR_CUDA          -10  /* a CUDA runtime call failed */
 
@@ -81,7 +82,8 @@ typedef struct fsi_params {
     int    precision;  /* 0 FP64 everywhere; 1 FP32 operators and preconditioner
                           inside FGMRES, FP64 Gram-Schmidt, least squares and
                           iterative refinement */
-    int    restart;    /* GMRES restart length, paper: 200 (Section 6); 0 = 200 */
+    int    restart;    /* GMRES restart length, paper: 200 (Section 6); 0 = 200;
+                          at most 250 (FSI_ERR_INVALID above) */
     double rtol;       /* relative residual target, paper: 1e-8 (Section 6); 0 = 1e-8 */
     int    max_it;     /* total Krylov iteration cap per step; 0 = 1000 */
     int    mg_degree;  /* Chebyshev degree of each multigrid smoothing; 0 = 2 */
@@ -90,7 +92,8 @@ typedef struct fsi_params {
     int    max_refine; /* precision 1: refinement steps cap; 0 = 30 */
     int    stokes_its; /* Richardson steps on the fluid (Stokes) block inside one
                           preconditioner application, each one V-cycle pair;
-                          0 = 1 (the one-shot approximation) */
+                          0 = 1 (the one-shot approximation); at most 16
+                          (FSI_ERR_INVALID above) */
     double stokes_omega; /* damping of the Richardson corrections after the first; 0 = 1 */
     int    mg_cluster; /* 0: the coarse multigrid levels whose operators fit in the
                           shared memory of one thread-block cluster run as one
@@ -289,14 +292,20 @@ const char* fsi_status_str(int status);
  *   cell_start  N*N + 1 outputs (CSR offsets), cell_points  6*n_tris outputs
  *   (point ids of each cell in increasing order; points outside are left out);
  *   n_outside  one int output: points found outside the domain.
- * Work is queued on cuda_stream (may be NULL) and the call returns without
+ * Work is queued on cuda_stream (may be NULL: the current device's legacy
+ * stream) on the device that stream belongs to, and the call returns without
  * waiting.  Returns FSI_ERR_INVALID, allocating and launching nothing, when a
  * pointer is NULL or N*N exceeds FSI_NOALLOC_MAX_CELLS (N <= 512).  The first
  * call on a device looks up the scratch array's device address and uploads the
- * rule table there (no allocation); make that first call before any stream
- * capture.  Every call shares the one scratch array and clears the part it
- * uses before using it; calls that overlap on the GPU race on it, so callers
- * must serialise them. */
+ * rule table there (no allocation, but a synchronous copy); make that first
+ * call before any stream capture: while it is still pending, a call on a
+ * capturing stream returns FSI_ERR_INVALID and leaves the capture untouched.
+ * An error left pending by an earlier CUDA call of the process is not
+ * cleared: the call returns FSI_ERR_CUDA without launching.  Every call shares
+ * the one scratch array and clears the part it uses before using it; calls
+ * that overlap on the GPU race on it, so callers must serialise them.  The
+ * per-cell lists are sorted by one thread per cell, in time quadratic in the
+ * points of a cell (about 50 when the solid mesh size is half the fluid's). */
 #define FSI_NOALLOC_MAX_CELLS 262144
 int fsi_locate_bin_noalloc(int N, int n_tris, const int* tris, const double* X,
                            int* cell, double* xi, double* eta,

@@ -18,6 +18,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <mutex>
 
 #include "../../include/fsi.h"
 #include "fsi_internal.h"
@@ -38,13 +39,22 @@ static __device__ __align__(256) NoAllocScratch g_scratch;
 
 __constant__ double c_na_lam[6][3];
 
-// Set-up once per device (first call on that device): the device address of
-// the scratch array and the quadrature table in constant memory.
+// Set-up once per device (first call on that device, with that device
+// current): the device address of the scratch array and the quadrature table
+// in constant memory.  Host threads that make their first calls at the same
+// time take turns on the mutex.
 constexpr int kMaxDevices = 64;
 NoAllocScratch* g_scratch_ptr[kMaxDevices] = {};
+std::mutex g_setup_mu;
+
+bool setup_done(int dev) {
+  std::lock_guard<std::mutex> lk(g_setup_mu);
+  return g_scratch_ptr[dev] != nullptr;
+}
 
 int device_setup(int dev, NoAllocScratch** out) {
   if (dev < 0 || dev >= kMaxDevices) return FSI_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(g_setup_mu);
   if (!g_scratch_ptr[dev]) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) return FSI_ERR_CUDA;
@@ -162,6 +172,8 @@ __global__ void k_na_scatter(int n_pts, const int* __restrict__ cell, int* __res
 }
 
 // the scatter order inside a cell is not fixed: sort each list by point id
+// (insertion sort, one thread per cell: quadratic in the points of one cell,
+// about 50 when the solid mesh size is half the fluid mesh size)
 __global__ void k_na_sort(int ncells, const int* __restrict__ cell_start, int* __restrict__ cell_points) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= ncells) return;
@@ -178,6 +190,9 @@ __global__ void k_na_outside(const NoAllocScratch* s, int* out) { *out = s->outs
 
 unsigned nb(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
+int run_locate_bin(int dev, int N, int n_tris, const int* tris, const double* X, int* cell, double* xi,
+                   double* eta, int* cell_start, int* cell_points, int* n_outside, cudaStream_t stream);
+
 }  // namespace
 
 extern "C" int fsi_locate_bin_noalloc(int N, int n_tris, const int* tris, const double* X, int* cell, double* xi,
@@ -188,12 +203,37 @@ extern "C" int fsi_locate_bin_noalloc(int N, int n_tris, const int* tris, const 
   const long long ncells = (long long)N * N;
   if (ncells > FSI_NOALLOC_MAX_CELLS) return FSI_ERR_INVALID;  // N*N above the compiled-in scratch
   if (6LL * n_tris > 0x7fffffffLL) return FSI_ERR_INVALID;
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return FSI_ERR_CUDA;
+  // an error left pending by an earlier, unrelated call stays for its owner
+  // to read: this call neither clears it nor claims it as its own
+  if (cudaPeekAtLastError() != cudaSuccess) return FSI_ERR_CUDA;
+  cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+  int cur = 0, dev = 0;
+  if (cudaGetDevice(&cur) != cudaSuccess) return FSI_ERR_CUDA;
+  dev = cur;
+  if (stream && cudaStreamGetDevice(stream, &dev) != cudaSuccess) return FSI_ERR_INVALID;
+  if (dev < 0 || dev >= kMaxDevices) return FSI_ERR_INVALID;
+  if (!setup_done(dev)) {
+    // the set-up copies synchronously, which would invalidate a capture in
+    // progress: refuse instead, leaving the capture untouched
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(stream, &cs) != cudaSuccess) return FSI_ERR_CUDA;
+    if (cs != cudaStreamCaptureStatusNone) return FSI_ERR_INVALID;
+  }
+  if (dev != cur && cudaSetDevice(dev) != cudaSuccess) return FSI_ERR_CUDA;
+  const int rc = run_locate_bin(dev, N, n_tris, tris, X, cell, xi, eta, cell_start, cell_points, n_outside, stream);
+  if (dev != cur && cudaSetDevice(cur) != cudaSuccess) return FSI_ERR_CUDA;
+  return rc;
+}
+
+namespace {
+
+// the work of one call on device `dev` (current)
+int run_locate_bin(int dev, int N, int n_tris, const int* tris, const double* X, int* cell, double* xi,
+                   double* eta, int* cell_start, int* cell_points, int* n_outside, cudaStream_t stream) {
+  const long long ncells = (long long)N * N;
   NoAllocScratch* s = nullptr;
   const int st = device_setup(dev, &s);
   if (st != FSI_OK) return st;
-  cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
   const int n_pts = 6 * n_tris;
   const int nc = (int)ncells;
   const unsigned nblocks = nb(nc, kNaBlock);
@@ -208,3 +248,5 @@ extern "C" int fsi_locate_bin_noalloc(int N, int n_tris, const int* tris, const 
   if (cudaGetLastError() != cudaSuccess) return FSI_ERR_CUDA;
   return FSI_OK;
 }
+
+}  // namespace

@@ -1163,6 +1163,9 @@ static void check_params(const fsi_params& p, int n_nodes, int n_tris) {
   if (p.solid_law != 0 && p.solid_law != 1) throw std::invalid_argument("solid_law");
   if (p.autotune != 0 && p.autotune != 1) throw std::invalid_argument("autotune");
   if (p.solid_law == 1 && !(p.gamma > 0 && p.eta > 0)) throw std::invalid_argument("gamma, eta");
+  // the Givens kernels hold one Hessenberg column in shared memory (256 doubles)
+  if (p.restart > 250) throw std::invalid_argument("restart must be <= 250");
+  if (p.stokes_its > 16) throw std::invalid_argument("stokes_its must be <= 16");
 }
 
 // Node ids per solid element and rule points per element (P1: the 6-point
@@ -1172,7 +1175,6 @@ static int elem_points(const fsi_params& p) { return p.solid_elem == 1 ? 9 : 6; 
 
 static fsi_params with_defaults(fsi_params p) {
   if (p.restart <= 0) p.restart = 200;
-  if (p.restart > 250) p.restart = 250;
   if (!(p.rtol > 0)) p.rtol = 1e-8;
   if (p.max_it <= 0) p.max_it = 1000;
   if (p.mg_degree <= 0) p.mg_degree = 2;
@@ -1182,7 +1184,6 @@ static fsi_params with_defaults(fsi_params p) {
   if (!(p.inner_rtol > 0)) p.inner_rtol = 1e-5;
   if (p.max_refine <= 0) p.max_refine = 30;
   if (p.stokes_its <= 0) p.stokes_its = 1;
-  if (p.stokes_its > 16) p.stokes_its = 16;
   if (!(p.stokes_omega > 0)) p.stokes_omega = 1.0;
   if (!(p.newton_tol > 0)) p.newton_tol = 1e-6;
   if (p.newton_max <= 0) p.newton_max = 20;

@@ -121,3 +121,43 @@ def test_body_at_rest_stays_at_rest(fsi):
     assert np.max(np.abs(u)) < 1e-9
     assert np.max(np.abs(X - xy)) < 1e-9
     g.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_iteration_cap_reports_not_converged(fsi, precision):
+    """max_it = 2 Krylov iterations cannot reach a 1e-12 residual: the step
+    ends with FSI_ERR_NOT_CONVERGED and reports the two iterations it took."""
+    case = fi.disk16_case()
+    g = fsi.problem_from_case(case, precision=precision, precond=1, rtol=1e-12, max_it=2)
+    g.assemble_step()
+    info = g.solve_step(check=False)
+    assert info.status == fsi.FSI_ERR_NOT_CONVERGED
+    assert info.iterations == 2 and info.rel_residual > 1e-12
+    g.close()
+
+
+@pytest.mark.parametrize("coupling", [0, 1])
+def test_row_over_capacity_reports_capacity(fsi, coupling):
+    """A coupling row holds the lattice nodes of the cells its triangles
+    overlap in the reference configuration.  A body stretched 2.2 times about
+    its centre (still inside the domain) makes the central node's row need
+    far more: both coupling rules end the step with FSI_ERR_CAPACITY."""
+    xy, tris = fi.ring_disk_mesh(2, 0.2, (0.5, 0.5))
+    g = fsi.Problem(fsi.make_params(16, 1.0, 1.0, 10.0, 0.01, precond=1, coupling=coupling), xy, tris,
+                    u0=fi.wall_velocity(16, 0.0), X0=xy)
+    g.set_state(None, 0.5 + 2.2 * (xy - 0.5))
+    g.assemble_step()
+    info = g.solve_step(check=False)
+    assert info.status == fsi.FSI_ERR_CAPACITY
+    g.close()
+
+
+def test_restart_and_stokes_steps_above_their_limits_are_refused(fsi):
+    """restart > 250 (one Hessenberg column lives in shared memory) and more
+    than 16 inner Stokes steps are refused at creation, not clamped."""
+    case = fi.disk16_case()
+    for kw in (dict(restart=251), dict(stokes_its=17)):
+        with pytest.raises(fsi.FsiError) as e:
+            fsi.problem_from_case(case, **kw)
+        assert e.value.code == fsi.FSI_ERR_INVALID
+    fsi.problem_from_case(case, restart=250, stokes_its=16).close()

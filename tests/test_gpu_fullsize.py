@@ -139,6 +139,52 @@ def test_ellipse_sweep_size(fsi, N):
     g.close()
 
 
+def _field_errors(g, case, ref):
+    u, p, X, lam = g.get_state()
+    uo, po, Xo, lamo = ref
+    return {"u": rel(u, uo), "p": rel(p, po), "X": rel(X - case.X0, Xo - case.X0), "lam": rel(lam, lamo)}
+
+
+@pytest.fixture(scope="module")
+def ellipse64_oracle_step():
+    case = fi.ellipse_case(64)
+    return case, _oracle(case).step(case.u0, case.X0)
+
+
+@pytest.mark.parametrize("mg_cluster", [0, -1])
+def test_ellipse64_fp64_step_matches_oracle(fsi, ellipse64_oracle_step, mg_cluster):
+    """One FP64 step of the N = 64 sweep member, solved to 1e-12 with the
+    bench's preconditioner (block upper-triangular, 8 Richardson steps of the
+    V-cycle pair), against the oracle's direct solve: every field within 1e-7
+    relative L2.  At N = 64 the finest velocity level and the finest pressure
+    level smooth with the per-level SpMV kernels; with mg_cluster = -1 every
+    coarser level does too (no cluster launch)."""
+    case, ref = ellipse64_oracle_step
+    g = fsi.problem_from_case(case, precision=0, precond=bench.PRECOND, rtol=1e-12, max_it=bench.MAX_IT,
+                              stokes_its=bench.STOKES_ITS, restart=bench.RESTART, mg_cluster=mg_cluster)
+    info = g.step()
+    assert info.status == 0 and info.rel_residual <= 1e-12
+    err = _field_errors(g, case, ref)
+    assert max(err.values()) < 1e-7, err
+    g.close()
+
+
+@pytest.mark.parametrize("mg_cluster", [0, -1])
+def test_ellipse64_mixed_step_error_per_field(fsi, ellipse64_oracle_step, mg_cluster):
+    """The mixed-precision arm (FP32 operators and multigrid inside FP64
+    refinement) in the bench's launch configuration, stopped at the time
+    step's 1e-8 residual: every field within 1e-5 relative L2 of the FP64
+    oracle."""
+    case, ref = ellipse64_oracle_step
+    g = fsi.problem_from_case(case, precision=1, precond=bench.PRECOND, rtol=RTOL, max_it=bench.MAX_IT,
+                              stokes_its=bench.STOKES_ITS, mg_cluster=mg_cluster, **bench.arm_settings(1))
+    info = g.step()
+    assert info.status == 0 and info.rel_residual <= RTOL
+    err = _field_errors(g, case, ref)
+    assert max(err.values()) < 1e-5, err
+    g.close()
+
+
 @pytest.mark.parametrize("label,precond,stokes_its", bench.SWEEP_VARIANTS)
 def test_ellipse64_every_sweep_preconditioner(fsi, label, precond, stokes_its):
     """Each preconditioner the sweep times reaches the tolerance in the

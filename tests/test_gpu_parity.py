@@ -42,7 +42,9 @@ def _deformed_case(N=24, m=9, seed=7):
                       u0=fi.initial_velocity(N, seed, lid_u=1.0), X0=X0, precond=1, rtol=1e-12)
 
 
-CASES = {"disk16": fi.disk16_case, "ragged24": _deformed_case}
+# lidbody16: rule points in the top row of cells under a moving lid, so the
+# wall columns of C_f enter the right-hand side (g2 = -(1/dt) C_s X^n - C_D u_D)
+CASES = {"disk16": fi.disk16_case, "ragged24": _deformed_case, "lidbody16": fi.lid_body_case}
 
 
 @pytest.mark.parametrize("name", list(CASES))

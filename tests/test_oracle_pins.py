@@ -344,6 +344,72 @@ def test_lid_driven_cavity_conserves_no_mass_through_walls():
     assert np.all(u[top, 0] == 1.0)
 
 
+def _q2_field_at(u_nodal, N, pts):
+    """The Q2 field with nodal values u_nodal [(2N+1)^2, 2] at points [n, 2]:
+    cell by truncation (no point here lies on a grid line), then the
+    tensor product of the three quadratic Lagrange polynomials on the local
+    nodes 0, 1/2, 1 written as products of their roots."""
+    n1 = 2 * N + 1
+    t = pts * N
+    c = np.minimum(np.floor(t).astype(np.int64), N - 1)
+    s = t - c
+
+    def lag(v):
+        return np.stack([2.0 * (v - 0.5) * (v - 1.0), -4.0 * v * (v - 1.0), 2.0 * v * (v - 0.5)], 1)
+
+    Lx, Ly = lag(s[:, 0]), lag(s[:, 1])
+    out = np.zeros((pts.shape[0], 2))
+    for b in range(3):
+        for a in range(3):
+            node = (2 * c[:, 1] + b) * n1 + (2 * c[:, 0] + a)
+            out += (Lx[:, a] * Ly[:, b])[:, None] * u_nodal[node]
+    return out
+
+
+def test_constraint_row_with_lid_data_on_the_body():
+    """The multiplier row of Eq. (matrix), with the Dirichlet data moved to
+    the right-hand side (g2 = -(1/dt) C_s X^n - C_D u_D), says that the whole
+    discrete velocity field, wall values included, matches the solid velocity
+    on the body: (chi_l, u^{n+1}(X^n))_B = (1/dt) (chi_l, X^{n+1} - X^n)_B
+    for every solid node l.  The left side is evaluated here without the
+    oracle's coupling matrix: the published degree-4 rule (golden table) on
+    each reference triangle, the body map by barycentric combination, and the
+    nodal field interpolated in its Q2 cell.  The body's rule points fill the
+    top row of cells under a moving lid, so the wall term C_D u_D is a large
+    part of the row; a wrong sign or wall index in it breaks the identity."""
+    c = fi.lid_body_case()
+    prob, u1, p, X1, lam = fo.run_steps(c, 1)
+    rows = np.loadtxt(os.path.join(HERE, "golden", "dunavant_deg4.txt"))
+    bary, wts = [], []
+    for w, l0, l1, l2 in rows:     # each orbit: the odd coordinate visits every vertex
+        for k in range(3):
+            bary.append(np.roll([l0, l1, l2], k))
+            wts.append(w)
+    bary, wts = np.array(bary), np.array(wts)
+    tris = c.tris.astype(np.int64)
+    P = c.X0[tris]                                     # [T, 3, 2] body at X^n
+    R = c.ref_xy[tris]
+    area = 0.5 * np.abs((R[:, 1, 0] - R[:, 0, 0]) * (R[:, 2, 1] - R[:, 0, 1])
+                        - (R[:, 2, 0] - R[:, 0, 0]) * (R[:, 1, 1] - R[:, 0, 1]))
+    pts = np.einsum("qk,tkd->tqd", bary, P).reshape(-1, 2)
+    top = pts[:, 1] >= (c.N - 1) / c.N
+    assert top.sum() > 0.2 * pts.shape[0]            # many rule points in the lid's row of cells
+    n_s = c.ref_xy.shape[0]
+
+    def rows_of(field):
+        v = _q2_field_at(field, c.N, pts).reshape(tris.shape[0], 6, 2)
+        out = np.zeros((n_s, 2))
+        for k in range(3):
+            np.add.at(out, tris[:, k], np.einsum("t,q,q,tqd->td", area, wts, bary[:, k], v))
+        return out
+
+    lhs = rows_of(u1)
+    rhs = (1.0 / c.dt) * (prob.Cs_scalar @ (X1 - c.X0))
+    lid_part = rows_of(fi.wall_velocity(c.N, c.lid_u))   # what the wall values contribute
+    assert np.linalg.norm(lid_part) > 0.1 * np.linalg.norm(lhs)
+    assert np.linalg.norm(lhs - rhs) < 1e-10 * np.linalg.norm(lhs)
+
+
 # ------------------------------------------- exact coupling (mesh intersection)
 
 def _duffy_rule(n: int):
