@@ -120,13 +120,14 @@ def _step_unchecked(prob):
 
 
 AUTOTUNE = 0     # 0: one fixed SpMV tile shape (faster inside a step); 1: the library's autotuner
+MG_FUSED = 0     # 0: fused matrix-free kernels on the finest FP32 multigrid levels; -1: per-level sparse kernels
 
 
 def arm_settings(precision):
-    """FGMRES restart, inner tolerance and tile-shape tuning of one arm."""
+    """FGMRES restart, inner tolerance, tile-shape tuning and multigrid kernels of one arm."""
     if precision == 1:
-        return dict(restart=RESTART_MIXED, inner_rtol=INNER_RTOL, autotune=AUTOTUNE)
-    return dict(restart=RESTART, autotune=AUTOTUNE)
+        return dict(restart=RESTART_MIXED, inner_rtol=INNER_RTOL, autotune=AUTOTUNE, mg_fused=MG_FUSED)
+    return dict(restart=RESTART, autotune=AUTOTUNE, mg_fused=MG_FUSED)
 
 
 def time_arm(fsi, torch, case, precision, steps, warmup, stream, flush, precond=PRECOND, stokes_its=STOKES_ITS,
@@ -525,12 +526,17 @@ def run_batch(args):
     ticks = []
     its = []
     failures = 0
-    for _ in range(args.steps):
+    failed = []   # (tick, instance, N, kappa, nu, status, iterations, refinements, rel_residual)
+    for k in range(args.steps):
         t = time.perf_counter()
         st, infos = fsi.step_batch(probs)
         ticks.append(time.perf_counter() - t)
         its.append(sum(i.iterations for i in infos))
         failures += sum(1 for i in infos if i.status != 0)
+        for j, i in enumerate(infos):
+            if i.status != 0 and len(failed) < 64:
+                c = cases[j]
+                failed.append([k, j, c.N, c.kappa, c.nu, i.status, i.iterations, i.refinements, i.rel_residual])
     for p in probs:
         p.close()
     total = sum(ticks)
@@ -539,6 +545,8 @@ def run_batch(args):
            "tick_ms": {"p50": float(np.percentile(ticks, 50)) * 1e3, "p99": float(np.percentile(ticks, 99)) * 1e3},
            "krylov_iterations_per_instance_step": float(np.sum(its)) / (n * args.steps),
            "create_s": t_create, "failed_instance_steps": failures,
+           "failed": {"columns": ["tick", "instance", "N", "kappa", "nu", "status", "iterations", "refinements",
+                                  "rel_residual"], "rows": failed},
            "dtype": "f32 operators + f64 refinement", "data": "synthetic",
            "config": {"workload": "256 cavity instances, N~U{16,32,48,64,96}, R~U[0.1,0.3], kappa log-U[1,1e4], "
                                   "nu log-U[1e-3,1], m=ceil(2RN), restart 60, block upper-triangular, 8 inner Stokes steps",
@@ -753,6 +761,8 @@ def main():
     ap.add_argument("--serve-max-resident", type=int, default=16)
     ap.add_argument("--serve-wall", type=float, default=60.0)
     ap.add_argument("--serve-stokes-its", type=int, default=8)
+    ap.add_argument("--no-mg-fused", action="store_true",
+                    help="per-level sparse kernels on every multigrid level instead of the fused matrix-free ones")
     ap.add_argument("--autotune", action="store_true",
                     help="per-level SpMV tile shapes chosen by the library's autotuner instead of one fixed shape")
     ap.add_argument("--coupling", choices=["point", "exact"], default="point",
@@ -771,9 +781,11 @@ def main():
     ap.add_argument("--sweep-steps", type=int, default=2)
     ap.add_argument("--sweep-max-it", type=int, default=SWEEP_MAX_IT)
     args = ap.parse_args()
-    global AUTOTUNE
+    global AUTOTUNE, MG_FUSED
     if args.autotune:
         AUTOTUNE = 1
+    if args.no_mg_fused:
+        MG_FUSED = -1
     if args.workload == "batch":
         return run_batch(args)
     if args.workload == "serve":

@@ -126,6 +126,12 @@ typedef struct fsi_params {
                           with A_s, C_s and the C_f point rule by the 3 x 3
                           Gauss rule on each element.  Q1 takes coupling 0 and
                           solid_law 0 only */
+    int    mg_fused;   /* 0: the finest multigrid levels of the FP32 hierarchy
+                          (down to the cluster-resident ones, at least 16 cells a
+                          side) run matrix-free, each V-cycle level as two fused
+                          launches (pre-smoothing + residual + restriction;
+                          prolongation + post-smoothing); -1: the per-level
+                          sparse kernels on every level */
 } fsi_params;
 
 /* Solid reference mesh (the body at t = 0): P1 triangles, or Q1

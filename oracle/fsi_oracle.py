@@ -764,7 +764,13 @@ class OracleProblem:
         (SuperLU).  Before it, rows and columns are scaled by positive
         diagonal matrices (this changes no solution, only the pivot sizes),
         and unknowns are ordered by a geometric nested dissection so that
-        the factors stay sparse.  Neither step is part of the method.
+        the factors stay sparse.  Neither step is part of the method.  One
+        step of iterative refinement with the same factors follows (residual
+        of the scaled bordered system in FP64, one more pair of triangular
+        solves): it removes the error of pivot growth, which on badly scaled
+        steps (a body at rest, whose large multiplier cancels against the
+        pressure) leaves the plain LU answer several orders of magnitude
+        above the rounding floor of the relative residual.
         """
         n_u, n_p, n_x = self.sizes()
         n = Kmat.shape[0]
@@ -793,7 +799,9 @@ class OracleProblem:
         perm = np.concatenate([nested_dissection(G, self.unknown_coordinates(X)), [n]])
         P = big[perm][:, perm].tocsc()
         b = np.concatenate([s * r * rhs, [0.0]])[perm]
-        yp = spla.splu(P, permc_spec="NATURAL", diag_pivot_thresh=0.01).solve(b)
+        lu = spla.splu(P, permc_spec="NATURAL", diag_pivot_thresh=0.01)
+        yp = lu.solve(b)
+        yp = yp + lu.solve(b - P @ yp)
         y = np.empty_like(yp)
         y[perm] = yp
         return cs * s * y[:n]

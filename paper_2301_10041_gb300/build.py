@@ -16,7 +16,8 @@ OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libfsi_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["fsi_solver.cu", "fsi_setup.cpp", "fsi_noalloc.cu"]
-HEADERS = ["fsi_internal.h", "fsi_kernels.cuh", "fsi_coupling.cuh", "fsi_cluster.cuh", "fsi_cluster_host.h", "fsi_solid.cuh"]
+HEADERS = ["fsi_internal.h", "fsi_kernels.cuh", "fsi_coupling.cuh", "fsi_cluster.cuh", "fsi_cluster_host.h", "fsi_solid.cuh",
+           "fsi_mgfused.cuh"]
 
 
 def nvcc() -> str:

@@ -41,6 +41,18 @@ struct FluidLevelHost {
                           // pressure residual R (b - L x) = R b - (R L) x in one pass
   std::vector<double> dinvA, dinvL;  // Jacobi inverses (per scalar dof)
   double lmaxA = 0, lmaxL = 0;       // lambda_max of D^-1 A and D^-1 L
+  // Matrix-free form of A and L on the uniform grid (levels with N >= 4).
+  // A: one 2x2 block per (node type, lattice offset) -- every interior row of
+  // a type has the same blocks, a wall neighbour's block is simply absent;
+  // type = (ix & 1) | (iy & 1) << 1 (corner, x-edge, y-edge, centre).
+  // L: one 3x3 block per (wall variant of the row cell, cell offset); the
+  // variant v = 3 vy + vx with vx = 0 (cx = 0), 1 (inside), 2 (cx = N-1).
+  // Both are the rows of the assembled matrices, bit for bit.
+  bool mf = false;
+  double stenA[4][5][5][4] = {};     // [type][dy+2][dx+2][2x2 row-major]
+  double dinvAt[4][2] = {};          // D^-1 per type and component
+  double stenL[9][3][3][9] = {};     // [variant][dy+1][dx+1][3x3 row-major]
+  double dinvLv[9][3] = {};          // D^-1 per variant and pressure dof
 };
 
 struct SetupParams {

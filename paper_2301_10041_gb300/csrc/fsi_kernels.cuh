@@ -101,12 +101,15 @@ struct SpmvArgs {
 constexpr int kSliceRows = 8;
 constexpr int kRowThreads = 4;
 
+#ifndef FSI_VEC2_DEFINED
+#define FSI_VEC2_DEFINED
 template <class T>
 struct Vec2;
 template <>
 struct Vec2<float> { using type = float2; };
 template <>
 struct Vec2<double> { using type = double2; };
+#endif
 
 template <class T, int NV>
 __device__ __forceinline__ void load_block(const T* __restrict__ p, T* v) {

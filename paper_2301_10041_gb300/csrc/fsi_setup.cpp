@@ -561,6 +561,46 @@ static void sym4_eig_range(double a[4][4], double& lo, double& hi) {
   }
 }
 
+// Matrix-free stencils of one level (cell size h), read from the rows of
+// proxy grids assembled by the same routines: an 8-cell grid for A (the rows
+// of the nodes at lattice (8 + ox, 8 + oy) have all their neighbours inside)
+// and a 4-cell grid for L (cells 0, 1 and 3 give the three variants per
+// axis).  The blocks are therefore the assembled values bit for bit.
+static void matrix_free_stencils(double h, double ma, double nu, FluidLevelHost& L) {
+  HostBlockMatrix A8, L4;
+  assemble_velocity(8, h, ma, nu, A8, nullptr, nullptr, nullptr);
+  VNum v8(8);
+  for (int tau = 0; tau < 4; ++tau) {
+    const int ix = 8 + (tau & 1), iy = 8 + (tau >> 1);
+    const int row = v8.id(ix, iy);
+    for (int k = A8.ptr[row]; k < A8.ptr[row + 1]; ++k) {
+      int jx, jy;
+      v8.lattice(A8.col[k], jx, jy);
+      const int dx = jx - ix, dy = jy - iy;
+      if (dx < -2 || dx > 2 || dy < -2 || dy > 2) throw std::logic_error("velocity stencil wider than 5x5");
+      for (int q = 0; q < 4; ++q) L.stenA[tau][dy + 2][dx + 2][q] = A8.val[4 * (size_t)k + q];
+      if (dx == 0 && dy == 0) {
+        L.dinvAt[tau][0] = 1.0 / A8.val[4 * (size_t)k];
+        L.dinvAt[tau][1] = 1.0 / A8.val[4 * (size_t)k + 3];
+      }
+    }
+  }
+  assemble_pressure_laplacian(4, h, L4);
+  const int rep[3] = {0, 1, 3};
+  for (int vy = 0; vy < 3; ++vy)
+    for (int vx = 0; vx < 3; ++vx) {
+      const int v = 3 * vy + vx, cx = rep[vx], cy = rep[vy], row = cy * 4 + cx;
+      for (int k = L4.ptr[row]; k < L4.ptr[row + 1]; ++k) {
+        const int c2 = L4.col[k], dx = c2 % 4 - cx, dy = c2 / 4 - cy;
+        if (dx < -1 || dx > 1 || dy < -1 || dy > 1) throw std::logic_error("pressure stencil wider than 3x3");
+        for (int q = 0; q < 9; ++q) L.stenL[v][dy + 1][dx + 1][q] = L4.val[9 * (size_t)k + q];
+        if (dx == 0 && dy == 0)
+          for (int i = 0; i < 3; ++i) L.dinvLv[v][i] = 1.0 / L4.val[9 * (size_t)k + 4 * i];
+      }
+    }
+  L.mf = true;
+}
+
 void build_setup(const SetupParams& sp, int n_s, int n_tri, const double* ref_xy, const int* tris,
                  HostSetup& out) {
   const int N = sp.N;
@@ -597,6 +637,7 @@ void build_setup(const SetupParams& sp, int n_s, int n_tri, const double* ref_xy
     assemble_pressure_laplacian(L.N, L.h, L.L);
     L.dinvA = block_diag_inverse_scalar(L.A);
     L.dinvL = block_diag_inverse_scalar(L.L);
+    if (L.N >= 4) matrix_free_stencils(L.h, ma, sp.nu, L);
     if (l + 1 < Ns.size()) {
       assemble_prolong_u(Ns[l + 1], L.Pu);
       L.Ru = transpose(L.Pu);

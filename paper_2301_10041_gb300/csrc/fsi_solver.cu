@@ -31,6 +31,7 @@
 #include "fsi_coupling.cuh"
 #include "fsi_internal.h"
 #include "fsi_kernels.cuh"
+#include "fsi_mgfused.cuh"
 #include "fsi_solid.cuh"
 
 namespace fsi {
@@ -302,7 +303,13 @@ struct MGLevel {
   T* dinv = nullptr;
   T *x = nullptr, *x2 = nullptr, *b = nullptr, *r = nullptr, *d = nullptr;
   int n = 0;        // scalar unknowns
+  int N = 0;        // cells per side
   Cheb ch;
+  // the level's stencils for the fused matrix-free kernels (fsi_mgfused.cuh),
+  // and whether the V-cycle runs them on this level
+  bool mf = false;
+  MfVelOp<T> mfu;        // velocity hierarchy
+  T* mftab = nullptr;    // pressure hierarchy: kMfPresTab values
 };
 
 // Coarse levels run as one thread-block-cluster launch per V-cycle
@@ -342,6 +349,7 @@ static void build_mg(Arena& ar, const HostSetup& hs, bool pressure, int degree, 
     L.A = upload_sell<T>(ar, sa);
     if (tune && !ar.count_only) autotune_sell<T>(L.A, sa.soff[sa.nslices]);
     L.n = A.nrows * A.BR;
+    L.N = H.N;
     L.dinv = upload_as<T>(ar, pressure ? H.dinvL : H.dinvA);
     if (l + 1 < nl) {
       L.P = upload_sell<T>(ar, to_sell(pressure ? H.Pp : H.Pu));
@@ -353,6 +361,24 @@ static void build_mg(Arena& ar, const HostSetup& hs, bool pressure, int degree, 
     L.d = ar.alloc<T>(L.n);
     const double hi = 1.05 * (pressure ? H.lmaxL : H.lmaxA);
     L.ch = cheb_coeffs(hi / (pressure ? kChebRatioP : kChebRatioU), hi, degree);
+    if (H.mf && !pressure) {
+      L.mfu.N = H.N;
+      for (int t = 0; t < 4; ++t) {
+        for (int y = 0; y < 5; ++y)
+          for (int x = 0; x < 5; ++x)
+            for (int q = 0; q < 4; ++q) L.mfu.c[t][y][x][q] = (T)H.stenA[t][y][x][q];
+        for (int c = 0; c < 2; ++c) L.mfu.dinv[t][c] = (T)H.dinvAt[t][c];
+      }
+    } else if (H.mf) {
+      std::vector<double> tab(kMfPresTab);
+      for (int v = 0; v < 9; ++v)
+        for (int y = 0; y < 3; ++y)
+          for (int x = 0; x < 3; ++x)
+            for (int q = 0; q < 9; ++q) tab[81 * v + 9 * (3 * y + x) + q] = H.stenL[v][y][x][q];
+      for (int v = 0; v < 9; ++v)
+        for (int k = 0; k < 3; ++k) tab[729 + 3 * v + k] = H.dinvLv[v][k];
+      L.mftab = upload_as<T>(ar, tab);
+    }
   }
   mg.coarse_n = pressure ? hs.coarse_nL : hs.coarse_nA;
   mg.coarse_inv = upload_as<T>(ar, pressure ? hs.coarseLinv : hs.coarseAinv);  // row-major
@@ -431,6 +457,106 @@ static void cluster_launch(MG<T>& mg, const T* in_b, T* out_x, cudaStream_t s) {
   if (e != cudaSuccess) throw CudaError(e, "cudaLaunchKernelEx (cluster V-cycle)");
 }
 
+// The finest levels, down to the first one that runs inside the cluster
+// launch (or is the coarsest, or is below 16 cells a side), take the fused
+// matrix-free kernels when the hierarchy is FP32 and the smoothing degree is
+// at most kMfMaxDeg.
+template <class T>
+static void select_mf(MG<T>& mg, const HostSetup& hs, int mg_fused, bool count_only) {
+  const int last = (int)mg.lv.size() - 1;
+  if (mg_fused == -1 || !std::is_same<T, float>::value || mg.degree > kMfMaxDeg) return;
+  bool any = false;
+  for (int l = 0; l < last; ++l) {
+    if (mg.cl.on && l >= mg.cl.lc) break;
+    if (!hs.levels[l].mf || hs.levels[l].N < 16) break;
+    mg.lv[l].mf = true;
+    any = true;
+  }
+  if (any && !count_only) {
+    static std::once_flag once;
+    std::call_once(once, [] {
+      CK(cudaFuncSetAttribute(k_mfu_down<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)mfu_down_smem<float>(kMfMaxDeg)));
+      CK(cudaFuncSetAttribute(k_mfu_up<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)mfu_up_smem<float>(kMfMaxDeg)));
+      CK(cudaFuncSetAttribute(k_mfp_down<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)mfp_down_smem<float>(kMfMaxDeg)));
+      CK(cudaFuncSetAttribute(k_mfp_up<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)mfp_up_smem<float>(kMfMaxDeg)));
+    });
+  }
+}
+
+template <class T>
+static MfCheb<T> mf_cheb(const MGLevel<T>& L, int degree) {
+  MfCheb<T> c;
+  c.k = degree;
+  c.c0 = (T)L.ch.c0;
+  for (int i = 0; i + 1 < degree; ++i) {
+    c.c1[i] = (T)L.ch.c1[i];
+    c.c2[i] = (T)L.ch.c2[i];
+  }
+  return c;
+}
+
+template <class T>
+static T* vcycle(MG<T>& mg, int l, cudaStream_t s, T* out, const SpmvArgs<T>* fin = nullptr, bool* fused = nullptr);
+
+// One V-cycle from fused level l (mg.lv[l].mf) with right-hand side b: the
+// down launch (pre-smoothing, residual, restriction), the coarser levels, the
+// up launch (prolongation, post-smoothing, epilogue).  The pre-smoothed
+// iterate lives in L.x2; the result goes to `out`, else to L.x (never L.x2).
+template <class T>
+static T* vcycle_mf(MG<T>& mg, int l, const T* b, cudaStream_t s, T* out, const MfFin<T>* fin) {
+  const int last = (int)mg.lv.size() - 1;
+  MGLevel<T>& L = mg.lv[l];
+  MGLevel<T>& C = mg.lv[l + 1];
+  const bool c_cluster = mg.cl.on && l + 1 == mg.cl.lc;
+  const bool c_sell = !C.mf && !c_cluster && l + 1 != last;
+  const int N = L.N;
+  MfInit<T> ci;
+  if (c_sell) { ci.x = C.x; ci.d = C.d; ci.dinv = C.dinv; ci.c0 = (T)C.ch.c0; }
+  T* dst = out ? out : L.x;
+  if (dst == L.x2) throw std::logic_error("vcycle_mf: the result may not overwrite the pre-smoothed iterate");
+  if (mg.pressure) {
+    MfPresArgs<T> a;
+    a.N = N; a.tab = L.mftab; a.ch = mf_cheb(L, mg.degree);
+    a.b = b; a.xout = L.x2; a.bc = C.b; a.ci = ci;
+    const unsigned g = nblk(N / 2, kMfTileP);
+    launch(k_mfp_down<T>, dim3(g, g), kMfThreads, mfp_down_smem<T>(mg.degree), s, a);
+  } else {
+    MfVelArgs<T> a;
+    a.op = L.mfu; a.ch = mf_cheb(L, mg.degree);
+    a.b = b; a.xout = L.x2; a.bc = C.b; a.ci = ci;
+    const unsigned g = nblk(N, kMfTileU);
+    launch(k_mfu_down<T>, dim3(g, g), kMfThreads, mfu_down_smem<T>(mg.degree), s, a);
+  }
+  T* xc = C.mf ? vcycle_mf<T>(mg, l + 1, C.b, s, nullptr, nullptr) : vcycle<T>(mg, l + 1, s, (T*)nullptr);
+  if (mg.pressure) {
+    MfPresArgs<T> a;
+    a.N = N; a.tab = L.mftab; a.ch = mf_cheb(L, mg.degree);
+    a.b = b; a.xpre = L.x2; a.xc = xc; a.xout = dst;
+    if (fin) a.fin = *fin;
+    const unsigned g = nblk(N, kMfTilePf);
+    launch(k_mfp_up<T>, dim3(g, g), kMfThreads, mfp_up_smem<T>(mg.degree), s, a);
+  } else {
+    MfVelArgs<T> a;
+    a.op = L.mfu; a.ch = mf_cheb(L, mg.degree);
+    a.b = b; a.xpre = L.x2; a.xc = xc; a.xout = dst;
+    if (fin) a.fin = *fin;
+    const unsigned g = nblk(2 * N, kMfTileUf);
+    launch(k_mfu_up<T>, dim3(g, g), kMfThreads, mfu_up_smem<T>(mg.degree), s, a);
+  }
+  return dst;
+}
+
+template <class T>
+static MfFin<T> mf_fin(const SpmvArgs<T>& f) {
+  MfFin<T> m;
+  m.sv = f.sv; m.smp = f.smp; m.sout = f.sout; m.snu = f.snu; m.srdt = f.srdt; m.acc = f.acc; m.omega = f.omega;
+  return m;
+}
+
 // Level l input: L.b, with L.x = L.d = c0 dinv b already set (l < last).
 // Result of the level is written to `out` (if given) or returned.  Levels
 // from mg.cl.lc down run as one cluster launch when mg.cl.on.
@@ -438,10 +564,16 @@ static void cluster_launch(MG<T>& mg, const T* in_b, T* out_x, cudaStream_t s) {
 // omega) to the last smoothing step of level l; *fused tells whether it was
 // applied (not when level l is solved by the cluster launch or densely).
 template <class T>
-static T* vcycle(MG<T>& mg, int l, cudaStream_t s, T* out, const SpmvArgs<T>* fin = nullptr, bool* fused = nullptr) {
+static T* vcycle(MG<T>& mg, int l, cudaStream_t s, T* out, const SpmvArgs<T>* fin, bool* fused) {
   const int last = (int)mg.lv.size() - 1;
   MGLevel<T>& L = mg.lv[l];
   if (fused) *fused = false;
+  if (L.mf) {  // fused levels need only L.b
+    MfFin<T> mfin;
+    if (fin) mfin = mf_fin(*fin);
+    if (fused) *fused = fin != nullptr;
+    return vcycle_mf<T>(mg, l, L.b, s, out, fin ? &mfin : nullptr);
+  }
   if (mg.cl.on && l == mg.cl.lc) {
     T* dst = out ? out : L.x;
     cluster_launch<T>(mg, L.b, dst, s);
@@ -653,12 +785,17 @@ static void stokes_pressure(Problem& P, Prec<T>& pr, const T* in_p, T* out_p, cu
                             T* acc = nullptr, T omega = 1) {
   const int n3 = 3 * P.nP;
   MGLevel<T>& L0p = pr.mgP.lv[0];
-  if (!started)
-    launch(k_cheb_first<T>, nblk(n3, 256), 256, 0, s, n3, in_p, L0p.dinv, (T)L0p.ch.c0, L0p.d, L0p.x, (T)1, L0p.b);
   SpmvArgs<T> fin;
   fin.sv = in_p; fin.smp = pr.mpinv; fin.sout = out_p;
   fin.snu = (T)P.prm.nu; fin.srdt = (T)(P.prm.rho_f / P.prm.dt);
   fin.acc = acc; fin.omega = omega;
+  if (L0p.mf) {  // the fused finest level reads in_p itself and applies the epilogue
+    const MfFin<T> mfin = mf_fin(fin);
+    vcycle_mf<T>(pr.mgP, 0, in_p, s, nullptr, &mfin);
+    return;
+  }
+  if (!started)
+    launch(k_cheb_first<T>, nblk(n3, 256), 256, 0, s, n3, in_p, L0p.dinv, (T)L0p.ch.c0, L0p.d, L0p.x, (T)1, L0p.b);
   bool fused = false;
   T* sp = vcycle<T>(pr.mgP, 0, s, (T*)nullptr, &fin, &fused);
   if (!fused) {
@@ -676,6 +813,17 @@ template <class T>
 static void stokes_velocity(Problem& P, Prec<T>& pr, const T* in_u, const T* p, T* out_u, cudaStream_t s,
                             T* acc = nullptr, T omega = 1) {
   MGLevel<T>& L0u = pr.mgU.lv[0];
+  if (L0u.mf) {  // the fused finest level starts its smoother itself
+    const T* b = in_u;
+    if (p) {
+      sell_launch(pr.op.Bt, MODE_AXPBY, axpby<T>(p, L0u.b, in_u, (T)-1, (T)1), s);
+      b = L0u.b;
+    }
+    MfFin<T> mfin;
+    mfin.acc = acc; mfin.omega = omega;
+    vcycle_mf<T>(pr.mgU, 0, b, s, out_u, acc ? &mfin : nullptr);
+    return;
+  }
   if (p) {
     SpmvArgs<T> a;
     a.x = p; a.y = L0u.b; a.z = in_u; a.alpha = -1; a.beta = 1;
@@ -768,8 +916,12 @@ static void precond_launch(Problem& P, Prec<T>& pr, cudaStream_t s) {
     } else {
       // residual (starting the pressure smoother), then the pressure and
       // velocity corrections, each added to z by its own last kernel
-      launch(k_stokes_res<T>, pr.op.gU + pr.op.gP, 128, 0, s, pr.op, pr.zw, vu, vp, pr.t, (const T*)L0p.dinv,
-             (T)L0p.ch.c0, L0p.b, L0p.d, L0p.x);
+      if (L0p.mf)
+        launch(k_stokes_res<T>, pr.op.gU + pr.op.gP, 128, 0, s, pr.op, pr.zw, vu, vp, pr.t, (const T*)nullptr, (T)0,
+               (T*)nullptr, (T*)nullptr, (T*)nullptr);
+      else
+        launch(k_stokes_res<T>, pr.op.gU + pr.op.gP, 128, 0, s, pr.op, pr.zw, vu, vp, pr.t, (const T*)L0p.dinv,
+               (T)L0p.ch.c0, L0p.b, L0p.d, L0p.x);
       stokes_pressure(P, pr, pr.t + P.offP, pr.dz + P.offP, s, true, pr.zw + P.offP, pr.stokes_omega);
       stokes_velocity(P, pr, pr.t, (const T*)(pr.dz + P.offP), pr.dz, s, pr.zw, pr.stokes_omega);
     }
@@ -1159,6 +1311,7 @@ static void check_params(const fsi_params& p, int n_nodes, int n_tris) {
   if (p.solid_elem == 1 && (p.coupling != 0 || p.solid_law != 0))
     throw std::invalid_argument("the Q1 solid takes the point rule and the linear law");
   if (p.mg_cluster != 0 && p.mg_cluster != -1) throw std::invalid_argument("mg_cluster");
+  if (p.mg_fused != 0 && p.mg_fused != -1) throw std::invalid_argument("mg_fused");
   if (p.coupling != 0 && p.coupling != 1) throw std::invalid_argument("coupling");
   if (p.solid_law != 0 && p.solid_law != 1) throw std::invalid_argument("solid_law");
   if (p.autotune != 0 && p.autotune != 1) throw std::invalid_argument("autotune");
@@ -1200,6 +1353,8 @@ static void build_prec(Problem& P, Prec<T>& pr, const FullOp<T>& op, bool alloc_
     setup_cluster<T>(ar, P.hs, pr.mgU, false);
     setup_cluster<T>(ar, P.hs, pr.mgP, true);
   }
+  select_mf<T>(pr.mgU, P.hs, P.prm.mg_fused, ar.count_only);
+  select_mf<T>(pr.mgP, P.hs, P.prm.mg_fused, ar.count_only);
   pr.op = op;
   pr.Cs = upload_sell<T>(ar, to_sell(P.hs.Cs));
   pr.As = upload_sell<T>(ar, to_sell(P.hs.As));
@@ -2223,7 +2378,7 @@ int fsi_time_kernel(fsi_problem* h, int which, int reps, double* avg_ms, double*
         case 4:    // one V-cycle on the Q2 velocity hierarchy, FP32
         case 5: {  // one V-cycle on the pressure Laplacian hierarchy, FP32
           MG<float>& mg = (which == 4) ? P.p32.mgU : P.p32.mgP;
-          vcycle<float>(mg, 0, s, mg.lv[0].x2);
+          vcycle<float>(mg, 0, s, mg.lv[0].mf ? mg.lv[0].x : mg.lv[0].x2);
           *bytes = 0;
           break;
         }

@@ -5,6 +5,9 @@
 //     for every pressure level with a fused restriction, the product R L
 //     applied to a random vector against R applied to L x (one line per
 //     level: {"level": l, "rel_err": e});
+//   setup_harness stencils N
+//     every row of the assembled level operators against their matrix-free
+//     stencils (one line per level);
 //   setup_harness solid <mesh file> <kappa>
 //     build the solid operators of a Q1 mesh (file: n_nodes n_el, then x y
 //     per node, then 4 node ids per element) and print C_s and A_s as
@@ -94,7 +97,72 @@ static int solid(const char* path, double kappa) {
   return 0;
 }
 
+// Every row of the assembled A and L of every level against the matrix-free
+// stencils of that level: same blocks bit for bit, and no stored block the
+// stencil lacks.  One line per level: {"level", "N", "a_mismatch",
+// "l_mismatch", "a_rows", "l_rows"}.
+static int stencils(int N) {
+  const double xy[6] = {0.4, 0.4, 0.6, 0.4, 0.5, 0.6};
+  const int tris[3] = {0, 1, 2};
+  SetupParams sp{N, 1.3, 0.07, 10.0, 0.004, 1.0};
+  HostSetup hs;
+  build_setup(sp, 3, 1, xy, tris, hs);
+  for (size_t l = 0; l < hs.levels.size(); ++l) {
+    const FluidLevelHost& L = hs.levels[l];
+    if (!L.mf) continue;
+    VNum vn(L.N);
+    long a_bad = 0, l_bad = 0;
+    for (int r = 0; r < L.A.nrows; ++r) {
+      int ix, iy;
+      vn.lattice(r, ix, iy);
+      const int tau = (ix & 1) | ((iy & 1) << 1);
+      int expect = 0;  // stencil blocks whose neighbour is interior
+      for (int dy = -2; dy <= 2; ++dy)
+        for (int dx = -2; dx <= 2; ++dx) {
+          const double* c = L.stenA[tau][dy + 2][dx + 2];
+          if ((c[0] != 0 || c[1] != 0 || c[2] != 0 || c[3] != 0) && vn.id(ix + dx, iy + dy) >= 0) ++expect;
+        }
+      if (L.A.ptr[r + 1] - L.A.ptr[r] != expect) ++a_bad;
+      for (int j = L.A.ptr[r]; j < L.A.ptr[r + 1]; ++j) {
+        int jx, jy;
+        vn.lattice(L.A.col[j], jx, jy);
+        const int dx = jx - ix, dy = jy - iy;
+        bool ok = dx >= -2 && dx <= 2 && dy >= -2 && dy <= 2;
+        for (int q = 0; ok && q < 4; ++q) ok = L.A.val[4 * (size_t)j + q] == L.stenA[tau][dy + 2][dx + 2][q];
+        if (!ok) ++a_bad;
+      }
+      for (int i = 0; i < 2; ++i)
+        if (L.dinvA[2 * (size_t)r + i] != L.dinvAt[tau][i]) ++a_bad;
+    }
+    for (int r = 0; r < L.L.nrows; ++r) {
+      const int cx = r % L.N, cy = r / L.N;
+      const int vx = cx == 0 ? 0 : (cx == L.N - 1 ? 2 : 1), vy = cy == 0 ? 0 : (cy == L.N - 1 ? 2 : 1);
+      const int v = 3 * vy + vx;
+      int expect = 0;
+      for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+          bool nz = false;
+          for (int q = 0; q < 9; ++q) nz = nz || L.stenL[v][dy + 1][dx + 1][q] != 0;
+          if (nz && cx + dx >= 0 && cx + dx < L.N && cy + dy >= 0 && cy + dy < L.N) ++expect;
+        }
+      if (L.L.ptr[r + 1] - L.L.ptr[r] != expect) ++l_bad;
+      for (int j = L.L.ptr[r]; j < L.L.ptr[r + 1]; ++j) {
+        const int c2 = L.L.col[j], dx = c2 % L.N - cx, dy = c2 / L.N - cy;
+        bool ok = dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1;
+        for (int q = 0; ok && q < 9; ++q) ok = L.L.val[9 * (size_t)j + q] == L.stenL[v][dy + 1][dx + 1][q];
+        if (!ok) ++l_bad;
+      }
+      for (int i = 0; i < 3; ++i)
+        if (L.dinvL[3 * (size_t)r + i] != L.dinvLv[v][i]) ++l_bad;
+    }
+    std::printf("{\"level\": %zu, \"N\": %d, \"a_mismatch\": %ld, \"l_mismatch\": %ld, \"a_rows\": %d, "
+                "\"l_rows\": %d}\n", l, L.N, a_bad, l_bad, L.A.nrows, L.L.nrows);
+  }
+  return 0;
+}
+
 int main(int argc, char** argv) {
+  if (argc >= 3 && std::string(argv[1]) == "stencils") return stencils(std::atoi(argv[2]));
   if (argc >= 3 && std::string(argv[1]) == "products") return products(std::atoi(argv[2]));
   if (argc >= 4 && std::string(argv[1]) == "solid") return solid(argv[2], std::atof(argv[3]));
   std::fprintf(stderr, "usage: setup_harness products N | solid mesh kappa\n");

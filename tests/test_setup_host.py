@@ -2,6 +2,7 @@
 `tests/setup_harness.cpp`:
 
 * the fused pressure restriction: (R L) x equals R (L x) on every level;
+* the matrix-free stencils of every level reproduce the assembled rows;
 * the Q1 solid operators (Section 6's element): C_s and A_s equal the
   oracle's independent 3 x 3 Gauss assembly, and the Chebyshev interval for
   D^-1 C_s (Wathen's element bound) contains the whole spectrum; on a
@@ -43,6 +44,19 @@ def test_fused_pressure_restriction_product(harness, N):
     assert len(rows) >= 1
     for r in rows:
         assert r["rel_err"] < 1e-14, r
+
+
+@pytest.mark.parametrize("N", [8, 24, 64, 128])
+def test_matrix_free_stencils_are_the_assembled_rows(harness, N):
+    """The constant-coefficient stencils used by the matrix-free multigrid
+    kernels reproduce every row of the assembled velocity operator and
+    pressure Laplacian of every level bit for bit (walls only remove
+    neighbours of A; L has one stencil per wall variant)."""
+    out = subprocess.run([harness, "stencils", str(N)], capture_output=True, text=True, check=True).stdout
+    rows = [json.loads(l) for l in out.splitlines() if l.strip()]
+    assert len(rows) >= 1
+    for r in rows:
+        assert r["a_mismatch"] == 0 and r["l_mismatch"] == 0, r
 
 
 def _solid(harness, tmp_path, xy, quads, kappa):
