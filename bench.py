@@ -121,13 +121,19 @@ def _step_unchecked(prob):
 
 AUTOTUNE = 0     # 0: one fixed SpMV tile shape (faster inside a step); 1: the library's autotuner
 MG_FUSED = 0     # 0: fused matrix-free kernels on the finest FP32 multigrid levels; -1: per-level sparse kernels
+MG_CLUSTER = 0   # 0: coarse levels in one cluster launch; -1: per-level launches; n > 0: cluster levels <= n cells
 
 
 def arm_settings(precision):
-    """FGMRES restart, inner tolerance, tile-shape tuning and multigrid kernels of one arm."""
+    """FGMRES restart, inner tolerance and tile-shape tuning of one arm."""
     if precision == 1:
-        return dict(restart=RESTART_MIXED, inner_rtol=INNER_RTOL, autotune=AUTOTUNE, mg_fused=MG_FUSED)
-    return dict(restart=RESTART, autotune=AUTOTUNE, mg_fused=MG_FUSED)
+        return dict(restart=RESTART_MIXED, inner_rtol=INNER_RTOL, autotune=AUTOTUNE)
+    return dict(restart=RESTART, autotune=AUTOTUNE)
+
+
+def mg_settings():
+    """Multigrid kernel choice of the bench's arms (command-line switches)."""
+    return dict(mg_fused=MG_FUSED, mg_cluster=MG_CLUSTER)
 
 
 def time_arm(fsi, torch, case, precision, steps, warmup, stream, flush, precond=PRECOND, stokes_its=STOKES_ITS,
@@ -135,7 +141,8 @@ def time_arm(fsi, torch, case, precision, steps, warmup, stream, flush, precond=
     """Time `steps` time steps after `warmup` untimed ones; with a list
     `first_state`, the state after the first (untimed) step is appended to it."""
     prob = fsi.problem_from_case(case, precision=precision, precond=precond, rtol=1e-8, stream=stream.cuda_stream,
-                                 max_it=max_it, stokes_its=stokes_its, **(settings or arm_settings(precision)))
+                                 max_it=max_it, stokes_its=stokes_its, **(settings or arm_settings(precision)),
+                                 **mg_settings())
     step = prob.step if check else (lambda: _step_unchecked(prob))
     infos = []
     for k in range(warmup):
@@ -173,7 +180,7 @@ def time_e2e(fsi, case, precision, steps, warmup, stream):
     (D2H), over the same time steps as the device-timed arm (after the same
     warm-up steps: the first steps of the trajectory need more iterations)."""
     prob = fsi.problem_from_case(case, precision=precision, precond=PRECOND, rtol=1e-8, stream=stream.cuda_stream,
-                                 max_it=MAX_IT, stokes_its=STOKES_ITS, **arm_settings(precision))
+                                 max_it=MAX_IT, stokes_its=STOKES_ITS, **arm_settings(precision), **mg_settings())
     for _ in range(warmup):
         prob.step()
     u, p, X, lam = prob.get_state()
@@ -498,7 +505,7 @@ def run_profile_step(args):
     build.build()
     case = workload()
     prob = fsi.problem_from_case(case, precision=1, precond=PRECOND, rtol=1e-8, max_it=MAX_IT, stokes_its=STOKES_ITS,
-                                 coupling=1 if args.coupling == "exact" else 0, **arm_settings(1))
+                                 coupling=1 if args.coupling == "exact" else 0, **arm_settings(1), **mg_settings())
     for _ in range(args.warmup):
         prob.step()
     info = prob.step()
@@ -763,6 +770,9 @@ def main():
     ap.add_argument("--serve-stokes-its", type=int, default=8)
     ap.add_argument("--no-mg-fused", action="store_true",
                     help="per-level sparse kernels on every multigrid level instead of the fused matrix-free ones")
+    ap.add_argument("--mg-cluster", type=int, default=0,
+                    help="0: coarse levels in one cluster launch; -1: per-level launches; n > 0: only levels of at "
+                         "most n cells a side in the cluster")
     ap.add_argument("--autotune", action="store_true",
                     help="per-level SpMV tile shapes chosen by the library's autotuner instead of one fixed shape")
     ap.add_argument("--coupling", choices=["point", "exact"], default="point",
@@ -781,7 +791,8 @@ def main():
     ap.add_argument("--sweep-steps", type=int, default=2)
     ap.add_argument("--sweep-max-it", type=int, default=SWEEP_MAX_IT)
     args = ap.parse_args()
-    global AUTOTUNE, MG_FUSED
+    global AUTOTUNE, MG_FUSED, MG_CLUSTER
+    MG_CLUSTER = args.mg_cluster
     if args.autotune:
         AUTOTUNE = 1
     if args.no_mg_fused:

@@ -98,7 +98,8 @@ typedef struct fsi_params {
     int    mg_cluster; /* 0: the coarse multigrid levels whose operators fit in the
                           shared memory of one thread-block cluster run as one
                           cluster launch per V-cycle (same arithmetic); -1: one
-                          kernel launch per phase on every level */
+                          kernel launch per phase on every level; n > 0: as 0,
+                          with levels of at most n cells a side in the cluster */
     int    coupling;   /* C_f(X^n) quadrature: 0 = the degree-4 6-point rule at
                           points located in the fluid grid; 1 = exact, by
                           intersecting each mapped solid triangle with the

@@ -98,11 +98,12 @@ inline ClMat cl_add_matrix(ClImages& im, const SellHost& S, int col_nsl, int cs)
 // qualifies.  On success mg.cl holds the launch arguments (without in_b and
 // out_x) and the images are uploaded through the arena.
 template <class T, class ArenaT, class MGT, class Viable>
-bool build_cluster(ArenaT& ar, const HostSetup& hs, bool pressure, MGT& mg, int cs, size_t cap, Viable viable) {
+bool build_cluster(ArenaT& ar, const HostSetup& hs, bool pressure, MGT& mg, int cs, size_t cap, Viable viable,
+                   int lc_min = 0) {
   const int last = (int)mg.lv.size() - 1;
   const int B = pressure ? 3 : 2;
   if (last < 1 || mg.degree > kClMaxDeg) return false;
-  for (int lc = std::max(0, last + 1 - kClMaxLevels); lc < last; ++lc) {
+  for (int lc = std::max(lc_min, last + 1 - kClMaxLevels); lc < last; ++lc) {
     ClImages im(cs);
     ClArgs<T> a;
     a.nlev = last - lc + 1;

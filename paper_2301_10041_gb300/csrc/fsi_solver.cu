@@ -420,7 +420,10 @@ static int cluster_fits(size_t smem, int csize) {
 // Cluster of 16 CTAs (non-portable size) when the device schedules one,
 // else 8; nothing when neither fits (the per-level kernels run instead).
 template <class T>
-static void setup_cluster(Arena& ar, const HostSetup& hs, MG<T>& mg, bool pressure) {
+static void setup_cluster(Arena& ar, const HostSetup& hs, MG<T>& mg, bool pressure, int max_n) {
+  int lc_min = 0;   // with max_n > 0 the cluster's finest level has at most max_n cells a side
+  if (max_n > 0)
+    while (lc_min + 1 < (int)hs.levels.size() && hs.levels[lc_min].N > max_n) ++lc_min;
   for (int cs : {16, 8}) {
     auto viable = [&](size_t smem) {
       if (ar.count_only) return true;
@@ -431,7 +434,7 @@ static void setup_cluster(Arena& ar, const HostSetup& hs, MG<T>& mg, bool pressu
       cluster_kernel_setup<T, 2, true>();
       return cluster_fits<T, 2, true>(smem, cs) > 0;
     };
-    if (build_cluster<T>(ar, hs, pressure, mg, cs, kClSmemCap, viable)) return;
+    if (build_cluster<T>(ar, hs, pressure, mg, cs, kClSmemCap, viable, lc_min)) return;
   }
 }
 
@@ -1310,7 +1313,7 @@ static void check_params(const fsi_params& p, int n_nodes, int n_tris) {
   if (n_nodes < (p.solid_elem == 1 ? 4 : 3) || n_tris < 1) throw std::invalid_argument("solid mesh");
   if (p.solid_elem == 1 && (p.coupling != 0 || p.solid_law != 0))
     throw std::invalid_argument("the Q1 solid takes the point rule and the linear law");
-  if (p.mg_cluster != 0 && p.mg_cluster != -1) throw std::invalid_argument("mg_cluster");
+  if (p.mg_cluster < -1) throw std::invalid_argument("mg_cluster");
   if (p.mg_fused != 0 && p.mg_fused != -1) throw std::invalid_argument("mg_fused");
   if (p.coupling != 0 && p.coupling != 1) throw std::invalid_argument("coupling");
   if (p.solid_law != 0 && p.solid_law != 1) throw std::invalid_argument("solid_law");
@@ -1349,9 +1352,9 @@ static void build_prec(Problem& P, Prec<T>& pr, const FullOp<T>& op, bool alloc_
   Arena& ar = P.ar;
   build_mg<T>(ar, P.hs, false, P.prm.mg_degree, pr.mgU, P.prm.autotune == 1);
   build_mg<T>(ar, P.hs, true, P.prm.mg_degree, pr.mgP, P.prm.autotune == 1);
-  if (P.prm.mg_cluster == 0) {
-    setup_cluster<T>(ar, P.hs, pr.mgU, false);
-    setup_cluster<T>(ar, P.hs, pr.mgP, true);
+  if (P.prm.mg_cluster >= 0) {
+    setup_cluster<T>(ar, P.hs, pr.mgU, false, P.prm.mg_cluster);
+    setup_cluster<T>(ar, P.hs, pr.mgP, true, P.prm.mg_cluster);
   }
   select_mf<T>(pr.mgU, P.hs, P.prm.mg_fused, ar.count_only);
   select_mf<T>(pr.mgP, P.hs, P.prm.mg_fused, ar.count_only);
