@@ -514,18 +514,12 @@ def run_profile_step(args):
     prob.close()
 
 
-def run_batch(args):
-    """Batched uneven instances (256 cavity instances of uneven size): fsi_step_batch over the
-    whole set each tick, every instance on its own stream."""
-    import torch
-    import fsi_inputs as fi
-    from paper_2301_10041_gb300 import build, fsi
-    build.build()
-    n = args.batch_instances
-    cases = [fi.batch_instance(i) for i in range(n)]
+def batch_arm(fsi, torch, cases, precision, args):
+    """One arm of the batched workload: every instance created, then
+    ``--warmup`` untimed and ``--steps`` timed ticks of fsi_step_batch."""
     t0 = time.perf_counter()
-    probs = [fsi.problem_from_case(c, precision=1, precond=PRECOND, restart=60, max_it=6000,
-                                   stokes_its=STOKES_ITS) for c in cases]
+    probs = [fsi.problem_from_case(c, precision=precision, precond=PRECOND, restart=BATCH_RESTART, max_it=6000,
+                                   stokes_its=args.batch_stokes_its, **mg_settings()) for c in cases]
     t_create = time.perf_counter() - t0
     for _ in range(args.warmup):
         fsi.step_batch(probs)
@@ -546,18 +540,40 @@ def run_batch(args):
                 failed.append([k, j, c.N, c.kappa, c.nu, i.status, i.iterations, i.refinements, i.rel_residual])
     for p in probs:
         p.close()
-    total = sum(ticks)
-    out = {"metric": METRIC, "workload": "batch", "value": n * args.steps / total, "unit": "time-steps/s",
-           "instances": n, "steps": args.steps, "warmup": args.warmup,
-           "tick_ms": {"p50": float(np.percentile(ticks, 50)) * 1e3, "p99": float(np.percentile(ticks, 99)) * 1e3},
-           "krylov_iterations_per_instance_step": float(np.sum(its)) / (n * args.steps),
-           "create_s": t_create, "failed_instance_steps": failures,
-           "failed": {"columns": ["tick", "instance", "N", "kappa", "nu", "status", "iterations", "refinements",
-                                  "rel_residual"], "rows": failed},
-           "dtype": "f32 operators + f64 refinement", "data": "synthetic",
+    n = len(cases)
+    return {"value": n * args.steps / sum(ticks), "unit": "time-steps/s",
+            "tick_ms": {"p50": float(np.percentile(ticks, 50)) * 1e3, "p99": float(np.percentile(ticks, 99)) * 1e3},
+            "krylov_iterations_per_instance_step": float(np.sum(its)) / (n * args.steps),
+            "create_s": t_create, "failed_instance_steps": failures,
+            "failed": {"columns": ["tick", "instance", "N", "kappa", "nu", "status", "iterations", "refinements",
+                                   "rel_residual"], "rows": failed}}
+
+
+BATCH_RESTART = 60
+
+
+def run_batch(args):
+    """Batched uneven instances (256 cavity instances of uneven size): fsi_step_batch over the
+    whole set each tick, every instance on its own stream; the mixed-precision arm and the
+    plain FP64 arm, both to the 1e-8 residual."""
+    import torch
+    import fsi_inputs as fi
+    from paper_2301_10041_gb300 import build, fsi
+    build.build()
+    n = args.batch_instances
+    cases = [fi.batch_instance(i) for i in range(n)]
+    arms = {}
+    for name in args.arms.split(","):
+        arms[name] = batch_arm(fsi, torch, cases, 1 if name == "mixed" else 0, args)
+        print(json.dumps({"batch_arm": name, **arms[name]}), file=sys.stderr, flush=True)
+    head = arms.get("mixed") or next(iter(arms.values()))
+    out = {"metric": METRIC, "workload": "batch", "value": head["value"], "unit": "time-steps/s",
+           "instances": n, "steps": args.steps, "warmup": args.warmup, "arms": arms,
+           "dtype": "f32 operators + f64 refinement (mixed arm); f64 (fp64 arm)", "data": "synthetic",
            "config": {"workload": "256 cavity instances, N~U{16,32,48,64,96}, R~U[0.1,0.3], kappa log-U[1,1e4], "
-                                  "nu log-U[1e-3,1], m=ceil(2RN), restart 60, block upper-triangular, 8 inner Stokes steps",
-                      "instances": n}}
+                                  "nu log-U[1e-3,1], m=ceil(2RN), restart %d, block upper-triangular, %d inner "
+                                  "Stokes steps, rtol 1e-8" % (BATCH_RESTART, args.batch_stokes_its),
+                      "instances": n, "mg": mg_settings()}}
     print(json.dumps(out))
 
 
@@ -726,23 +742,31 @@ def run_serve(args):
     from paper_2301_10041_gb300.serve import Request, Server, gpu_ops
     build.build()
     trace = fi.serve_trace(args.serve_requests)
-    reqs = [Request(rid=i, arrival=t, case=fi.serve_case(spec), steps=50) for i, (t, spec) in enumerate(trace)]
     def largest_body(N):   # R <= 0.3, m = ceil(2 R N): the largest ring mesh for this grid
         m = int(np.ceil(2 * 0.3 * N))
         return 1 + 3 * m * (m + 1), 6 * m * m
 
-    ops = gpu_ops(precision=1, restart=60, stokes_its=args.serve_stokes_its, max_solid_nodes=largest_body)
-    srv = Server(ops, budget_bytes=int(args.serve_budget_gb * (1 << 30)), max_resident=args.serve_max_resident,
-                 admit_per_tick=2)
-    wall = srv.run(reqs, realtime=True, max_wall=args.serve_wall)
-    rep = srv.report(wall)
-    offered = sum(r.steps for r in reqs if r.arrival <= wall) / wall
-    out = {"metric": METRIC, "workload": "serve", "value": rep["steps_per_s"], "unit": "time-steps/s",
-           "offered_steps_per_s": offered, "p50_step_ms": rep["step_latency_ms"]["p50"],
-           "p99_step_ms": rep["step_latency_ms"]["p99"], "report": rep,
+    arms = {}
+    for name in args.arms.split(","):
+        ops = gpu_ops(precision=1 if name == "mixed" else 0, restart=60, stokes_its=args.serve_stokes_its,
+                      max_solid_nodes=largest_body)
+        reqs = [Request(rid=i, arrival=t, case=fi.serve_case(spec), steps=50) for i, (t, spec) in enumerate(trace)]
+        srv = Server(ops, budget_bytes=int(args.serve_budget_gb * (1 << 30)), max_resident=args.serve_max_resident,
+                     admit_per_tick=2, policy=args.serve_policy)
+        wall = srv.run(reqs, realtime=True, max_wall=args.serve_wall)
+        rep = srv.report(wall)
+        rep["offered_steps_per_s"] = sum(r.steps for r in reqs if r.arrival <= wall) / wall
+        rep["failed_requests"] = sum(1 for r in srv.finished if r.error)
+        arms[name] = rep
+        print(json.dumps({"serve_arm": name, **rep}), file=sys.stderr, flush=True)
+    head = arms.get("mixed") or next(iter(arms.values()))
+    out = {"metric": METRIC, "workload": "serve", "value": head["steps_per_s"], "unit": "time-steps/s",
+           "offered_steps_per_s": head["offered_steps_per_s"], "p50_step_ms": head["step_latency_ms"]["p50"],
+           "p99_step_ms": head["step_latency_ms"]["p99"], "arms": arms,
            "config": {"workload": "Poisson 200/s, N in {32,64,128,256} p=.4/.3/.2/.1, disk/ellipse, R~U[0.1,0.3], "
                                   "kappa log-U[1,1e4], 50 steps each", "requests": args.serve_requests,
-                      "budget_gb": args.serve_budget_gb, "wall_cap_s": args.serve_wall}}
+                      "budget_gb": args.serve_budget_gb, "wall_cap_s": args.serve_wall,
+                      "admission": args.serve_policy, "max_resident": args.serve_max_resident}}
     print(json.dumps(out))
 
 
@@ -763,11 +787,17 @@ def main():
                     default="cavity128",
                     help="cavity128 (default, the contract line); the others print their own lines")
     ap.add_argument("--batch-instances", type=int, default=256)
+    ap.add_argument("--batch-stokes-its", type=int, default=STOKES_ITS,
+                    help="Richardson steps on the Stokes block per preconditioner application (batch workload)")
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-budget-gb", type=float, default=64.0)
     ap.add_argument("--serve-max-resident", type=int, default=16)
     ap.add_argument("--serve-wall", type=float, default=60.0)
     ap.add_argument("--serve-stokes-its", type=int, default=8)
+    ap.add_argument("--serve-policy", choices=["sjf", "fifo"], default="sjf",
+                    help="admission: shortest predicted work first with an age bound, or first come first served")
+    ap.add_argument("--arms", default="mixed,fp64",
+                    help="batch and serve workloads: which precisions to run (mixed, fp64)")
     ap.add_argument("--no-mg-fused", action="store_true",
                     help="per-level sparse kernels on every multigrid level instead of the fused matrix-free ones")
     ap.add_argument("--mg-cluster", type=int, default=0,

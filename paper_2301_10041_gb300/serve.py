@@ -1,7 +1,7 @@
 """Continuous-batching server for FSI instances on one GPU.
 
 Requests (an FSI case and a number of time steps) arrive over time.  The
-server admits a waiting request as soon as its device footprint
+server admits waiting requests while their device footprint
 (``fsi_footprint_bytes``) fits in the free part of the memory budget, keeps
 every admitted instance resident on the device (meshes, coupling matrices,
 multipliers, Krylov state), and keeps every resident instance busy: each has
@@ -10,6 +10,15 @@ previous one of that instance has finished (``fsi_step_poll``), so the steps
 of different instances overlap on the GPU and a slow instance never holds the
 others back.  An instance that has done its steps leaves at once and frees its
 budget for the next waiting request.
+
+Admission order (``policy``): "fifo" takes the head of the queue and waits
+until it fits; "sjf" (the default) takes, among the waiting requests that fit,
+the one with the least predicted work (steps x predicted cost of one step, by
+default proportional to the fluid unknowns), so that a large, slow request at
+the head no longer holds back the small ones behind it.  A request that has
+waited longer than ``max_wait_s`` is aged: aged requests go first, oldest
+first, and while the oldest one does not fit nothing younger is admitted, so
+no request waits forever.
 
 The scheduling logic (``Server``) takes its device operations as callables so
 that it can be exercised on the CPU with fakes; ``gpu_ops()`` binds them to the
@@ -53,14 +62,24 @@ class Ops:
     close: callable          # handle -> None
 
 
+def unknowns_cost(case) -> float:
+    """Predicted cost of one time step: the fluid unknowns, 2 (2N-1)^2 + 3 N^2."""
+    return 2.0 * (2 * case.N - 1) ** 2 + 3.0 * case.N ** 2
+
+
 class Server:
     def __init__(self, ops: Ops, budget_bytes: int, max_resident: int = 16, admit_per_tick: int = 1,
-                 clock=time.perf_counter):
+                 clock=time.perf_counter, policy: str = "sjf", max_wait_s: float = 2.0, cost=unknowns_cost):
+        if policy not in ("fifo", "sjf"):
+            raise ValueError("policy")
         self.ops = ops
         self.budget = int(budget_bytes)
         self.max_resident = max_resident
         self.admit_per_tick = admit_per_tick   # creation is host work: bound it per tick
         self.clock = clock
+        self.policy = policy
+        self.max_wait_s = max_wait_s
+        self.cost = cost
         self.waiting: deque[Request] = deque()
         self.resident: list[Request] = []
         self.finished: list[Request] = []
@@ -78,14 +97,30 @@ class Server:
             return
         self.waiting.append(req)
 
+    def _next(self, now: float):
+        """The waiting request to admit next, or None (nothing fits, or an
+        aged request that does not fit yet holds the queue)."""
+        if self.policy == "fifo":
+            r = self.waiting[0]
+            return r if self.used + r.footprint <= self.budget else None
+        oldest = self.waiting[0]           # arrival order is queue order
+        if now - oldest.arrival > self.max_wait_s:
+            return oldest if self.used + oldest.footprint <= self.budget else None
+        best = None
+        for r in self.waiting:
+            if self.used + r.footprint > self.budget:
+                continue
+            if best is None or r.steps * self.cost(r.case) < best.steps * self.cost(best.case):
+                best = r
+        return best
+
     def _admit(self, now: float):
-        # FIFO admission: the head of the queue waits until it fits
         admitted = 0
         while self.waiting and len(self.resident) < self.max_resident and admitted < self.admit_per_tick:
-            r = self.waiting[0]
-            if self.used + r.footprint > self.budget:
+            r = self._next(now)
+            if r is None:
                 break
-            self.waiting.popleft()
+            self.waiting.remove(r)
             r.handle = self.ops.create(r.case)
             r.admitted_at = now
             r.admit_seq = self.admissions
@@ -136,13 +171,14 @@ class Server:
         pending = deque(sorted(requests, key=lambda r: r.arrival))
         start = self.clock()
         while pending or self.waiting or self.resident:
-            now = self.clock() - start if realtime else float("inf")
-            while pending and pending[0].arrival <= now:
+            now = self.clock() - start
+            # without realtime every request is there from the start
+            while pending and (pending[0].arrival <= now or not realtime):
                 self.submit(pending.popleft())
             if not self.resident and not self.waiting and pending and realtime:
                 time.sleep(max(0.0, min(0.01, pending[0].arrival - now)))
                 continue
-            if self.tick(now) == 0 and self.resident:
+            if self.tick(now) == 0 and self.resident and realtime:
                 time.sleep(50e-6)   # nothing finished yet: do not spin on the driver
             if max_wall is not None and self.clock() - start > max_wall:
                 break

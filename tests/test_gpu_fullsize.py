@@ -183,15 +183,19 @@ def test_ellipse64_fp64_step_matches_oracle(fsi, ellipse64_oracle_step, mg_clust
     """The N = 64 sweep member in FP64.  Its body starts at rest, so a large
     multiplier cancels against the pressure: |A| |x| is 3e5 times |b|, and
     the relative residual cannot go below about 2e-11 in FP64 (the oracle's
-    refined direct solve reaches 2.4e-11).  Solved to 1e-10, every field is
-    within 1e-7 of the oracle."""
+    refined direct solve reaches 2.4e-11).  The error of a solution is up to
+    the residual times the condition number; on this system a 1e-10 residual
+    leaves about 3e-7 in u and X (measured on GB300), so 1e-7 would need a
+    residual at the FP64 floor.  Solved to 1e-10, every field is within 1e-6
+    of the oracle (the well-scaled N = 64 disk carries the 1e-12 / 1e-7
+    check)."""
     case, ref = ellipse64_oracle_step
     g = fsi.problem_from_case(case, precision=0, precond=bench.PRECOND, rtol=1e-10, max_it=bench.MAX_IT,
                               stokes_its=bench.STOKES_ITS, restart=bench.RESTART, mg_cluster=mg_cluster)
     info = g.step()
     assert info.status == 0 and info.rel_residual <= 1e-10
     err = _field_errors(g, case, ref)
-    assert max(err.values()) < 1e-7, err
+    assert max(err.values()) < 1e-6, err
     g.close()
 
 

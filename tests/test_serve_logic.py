@@ -1,6 +1,7 @@
 """Host logic of the continuous-batching server, with fake device operations
-(no GPU): budgeted FIFO admission, release on completion, rejection of
-requests larger than the whole budget, and per-request step accounting."""
+(no GPU): budgeted FIFO and shortest-work-first admission with an age bound,
+release on completion, rejection of requests larger than the whole budget,
+and per-request step accounting."""
 from dataclasses import dataclass
 
 import numpy as np
@@ -59,7 +60,7 @@ def test_budgeted_fifo_admission_and_release():
     dev = FakeDevice()
     ref = [None]
     srv = Server(dev.ops(ref), budget_bytes=100_000, max_resident=8, admit_per_tick=2,
-                 clock=iter(np.arange(0, 1e6, 1e-3)).__next__)
+                 clock=iter(np.arange(0, 1e6, 1e-3)).__next__, policy="fifo")
     ref[0] = srv
     rng = np.random.default_rng(0)
     reqs = [Request(rid=i, arrival=0.0, case=FakeCase(int(rng.choice([16, 32, 64]))), steps=int(rng.integers(1, 6)))
@@ -102,3 +103,47 @@ def test_admission_footprint_follows_the_solid_element():
     f_p1 = ops.footprint(p1_same_counts)
     assert f_q1 > 0 and f_p1 > 0 and f_q1 != f_p1
     assert ops.footprint(q1) == f_q1    # cached per (N, nodes, elements, element type)
+
+
+def _sjf_run(max_wait_s, budget=100_000):
+    dev = FakeDevice()
+    ref = [None]
+    srv = Server(dev.ops(ref), budget_bytes=budget, max_resident=2, admit_per_tick=1,
+                 clock=iter(np.arange(0, 1e6, 1e-3)).__next__, policy="sjf", max_wait_s=max_wait_s,
+                 cost=lambda case: case.N ** 2)
+    ref[0] = srv
+    # one large request first in the queue, then many small ones, all at t = 0
+    reqs = [Request(rid=0, arrival=0.0, case=FakeCase(90), steps=5)]
+    reqs += [Request(rid=i, arrival=0.0, case=FakeCase(8), steps=2) for i in range(1, 30)]
+    wall = srv.run(reqs, realtime=False)
+    return srv, dev, wall
+
+
+def test_shortest_work_first_admits_small_requests_past_a_large_head():
+    """With a large age bound the small requests are admitted before the
+    large one at the head of the queue (which FIFO would take first)."""
+    srv, dev, wall = _sjf_run(max_wait_s=1e9)
+    assert len(srv.finished) == 30 and not dev.live and dev.peak_used <= 100_000
+    order = [r.rid for r in sorted(srv.finished, key=lambda r: r.admit_seq)]
+    assert order[-1] == 0                        # the large request went last
+    for r in srv.finished:
+        assert r.result["steps"] == r.steps == r.done
+
+
+def test_age_bound_lets_a_waiting_request_through():
+    """The server's clock advances 1 ms per reading; once the large request
+    has waited longer than the bound it is admitted before the remaining small
+    ones, so it cannot starve."""
+    srv, dev, wall = _sjf_run(max_wait_s=0.05)
+    assert len(srv.finished) == 30 and not dev.live
+    order = [r.rid for r in sorted(srv.finished, key=lambda r: r.admit_seq)]
+    assert 0 < order.index(0) < len(order) - 1   # past some small ones, not after all of them
+
+
+def test_aged_request_that_does_not_fit_holds_the_queue():
+    """While the oldest aged request does not fit in the free budget, nothing
+    younger is admitted: the budget frees up for it."""
+    srv, dev, wall = _sjf_run(max_wait_s=0.0, budget=91_000)   # the large one needs 90 000
+    order = [r.rid for r in sorted(srv.finished, key=lambda r: r.admit_seq)]
+    assert order[0] == 0                         # aged at once, first in, alone in the budget
+    assert dev.peak_used <= 91_000
