@@ -22,13 +22,22 @@
 // order, so every node gets the same value whichever tile computes it.
 // Positions on the wall or outside the grid hold zero (absent unknowns).
 //
+// Work is spread without integer division: a sweep gives each row of a
+// rectangle to a group of 8, 16 or 32 lanes, and the velocity sweeps take
+// the four node types as four blocks of rows padded so that a warp never
+// straddles two of them; the type (and with it the whole stencil) is then a
+// compile-time constant of the code a warp runs.
+//
 // Each kernel is a thin wrapper around a __host__ __device__ body that takes
-// the CTA's coordinates explicitly.  Every loop of a body is strided over the
-// CTA's threads and the phases are separated by barriers, so a body run by
-// one thread per CTA computes the same values; the host test of these
-// kernels runs the bodies that way.
+// the CTA's coordinates explicitly.  A body loops over the "virtual threads"
+// of the launch it is written for, strided by the threads that actually run
+// it, and its phases are separated by barriers, so a body run by one thread
+// per CTA computes the same values; the host test of these kernels runs the
+// bodies that way.
 #pragma once
 #include <cuda_runtime.h>
+
+#include <type_traits>
 
 #include "fsi_internal.h"
 
@@ -44,10 +53,11 @@ template <>
 struct Vec2<double> { using type = double2; };
 #endif
 
-// the CTA a body works for: block coordinates, this thread, the thread count
-// and the dynamic shared memory
+// the CTA a body works for: block coordinates, this thread, the threads that
+// run the body (1 on the host), the threads of the launch (the body's
+// virtual threads) and the dynamic shared memory
 struct MfCta {
-  int bx, by, tid, nthr;
+  int bx, by, tid, nthr, vthr;
   unsigned char* sm;
 };
 
@@ -60,12 +70,13 @@ struct MfCta {
 __host__ __device__ __forceinline__ int mf_min(int a, int b) { return a < b ? a : b; }
 __host__ __device__ __forceinline__ int mf_max(int a, int b) { return a > b ? a : b; }
 
-constexpr int kMfThreads = 256;
-constexpr int kMfMaxDeg = 4;   // Chebyshev degrees 1..4 (the default is 2)
-constexpr int kMfTileU = 8;    // velocity down: coarse lattice nodes per tile side
-constexpr int kMfTileUf = 16;  // velocity up: fine lattice nodes per tile side
-constexpr int kMfTileP = 4;    // pressure down: coarse cells per tile side
-constexpr int kMfTilePf = 8;   // pressure up: fine cells per tile side
+constexpr int kMfThreadsU = 512;  // velocity kernels
+constexpr int kMfThreadsP = 256;  // pressure kernels
+constexpr int kMfMaxDeg = 4;      // Chebyshev degrees 1..4 (the default is 2)
+constexpr int kMfTileU = 8;       // velocity down: coarse lattice nodes per tile side
+constexpr int kMfTileUf = 16;     // velocity up: fine lattice nodes per tile side
+constexpr int kMfTileP = 4;       // pressure down: coarse cells per tile side
+constexpr int kMfTilePf = 8;      // pressure up: fine cells per tile side
 constexpr int kMfPresTab = 9 * 9 * 9 + 9 * 3;  // pressure stencil table: blocks, then D^-1
 
 template <class T>
@@ -134,16 +145,73 @@ struct MfPresArgs {
   MfFin<T> fin;
 };
 
+// Quadratic Lagrange basis on [0, 1] (nodes 0, 1/2, 1) at t; exact in
+// binary floating point at the quarter points the transfers use.
+__host__ __device__ __forceinline__ float mf_l0(float t) { return (1.f - t) * (1.f - 2.f * t); }
+__host__ __device__ __forceinline__ float mf_l1(float t) { return 4.f * t * (1.f - t); }
+__host__ __device__ __forceinline__ float mf_l2(float t) { return t * (2.f * t - 1.f); }
+
+// ------------------------------------------------------------------ sweeps
+// fn(x, y) for every (x, y) in [0, nx) x [0, ny): groups of cw = 2^sh lanes
+// (the smallest of 8, 16, 32 that holds a row) take one row each.
+template <class F>
+__host__ __device__ __forceinline__ void mf_rows(const MfCta& c, int nx, int ny, F&& fn) {
+  const int sh = nx <= 8 ? 3 : (nx <= 16 ? 4 : 5);
+  const int cw = 1 << sh, rpw = 32 >> sh, step = (c.vthr >> 5) * rpw;
+  for (int t = c.tid; t < c.vthr; t += c.nthr) {
+    const int lane = t & 31;
+    for (int y = (t >> 5) * rpw + (lane >> sh); y < ny; y += step)
+      for (int x = lane & (cw - 1); x < nx; x += cw) fn(x, y);
+  }
+}
+
+// fn(type, px, py) over the plane rectangle [qx0, qx1) x [qy0, qy1) of all
+// four planes, the type as std::integral_constant: each plane's rows are
+// padded to a multiple of the rows a warp takes, so a warp stays in one plane.
+template <class F>
+__host__ __device__ __forceinline__ void mf_vsweep(const MfCta& c, int qx0, int qx1, int qy0, int qy1, F&& fn) {
+  const int nqx = qx1 - qx0, nqy = qy1 - qy0;
+  const int sh = nqx <= 8 ? 3 : (nqx <= 16 ? 4 : 5);
+  const int cw = 1 << sh, rsh = 5 - sh, rpw = 1 << rsh;
+  const int nyp = ((nqy + rpw - 1) >> rsh) << rsh;
+  const int nrow = 4 * nyp, step = (c.vthr >> 5) * rpw;
+  for (int t = c.tid; t < c.vthr; t += c.nthr) {
+    const int lane = t & 31;
+    for (int yy = (t >> 5) * rpw + (lane >> sh); yy < nrow; yy += step) {
+      const int tau = (yy >= nyp) + (yy >= 2 * nyp) + (yy >= 3 * nyp);
+      const int y = yy - tau * nyp;
+      if (y >= nqy) continue;
+      for (int x = lane & (cw - 1); x < nqx; x += cw) {
+        switch (tau) {
+          case 0: fn(std::integral_constant<int, 0>(), qx0 + x, qy0 + y); break;
+          case 1: fn(std::integral_constant<int, 1>(), qx0 + x, qy0 + y); break;
+          case 2: fn(std::integral_constant<int, 2>(), qx0 + x, qy0 + y); break;
+          default: fn(std::integral_constant<int, 3>(), qx0 + x, qy0 + y); break;
+        }
+      }
+    }
+  }
+}
+
 // --------------------------------------------------------------- velocity
 // interior Q2 node (1 <= ix, iy <= 2N-1) -> id in the type-blocked order
 // (corners, x-edge midpoints, y-edge midpoints, centres; lattice order inside)
-__host__ __device__ __forceinline__ int mf_vnode(int N, int ix, int iy) {
+template <int TAU>
+__host__ __device__ __forceinline__ int mf_vnode_t(int N, int ix, int iy) {
   const int nV = (N - 1) * (N - 1), nX = N * (N - 1);
-  const int ox = ix & 1, oy = iy & 1;
-  if (!ox && !oy) return (iy / 2 - 1) * (N - 1) + (ix / 2 - 1);
-  if (ox && !oy) return nV + (iy / 2 - 1) * N + (ix - 1) / 2;
-  if (!ox && oy) return nV + nX + ((iy - 1) / 2) * (N - 1) + (ix / 2 - 1);
-  return nV + 2 * nX + ((iy - 1) / 2) * N + (ix - 1) / 2;
+  if (TAU == 0) return ((iy >> 1) - 1) * (N - 1) + ((ix >> 1) - 1);
+  if (TAU == 1) return nV + ((iy >> 1) - 1) * N + (ix >> 1);
+  if (TAU == 2) return nV + nX + (iy >> 1) * (N - 1) + ((ix >> 1) - 1);
+  return nV + 2 * nX + (iy >> 1) * N + (ix >> 1);
+}
+
+__host__ __device__ __forceinline__ int mf_vnode(int N, int ix, int iy) {
+  switch ((ix & 1) | ((iy & 1) << 1)) {
+    case 0: return mf_vnode_t<0>(N, ix, iy);
+    case 1: return mf_vnode_t<1>(N, ix, iy);
+    case 2: return mf_vnode_t<2>(N, ix, iy);
+    default: return mf_vnode_t<3>(N, ix, iy);
+  }
 }
 
 __host__ __device__ __forceinline__ bool mf_vinterior(int N, int ix, int iy) {
@@ -156,14 +224,21 @@ __host__ __device__ __forceinline__ bool mf_vinterior(int N, int ix, int iy) {
 struct MfFrame {
   int ox, oy, pw, ph;
   __host__ __device__ __forceinline__ int plane() const { return pw * ph; }
+  __host__ __device__ __forceinline__ int at(int t, int px, int py) const { return (t * ph + py) * pw + px; }
+  __host__ __device__ __forceinline__ int at_lattice(int ix, int iy) const {
+    return at((ix & 1) | ((iy & 1) << 1), (ix - ox) >> 1, (iy - oy) >> 1);
+  }
 };
 
-// y += A v at the node of type TAU with plane coordinates (px, py)
+// y = A v at the node of type TAU with plane coordinates (px, py); the
+// neighbours of even and odd rows go to two accumulator pairs (two shorter
+// dependency chains), added at the end
 template <class T, int TAU>
 __host__ __device__ __forceinline__ void mf_vel_apply(const MfVelOp<T>& op, const typename Vec2<T>::type* __restrict__ v,
-                                             const MfFrame& f, int px, int py, T& y0, T& y1) {
+                                                      const MfFrame& f, int px, int py, T& y0, T& y1) {
   constexpr int PX = TAU & 1, PY = TAU >> 1;
   constexpr int RX = PX ? 1 : 2, RY = PY ? 1 : 2;
+  T a0 = 0, a1 = 0, b0 = 0, b1 = 0;
 #pragma unroll
   for (int dy = -RY; dy <= RY; ++dy) {
 #pragma unroll
@@ -172,37 +247,17 @@ __host__ __device__ __forceinline__ void mf_vel_apply(const MfVelOp<T>& op, cons
       const int qx = px + ((PX + dx) >> 1), qy = py + ((PY + dy) >> 1);
       const auto x = v[(t2 * f.ph + qy) * f.pw + qx];
       const T* c = op.c[TAU][dy + 2][dx + 2];
-      y0 += c[0] * x.x + c[1] * x.y;
-      y1 += c[2] * x.x + c[3] * x.y;
+      if ((dy & 1) == 0) {
+        a0 += c[0] * x.x + c[1] * x.y;
+        a1 += c[2] * x.x + c[3] * x.y;
+      } else {
+        b0 += c[0] * x.x + c[1] * x.y;
+        b1 += c[2] * x.x + c[3] * x.y;
+      }
     }
   }
-}
-
-template <class T>
-__host__ __device__ __forceinline__ void mf_vel_res(const MfVelOp<T>& op, int tau, const typename Vec2<T>::type* __restrict__ v,
-                                           const MfFrame& f, int px, int py, T& y0, T& y1) {
-  switch (tau) {
-    case 0: mf_vel_apply<T, 0>(op, v, f, px, py, y0, y1); break;
-    case 1: mf_vel_apply<T, 1>(op, v, f, px, py, y0, y1); break;
-    case 2: mf_vel_apply<T, 2>(op, v, f, px, py, y0, y1); break;
-    default: mf_vel_apply<T, 3>(op, v, f, px, py, y0, y1); break;
-  }
-}
-
-// Visit every frame entry of the plane rectangle [q0, q1) (x and y) in all
-// four planes; warps never straddle two planes, so the node type (and with
-// it the stencil) is the same across a warp.
-template <class F>
-__host__ __device__ __forceinline__ void mf_vsweep(const MfCta& c, const MfFrame& f, int qx0, int qx1, int qy0,
-                                                   int qy1, F&& fn) {
-  const int nqx = qx1 - qx0, nq = nqx * (qy1 - qy0);
-  const int nq32 = (nq + 31) & ~31;
-  for (int i = c.tid; i < 4 * nq32; i += c.nthr) {
-    const int tau = i / nq32, j = i - tau * nq32;
-    if (j >= nq) continue;
-    const int px = qx0 + j % nqx, py = qy0 + j / nqx;
-    fn(tau, px, py, (tau * f.ph + py) * f.pw + px);
-  }
+  y0 = a0 + b0;
+  y1 = a1 + b1;
 }
 
 // One Chebyshev step on the plane rectangle shrunk by `s` from the frame:
@@ -210,28 +265,30 @@ __host__ __device__ __forceinline__ void mf_vsweep(const MfCta& c, const MfFrame
 // dn = c1 do + c2 D^-1 (b - A xo); xn = xo + dn.  Outside the interior 0.
 template <class T>
 __host__ __device__ __forceinline__ void mf_vel_cheb(const MfCta& cta, const MfVelOp<T>& op, const MfFrame& f, int s,
-                                            const typename Vec2<T>::type* __restrict__ B,
-                                            const typename Vec2<T>::type* __restrict__ Xo,
-                                            const typename Vec2<T>::type* __restrict__ Do,
-                                            typename Vec2<T>::type* __restrict__ Xn,
-                                            typename Vec2<T>::type* __restrict__ Dn, bool first, T c1, T c2) {
+                                                     const typename Vec2<T>::type* __restrict__ B,
+                                                     const typename Vec2<T>::type* __restrict__ Xo,
+                                                     const typename Vec2<T>::type* __restrict__ Do,
+                                                     typename Vec2<T>::type* __restrict__ Xn,
+                                                     typename Vec2<T>::type* __restrict__ Dn, bool first, T c1, T c2) {
   using T2 = typename Vec2<T>::type;
   const int N = op.N;
-  mf_vsweep(cta, f, s, f.pw - s, s, f.ph - s, [&](int tau, int px, int py, int e) {
-    const int ix = f.ox + 2 * px + (tau & 1), iy = f.oy + 2 * py + (tau >> 1);
+  mf_vsweep(cta, s, f.pw - s, s, f.ph - s, [&](auto tc, int px, int py) {
+    constexpr int TAU = decltype(tc)::value;
+    const int ix = f.ox + 2 * px + (TAU & 1), iy = f.oy + 2 * py + (TAU >> 1);
+    const int e = f.at(TAU, px, py);
     T2 xn, dn;
     if (mf_vinterior(N, ix, iy)) {
-      T a0 = 0, a1 = 0;
-      mf_vel_res<T>(op, tau, Xo, f, px, py, a0, a1);
+      T a0, a1;
+      mf_vel_apply<T, TAU>(op, Xo, f, px, py, a0, a1);
       const T2 b = B[e], xo = Xo[e];
       const T r0 = b.x - a0, r1 = b.y - a1;
       if (first) {
-        dn.x = c2 * op.dinv[tau][0] * r0;
-        dn.y = c2 * op.dinv[tau][1] * r1;
+        dn.x = c2 * op.dinv[TAU][0] * r0;
+        dn.y = c2 * op.dinv[TAU][1] * r1;
       } else {
         const T2 d = Do[e];
-        dn.x = c1 * d.x + c2 * op.dinv[tau][0] * r0;
-        dn.y = c1 * d.y + c2 * op.dinv[tau][1] * r1;
+        dn.x = c1 * d.x + c2 * op.dinv[TAU][0] * r0;
+        dn.y = c1 * d.y + c2 * op.dinv[TAU][1] * r1;
       }
       xn.x = xo.x + dn.x;
       xn.y = xo.y + dn.y;
@@ -243,31 +300,10 @@ __host__ __device__ __forceinline__ void mf_vel_cheb(const MfCta& cta, const MfV
   });
 }
 
-// Q2 prolongation weights: a fine lattice coordinate f lies in coarse cell
-// cc = min(f / 4, Nc - 1) at r = f - 4 cc; coarse node 2 cc + a gets the
-// coarse quadratic's value there, mf_pw(r, a)
-__host__ __device__ __forceinline__ float mf_pw(int r, int a) {
-  switch (r) {
-    case 0: return a == 0 ? 1.f : 0.f;
-    case 1: return a == 0 ? 0.375f : (a == 1 ? 0.75f : -0.125f);
-    case 2: return a == 1 ? 1.f : 0.f;
-    case 3: return a == 0 ? -0.125f : (a == 1 ? 0.75f : 0.375f);
-    default: return a == 2 ? 1.f : 0.f;
-  }
-}
-
-// restriction weight of a fine node at offset d from 2X (coarse node X) in 1-D
-__host__ __device__ __forceinline__ float mf_rw(int odd, int d) {
-  const int a = d < 0 ? -d : d;
-  if (odd) return a == 0 ? 1.f : (a == 1 ? 0.75f : 0.f);
-  return a == 0 ? 1.f : (a == 1 ? 0.375f : (a == 3 ? -0.125f : 0.f));
-}
-
 // down: grid (ceil(N / kMfTileU))^2 over the coarse lattice [0, N)^2
 template <class T>
 __host__ __device__ void mfu_down_body(const MfVelArgs<T>& a, const MfCta& cta) {
   using T2 = typename Vec2<T>::type;
-  unsigned char* mf_sm = cta.sm;
   const MfVelOp<T>& op = a.op;
   const int N = op.N, K = a.ch.k;
   const int CX0 = cta.bx * kMfTileU, CY0 = cta.by * kMfTileU;
@@ -276,23 +312,24 @@ __host__ __device__ void mfu_down_body(const MfVelArgs<T>& a, const MfCta& cta) 
   f.oy = 2 * CY0 - 4 - 2 * K;
   f.pw = f.ph = (2 * kMfTileU + 8 + 4 * K) / 2;
   const int nf = 4 * f.plane();
-  T2* B = reinterpret_cast<T2*>(mf_sm);
+  T2* B = reinterpret_cast<T2*>(cta.sm);
   T2 *Xc = B + nf, *Xn = B + 2 * nf, *Dc = B + 3 * nf, *Dn = B + 4 * nf;   // current / next iterate
   T2* R = B + 5 * nf;
   // b on the frame; x0 = d0 = c0 D^-1 b
-  for (int e = cta.tid; e < nf; e += cta.nthr) {
-    const int tau = e / f.plane(), j = e - tau * f.plane();
-    const int ix = f.ox + 2 * (j % f.pw) + (tau & 1), iy = f.oy + 2 * (j / f.pw) + (tau >> 1);
+  mf_vsweep(cta, 0, f.pw, 0, f.ph, [&](auto tc, int px, int py) {
+    constexpr int TAU = decltype(tc)::value;
+    const int ix = f.ox + 2 * px + (TAU & 1), iy = f.oy + 2 * py + (TAU >> 1);
     T2 v;
     v.x = v.y = 0;
-    if (mf_vinterior(N, ix, iy)) v = *reinterpret_cast<const T2*>(a.b + 2 * (size_t)mf_vnode(N, ix, iy));
+    if (mf_vinterior(N, ix, iy)) v = *reinterpret_cast<const T2*>(a.b + 2 * (size_t)mf_vnode_t<TAU>(N, ix, iy));
+    const int e = f.at(TAU, px, py);
     B[e] = v;
     T2 x0;
-    x0.x = a.ch.c0 * op.dinv[tau][0] * v.x;
-    x0.y = a.ch.c0 * op.dinv[tau][1] * v.y;
+    x0.x = a.ch.c0 * op.dinv[TAU][0] * v.x;
+    x0.y = a.ch.c0 * op.dinv[TAU][1] * v.y;
     Xc[e] = x0;
     Dc[e] = x0;
-  }
+  });
   MF_SYNC();
   for (int s = 1; s < K; ++s) {  // pre-smoothing steps 1 .. K-1 on the frame shrunk by s nodes per plane
     mf_vel_cheb<T>(cta, op, f, s, B, Xc, Dc, Xn, Dn, false, a.ch.c1[s - 1], a.ch.c2[s - 1]);
@@ -300,44 +337,46 @@ __host__ __device__ void mfu_down_body(const MfVelArgs<T>& a, const MfCta& cta) 
     t = Dc; Dc = Dn; Dn = t;
     MF_SYNC();
   }
-  // residual on the frame shrunk by K (plane units): the restriction's support
-  mf_vsweep(cta, f, K, f.pw - K, K, f.ph - K, [&](int tau, int px, int py, int e) {
-    const int ix = f.ox + 2 * px + (tau & 1), iy = f.oy + 2 * py + (tau >> 1);
+  // residual on the frame shrunk by K (plane units): the restriction's
+  // support; the pre-smoothed iterate on the owned fine nodes [2 CX0, 2 CX0
+  // + 2 tile), plane entries [o, o + tile), goes out in the same sweep
+  const int o = 2 + K;
+  mf_vsweep(cta, K, f.pw - K, K, f.ph - K, [&](auto tc, int px, int py) {
+    constexpr int TAU = decltype(tc)::value;
+    const int ix = f.ox + 2 * px + (TAU & 1), iy = f.oy + 2 * py + (TAU >> 1);
+    const int e = f.at(TAU, px, py);
     T2 r;
     r.x = r.y = 0;
     if (mf_vinterior(N, ix, iy)) {
-      T a0 = 0, a1 = 0;
-      mf_vel_res<T>(op, tau, Xc, f, px, py, a0, a1);
+      T a0, a1;
+      mf_vel_apply<T, TAU>(op, Xc, f, px, py, a0, a1);
       r.x = B[e].x - a0;
       r.y = B[e].y - a1;
+      if (px >= o && px < o + kMfTileU && py >= o && py < o + kMfTileU)
+        *reinterpret_cast<T2*>(a.xout + 2 * (size_t)mf_vnode_t<TAU>(N, ix, iy)) = Xc[e];
     }
     R[e] = r;
   });
-  // the pre-smoothed iterate on the owned fine nodes [2 CX0, 2 CX0 + 2 tile)
-  const int o = (4 + 2 * K) / 2;   // plane offset of the owned region in the frame
-  for (int i = cta.tid; i < 4 * kMfTileU * kMfTileU; i += cta.nthr) {
-    const int tau = i / (kMfTileU * kMfTileU), j = i - tau * kMfTileU * kMfTileU;
-    const int px = o + j % kMfTileU, py = o + j / kMfTileU;
-    const int ix = f.ox + 2 * px + (tau & 1), iy = f.oy + 2 * py + (tau >> 1);
-    if (mf_vinterior(N, ix, iy))
-      *reinterpret_cast<T2*>(a.xout + 2 * (size_t)mf_vnode(N, ix, iy)) = Xc[(tau * f.ph + py) * f.pw + px];
-  }
   MF_SYNC();
-  // restriction to the coarse nodes of the tile (coarse lattice interior 1 .. N - 1)
+  // restriction to the coarse nodes of the tile (coarse lattice interior
+  // 1 .. N - 1): the 1-D weight of a fine node at 2X + d is the coarse
+  // quadratic of node X there, L0(|d| / 4) at a cell corner, L1((d + 2) / 4)
+  // at an edge or cell midpoint (|d| <= 1)
   const int Nc = N / 2;
-  for (int i = cta.tid; i < kMfTileU * kMfTileU; i += cta.nthr) {
-    const int X0 = CX0 + i % kMfTileU, Y0 = CY0 + i / kMfTileU;
-    if (!mf_vinterior(Nc, X0, Y0)) continue;
+  mf_rows(cta, kMfTileU, kMfTileU, [&](int i, int j) {
+    const int X0 = CX0 + i, Y0 = CY0 + j;
+    if (!mf_vinterior(Nc, X0, Y0)) return;
     T s0 = 0, s1 = 0;
     const int rx = (X0 & 1) ? 1 : 3, ry = (Y0 & 1) ? 1 : 3;
     for (int dy = -ry; dy <= ry; ++dy) {
-      const T wy = (T)mf_rw(Y0 & 1, dy);
+      const float ty = (Y0 & 1) ? 0.25f * (float)(dy + 2) : 0.25f * (float)(dy < 0 ? -dy : dy);
+      const T wy = (T)((Y0 & 1) ? mf_l1(ty) : mf_l0(ty));
       if (wy == (T)0) continue;
       for (int dx = -rx; dx <= rx; ++dx) {
-        const T wx = (T)mf_rw(X0 & 1, dx);
+        const float tx = (X0 & 1) ? 0.25f * (float)(dx + 2) : 0.25f * (float)(dx < 0 ? -dx : dx);
+        const T wx = (T)((X0 & 1) ? mf_l1(tx) : mf_l0(tx));
         if (wx == (T)0) continue;
-        const int ix = 2 * X0 + dx, iy = 2 * Y0 + dy;
-        const T2 r = R[((((ix & 1) | ((iy & 1) << 1)) * f.ph + ((iy - f.oy) >> 1)) * f.pw) + ((ix - f.ox) >> 1)];
+        const T2 r = R[f.at_lattice(2 * X0 + dx, 2 * Y0 + dy)];
         const T w = wx * wy;
         s0 += w * r.x;
         s1 += w * r.y;
@@ -353,14 +392,13 @@ __host__ __device__ void mfu_down_body(const MfVelArgs<T>& a, const MfCta& cta) 
       a.ci.d[2 * id] = d0;
       a.ci.d[2 * id + 1] = d1;
     }
-  }
+  });
 }
 
 // up: grid (ceil(2N / kMfTileUf))^2 over the fine lattice [0, 2N)^2
 template <class T>
 __host__ __device__ void mfu_up_body(const MfVelArgs<T>& a, const MfCta& cta) {
   using T2 = typename Vec2<T>::type;
-  unsigned char* mf_sm = cta.sm;
   const MfVelOp<T>& op = a.op;
   const int N = op.N, K = a.ch.k, Nc = N / 2;
   const int FX0 = cta.bx * kMfTileUf, FY0 = cta.by * kMfTileUf;
@@ -378,40 +416,41 @@ __host__ __device__ void mfu_up_body(const MfVelArgs<T>& a, const MfCta& cta) {
     g.pw = hix - lox + 2;   // coarse lattice 2 lo .. 2 hi + 2, i.e. 2 (hi - lo) + 3 nodes
     g.ph = hiy - loy + 2;
   }
-  const int nf = 4 * f.plane(), ng = 4 * g.plane();
-  T2* B = reinterpret_cast<T2*>(mf_sm);
+  const int nf = 4 * f.plane();
+  T2* B = reinterpret_cast<T2*>(cta.sm);
   T2 *Xc = B + nf, *Xn = B + 2 * nf, *Dc = B + 3 * nf, *Dn = B + 4 * nf;
   T2* XC = B + 5 * nf;
-  for (int e = cta.tid; e < ng; e += cta.nthr) {
-    const int tau = e / g.plane(), j = e - tau * g.plane();
-    const int ix = g.ox + 2 * (j % g.pw) + (tau & 1), iy = g.oy + 2 * (j / g.pw) + (tau >> 1);
+  mf_vsweep(cta, 0, g.pw, 0, g.ph, [&](auto tc, int px, int py) {
+    constexpr int TAU = decltype(tc)::value;
+    const int ix = g.ox + 2 * px + (TAU & 1), iy = g.oy + 2 * py + (TAU >> 1);
     T2 v;
     v.x = v.y = 0;
-    if (mf_vinterior(Nc, ix, iy)) v = *reinterpret_cast<const T2*>(a.xc + 2 * (size_t)mf_vnode(Nc, ix, iy));
-    XC[e] = v;
-  }
+    if (mf_vinterior(Nc, ix, iy)) v = *reinterpret_cast<const T2*>(a.xc + 2 * (size_t)mf_vnode_t<TAU>(Nc, ix, iy));
+    XC[g.at(TAU, px, py)] = v;
+  });
   MF_SYNC();
-  // b and x + P x_coarse on the frame
-  for (int e = cta.tid; e < nf; e += cta.nthr) {
-    const int tau = e / f.plane(), j = e - tau * f.plane();
-    const int ix = f.ox + 2 * (j % f.pw) + (tau & 1), iy = f.oy + 2 * (j / f.pw) + (tau >> 1);
+  // b and x + P x_coarse on the frame: the coarse quadratic of the coarse
+  // cell cc = min(ix / 4, Nc - 1) at t = (ix - 4 cc) / 4 in each direction
+  mf_vsweep(cta, 0, f.pw, 0, f.ph, [&](auto tc, int px, int py) {
+    constexpr int TAU = decltype(tc)::value;
+    const int ix = f.ox + 2 * px + (TAU & 1), iy = f.oy + 2 * py + (TAU >> 1);
     T2 bv, xv;
     bv.x = bv.y = xv.x = xv.y = 0;
     if (mf_vinterior(N, ix, iy)) {
-      const size_t id = mf_vnode(N, ix, iy);
+      const size_t id = mf_vnode_t<TAU>(N, ix, iy);
       bv = *reinterpret_cast<const T2*>(a.b + 2 * id);
       xv = *reinterpret_cast<const T2*>(a.xpre + 2 * id);
       const int ccx = mf_min(ix >> 2, Nc - 1), ccy = mf_min(iy >> 2, Nc - 1);
-      const int rx = ix - 4 * ccx, ry = iy - 4 * ccy;
+      const float tx = 0.25f * (float)(ix - 4 * ccx), ty = 0.25f * (float)(iy - 4 * ccy);
+      const T wx[3] = {(T)mf_l0(tx), (T)mf_l1(tx), (T)mf_l2(tx)};
+      const T wy[3] = {(T)mf_l0(ty), (T)mf_l1(ty), (T)mf_l2(ty)};
       T p0 = 0, p1 = 0;
 #pragma unroll
       for (int bb = 0; bb < 3; ++bb) {
-        const T wy = (T)mf_pw(ry, bb);
 #pragma unroll
         for (int aa = 0; aa < 3; ++aa) {
-          const T w = (T)mf_pw(rx, aa) * wy;
-          const int X0 = 2 * ccx + aa, Y0 = 2 * ccy + bb;
-          const T2 c = XC[((((X0 & 1) | ((Y0 & 1) << 1)) * g.ph + ((Y0 - g.oy) >> 1)) * g.pw) + ((X0 - g.ox) >> 1)];
+          const T w = wx[aa] * wy[bb];
+          const T2 c = XC[g.at_lattice(2 * ccx + aa, 2 * ccy + bb)];
           p0 += w * c.x;
           p1 += w * c.y;
         }
@@ -419,47 +458,47 @@ __host__ __device__ void mfu_up_body(const MfVelArgs<T>& a, const MfCta& cta) {
       xv.x = p0 + xv.x;
       xv.y = p1 + xv.y;
     }
+    const int e = f.at(TAU, px, py);
     B[e] = bv;
     Xc[e] = xv;
-  }
+  });
   MF_SYNC();
-  for (int s = 0; s < K; ++s) {  // post-smoothing: CHEB0, then CHEB steps, each on a frame 1 plane entry smaller
-    const bool last = (s == K - 1);
-    if (!last) {
-      mf_vel_cheb<T>(cta, op, f, s + 1, B, Xc, Dc, Xn, Dn, s == 0,
-                     s == 0 ? (T)0 : a.ch.c1[s - 1], s == 0 ? a.ch.c0 : a.ch.c2[s - 1]);
-      T2* t = Xc; Xc = Xn; Xn = t;
-      t = Dc; Dc = Dn; Dn = t;
-      MF_SYNC();
-      continue;
-    }
-    // last step on the owned tile: write the result and the epilogue
-    const T c1 = s == 0 ? (T)0 : a.ch.c1[s - 1], c2 = s == 0 ? a.ch.c0 : a.ch.c2[s - 1];
-    mf_vsweep(cta, f, K, f.pw - K, K, f.ph - K, [&](int tau, int px, int py, int e) {
-      const int ix = f.ox + 2 * px + (tau & 1), iy = f.oy + 2 * py + (tau >> 1);
-      if (!mf_vinterior(N, ix, iy)) return;
-      T a0 = 0, a1 = 0;
-      mf_vel_res<T>(op, tau, Xc, f, px, py, a0, a1);
-      const T2 b = B[e], xo = Xc[e];
-      const T r0 = b.x - a0, r1 = b.y - a1;
-      T d0 = c2 * op.dinv[tau][0] * r0, d1 = c2 * op.dinv[tau][1] * r1;
-      if (s > 0) {
-        const T2 d = Dc[e];
-        d0 = c1 * d.x + c2 * op.dinv[tau][0] * r0;
-        d1 = c1 * d.y + c2 * op.dinv[tau][1] * r1;
-      }
-      const size_t id = mf_vnode(N, ix, iy);
-      const T y0 = xo.x + d0, y1 = xo.y + d1;
-      T2 y;
-      y.x = y0;
-      y.y = y1;
-      *reinterpret_cast<T2*>(a.xout + 2 * id) = y;
-      if (a.fin.acc) {
-        a.fin.acc[2 * id] += a.fin.omega * y0;
-        a.fin.acc[2 * id + 1] += a.fin.omega * y1;
-      }
-    });
+  for (int s = 0; s + 1 < K; ++s) {  // post-smoothing: CHEB0, then CHEB steps, each on a frame 1 plane entry smaller
+    mf_vel_cheb<T>(cta, op, f, s + 1, B, Xc, Dc, Xn, Dn, s == 0,
+                   s == 0 ? (T)0 : a.ch.c1[s - 1], s == 0 ? a.ch.c0 : a.ch.c2[s - 1]);
+    T2* t = Xc; Xc = Xn; Xn = t;
+    t = Dc; Dc = Dn; Dn = t;
+    MF_SYNC();
   }
+  // last step on the owned tile: write the result and the epilogue
+  const int s = K - 1;
+  const T c1 = s == 0 ? (T)0 : a.ch.c1[s - 1], c2 = s == 0 ? a.ch.c0 : a.ch.c2[s - 1];
+  mf_vsweep(cta, K, f.pw - K, K, f.ph - K, [&](auto tc, int px, int py) {
+    constexpr int TAU = decltype(tc)::value;
+    const int ix = f.ox + 2 * px + (TAU & 1), iy = f.oy + 2 * py + (TAU >> 1);
+    if (!mf_vinterior(N, ix, iy)) return;
+    const int e = f.at(TAU, px, py);
+    T a0, a1;
+    mf_vel_apply<T, TAU>(op, Xc, f, px, py, a0, a1);
+    const T2 b = B[e], xo = Xc[e];
+    const T r0 = b.x - a0, r1 = b.y - a1;
+    T d0 = c2 * op.dinv[TAU][0] * r0, d1 = c2 * op.dinv[TAU][1] * r1;
+    if (s > 0) {
+      const T2 d = Dc[e];
+      d0 = c1 * d.x + c2 * op.dinv[TAU][0] * r0;
+      d1 = c1 * d.y + c2 * op.dinv[TAU][1] * r1;
+    }
+    const size_t id = mf_vnode_t<TAU>(N, ix, iy);
+    const T y0 = xo.x + d0, y1 = xo.y + d1;
+    T2 y;
+    y.x = y0;
+    y.y = y1;
+    *reinterpret_cast<T2*>(a.xout + 2 * id) = y;
+    if (a.fin.acc) {
+      a.fin.acc[2 * id] += a.fin.omega * y0;
+      a.fin.acc[2 * id + 1] += a.fin.omega * y1;
+    }
+  });
 }
 
 // --------------------------------------------------------------- pressure
@@ -470,69 +509,70 @@ struct MfCells {
   __host__ __device__ __forceinline__ int n() const { return w * w; }
 };
 
-template <class T>
 __host__ __device__ __forceinline__ int mf_variant(int N, int cx, int cy) {
   const int vx = cx == 0 ? 0 : (cx == N - 1 ? 2 : 1), vy = cy == 0 ? 0 : (cy == N - 1 ? 2 : 1);
   return 3 * vy + vx;
 }
 
-// y = L v at cell (cx, cy) (frame entry e) with the stencil table in shared memory
+__host__ __device__ __forceinline__ bool mf_cin(int N, int cx, int cy) {
+  return cx >= 0 && cy >= 0 && cx < N && cy < N;
+}
+
+// y = L v at cell (cx, cy) (frame entry e) with the stencil table in shared
+// memory; the three cell rows go to separate partial sums
 template <class T>
-__host__ __device__ __forceinline__ void mf_pres_apply(const T* __restrict__ tab, const T* __restrict__ v, const MfCells& f,
-                                              int N, int cx, int cy, int e, T y[3]) {
-  const T* base = tab + 81 * mf_variant<T>(N, cx, cy);
+__host__ __device__ __forceinline__ void mf_pres_apply(const T* __restrict__ tab, const T* __restrict__ v,
+                                                       const MfCells& f, int N, int cx, int cy, int e, T y[3]) {
+  const T* base = tab + 81 * mf_variant(N, cx, cy);
   const int n = f.n();
-  y[0] = y[1] = y[2] = 0;
+  T p[3][3];
 #pragma unroll
   for (int dy = -1; dy <= 1; ++dy) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) p[dy + 1][i] = 0;
 #pragma unroll
     for (int dx = -1; dx <= 1; ++dx) {
       const int q = e + dy * f.w + dx;
       const T x0 = v[q], x1 = v[n + q], x2 = v[2 * n + q];
       const T* c = base + 9 * ((dy + 1) * 3 + dx + 1);
 #pragma unroll
-      for (int i = 0; i < 3; ++i) y[i] += c[3 * i] * x0 + c[3 * i + 1] * x1 + c[3 * i + 2] * x2;
+      for (int i = 0; i < 3; ++i) p[dy + 1][i] += c[3 * i] * x0 + c[3 * i + 1] * x1 + c[3 * i + 2] * x2;
     }
   }
-}
-
-template <class T>
-__host__ __device__ __forceinline__ bool mf_cin(int N, int cx, int cy) {
-  return cx >= 0 && cy >= 0 && cx < N && cy < N;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) y[i] = (p[0][i] + p[1][i]) + p[2][i];
 }
 
 // one Chebyshev step on the cell frame shrunk by s cells
 template <class T>
 __host__ __device__ __forceinline__ void mf_pres_cheb(const MfCta& cta, const T* __restrict__ tab, int N,
-                                                      const MfCells& f, int s,
-                                             const T* __restrict__ B, const T* __restrict__ Xo,
-                                             const T* __restrict__ Do, T* __restrict__ Xn, T* __restrict__ Dn,
-                                             bool first, T c1, T c2) {
+                                                      const MfCells& f, int s, const T* __restrict__ B,
+                                                      const T* __restrict__ Xo, const T* __restrict__ Do,
+                                                      T* __restrict__ Xn, T* __restrict__ Dn, bool first, T c1, T c2) {
   const int m = f.w - 2 * s, n = f.n();
   const T* dv = tab + 729;
-  for (int i = cta.tid; i < m * m; i += cta.nthr) {
-    const int lx = s + i % m, ly = s + i / m, e = ly * f.w + lx;
+  mf_rows(cta, m, m, [&](int i, int j) {
+    const int lx = s + i, ly = s + j, e = ly * f.w + lx;
     const int cx = f.ox + lx, cy = f.oy + ly;
-    if (!mf_cin<T>(N, cx, cy)) {
+    if (!mf_cin(N, cx, cy)) {
       for (int k = 0; k < 3; ++k) Xn[k * n + e] = Dn[k * n + e] = 0;
-      continue;
+      return;
     }
     T y[3];
     mf_pres_apply<T>(tab, Xo, f, N, cx, cy, e, y);
-    const int v = mf_variant<T>(N, cx, cy);
+    const int v = mf_variant(N, cx, cy);
     for (int k = 0; k < 3; ++k) {
       const T r = B[k * n + e] - y[k];
       const T dn = first ? c2 * dv[3 * v + k] * r : c1 * Do[k * n + e] + c2 * dv[3 * v + k] * r;
       Dn[k * n + e] = dn;
       Xn[k * n + e] = Xo[k * n + e] + dn;
     }
-  }
+  });
 }
 
 // down: grid (ceil(Nc / kMfTileP))^2 over the coarse cells
 template <class T>
 __host__ __device__ void mfp_down_body(const MfPresArgs<T>& a, const MfCta& cta) {
-  unsigned char* mf_sm = cta.sm;
   const int N = a.N, K = a.ch.k, Nc = N / 2;
   const int CX0 = cta.bx * kMfTileP, CY0 = cta.by * kMfTileP;
   MfCells f;
@@ -540,16 +580,16 @@ __host__ __device__ void mfp_down_body(const MfPresArgs<T>& a, const MfCta& cta)
   f.oy = 2 * CY0 - K;
   f.w = 2 * kMfTileP + 2 * K;
   const int n = f.n();
-  T* tab = reinterpret_cast<T*>(mf_sm);
+  T* tab = reinterpret_cast<T*>(cta.sm);
   T* B = tab + ((kMfPresTab + 3) & ~3);
   T *Xc = B + 3 * n, *Xn = B + 6 * n, *Dc = B + 9 * n, *Dn = B + 12 * n;
-  for (int i = cta.tid; i < kMfPresTab; i += cta.nthr) tab[i] = a.tab[i];
+  for (int t = cta.tid; t < kMfPresTab; t += cta.nthr) tab[t] = a.tab[t];
   MF_SYNC();
   const T* dv = tab + 729;
-  for (int e = cta.tid; e < n; e += cta.nthr) {
-    const int cx = f.ox + e % f.w, cy = f.oy + e / f.w;
-    const bool in = mf_cin<T>(N, cx, cy);
-    const int v = in ? mf_variant<T>(N, cx, cy) : 0;
+  mf_rows(cta, f.w, f.w, [&](int i, int j) {
+    const int e = j * f.w + i, cx = f.ox + i, cy = f.oy + j;
+    const bool in = mf_cin(N, cx, cy);
+    const int v = in ? mf_variant(N, cx, cy) : 0;
     for (int k = 0; k < 3; ++k) {
       const T bv = in ? a.b[3 * ((size_t)cy * N + cx) + k] : (T)0;
       B[k * n + e] = bv;
@@ -557,7 +597,7 @@ __host__ __device__ void mfp_down_body(const MfPresArgs<T>& a, const MfCta& cta)
       Xc[k * n + e] = x0;
       Dc[k * n + e] = x0;
     }
-  }
+  });
   MF_SYNC();
   for (int s = 1; s < K; ++s) {
     mf_pres_cheb<T>(cta, tab, N, f, s, B, Xc, Dc, Xn, Dn, false, a.ch.c1[s - 1], a.ch.c2[s - 1]);
@@ -569,12 +609,12 @@ __host__ __device__ void mfp_down_body(const MfPresArgs<T>& a, const MfCta& cta)
   T* R = Dn;
   {
     const int m = f.w - 2 * K;
-    for (int i = cta.tid; i < m * m; i += cta.nthr) {
-      const int lx = K + i % m, ly = K + i / m, e = ly * f.w + lx;
+    mf_rows(cta, m, m, [&](int i, int j) {
+      const int lx = K + i, ly = K + j, e = ly * f.w + lx;
       const int cx = f.ox + lx, cy = f.oy + ly;
-      if (!mf_cin<T>(N, cx, cy)) {
+      if (!mf_cin(N, cx, cy)) {
         for (int k = 0; k < 3; ++k) R[k * n + e] = 0;
-        continue;
+        return;
       }
       T y[3];
       mf_pres_apply<T>(tab, Xc, f, N, cx, cy, e, y);
@@ -583,19 +623,19 @@ __host__ __device__ void mfp_down_body(const MfPresArgs<T>& a, const MfCta& cta)
         R[k * n + e] = B[k * n + e] - y[k];
         a.xout[id + k] = Xc[k * n + e];
       }
-    }
+    });
   }
   MF_SYNC();
   // restriction R = P^T to the tile's coarse cells: the children's
   // coefficients with the transposed P1disc blocks [1 sx sy; 0 1/2 0; 0 0 1/2]
-  for (int i = cta.tid; i < kMfTileP * kMfTileP; i += cta.nthr) {
-    const int X0 = CX0 + i % kMfTileP, Y0 = CY0 + i / kMfTileP;
-    if (X0 >= Nc || Y0 >= Nc) continue;
+  mf_rows(cta, kMfTileP, kMfTileP, [&](int i, int j) {
+    const int X0 = CX0 + i, Y0 = CY0 + j;
+    if (X0 >= Nc || Y0 >= Nc) return;
     T s0 = 0, s1 = 0, s2 = 0;
-    for (int j = 0; j < 4; ++j) {
-      const int cx = 2 * X0 + (j & 1), cy = 2 * Y0 + (j >> 1);
+    for (int q = 0; q < 4; ++q) {
+      const int cx = 2 * X0 + (q & 1), cy = 2 * Y0 + (q >> 1);
       const int e = (cy - f.oy) * f.w + (cx - f.ox);
-      const T sx = (j & 1) ? (T)0.25 : (T)-0.25, sy = (j >> 1) ? (T)0.25 : (T)-0.25;
+      const T sx = (q & 1) ? (T)0.25 : (T)-0.25, sy = (q >> 1) ? (T)0.25 : (T)-0.25;
       const T r0 = R[e], r1 = R[n + e], r2 = R[2 * n + e];
       s0 += r0;
       s1 += sx * r0 + (T)0.5 * r1;
@@ -613,13 +653,12 @@ __host__ __device__ void mfp_down_body(const MfPresArgs<T>& a, const MfCta& cta)
         a.ci.d[id + k] = d;
       }
     }
-  }
+  });
 }
 
 // up: grid (ceil(N / kMfTilePf))^2 over the fine cells
 template <class T>
 __host__ __device__ void mfp_up_body(const MfPresArgs<T>& a, const MfCta& cta) {
-  unsigned char* mf_sm = cta.sm;
   const int N = a.N, K = a.ch.k, Nc = N / 2;
   const int FX0 = cta.bx * kMfTilePf, FY0 = cta.by * kMfTilePf;
   MfCells f;
@@ -627,15 +666,15 @@ __host__ __device__ void mfp_up_body(const MfPresArgs<T>& a, const MfCta& cta) {
   f.oy = FY0 - K;
   f.w = kMfTilePf + 2 * K;
   const int n = f.n();
-  T* tab = reinterpret_cast<T*>(mf_sm);
+  T* tab = reinterpret_cast<T*>(cta.sm);
   T* B = tab + ((kMfPresTab + 3) & ~3);
   T *Xc = B + 3 * n, *Xn = B + 6 * n, *Dc = B + 9 * n, *Dn = B + 12 * n;
-  for (int i = cta.tid; i < kMfPresTab; i += cta.nthr) tab[i] = a.tab[i];
+  for (int t = cta.tid; t < kMfPresTab; t += cta.nthr) tab[t] = a.tab[t];
   // b and x + P x_coarse (each fine cell from its parent: [1 sx sy; 0 1/2 0; 0 0 1/2])
-  for (int e = cta.tid; e < n; e += cta.nthr) {
-    const int cx = f.ox + e % f.w, cy = f.oy + e / f.w;
+  mf_rows(cta, f.w, f.w, [&](int i, int j) {
+    const int e = j * f.w + i, cx = f.ox + i, cy = f.oy + j;
     T bv[3] = {0, 0, 0}, xv[3] = {0, 0, 0};
-    if (mf_cin<T>(N, cx, cy)) {
+    if (mf_cin(N, cx, cy)) {
       const size_t id = 3 * ((size_t)cy * N + cx), pc = 3 * ((size_t)(cy >> 1) * Nc + (cx >> 1));
       const T sx = (cx & 1) ? (T)0.25 : (T)-0.25, sy = (cy & 1) ? (T)0.25 : (T)-0.25;
       const T c0 = a.xc[pc], c1 = a.xc[pc + 1], c2 = a.xc[pc + 2];
@@ -649,7 +688,7 @@ __host__ __device__ void mfp_up_body(const MfPresArgs<T>& a, const MfCta& cta) {
       B[k * n + e] = bv[k];
       Xc[k * n + e] = xv[k];
     }
-  }
+  });
   MF_SYNC();
   const T* dv = tab + 729;
   for (int s = 0; s < K - 1; ++s) {
@@ -663,13 +702,13 @@ __host__ __device__ void mfp_up_body(const MfPresArgs<T>& a, const MfCta& cta) {
   const int s = K - 1;
   const T c1 = s == 0 ? (T)0 : a.ch.c1[s - 1], c2 = s == 0 ? a.ch.c0 : a.ch.c2[s - 1];
   const int m = f.w - 2 * K;
-  for (int i = cta.tid; i < m * m; i += cta.nthr) {
-    const int lx = K + i % m, ly = K + i / m, e = ly * f.w + lx;
+  mf_rows(cta, m, m, [&](int i, int j) {
+    const int lx = K + i, ly = K + j, e = ly * f.w + lx;
     const int cx = f.ox + lx, cy = f.oy + ly;
-    if (!mf_cin<T>(N, cx, cy)) continue;
+    if (!mf_cin(N, cx, cy)) return;
     T y[3];
     mf_pres_apply<T>(tab, Xc, f, N, cx, cy, e, y);
-    const int v = mf_variant<T>(N, cx, cy);
+    const int v = mf_variant(N, cx, cy);
     const size_t id = 3 * ((size_t)cy * N + cx);
     for (int k = 0; k < 3; ++k) {
       const T r = B[k * n + e] - y[k];
@@ -683,23 +722,24 @@ __host__ __device__ void mfp_up_body(const MfPresArgs<T>& a, const MfCta& cta) {
       }
       if (a.fin.acc) a.fin.acc[id + k] += a.fin.omega * ov;
     }
-  }
+  });
 }
 
 #ifdef __CUDACC__
-// The kernels: one CTA of kMfThreads threads per tile.
-#define FSI_MF_KERNEL(name, body, Args)                                      \
-  template <class T>                                                         \
-  __global__ void __launch_bounds__(kMfThreads) name(const __grid_constant__ Args<T> a) { \
-    asm volatile("griddepcontrol.wait;" ::: "memory");                       \
-    extern __shared__ __align__(16) unsigned char mf_smem[];                 \
-    const MfCta c{(int)blockIdx.x, (int)blockIdx.y, (int)threadIdx.x, (int)blockDim.x, mf_smem}; \
-    body<T>(a, c);                                                           \
+// The kernels: one CTA per tile.
+#define FSI_MF_KERNEL(name, body, Args, NT)                                                  \
+  template <class T>                                                                         \
+  __global__ void __launch_bounds__(NT) name(const __grid_constant__ Args<T> a) {            \
+    asm volatile("griddepcontrol.wait;" ::: "memory");                                       \
+    extern __shared__ __align__(16) unsigned char mf_smem[];                                 \
+    const MfCta c{(int)blockIdx.x, (int)blockIdx.y, (int)threadIdx.x, (int)blockDim.x,       \
+                  (int)blockDim.x, mf_smem};                                                 \
+    body<T>(a, c);                                                                           \
   }
-FSI_MF_KERNEL(k_mfu_down, mfu_down_body, MfVelArgs)
-FSI_MF_KERNEL(k_mfu_up, mfu_up_body, MfVelArgs)
-FSI_MF_KERNEL(k_mfp_down, mfp_down_body, MfPresArgs)
-FSI_MF_KERNEL(k_mfp_up, mfp_up_body, MfPresArgs)
+FSI_MF_KERNEL(k_mfu_down, mfu_down_body, MfVelArgs, kMfThreadsU)
+FSI_MF_KERNEL(k_mfu_up, mfu_up_body, MfVelArgs, kMfThreadsU)
+FSI_MF_KERNEL(k_mfp_down, mfp_down_body, MfPresArgs, kMfThreadsP)
+FSI_MF_KERNEL(k_mfp_up, mfp_up_body, MfPresArgs, kMfThreadsP)
 #undef FSI_MF_KERNEL
 #endif
 

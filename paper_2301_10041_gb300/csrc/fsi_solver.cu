@@ -526,13 +526,13 @@ static T* vcycle_mf(MG<T>& mg, int l, const T* b, cudaStream_t s, T* out, const 
     a.N = N; a.tab = L.mftab; a.ch = mf_cheb(L, mg.degree);
     a.b = b; a.xout = L.x2; a.bc = C.b; a.ci = ci;
     const unsigned g = nblk(N / 2, kMfTileP);
-    launch(k_mfp_down<T>, dim3(g, g), kMfThreads, mfp_down_smem<T>(mg.degree), s, a);
+    launch(k_mfp_down<T>, dim3(g, g), kMfThreadsP, mfp_down_smem<T>(mg.degree), s, a);
   } else {
     MfVelArgs<T> a;
     a.op = L.mfu; a.ch = mf_cheb(L, mg.degree);
     a.b = b; a.xout = L.x2; a.bc = C.b; a.ci = ci;
     const unsigned g = nblk(N, kMfTileU);
-    launch(k_mfu_down<T>, dim3(g, g), kMfThreads, mfu_down_smem<T>(mg.degree), s, a);
+    launch(k_mfu_down<T>, dim3(g, g), kMfThreadsU, mfu_down_smem<T>(mg.degree), s, a);
   }
   T* xc = C.mf ? vcycle_mf<T>(mg, l + 1, C.b, s, nullptr, nullptr) : vcycle<T>(mg, l + 1, s, (T*)nullptr);
   if (mg.pressure) {
@@ -541,14 +541,14 @@ static T* vcycle_mf(MG<T>& mg, int l, const T* b, cudaStream_t s, T* out, const 
     a.b = b; a.xpre = L.x2; a.xc = xc; a.xout = dst;
     if (fin) a.fin = *fin;
     const unsigned g = nblk(N, kMfTilePf);
-    launch(k_mfp_up<T>, dim3(g, g), kMfThreads, mfp_up_smem<T>(mg.degree), s, a);
+    launch(k_mfp_up<T>, dim3(g, g), kMfThreadsP, mfp_up_smem<T>(mg.degree), s, a);
   } else {
     MfVelArgs<T> a;
     a.op = L.mfu; a.ch = mf_cheb(L, mg.degree);
     a.b = b; a.xpre = L.x2; a.xc = xc; a.xout = dst;
     if (fin) a.fin = *fin;
     const unsigned g = nblk(2 * N, kMfTileUf);
-    launch(k_mfu_up<T>, dim3(g, g), kMfThreads, mfu_up_smem<T>(mg.degree), s, a);
+    launch(k_mfu_up<T>, dim3(g, g), kMfThreadsU, mfu_up_smem<T>(mg.degree), s, a);
   }
   return dst;
 }

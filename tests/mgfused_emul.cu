@@ -80,14 +80,15 @@ static std::vector<double> back(const std::vector<T>& v) {
   return std::vector<double>(v.begin(), v.end());
 }
 
-// run every CTA of a grid, each with its own exactly sized frame
+// run every CTA of a grid (vthr threads per CTA on the device) by one host
+// thread, each with its own exactly sized frame
 template <class Body>
-static void run_grid(int gx, int gy, size_t smem, Body body) {
+static void run_grid(int gx, int gy, int vthr, size_t smem, Body body) {
   for (int by = 0; by < gy; ++by)
     for (int bx = 0; bx < gx; ++bx) {
       std::vector<unsigned char>* buf = new std::vector<unsigned char>(smem);
       std::memset(buf->data(), 0xA5, smem);  // stale data: every read must be of a written entry
-      const MfCta c{bx, by, 0, 1, buf->data()};
+      const MfCta c{bx, by, 0, 1, vthr, buf->data()};
       body(c);
       delete buf;
     }
@@ -132,7 +133,7 @@ static void velocity(const HostSetup& hs, int l, int K, double tol, std::mt19937
   a.b = bT.data(); a.xout = xout.data(); a.bc = bc.data();
   a.ci.x = cix.data(); a.ci.d = cid.data(); a.ci.dinv = dcT.data(); a.ci.c0 = (T)c0c;
   const int gd = (N + kMfTileU - 1) / kMfTileU;
-  run_grid(gd, gd, mfu_down_smem<T>(K), [&](const MfCta& c) { mfu_down_body<T>(a, c); });
+  run_grid(gd, gd, kMfThreadsU, mfu_down_smem<T>(K), [&](const MfCta& c) { mfu_down_body<T>(a, c); });
   // reference: smoothing from x0 = c0 D^-1 b, then residual and restriction
   std::vector<double> x(n), d(n), Ax, r(n), Rr, xr;
   for (int i = 0; i < n; ++i) x[i] = d[i] = ch.c0 * H.dinvA[i] * b[i];
@@ -159,7 +160,7 @@ static void velocity(const HostSetup& hs, int l, int K, double tol, std::mt19937
   u.b = bT.data(); u.xpre = xpT.data(); u.xc = xcT.data(); u.xout = out.data(); u.bc = nullptr;
   u.fin.acc = accT.data(); u.fin.omega = (T)0.8;
   const int gu = (2 * N + kMfTileUf - 1) / kMfTileUf;
-  run_grid(gu, gu, mfu_up_smem<T>(K), [&](const MfCta& c) { mfu_up_body<T>(u, c); });
+  run_grid(gu, gu, kMfThreadsU, mfu_up_smem<T>(K), [&](const MfCta& c) { mfu_up_body<T>(u, c); });
   std::vector<double> Pxc;
   spmv(H.Pu, xc, Pxc);
   for (int i = 0; i < n; ++i) x[i] = xpre[i] + Pxc[i];
@@ -211,7 +212,7 @@ static void pressure(const HostSetup& hs, int l, int K, double tol, std::mt19937
   a.b = bT.data(); a.xout = xout.data(); a.bc = bc.data();
   a.ci.x = cix.data(); a.ci.d = cid.data(); a.ci.dinv = dcT.data(); a.ci.c0 = (T)c0c;
   const int gd = (N / 2 + kMfTileP - 1) / kMfTileP;
-  run_grid(gd, gd, mfp_down_smem<T>(K), [&](const MfCta& c) { mfp_down_body<T>(a, c); });
+  run_grid(gd, gd, kMfThreadsP, mfp_down_smem<T>(K), [&](const MfCta& c) { mfp_down_body<T>(a, c); });
   std::vector<double> x(n), d(n), Lx, r(n), Rr;
   for (int i = 0; i < n; ++i) x[i] = d[i] = ch.c0 * H.dinvL[i] * b[i];
   for (int s = 1; s < K; ++s) {
@@ -239,7 +240,7 @@ static void pressure(const HostSetup& hs, int l, int K, double tol, std::mt19937
   u.fin.sv = svT.data(); u.fin.smp = smpT.data(); u.fin.sout = sout.data();
   u.fin.snu = (T)0.07; u.fin.srdt = (T)325.0; u.fin.acc = accT.data(); u.fin.omega = (T)0.9;
   const int gu = (N + kMfTilePf - 1) / kMfTilePf;
-  run_grid(gu, gu, mfp_up_smem<T>(K), [&](const MfCta& c) { mfp_up_body<T>(u, c); });
+  run_grid(gu, gu, kMfThreadsP, mfp_up_smem<T>(K), [&](const MfCta& c) { mfp_up_body<T>(u, c); });
   std::vector<double> Pxc;
   spmv(H.Pp, xc, Pxc);
   for (int i = 0; i < n; ++i) x[i] = xpre[i] + Pxc[i];
