@@ -47,7 +47,9 @@ def workload():
 def workload_config(case):
     return {"workload": "cavity128_lid_disk7776: N=128 Q2/P1disc fluid, disk R=0.2 m=36 (3997 nodes, 7776 P1 "
                         "triangles), kappa=1e3, nu=0.01, rho=1, dt=1e-3, lid 1, rtol 1e-8",
-            "preconditioner": "block upper-triangular; Stokes block by 8 Richardson steps of a V-cycle pair",
+            "preconditioner": "block upper-triangular; Stokes block by %d Richardson steps of a V-cycle pair "
+                              "(Chebyshev degree %d)" % (STOKES_ITS, MG_DEGREE or 2),
+            "multigrid": {"fused_fine_levels": MG_FUSED == 0, "cluster": MG_CLUSTER},
             "restart": {"mixed": RESTART_MIXED, "fp64": RESTART}, "inner_rtol": INNER_RTOL,
             "N": case.N, "solid_nodes": int(case.ref_xy.shape[0]), "solid_tris": int(case.tris.shape[0]),
             "dofs": None, "l2": "flushed between timed steps (512 MiB write)"}
@@ -122,6 +124,7 @@ def _step_unchecked(prob):
 AUTOTUNE = 0     # 0: one fixed SpMV tile shape (faster inside a step); 1: the library's autotuner
 MG_FUSED = 0     # 0: fused matrix-free kernels on the finest FP32 multigrid levels; -1: per-level sparse kernels
 MG_CLUSTER = 0   # 0: coarse levels in one cluster launch; -1: per-level launches; n > 0: cluster levels <= n cells
+MG_DEGREE = 0    # Chebyshev degree of each multigrid smoothing (0: the library's default, 2)
 
 
 def arm_settings(precision):
@@ -132,8 +135,8 @@ def arm_settings(precision):
 
 
 def mg_settings():
-    """Multigrid kernel choice of the bench's arms (command-line switches)."""
-    return dict(mg_fused=MG_FUSED, mg_cluster=MG_CLUSTER)
+    """Multigrid kernel choice and smoothing degree of the bench's arms (command-line switches)."""
+    return dict(mg_fused=MG_FUSED, mg_cluster=MG_CLUSTER, mg_degree=MG_DEGREE)
 
 
 def time_arm(fsi, torch, case, precision, steps, warmup, stream, flush, precond=PRECOND, stokes_its=STOKES_ITS,
@@ -249,10 +252,12 @@ def run_ours(args):
     clocks.start()
     t_wall0 = time.perf_counter()
     first_m, first_d = [], []
-    prob_m, mixed = time_arm(fsi, torch, case, 1, args.steps, args.warmup, stream, flush, first_state=first_m)
+    prob_m, mixed = time_arm(fsi, torch, case, 1, args.steps, args.warmup, stream, flush, stokes_its=STOKES_ITS,
+                             first_state=first_m)
     t_wall1 = time.perf_counter()
     clk = clocks.stop()
-    prob_d, fp64 = time_arm(fsi, torch, case, 0, args.steps, args.warmup, stream, flush, first_state=first_d)
+    prob_d, fp64 = time_arm(fsi, torch, case, 0, args.steps, args.warmup, stream, flush, stokes_its=STOKES_ITS,
+                            first_state=first_d)
     roof = roofline(prob_m, args)
     if not args.no_large_n:
         roof["large_n"] = large_n_roofline(fsi, stream, local, roof["peak"], args.large_n)
@@ -771,6 +776,7 @@ def run_serve(args):
 
 
 def main():
+    global AUTOTUNE, MG_FUSED, MG_CLUSTER, MG_DEGREE, STOKES_ITS
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
@@ -800,6 +806,9 @@ def main():
                     help="batch and serve workloads: which precisions to run (mixed, fp64)")
     ap.add_argument("--no-mg-fused", action="store_true",
                     help="per-level sparse kernels on every multigrid level instead of the fused matrix-free ones")
+    ap.add_argument("--stokes-its", type=int, default=STOKES_ITS,
+                    help="Richardson steps on the Stokes block per preconditioner application (bench workload)")
+    ap.add_argument("--mg-degree", type=int, default=0, help="Chebyshev degree of each multigrid smoothing")
     ap.add_argument("--mg-cluster", type=int, default=0,
                     help="0: coarse levels in one cluster launch; -1: per-level launches; n > 0: only levels of at "
                          "most n cells a side in the cluster")
@@ -821,8 +830,9 @@ def main():
     ap.add_argument("--sweep-steps", type=int, default=2)
     ap.add_argument("--sweep-max-it", type=int, default=SWEEP_MAX_IT)
     args = ap.parse_args()
-    global AUTOTUNE, MG_FUSED, MG_CLUSTER
     MG_CLUSTER = args.mg_cluster
+    MG_DEGREE = args.mg_degree
+    STOKES_ITS = args.stokes_its
     if args.autotune:
         AUTOTUNE = 1
     if args.no_mg_fused:

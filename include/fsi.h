@@ -95,11 +95,13 @@ typedef struct fsi_params {
                           0 = 1 (the one-shot approximation); at most 16
                           (FSI_ERR_INVALID above) */
     double stokes_omega; /* damping of the Richardson corrections after the first; 0 = 1 */
-    int    mg_cluster; /* 0: the coarse multigrid levels whose operators fit in the
-                          shared memory of one thread-block cluster run as one
-                          cluster launch per V-cycle (same arithmetic); -1: one
-                          kernel launch per phase on every level; n > 0: as 0,
-                          with levels of at most n cells a side in the cluster */
+    int    mg_cluster; /* 0: automatic -- the coarse multigrid levels whose operators
+                          fit in the shared memory of one thread-block cluster
+                          run as one cluster launch per V-cycle (same
+                          arithmetic), except that an FP32 hierarchy with the
+                          fused matrix-free levels (mg_fused = 0) keeps only
+                          levels of at most 8 cells there; -1: no cluster; n > 0:
+                          levels of at most n cells a side in the cluster */
     int    coupling;   /* C_f(X^n) quadrature: 0 = the degree-4 6-point rule at
                           points located in the fluid grid; 1 = exact, by
                           intersecting each mapped solid triangle with the
