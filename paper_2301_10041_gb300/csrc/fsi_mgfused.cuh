@@ -70,14 +70,44 @@ struct MfCta {
 __host__ __device__ __forceinline__ int mf_min(int a, int b) { return a < b ? a : b; }
 __host__ __device__ __forceinline__ int mf_max(int a, int b) { return a > b ? a : b; }
 
-constexpr int kMfThreadsU = 512;  // velocity kernels
-constexpr int kMfThreadsP = 256;  // pressure kernels
 constexpr int kMfMaxDeg = 4;      // Chebyshev degrees 1..4 (the default is 2)
-constexpr int kMfTileU = 8;       // velocity down: coarse lattice nodes per tile side
-constexpr int kMfTileUf = 16;     // velocity up: fine lattice nodes per tile side
-constexpr int kMfTileP = 4;       // pressure down: coarse cells per tile side
-constexpr int kMfTilePf = 8;      // pressure up: fine cells per tile side
 constexpr int kMfPresTab = 9 * 9 * 9 + 9 * 3;  // pressure stencil table: blocks, then D^-1
+
+// Tile sizes by level, so that a launch has about 256 CTAs on the grids
+// down to 32 cells (on coarse levels a CTA's chain of phases is the launch's
+// time, so smaller tiles finish sooner even with more overlap work; on large
+// grids bigger tiles repeat less of their neighbours' work):
+//   velocity down: TC = clamp(N / 16, 2, 16) coarse lattice nodes a side,
+//   velocity up:   2 TC fine lattice nodes,
+//   pressure down: TP = clamp(N / 32, 1, 8) coarse cells,
+//   pressure up:   2 TP fine cells;
+// threads per CTA grow with the tile.
+__host__ __device__ __forceinline__ int mf_tile_u(int N) { return N >= 256 ? 16 : (N >= 128 ? 8 : (N >= 64 ? 4 : 2)); }
+__host__ __device__ __forceinline__ int mf_tile_p(int N) {
+  return N >= 256 ? 8 : (N >= 128 ? 4 : (N >= 64 ? 2 : 1));
+}
+constexpr int mf_threads_u(int tc) { return tc >= 8 ? 512 : (tc == 4 ? 256 : 128); }
+constexpr int mf_threads_p(int tp) { return tp >= 4 ? 256 : 128; }
+
+// Call f(integral_constant<tile>) with the tile of the level.
+template <class F>
+inline void mf_with_tile_u(int N, F&& f) {
+  switch (mf_tile_u(N)) {
+    case 16: f(std::integral_constant<int, 16>()); break;
+    case 8: f(std::integral_constant<int, 8>()); break;
+    case 4: f(std::integral_constant<int, 4>()); break;
+    default: f(std::integral_constant<int, 2>()); break;
+  }
+}
+template <class F>
+inline void mf_with_tile_p(int N, F&& f) {
+  switch (mf_tile_p(N)) {
+    case 8: f(std::integral_constant<int, 8>()); break;
+    case 4: f(std::integral_constant<int, 4>()); break;
+    case 2: f(std::integral_constant<int, 2>()); break;
+    default: f(std::integral_constant<int, 1>()); break;
+  }
+}
 
 template <class T>
 struct MfCheb {
@@ -300,17 +330,17 @@ __host__ __device__ __forceinline__ void mf_vel_cheb(const MfCta& cta, const MfV
   });
 }
 
-// down: grid (ceil(N / kMfTileU))^2 over the coarse lattice [0, N)^2
-template <class T>
+// down: grid (ceil(N / TC))^2 over the coarse lattice [0, N)^2
+template <class T, int TC>
 __host__ __device__ void mfu_down_body(const MfVelArgs<T>& a, const MfCta& cta) {
   using T2 = typename Vec2<T>::type;
   const MfVelOp<T>& op = a.op;
   const int N = op.N, K = a.ch.k;
-  const int CX0 = cta.bx * kMfTileU, CY0 = cta.by * kMfTileU;
+  const int CX0 = cta.bx * TC, CY0 = cta.by * TC;
   MfFrame f;
   f.ox = 2 * CX0 - 4 - 2 * K;
   f.oy = 2 * CY0 - 4 - 2 * K;
-  f.pw = f.ph = (2 * kMfTileU + 8 + 4 * K) / 2;
+  f.pw = f.ph = (2 * TC + 8 + 4 * K) / 2;
   const int nf = 4 * f.plane();
   T2* B = reinterpret_cast<T2*>(cta.sm);
   T2 *Xc = B + nf, *Xn = B + 2 * nf, *Dc = B + 3 * nf, *Dn = B + 4 * nf;   // current / next iterate
@@ -352,7 +382,7 @@ __host__ __device__ void mfu_down_body(const MfVelArgs<T>& a, const MfCta& cta) 
       mf_vel_apply<T, TAU>(op, Xc, f, px, py, a0, a1);
       r.x = B[e].x - a0;
       r.y = B[e].y - a1;
-      if (px >= o && px < o + kMfTileU && py >= o && py < o + kMfTileU)
+      if (px >= o && px < o + TC && py >= o && py < o + TC)
         *reinterpret_cast<T2*>(a.xout + 2 * (size_t)mf_vnode_t<TAU>(N, ix, iy)) = Xc[e];
     }
     R[e] = r;
@@ -363,7 +393,7 @@ __host__ __device__ void mfu_down_body(const MfVelArgs<T>& a, const MfCta& cta) 
   // quadratic of node X there, L0(|d| / 4) at a cell corner, L1((d + 2) / 4)
   // at an edge or cell midpoint (|d| <= 1)
   const int Nc = N / 2;
-  mf_rows(cta, kMfTileU, kMfTileU, [&](int i, int j) {
+  mf_rows(cta, TC, TC, [&](int i, int j) {
     const int X0 = CX0 + i, Y0 = CY0 + j;
     if (!mf_vinterior(Nc, X0, Y0)) return;
     T s0 = 0, s1 = 0;
@@ -395,17 +425,18 @@ __host__ __device__ void mfu_down_body(const MfVelArgs<T>& a, const MfCta& cta) 
   });
 }
 
-// up: grid (ceil(2N / kMfTileUf))^2 over the fine lattice [0, 2N)^2
-template <class T>
+// up: grid (ceil(2N / (2 TC)))^2 over the fine lattice [0, 2N)^2
+template <class T, int TC>
 __host__ __device__ void mfu_up_body(const MfVelArgs<T>& a, const MfCta& cta) {
   using T2 = typename Vec2<T>::type;
+  constexpr int TF = 2 * TC;
   const MfVelOp<T>& op = a.op;
   const int N = op.N, K = a.ch.k, Nc = N / 2;
-  const int FX0 = cta.bx * kMfTileUf, FY0 = cta.by * kMfTileUf;
+  const int FX0 = cta.bx * TF, FY0 = cta.by * TF;
   MfFrame f;
   f.ox = FX0 - 2 * K;
   f.oy = FY0 - 2 * K;
-  f.pw = f.ph = (kMfTileUf + 4 * K) / 2;
+  f.pw = f.ph = (TF + 4 * K) / 2;
   // coarse lattice frame covering the prolongation taps of the fine frame
   MfFrame g;
   {
@@ -570,15 +601,15 @@ __host__ __device__ __forceinline__ void mf_pres_cheb(const MfCta& cta, const T*
   });
 }
 
-// down: grid (ceil(Nc / kMfTileP))^2 over the coarse cells
-template <class T>
+// down: grid (ceil(Nc / TP))^2 over the coarse cells
+template <class T, int TP>
 __host__ __device__ void mfp_down_body(const MfPresArgs<T>& a, const MfCta& cta) {
   const int N = a.N, K = a.ch.k, Nc = N / 2;
-  const int CX0 = cta.bx * kMfTileP, CY0 = cta.by * kMfTileP;
+  const int CX0 = cta.bx * TP, CY0 = cta.by * TP;
   MfCells f;
   f.ox = 2 * CX0 - K;
   f.oy = 2 * CY0 - K;
-  f.w = 2 * kMfTileP + 2 * K;
+  f.w = 2 * TP + 2 * K;
   const int n = f.n();
   T* tab = reinterpret_cast<T*>(cta.sm);
   T* B = tab + ((kMfPresTab + 3) & ~3);
@@ -628,7 +659,7 @@ __host__ __device__ void mfp_down_body(const MfPresArgs<T>& a, const MfCta& cta)
   MF_SYNC();
   // restriction R = P^T to the tile's coarse cells: the children's
   // coefficients with the transposed P1disc blocks [1 sx sy; 0 1/2 0; 0 0 1/2]
-  mf_rows(cta, kMfTileP, kMfTileP, [&](int i, int j) {
+  mf_rows(cta, TP, TP, [&](int i, int j) {
     const int X0 = CX0 + i, Y0 = CY0 + j;
     if (X0 >= Nc || Y0 >= Nc) return;
     T s0 = 0, s1 = 0, s2 = 0;
@@ -656,15 +687,16 @@ __host__ __device__ void mfp_down_body(const MfPresArgs<T>& a, const MfCta& cta)
   });
 }
 
-// up: grid (ceil(N / kMfTilePf))^2 over the fine cells
-template <class T>
+// up: grid (ceil(N / (2 TP)))^2 over the fine cells
+template <class T, int TP>
 __host__ __device__ void mfp_up_body(const MfPresArgs<T>& a, const MfCta& cta) {
+  constexpr int TPF = 2 * TP;
   const int N = a.N, K = a.ch.k, Nc = N / 2;
-  const int FX0 = cta.bx * kMfTilePf, FY0 = cta.by * kMfTilePf;
+  const int FX0 = cta.bx * TPF, FY0 = cta.by * TPF;
   MfCells f;
   f.ox = FX0 - K;
   f.oy = FY0 - K;
-  f.w = kMfTilePf + 2 * K;
+  f.w = TPF + 2 * K;
   const int n = f.n();
   T* tab = reinterpret_cast<T*>(cta.sm);
   T* B = tab + ((kMfPresTab + 3) & ~3);
@@ -726,43 +758,44 @@ __host__ __device__ void mfp_up_body(const MfPresArgs<T>& a, const MfCta& cta) {
 }
 
 #ifdef __CUDACC__
-// The kernels: one CTA per tile.
-#define FSI_MF_KERNEL(name, body, Args, NT)                                                  \
-  template <class T>                                                                         \
+// The kernels: one CTA per tile, NT threads.
+#define FSI_MF_KERNEL(name, body, Args)                                                      \
+  template <class T, int TILE, int NT>                                                       \
   __global__ void __launch_bounds__(NT) name(const __grid_constant__ Args<T> a) {            \
     asm volatile("griddepcontrol.wait;" ::: "memory");                                       \
     extern __shared__ __align__(16) unsigned char mf_smem[];                                 \
-    const MfCta c{(int)blockIdx.x, (int)blockIdx.y, (int)threadIdx.x, (int)blockDim.x,       \
-                  (int)blockDim.x, mf_smem};                                                 \
-    body<T>(a, c);                                                                           \
+    const MfCta c{(int)blockIdx.x, (int)blockIdx.y, (int)threadIdx.x, (int)blockDim.x, NT,   \
+                  mf_smem};                                                                  \
+    body<T, TILE>(a, c);                                                                     \
   }
-FSI_MF_KERNEL(k_mfu_down, mfu_down_body, MfVelArgs, kMfThreadsU)
-FSI_MF_KERNEL(k_mfu_up, mfu_up_body, MfVelArgs, kMfThreadsU)
-FSI_MF_KERNEL(k_mfp_down, mfp_down_body, MfPresArgs, kMfThreadsP)
-FSI_MF_KERNEL(k_mfp_up, mfp_up_body, MfPresArgs, kMfThreadsP)
+FSI_MF_KERNEL(k_mfu_down, mfu_down_body, MfVelArgs)
+FSI_MF_KERNEL(k_mfu_up, mfu_up_body, MfVelArgs)
+FSI_MF_KERNEL(k_mfp_down, mfp_down_body, MfPresArgs)
+FSI_MF_KERNEL(k_mfp_up, mfp_up_body, MfPresArgs)
 #undef FSI_MF_KERNEL
 #endif
 
-// shared memory of one launch (bytes)
+// shared memory of one launch (bytes) for tile tc (velocity: coarse lattice
+// nodes; pressure: coarse cells) and Chebyshev degree K
 template <class T>
-inline size_t mfu_down_smem(int K) {
-  const int w = 2 * kMfTileU + 8 + 4 * K;
+inline size_t mfu_down_smem(int tc, int K) {
+  const int w = 2 * tc + 8 + 4 * K;
   return 6 * (size_t)w * w * 2 * sizeof(T);
 }
 template <class T>
-inline size_t mfu_up_smem(int K) {
-  const int w = kMfTileUf + 4 * K;
+inline size_t mfu_up_smem(int tc, int K) {
+  const int w = 2 * tc + 4 * K;
   const int gw = 2 * ((w + 3) / 4 + 2);   // coarse frame side (upper bound)
   return (5 * (size_t)w * w + (size_t)gw * gw) * 2 * sizeof(T);
 }
 template <class T>
-inline size_t mfp_down_smem(int K) {
-  const int w = 2 * kMfTileP + 2 * K;
+inline size_t mfp_down_smem(int tp, int K) {
+  const int w = 2 * tp + 2 * K;
   return (((kMfPresTab + 3) & ~3) + 15 * (size_t)w * w) * sizeof(T);
 }
 template <class T>
-inline size_t mfp_up_smem(int K) {
-  const int w = kMfTilePf + 2 * K;
+inline size_t mfp_up_smem(int tp, int K) {
+  const int w = 2 * tp + 2 * K;
   return (((kMfPresTab + 3) & ~3) + 15 * (size_t)w * w) * sizeof(T);
 }
 

@@ -478,14 +478,22 @@ static void select_mf(MG<T>& mg, const HostSetup& hs, int mg_fused, bool count_o
   if (any && !count_only) {
     static std::once_flag once;
     std::call_once(once, [] {
-      CK(cudaFuncSetAttribute(k_mfu_down<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)mfu_down_smem<float>(kMfMaxDeg)));
-      CK(cudaFuncSetAttribute(k_mfu_up<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)mfu_up_smem<float>(kMfMaxDeg)));
-      CK(cudaFuncSetAttribute(k_mfp_down<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)mfp_down_smem<float>(kMfMaxDeg)));
-      CK(cudaFuncSetAttribute(k_mfp_up<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)mfp_up_smem<float>(kMfMaxDeg)));
+      auto vel = [](auto tc) {
+        constexpr int TC = decltype(tc)::value, NT = mf_threads_u(TC);
+        CK(cudaFuncSetAttribute(k_mfu_down<float, TC, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)mfu_down_smem<float>(TC, kMfMaxDeg)));
+        CK(cudaFuncSetAttribute(k_mfu_up<float, TC, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)mfu_up_smem<float>(TC, kMfMaxDeg)));
+      };
+      auto pres = [](auto tp) {
+        constexpr int TP = decltype(tp)::value, NT = mf_threads_p(TP);
+        CK(cudaFuncSetAttribute(k_mfp_down<float, TP, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)mfp_down_smem<float>(TP, kMfMaxDeg)));
+        CK(cudaFuncSetAttribute(k_mfp_up<float, TP, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)mfp_up_smem<float>(TP, kMfMaxDeg)));
+      };
+      for (int N : {16, 64, 128, 256}) mf_with_tile_u(N, vel);
+      for (int N : {16, 64, 128, 256}) mf_with_tile_p(N, pres);
     });
   }
 }
@@ -521,34 +529,47 @@ static T* vcycle_mf(MG<T>& mg, int l, const T* b, cudaStream_t s, T* out, const 
   if (c_sell) { ci.x = C.x; ci.d = C.d; ci.dinv = C.dinv; ci.c0 = (T)C.ch.c0; }
   T* dst = out ? out : L.x;
   if (dst == L.x2) throw std::logic_error("vcycle_mf: the result may not overwrite the pre-smoothed iterate");
+  const int K = mg.degree;
   if (mg.pressure) {
     MfPresArgs<T> a;
-    a.N = N; a.tab = L.mftab; a.ch = mf_cheb(L, mg.degree);
+    a.N = N; a.tab = L.mftab; a.ch = mf_cheb(L, K);
     a.b = b; a.xout = L.x2; a.bc = C.b; a.ci = ci;
-    const unsigned g = nblk(N / 2, kMfTileP);
-    launch(k_mfp_down<T>, dim3(g, g), kMfThreadsP, mfp_down_smem<T>(mg.degree), s, a);
+    mf_with_tile_p(N, [&](auto tp) {
+      constexpr int TP = decltype(tp)::value, NT = mf_threads_p(TP);
+      const unsigned g = nblk(N / 2, TP);
+      launch(k_mfp_down<T, TP, NT>, dim3(g, g), NT, mfp_down_smem<T>(TP, K), s, a);
+    });
   } else {
     MfVelArgs<T> a;
-    a.op = L.mfu; a.ch = mf_cheb(L, mg.degree);
+    a.op = L.mfu; a.ch = mf_cheb(L, K);
     a.b = b; a.xout = L.x2; a.bc = C.b; a.ci = ci;
-    const unsigned g = nblk(N, kMfTileU);
-    launch(k_mfu_down<T>, dim3(g, g), kMfThreadsU, mfu_down_smem<T>(mg.degree), s, a);
+    mf_with_tile_u(N, [&](auto tc) {
+      constexpr int TC = decltype(tc)::value, NT = mf_threads_u(TC);
+      const unsigned g = nblk(N, TC);
+      launch(k_mfu_down<T, TC, NT>, dim3(g, g), NT, mfu_down_smem<T>(TC, K), s, a);
+    });
   }
   T* xc = C.mf ? vcycle_mf<T>(mg, l + 1, C.b, s, nullptr, nullptr) : vcycle<T>(mg, l + 1, s, (T*)nullptr);
   if (mg.pressure) {
     MfPresArgs<T> a;
-    a.N = N; a.tab = L.mftab; a.ch = mf_cheb(L, mg.degree);
+    a.N = N; a.tab = L.mftab; a.ch = mf_cheb(L, K);
     a.b = b; a.xpre = L.x2; a.xc = xc; a.xout = dst;
     if (fin) a.fin = *fin;
-    const unsigned g = nblk(N, kMfTilePf);
-    launch(k_mfp_up<T>, dim3(g, g), kMfThreadsP, mfp_up_smem<T>(mg.degree), s, a);
+    mf_with_tile_p(N, [&](auto tp) {
+      constexpr int TP = decltype(tp)::value, NT = mf_threads_p(TP);
+      const unsigned g = nblk(N, 2 * TP);
+      launch(k_mfp_up<T, TP, NT>, dim3(g, g), NT, mfp_up_smem<T>(TP, K), s, a);
+    });
   } else {
     MfVelArgs<T> a;
-    a.op = L.mfu; a.ch = mf_cheb(L, mg.degree);
+    a.op = L.mfu; a.ch = mf_cheb(L, K);
     a.b = b; a.xpre = L.x2; a.xc = xc; a.xout = dst;
     if (fin) a.fin = *fin;
-    const unsigned g = nblk(2 * N, kMfTileUf);
-    launch(k_mfu_up<T>, dim3(g, g), kMfThreadsU, mfu_up_smem<T>(mg.degree), s, a);
+    mf_with_tile_u(N, [&](auto tc) {
+      constexpr int TC = decltype(tc)::value, NT = mf_threads_u(TC);
+      const unsigned g = nblk(2 * N, 2 * TC);
+      launch(k_mfu_up<T, TC, NT>, dim3(g, g), NT, mfu_up_smem<T>(TC, K), s, a);
+    });
   }
   return dst;
 }

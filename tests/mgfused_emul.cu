@@ -132,8 +132,11 @@ static void velocity(const HostSetup& hs, int l, int K, double tol, std::mt19937
   const double c0c = 0.37;
   a.b = bT.data(); a.xout = xout.data(); a.bc = bc.data();
   a.ci.x = cix.data(); a.ci.d = cid.data(); a.ci.dinv = dcT.data(); a.ci.c0 = (T)c0c;
-  const int gd = (N + kMfTileU - 1) / kMfTileU;
-  run_grid(gd, gd, kMfThreadsU, mfu_down_smem<T>(K), [&](const MfCta& c) { mfu_down_body<T>(a, c); });
+  mf_with_tile_u(N, [&](auto tc) {   // the tile the library uses on this level
+    constexpr int TC = decltype(tc)::value;
+    const int gd = (N + TC - 1) / TC;
+    run_grid(gd, gd, mf_threads_u(TC), mfu_down_smem<T>(TC, K), [&](const MfCta& c) { mfu_down_body<T, TC>(a, c); });
+  });
   // reference: smoothing from x0 = c0 D^-1 b, then residual and restriction
   std::vector<double> x(n), d(n), Ax, r(n), Rr, xr;
   for (int i = 0; i < n; ++i) x[i] = d[i] = ch.c0 * H.dinvA[i] * b[i];
@@ -159,8 +162,11 @@ static void velocity(const HostSetup& hs, int l, int K, double tol, std::mt19937
   u.ci = MfInit<T>();
   u.b = bT.data(); u.xpre = xpT.data(); u.xc = xcT.data(); u.xout = out.data(); u.bc = nullptr;
   u.fin.acc = accT.data(); u.fin.omega = (T)0.8;
-  const int gu = (2 * N + kMfTileUf - 1) / kMfTileUf;
-  run_grid(gu, gu, kMfThreadsU, mfu_up_smem<T>(K), [&](const MfCta& c) { mfu_up_body<T>(u, c); });
+  mf_with_tile_u(N, [&](auto tc) {
+    constexpr int TC = decltype(tc)::value;
+    const int gu = (2 * N + 2 * TC - 1) / (2 * TC);
+    run_grid(gu, gu, mf_threads_u(TC), mfu_up_smem<T>(TC, K), [&](const MfCta& c) { mfu_up_body<T, TC>(u, c); });
+  });
   std::vector<double> Pxc;
   spmv(H.Pu, xc, Pxc);
   for (int i = 0; i < n; ++i) x[i] = xpre[i] + Pxc[i];
@@ -211,8 +217,11 @@ static void pressure(const HostSetup& hs, int l, int K, double tol, std::mt19937
   const double c0c = 0.41;
   a.b = bT.data(); a.xout = xout.data(); a.bc = bc.data();
   a.ci.x = cix.data(); a.ci.d = cid.data(); a.ci.dinv = dcT.data(); a.ci.c0 = (T)c0c;
-  const int gd = (N / 2 + kMfTileP - 1) / kMfTileP;
-  run_grid(gd, gd, kMfThreadsP, mfp_down_smem<T>(K), [&](const MfCta& c) { mfp_down_body<T>(a, c); });
+  mf_with_tile_p(N, [&](auto tp) {
+    constexpr int TP = decltype(tp)::value;
+    const int gd = (N / 2 + TP - 1) / TP;
+    run_grid(gd, gd, mf_threads_p(TP), mfp_down_smem<T>(TP, K), [&](const MfCta& c) { mfp_down_body<T, TP>(a, c); });
+  });
   std::vector<double> x(n), d(n), Lx, r(n), Rr;
   for (int i = 0; i < n; ++i) x[i] = d[i] = ch.c0 * H.dinvL[i] * b[i];
   for (int s = 1; s < K; ++s) {
@@ -239,8 +248,11 @@ static void pressure(const HostSetup& hs, int l, int K, double tol, std::mt19937
   u.b = bT.data(); u.xpre = xpT.data(); u.xc = xcT.data(); u.xout = out.data(); u.bc = nullptr;
   u.fin.sv = svT.data(); u.fin.smp = smpT.data(); u.fin.sout = sout.data();
   u.fin.snu = (T)0.07; u.fin.srdt = (T)325.0; u.fin.acc = accT.data(); u.fin.omega = (T)0.9;
-  const int gu = (N + kMfTilePf - 1) / kMfTilePf;
-  run_grid(gu, gu, kMfThreadsP, mfp_up_smem<T>(K), [&](const MfCta& c) { mfp_up_body<T>(u, c); });
+  mf_with_tile_p(N, [&](auto tp) {
+    constexpr int TP = decltype(tp)::value;
+    const int gu = (N + 2 * TP - 1) / (2 * TP);
+    run_grid(gu, gu, mf_threads_p(TP), mfp_up_smem<T>(TP, K), [&](const MfCta& c) { mfp_up_body<T, TP>(u, c); });
+  });
   std::vector<double> Pxc;
   spmv(H.Pp, xc, Pxc);
   for (int i = 0; i < n; ++i) x[i] = xpre[i] + Pxc[i];
@@ -263,7 +275,7 @@ static void pressure(const HostSetup& hs, int l, int K, double tol, std::mt19937
 }
 
 int main(int argc, char** argv) {
-  std::vector<int> grids{16, 24, 48, 128};
+  std::vector<int> grids{16, 24, 48, 128, 256};
   if (argc > 1) {
     grids.clear();
     for (int i = 1; i < argc; ++i) grids.push_back(std::atoi(argv[i]));
@@ -278,7 +290,7 @@ int main(int argc, char** argv) {
     for (int l = 0; l + 1 < (int)hs.levels.size() && l < 2; ++l) {
       if (!hs.levels[l].mf) continue;
       for (int K = 1; K <= kMfMaxDeg; ++K) {
-        if (N > 48 && K != 2) continue;  // the largest grid only at the default degree
+        if (N > 48 && K != 2) continue;  // the largest grids only at the default degree
         velocity<double>(hs, l, K, 1e-12, rng);
         pressure<double>(hs, l, K, 1e-12, rng);
         velocity<float>(hs, l, K, 1e-5, rng);
