@@ -55,11 +55,12 @@ def test_fused_levels_match_per_level_kernels(fsi, name, precond, stokes_its, mg
     off = fsi.problem_from_case(case, mg_fused=-1, **kw)
     on.assemble_step()
     off.assemble_step()
-    # with the cluster off every level of 16 cells or more above the coarsest is fused
+    # with the cluster off on both sides every level of 16 cells or more above
+    # the coarsest takes two fused launches instead of the per-level kernels
+    # (with mg_cluster = 0 the per-level side may hold its coarse levels in
+    # one cluster launch, the fused side does not)
     if mg_cluster == -1:
         assert on.graph_kernel_counts()[3] < off.graph_kernel_counts()[3]
-    else:
-        assert on.graph_kernel_counts()[3] <= off.graph_kernel_counts()[3]
     rng = np.random.default_rng(17)
     for _ in range(2):
         v = rng.standard_normal(on.n)
