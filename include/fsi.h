@@ -270,11 +270,20 @@ int fsi_graph_kernel_counts(const fsi_problem* p, int* counts);
  * hierarchy's coarse levels alone (FSI_ERR_INVALID when they run as
  * per-level kernels); 8: the C_f row assembly by located points (coupling
  * 0 only), 9: by mesh intersection (coupling 1 only), both on the current
- * X^n (L2 evicted; bytes = 0).  avg_ms: mean launch time; bytes:
- * algorithmic bytes of one launch (stored blocks and indices without
- * padding, each vector once).  Allocates
- * and frees a 256 MiB scratch buffer. */
+ * X^n (L2 evicted; bytes = 0); 10 .. 13 (precision 1, fused finest levels
+ * only, else FSI_ERR_INVALID): the fused matrix-free launch of the finest
+ * level, velocity down (pre-smoothing, residual, restriction) and up
+ * (prolongation, post-smoothing), pressure down and up, L2 evicted.
+ * avg_ms: mean launch time; bytes: algorithmic bytes of one launch (stored
+ * blocks and indices without padding, each vector once).  Allocates and
+ * frees a 256 MiB scratch buffer. */
 int fsi_time_kernel(fsi_problem* p, int which, int reps, double* avg_ms, double* bytes);
+
+/* Measurement hook: algorithmic floating-point operations of one launch of
+ * kernel `which` (10 .. 13 of fsi_time_kernel): two per stored scalar entry
+ * of each operator and transfer application, six per unknown per smoothing
+ * step, without the work the tiles repeat on their overlaps. */
+int fsi_kernel_flops(fsi_problem* p, int which, double* flops);
 
 /* Right-hand side of the last fsi_assemble_step in block order (n_total). */
 int fsi_get_rhs(fsi_problem* p, double* b);

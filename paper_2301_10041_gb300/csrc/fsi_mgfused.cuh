@@ -73,19 +73,16 @@ __host__ __device__ __forceinline__ int mf_max(int a, int b) { return a > b ? a 
 constexpr int kMfMaxDeg = 4;      // Chebyshev degrees 1..4 (the default is 2)
 constexpr int kMfPresTab = 9 * 9 * 9 + 9 * 3;  // pressure stencil table: blocks, then D^-1
 
-// Tile sizes by level, so that a launch has about 256 CTAs on the grids
-// down to 32 cells (on coarse levels a CTA's chain of phases is the launch's
-// time, so smaller tiles finish sooner even with more overlap work; on large
-// grids bigger tiles repeat less of their neighbours' work):
-//   velocity down: TC = clamp(N / 16, 2, 16) coarse lattice nodes a side,
-//   velocity up:   2 TC fine lattice nodes,
-//   pressure down: TP = clamp(N / 32, 1, 8) coarse cells,
-//   pressure up:   2 TP fine cells;
-// threads per CTA grow with the tile.
-__host__ __device__ __forceinline__ int mf_tile_u(int N) { return N >= 256 ? 16 : (N >= 128 ? 8 : (N >= 64 ? 4 : 2)); }
-__host__ __device__ __forceinline__ int mf_tile_p(int N) {
-  return N >= 256 ? 8 : (N >= 128 ? 4 : (N >= 64 ? 2 : 1));
-}
+// Tile sizes by level: velocity down TC coarse lattice nodes a side (up:
+// 2 TC fine lattice nodes), pressure down TP coarse cells (up: 2 TP fine
+// cells).  A launch's time on these grids is mostly its fixed cost (launch,
+// one global round trip, the barriers between its phases), not the work of
+// the overlaps the tiles repeat: on the 128 x 128 cavity, tiles shrunk to
+// keep 256 CTAs on every level measured slower (9.8 against 10.7 steps/s)
+// than one tile size for all levels.  From 512 cells on, the larger tiles
+// repeat less of their neighbours' work.
+__host__ __device__ __forceinline__ int mf_tile_u(int N) { return N >= 512 ? 16 : 8; }
+__host__ __device__ __forceinline__ int mf_tile_p(int N) { return N >= 512 ? 8 : 4; }
 constexpr int mf_threads_u(int tc) { return tc >= 8 ? 512 : (tc == 4 ? 256 : 128); }
 constexpr int mf_threads_p(int tp) { return tp >= 4 ? 256 : 128; }
 

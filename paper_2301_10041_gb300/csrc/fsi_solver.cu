@@ -492,8 +492,8 @@ static void select_mf(MG<T>& mg, const HostSetup& hs, int mg_fused, bool count_o
         CK(cudaFuncSetAttribute(k_mfp_up<float, TP, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)mfp_up_smem<float>(TP, kMfMaxDeg)));
       };
-      for (int N : {16, 64, 128, 256}) mf_with_tile_u(N, vel);
-      for (int N : {16, 64, 128, 256}) mf_with_tile_p(N, pres);
+      for (int N : {16, 512}) mf_with_tile_u(N, vel);
+      for (int N : {16, 512}) mf_with_tile_p(N, pres);
     });
   }
 }
@@ -513,23 +513,20 @@ static MfCheb<T> mf_cheb(const MGLevel<T>& L, int degree) {
 template <class T>
 static T* vcycle(MG<T>& mg, int l, cudaStream_t s, T* out, const SpmvArgs<T>* fin = nullptr, bool* fused = nullptr);
 
-// One V-cycle from fused level l (mg.lv[l].mf) with right-hand side b: the
-// down launch (pre-smoothing, residual, restriction), the coarser levels, the
-// up launch (prolongation, post-smoothing, epilogue).  The pre-smoothed
-// iterate lives in L.x2; the result goes to `out`, else to L.x (never L.x2).
+// The down launch of fused level l: pre-smoothing from x0 = c0 D^-1 b, the
+// residual and its restriction; the pre-smoothed iterate goes to L.x2, the
+// coarse right-hand side to C.b (and the coarse smoother start when the next
+// level runs the per-level sparse kernels).
 template <class T>
-static T* vcycle_mf(MG<T>& mg, int l, const T* b, cudaStream_t s, T* out, const MfFin<T>* fin) {
+static void mf_down_launch(MG<T>& mg, int l, const T* b, cudaStream_t s) {
   const int last = (int)mg.lv.size() - 1;
   MGLevel<T>& L = mg.lv[l];
   MGLevel<T>& C = mg.lv[l + 1];
   const bool c_cluster = mg.cl.on && l + 1 == mg.cl.lc;
   const bool c_sell = !C.mf && !c_cluster && l + 1 != last;
-  const int N = L.N;
+  const int N = L.N, K = mg.degree;
   MfInit<T> ci;
   if (c_sell) { ci.x = C.x; ci.d = C.d; ci.dinv = C.dinv; ci.c0 = (T)C.ch.c0; }
-  T* dst = out ? out : L.x;
-  if (dst == L.x2) throw std::logic_error("vcycle_mf: the result may not overwrite the pre-smoothed iterate");
-  const int K = mg.degree;
   if (mg.pressure) {
     MfPresArgs<T> a;
     a.N = N; a.tab = L.mftab; a.ch = mf_cheb(L, K);
@@ -549,7 +546,15 @@ static T* vcycle_mf(MG<T>& mg, int l, const T* b, cudaStream_t s, T* out, const 
       launch(k_mfu_down<T, TC, NT>, dim3(g, g), NT, mfu_down_smem<T>(TC, K), s, a);
     });
   }
-  T* xc = C.mf ? vcycle_mf<T>(mg, l + 1, C.b, s, nullptr, nullptr) : vcycle<T>(mg, l + 1, s, (T*)nullptr);
+}
+
+// The up launch of fused level l: x = L.x2 + P xc, post-smoothing, result to
+// dst (never L.x2), with the epilogue fin.
+template <class T>
+static void mf_up_launch(MG<T>& mg, int l, const T* b, const T* xc, T* dst, const MfFin<T>* fin, cudaStream_t s) {
+  MGLevel<T>& L = mg.lv[l];
+  if (dst == L.x2) throw std::logic_error("mf_up_launch: the result may not overwrite the pre-smoothed iterate");
+  const int N = L.N, K = mg.degree;
   if (mg.pressure) {
     MfPresArgs<T> a;
     a.N = N; a.tab = L.mftab; a.ch = mf_cheb(L, K);
@@ -571,7 +576,42 @@ static T* vcycle_mf(MG<T>& mg, int l, const T* b, cudaStream_t s, T* out, const 
       launch(k_mfu_up<T, TC, NT>, dim3(g, g), NT, mfu_up_smem<T>(TC, K), s, a);
     });
   }
+}
+
+// One V-cycle from fused level l (mg.lv[l].mf) with right-hand side b: the
+// down launch, the coarser levels, the up launch.  The result goes to `out`,
+// else to L.x.
+template <class T>
+static T* vcycle_mf(MG<T>& mg, int l, const T* b, cudaStream_t s, T* out, const MfFin<T>* fin) {
+  MGLevel<T>& L = mg.lv[l];
+  MGLevel<T>& C = mg.lv[l + 1];
+  T* dst = out ? out : L.x;
+  mf_down_launch<T>(mg, l, b, s);
+  T* xc = C.mf ? vcycle_mf<T>(mg, l + 1, C.b, s, nullptr, nullptr) : vcycle<T>(mg, l + 1, s, (T*)nullptr);
+  mf_up_launch<T>(mg, l, b, xc, dst, fin, s);
   return dst;
+}
+
+// Algorithmic work of the fused launches of level l (not counting the work
+// the tiles repeat on their overlaps): bytes of the vectors read and written
+// once, and floating-point operations of the K operator applications (two per
+// stored scalar entry), the transfer (two per entry of R or P) and the
+// Chebyshev and epilogue updates (about six per unknown per step).
+struct MfWork {
+  double bytes = 0, flops = 0;
+};
+static MfWork mf_work(const HostSetup& hs, int l, bool pressure, bool up, int K, size_t tsize) {
+  const FluidLevelHost& H = hs.levels[l];
+  const FluidLevelHost& Hc = hs.levels[l + 1];
+  const HostBlockMatrix& A = pressure ? H.L : H.A;
+  const HostBlockMatrix& Tr = pressure ? (up ? H.Pp : H.Rp) : (up ? H.Pu : H.Ru);
+  const double n = (double)A.nrows * A.BR, nc = pressure ? 3.0 * Hc.N * Hc.N : 2.0 * Hc.A.nrows;
+  const double a_entries = (double)A.nnzb() * A.BR * A.BC;
+  const double t_entries = (double)Tr.nnzb() * (Tr.kron ? Tr.BR : Tr.BR * Tr.BC);
+  MfWork w;
+  w.flops = K * 2.0 * a_entries + 2.0 * t_entries + 6.0 * K * n;
+  w.bytes = up ? (3.0 * n + nc) * tsize : (2.0 * n + nc) * tsize;
+  return w;
 }
 
 template <class T>
@@ -2356,7 +2396,9 @@ int fsi_graph_kernel_counts(const fsi_problem* h, int* counts) {
 int fsi_time_kernel(fsi_problem* h, int which, int reps, double* avg_ms, double* bytes) {
   if (!h || !avg_ms || !bytes || reps <= 0) return FSI_ERR_INVALID;
   Problem& P = h->P;
-  if ((which == 0 || which == 2 || (which >= 4 && which <= 7)) && P.prm.precision != 1) return FSI_ERR_INVALID;
+  if ((which == 0 || which == 2 || (which >= 4 && which <= 7) || (which >= 10 && which <= 13)) &&
+      P.prm.precision != 1)
+    return FSI_ERR_INVALID;
   if (which == 8 && P.prm.coupling != 0) return FSI_ERR_INVALID;  // would overwrite the exact rows
   if (which == 9 && P.prm.coupling != 1) return FSI_ERR_INVALID;
   if (which == 3 && P.p64.mgU.lv.empty()) return FSI_ERR_INVALID;  // no FP64 hierarchy in mixed mode
@@ -2376,7 +2418,7 @@ int fsi_time_kernel(fsi_problem* h, int which, int reps, double* avg_ms, double*
     cudaStream_t s = P.stream;
     const HostBlockMatrix& A0 = P.hs.levels[0].A;
     for (int r = 0; r < reps + 1; ++r) {
-      if (which < 4) launch(k_flush, 2 * 152, 512, 0, s, flush_n, fl, (unsigned)r);
+      if (which < 4 || which >= 10) launch(k_flush, 2 * 152, 512, 0, s, flush_n, fl, (unsigned)r);
       CK(cudaEventRecord(e0, s));
       switch (which) {
         case 0:  // full operator, FP32 (mixed inner iteration)
@@ -2421,6 +2463,23 @@ int fsi_time_kernel(fsi_problem* h, int which, int reps, double* avg_ms, double*
                  P.area, P.l2n, P.wall, P.cf_cap, P.cf_len, P.cf_col, P.cf_val, P.cf_val32, P.cflift, &P.ctl->aflags);
           *bytes = 0;
           break;
+        case 10:   // fused finest-level launches, FP32: velocity down / up,
+        case 11:   // pressure down / up (the level's current vectors)
+        case 12:
+        case 13: {
+          MG<float>& mg = (which <= 11) ? P.p32.mgU : P.p32.mgP;
+          MGLevel<float>& L = mg.lv[0];
+          if (!L.mf) {
+            cudaFree(fl);
+            return FSI_ERR_INVALID;
+          }
+          MGLevel<float>& C = mg.lv[1];
+          const bool up = (which & 1) != 0;
+          if (up) mf_up_launch<float>(mg, 0, L.b, C.x, L.x, nullptr, s);
+          else mf_down_launch<float>(mg, 0, L.b, s);
+          *bytes = mf_work(P.hs, 0, which >= 12, up, mg.degree, sizeof(float)).bytes;
+          break;
+        }
         case 6:    // the cluster launch of the velocity coarse levels alone, FP32
         case 7: {  // the same for the pressure Laplacian
           MG<float>& mg = (which == 6) ? P.p32.mgU : P.p32.mgP;
@@ -2451,6 +2510,16 @@ int fsi_time_kernel(fsi_problem* h, int which, int reps, double* avg_ms, double*
   } catch (...) {
     return map_exception();
   }
+}
+
+int fsi_kernel_flops(fsi_problem* h, int which, double* flops) {
+  if (!h || !flops) return FSI_ERR_INVALID;
+  Problem& P = h->P;
+  if (which < 10 || which > 13 || P.prm.precision != 1) return FSI_ERR_INVALID;
+  const MG<float>& mg = (which <= 11) ? P.p32.mgU : P.p32.mgP;
+  if (mg.lv.empty() || !mg.lv[0].mf) return FSI_ERR_INVALID;
+  *flops = mf_work(P.hs, 0, which >= 12, (which & 1) != 0, mg.degree, sizeof(float)).flops;
+  return FSI_OK;
 }
 
 int fsi_interior_nodes(const fsi_problem* h, int* lattice_ids) {

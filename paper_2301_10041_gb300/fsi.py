@@ -74,6 +74,7 @@ EXPORTS = {
     "fsi_get_rhs": (C.c_int, [C.c_void_p, C.c_void_p]),
     "fsi_graph_kernel_counts": (C.c_int, [C.c_void_p, C.c_void_p]),
     "fsi_time_kernel": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "fsi_kernel_flops": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double)]),
     "fsi_locate_bin_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                          C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "fsi_destroy": (None, [C.c_void_p]),
@@ -282,6 +283,12 @@ class Problem:
         self._check(load_library().fsi_time_kernel(self._h, int(which), int(reps), C.byref(ms), C.byref(by)),
                     "fsi_time_kernel")
         return ms.value, by.value
+
+    def kernel_flops(self, which: int) -> float:
+        """Algorithmic floating-point operations of one launch of kernel `which`."""
+        f = C.c_double()
+        self._check(load_library().fsi_kernel_flops(self._h, int(which), C.byref(f)), "fsi_kernel_flops")
+        return f.value
 
     def get_rhs(self):
         b = np.empty(self.n)

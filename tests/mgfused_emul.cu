@@ -275,7 +275,7 @@ static void pressure(const HostSetup& hs, int l, int K, double tol, std::mt19937
 }
 
 int main(int argc, char** argv) {
-  std::vector<int> grids{16, 24, 48, 128, 256};
+  std::vector<int> grids{16, 24, 48, 128, 512};
   if (argc > 1) {
     grids.clear();
     for (int i = 1; i < argc; ++i) grids.push_back(std::atoi(argv[i]));
@@ -291,6 +291,7 @@ int main(int argc, char** argv) {
       if (!hs.levels[l].mf) continue;
       for (int K = 1; K <= kMfMaxDeg; ++K) {
         if (N > 48 && K != 2) continue;  // the largest grids only at the default degree
+        if (N > 128 && l > 0) continue;
         velocity<double>(hs, l, K, 1e-12, rng);
         pressure<double>(hs, l, K, 1e-12, rng);
         velocity<float>(hs, l, K, 1e-5, rng);

@@ -7,9 +7,8 @@ launch with the same multigrid step written on the assembled level matrices
 of the host setup: the down launch (Chebyshev pre-smoothing from
 c0 D^-1 b, residual, Q2 / P1disc restriction, coarse smoother start) and the
 up launch (prolongation, post-smoothing, Richardson and Cahouet-Chabard
-epilogues), velocity and pressure, degrees 1-4, grids N = 16, 24, 48, 128,
-256 and the next coarser level (every tile size the library picks): FP64 to
-1e-12, FP32 to 1e-5.
+epilogues), velocity and pressure, degrees 1-4, grids N = 16, 24, 48, 128 and the next coarser level, and N = 512 (the
+larger tiles): FP64 to 1e-12, FP32 to 1e-5.
 """
 import os
 import shutil
