@@ -763,7 +763,7 @@ __host__ __device__ void mfp_up_body(const MfPresArgs<T>& a, const MfCta& cta) {
 // prolongation and smoothing back up -- are separated by __syncthreads only,
 // not by kernel launches.  The arithmetic of each phase is that of the fused
 // kernels above (same stencils, transfers and order of operations).
-constexpr int kMfBottomThreads = 512;
+constexpr int kMfBottomThreads = 1024;
 constexpr int kMfBottomLevels = 3;   // smoothing levels held by one bottom launch (the dense level not counted)
 constexpr int kMfBottomMaxU = 16;    // velocity: levels of at most 16 cells a side
 constexpr int kMfBottomMaxP = 32;    // pressure: levels of at most 32 cells a side
@@ -774,8 +774,7 @@ struct MfBottomU {
   MfVelOp<T> op[kMfBottomLevels];
   MfCheb<T> ch[kMfBottomLevels];
   int Nd = 0;                        // coarsest grid, solved densely
-  const T* dinv = nullptr;           // its dense inverse, row-major, 2 (2 Nd - 1)^2 rows, row stride a
-                                     // multiple of 4 (zero beyond the last column)
+  const T* dinv = nullptr;           // its dense inverse, row-major, 2 (2 Nd - 1)^2 rows
   const T* b = nullptr;              // right-hand side of the first level (node order)
   T* x = nullptr;                    // its result (node order)
   MfFin<T> fin;
@@ -788,8 +787,7 @@ struct MfBottomP {
   const T* tab[kMfBottomLevels] = {};  // stencil tables (kMfPresTab values each)
   MfCheb<T> ch[kMfBottomLevels];
   int Nd = 0;
-  const T* dinv = nullptr;           // pseudo-inverse of the coarsest pressure Laplacian, 3 Nd^2 rows,
-                                     // row stride a multiple of 4 (zero beyond the last column)
+  const T* dinv = nullptr;           // pseudo-inverse of the coarsest pressure Laplacian, 3 Nd^2 rows
   const T* b = nullptr;
   T* x = nullptr;
   MfFin<T> fin;
@@ -816,81 +814,40 @@ __host__ __device__ __forceinline__ MfFrame mf_grid_frame(int N) {
   return f;
 }
 
-// dense solve y = Dinv b of one CTA (rows in node order).  Dinv is row-major
-// with a row stride ld (a multiple of 4, zero beyond column n); bvec holds ld
-// entries.  A warp takes four rows at a time and each lane loads its float4
-// column chunks of the four rows (up to 4 chunks of 128 columns: n <= 512)
-// before any multiply, so one SM keeps many loads in flight; the lanes'
-// partial sums meet in a butterfly.  b and y are reached through the caller's
-// gather and scatter functions.
-constexpr int kMfDenseMaxN = 512;
+// dense solve y = Dinv b of one CTA, a warp per row (rows in node order);
+// b and y are reached through the caller's gather and scatter functions
 template <class T, class G, class S>
-__host__ __device__ __forceinline__ void mf_dense(const MfCta& c, const T* __restrict__ dinv, int n, int ld, T* bvec,
+__host__ __device__ __forceinline__ void mf_dense(const MfCta& c, const T* __restrict__ dinv, int n, T* bvec,
                                                    G&& gather, S&& scatter) {
   for (int t = c.tid; t < c.vthr; t += c.nthr)
-    for (int k = t; k < ld; k += c.vthr) bvec[k] = (k < n) ? gather(k) : (T)0;
+    for (int k = t; k < n; k += c.vthr) bvec[k] = gather(k);
   MF_SYNC();
-  constexpr int RG = 4, KC = kMfDenseMaxN / 128;
   const int nw = c.vthr >> 5;
   for (int t = c.tid; t < c.vthr; t += c.nthr) {
     const int lane = t & 31;
-    for (int r0 = (t >> 5) * RG; r0 < n; r0 += nw * RG) {
+    for (int r = t >> 5; r < n; r += nw) {
+      T acc = 0;
+      for (int k = lane; k < n; k += 32) acc += dinv[(size_t)r * n + k] * bvec[k];
 #ifdef __CUDA_ARCH__
-      T v[RG][KC][4];   // FP32: one float4 load per chunk
-#pragma unroll
-      for (int j = 0; j < RG; ++j)
-#pragma unroll
-        for (int q = 0; q < KC; ++q) {
-          const int k = 4 * lane + 128 * q;
-          const bool in = r0 + j < n && k < ld;
-          if constexpr (sizeof(T) == 4) {
-            const float4 w = in ? *reinterpret_cast<const float4*>(dinv + (size_t)(r0 + j) * ld + k)
-                                : make_float4(0.f, 0.f, 0.f, 0.f);
-            v[j][q][0] = w.x; v[j][q][1] = w.y; v[j][q][2] = w.z; v[j][q][3] = w.w;
-          } else {
-#pragma unroll
-            for (int e = 0; e < 4; ++e) v[j][q][e] = in ? dinv[(size_t)(r0 + j) * ld + k + e] : (T)0;
-          }
-        }
-      T acc[RG];
-#pragma unroll
-      for (int j = 0; j < RG; ++j) {
-        acc[j] = 0;
-#pragma unroll
-        for (int q = 0; q < KC; ++q) {
-          const int k = 4 * lane + 128 * q;
-          if (k < ld) {
-#pragma unroll
-            for (int e = 0; e < 4; ++e) acc[j] += v[j][q][e] * bvec[k + e];
-          }
-        }
-      }
-#pragma unroll
-      for (int j = 0; j < RG; ++j) {
-        for (int o = 16; o > 0; o >>= 1) acc[j] += __shfl_xor_sync(0xffffffffu, acc[j], o);
-        if (lane == 0 && r0 + j < n) scatter(r0 + j, acc[j]);
-      }
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == 0) scatter(r, acc);
 #else
-      // one host thread plays every lane of the warp, in the device's order
+      // one host thread plays every lane of the warp: the lanes' partial sums
+      // are added in the device's butterfly order
       if (lane == 0) {
-        for (int j = 0; j < RG && r0 + j < n; ++j) {
-          T part[32];
-          for (int l = 0; l < 32; ++l) {
-            part[l] = 0;
-            for (int q = 0; q < KC; ++q) {
-              const int k = 4 * l + 128 * q;
-              if (k >= ld) continue;
-              for (int e = 0; e < 4; ++e) part[l] += dinv[(size_t)(r0 + j) * ld + k + e] * bvec[k + e];
-            }
-          }
-          for (int o = 16; o > 0; o >>= 1) {
-            T nxt[32];
-            for (int l = 0; l < 32; ++l) nxt[l] = part[l] + part[l ^ o];
-            for (int l = 0; l < 32; ++l) part[l] = nxt[l];
-          }
-          scatter(r0 + j, part[0]);
+        T part[32];
+        for (int l = 0; l < 32; ++l) {
+          part[l] = 0;
+          for (int k = l; k < n; k += 32) part[l] += dinv[(size_t)r * n + k] * bvec[k];
         }
+        for (int o = 16; o > 0; o >>= 1) {
+          T nxt[32];
+          for (int l = 0; l < 32; ++l) nxt[l] = part[l] + part[l ^ o];
+          for (int l = 0; l < 32; ++l) part[l] = nxt[l];
+        }
+        scatter(r, part[0]);
       }
+      (void)acc;
 #endif
     }
   }
@@ -901,8 +858,8 @@ inline size_t mfu_bottom_smem(const int* Ns, int nl, int Nd) {
   size_t e = 0;
   for (int i = 0; i < nl; ++i) e += 5 * 4 * (size_t)(Ns[i] + 4) * (Ns[i] + 4);
   e += 2 * 4 * (size_t)(Nd + 4) * (Nd + 4);
-  const size_t ld = (2 * (size_t)(2 * Nd - 1) * (2 * Nd - 1) + 3) & ~(size_t)3;
-  return e * 2 * sizeof(T) + ld * sizeof(T);
+  const size_t nd = 2 * (size_t)(2 * Nd - 1) * (2 * Nd - 1);
+  return e * 2 * sizeof(T) + ((nd * sizeof(T) + 15) & ~(size_t)15);
 }
 
 template <class T>
@@ -1008,7 +965,7 @@ __host__ __device__ void mfu_bottom_body(const MfBottomU<T>& a, const MfCta& cta
   // dense coarsest solve
   {
     const int Nd = a.Nd, n = 2 * (2 * Nd - 1) * (2 * Nd - 1);
-    mf_dense<T>(cta, a.dinv, n, (n + 3) & ~3, bvec,
+    mf_dense<T>(cta, a.dinv, n, bvec,
                 [&](int k) {
                   int ix, iy;
                   mf_vlattice(Nd, k >> 1, ix, iy);
@@ -1100,7 +1057,7 @@ template <class T>
 inline size_t mfp_bottom_smem(const int* Ns, int nl, int Nd) {
   size_t e = (size_t)nl * ((kMfPresTab + 3) & ~3);
   for (int i = 0; i < nl; ++i) e += 15 * (size_t)(Ns[i] + 2) * (Ns[i] + 2);
-  e += 6 * (size_t)(Nd + 2) * (Nd + 2) + ((3 * (size_t)Nd * Nd + 3) & ~(size_t)3);
+  e += 6 * (size_t)(Nd + 2) * (Nd + 2) + 3 * (size_t)Nd * Nd;
   return e * sizeof(T);
 }
 
@@ -1120,7 +1077,7 @@ __host__ __device__ void mfp_bottom_body(const MfBottomP<T>& a, const MfCta& cta
   T* Bd = dl;
   T* Xd = dl + 3 * fd.n();
   T* bvec = Xd + 3 * fd.n();
-  const size_t total = (size_t)(bvec - sm) + ((3 * (size_t)a.Nd * a.Nd + 3) & ~(size_t)3);
+  const size_t total = (size_t)(bvec - sm) + 3 * (size_t)a.Nd * a.Nd;
   for (size_t e = cta.tid; e < total; e += cta.nthr) sm[e] = 0;
   MF_SYNC();
   for (int i = 0; i < a.nl; ++i)
@@ -1190,7 +1147,7 @@ __host__ __device__ void mfp_bottom_body(const MfBottomP<T>& a, const MfCta& cta
   }
   {
     const int Nd = a.Nd, n = 3 * Nd * Nd, nd = fd.n();
-    mf_dense<T>(cta, a.dinv, n, (n + 3) & ~3, bvec,
+    mf_dense<T>(cta, a.dinv, n, bvec,
                 [&](int k) {
                   const int c = k / 3, j = k - 3 * c;
                   return Bd[j * nd + (c / Nd + 1) * fd.w + c % Nd + 1];

@@ -326,7 +326,6 @@ template <class T>
 struct MG {
   std::vector<MGLevel<T>> lv;
   T* coarse_inv = nullptr;
-  T* coarse_inv_ld = nullptr;   // the same with rows padded to a multiple of 4 columns (bottom launch)
   int coarse_n = 0;
   int degree = 2;
   bool pressure = false;
@@ -388,14 +387,6 @@ static void build_mg(Arena& ar, const HostSetup& hs, bool pressure, int degree, 
   }
   mg.coarse_n = pressure ? hs.coarse_nL : hs.coarse_nA;
   mg.coarse_inv = upload_as<T>(ar, pressure ? hs.coarseLinv : hs.coarseAinv);  // row-major
-  if (std::is_same<T, float>::value && mg.coarse_n <= kMfDenseMaxN) {
-    const std::vector<double>& D = pressure ? hs.coarseLinv : hs.coarseAinv;
-    const int n = mg.coarse_n, ld = (n + 3) & ~3;
-    std::vector<double> pad((size_t)n * ld, 0.0);
-    for (int r = 0; r < n; ++r)
-      for (int c = 0; c < n; ++c) pad[(size_t)r * ld + c] = D[(size_t)r * n + c];
-    mg.coarse_inv_ld = upload_as<T>(ar, pad);
-  }
 }
 
 // ------------------------------------------- cluster-resident coarse levels
@@ -500,7 +491,7 @@ static void select_mf(MG<T>& mg, const HostSetup& hs, int mg_fused, bool count_o
       for (int l = lb; l < last; ++l) Ns[l - lb] = hs.levels[l].N;
       const int Nd = hs.levels[last].N;
       const size_t smem = mg.pressure ? mfp_bottom_smem<T>(Ns, last - lb, Nd) : mfu_bottom_smem<T>(Ns, last - lb, Nd);
-      if (smem <= kClSmemCap && mg.coarse_n <= kMfDenseMaxN) {
+      if (smem <= kClSmemCap) {
         mg.lb = lb;
         mg.bot_smem = smem;
         if (mg.pressure) {
@@ -511,7 +502,7 @@ static void select_mf(MG<T>& mg, const HostSetup& hs, int mg_fused, bool count_o
             mg.botP.ch[l - lb] = mf_cheb(mg.lv[l], mg.degree);
           }
           mg.botP.Nd = Nd;
-          mg.botP.dinv = mg.coarse_inv_ld;
+          mg.botP.dinv = mg.coarse_inv;
         } else {
           mg.botU.nl = last - lb;
           for (int l = lb; l < last; ++l) {
@@ -519,7 +510,7 @@ static void select_mf(MG<T>& mg, const HostSetup& hs, int mg_fused, bool count_o
             mg.botU.ch[l - lb] = mf_cheb(mg.lv[l], mg.degree);
           }
           mg.botU.Nd = Nd;
-          mg.botU.dinv = mg.coarse_inv_ld;
+          mg.botU.dinv = mg.coarse_inv;
         }
       }
     }

@@ -338,12 +338,7 @@ static void bottom(const HostSetup& hs, bool pressure, int K, double tol, std::m
   for (double& v : acc0) v = U(rng);
   const std::vector<double> x = ref_vcycle(hs, pressure, lb, b, ch, K);
   std::vector<T> bT = as<T>(b), xT(n, (T)7), accT = as<T>(acc0);
-  const std::vector<double>& Dn = pressure ? hs.coarseLinv : hs.coarseAinv;
-  const int nd = pressure ? hs.coarse_nL : hs.coarse_nA, ldd = (nd + 3) & ~3;
-  std::vector<double> pad((size_t)nd * ldd, 0.0);
-  for (int r = 0; r < nd; ++r)
-    for (int c = 0; c < nd; ++c) pad[(size_t)r * ldd + c] = Dn[(size_t)r * nd + c];
-  std::vector<T> dinvT = as<T>(pad);
+  std::vector<T> dinvT = as<T>(pressure ? hs.coarseLinv : hs.coarseAinv);
   int Ns[kMfBottomLevels];
   for (int l = lb; l < last; ++l) Ns[l - lb] = hs.levels[l].N;
   const int Nd = hs.levels[last].N;
