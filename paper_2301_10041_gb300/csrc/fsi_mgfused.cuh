@@ -754,458 +754,6 @@ __host__ __device__ void mfp_up_body(const MfPresArgs<T>& a, const MfCta& cta) {
   });
 }
 
-// ------------------------------------------------------------------ bottom
-// The smallest levels of a hierarchy and its dense coarsest solve in one CTA
-// of kMfBottomThreads threads.  Every vector of those levels lives in the
-// CTA's shared memory for the whole launch (frames covering the whole grid
-// with a zero border), so the dependent phases of the bottom of a V-cycle --
-// smoothing, residual, restriction on each level, the dense solve, then
-// prolongation and smoothing back up -- are separated by __syncthreads only,
-// not by kernel launches.  The arithmetic of each phase is that of the fused
-// kernels above (same stencils, transfers and order of operations).
-constexpr int kMfBottomThreads = 1024;
-constexpr int kMfBottomLevels = 3;   // smoothing levels held by one bottom launch (the dense level not counted)
-constexpr int kMfBottomMaxU = 16;    // velocity: levels of at most 16 cells a side
-constexpr int kMfBottomMaxP = 32;    // pressure: levels of at most 32 cells a side
-
-template <class T>
-struct MfBottomU {
-  int nl = 0;                        // smoothing levels, finest first (op[i].N cells a side)
-  MfVelOp<T> op[kMfBottomLevels];
-  MfCheb<T> ch[kMfBottomLevels];
-  int Nd = 0;                        // coarsest grid, solved densely
-  const T* dinv = nullptr;           // its dense inverse, row-major, 2 (2 Nd - 1)^2 rows
-  const T* b = nullptr;              // right-hand side of the first level (node order)
-  T* x = nullptr;                    // its result (node order)
-  MfFin<T> fin;
-};
-
-template <class T>
-struct MfBottomP {
-  int nl = 0;
-  int N[kMfBottomLevels] = {};
-  const T* tab[kMfBottomLevels] = {};  // stencil tables (kMfPresTab values each)
-  MfCheb<T> ch[kMfBottomLevels];
-  int Nd = 0;
-  const T* dinv = nullptr;           // pseudo-inverse of the coarsest pressure Laplacian, 3 Nd^2 rows
-  const T* b = nullptr;
-  T* x = nullptr;
-  MfFin<T> fin;
-};
-
-// interior Q2 node id -> lattice position (the inverse of mf_vnode)
-__host__ __device__ __forceinline__ void mf_vlattice(int N, int k, int& ix, int& iy) {
-  const int nV = (N - 1) * (N - 1), nX = N * (N - 1);
-  if (k < nV) { ix = 2 * (k % (N - 1) + 1); iy = 2 * (k / (N - 1) + 1); return; }
-  k -= nV;
-  if (k < nX) { ix = 2 * (k % N) + 1; iy = 2 * (k / N + 1); return; }
-  k -= nX;
-  if (k < nX) { ix = 2 * (k % (N - 1) + 1); iy = 2 * (k / (N - 1)) + 1; return; }
-  k -= nX;
-  ix = 2 * (k % N) + 1;
-  iy = 2 * (k / N) + 1;
-}
-
-// whole-grid velocity frame of an N-cell level: lattice [-4, 2N + 4)
-__host__ __device__ __forceinline__ MfFrame mf_grid_frame(int N) {
-  MfFrame f;
-  f.ox = f.oy = -4;
-  f.pw = f.ph = N + 4;
-  return f;
-}
-
-// dense solve y = Dinv b of one CTA, a warp per row (rows in node order);
-// b and y are reached through the caller's gather and scatter functions
-template <class T, class G, class S>
-__host__ __device__ __forceinline__ void mf_dense(const MfCta& c, const T* __restrict__ dinv, int n, T* bvec,
-                                                   G&& gather, S&& scatter) {
-  for (int t = c.tid; t < c.vthr; t += c.nthr)
-    for (int k = t; k < n; k += c.vthr) bvec[k] = gather(k);
-  MF_SYNC();
-  const int nw = c.vthr >> 5;
-  for (int t = c.tid; t < c.vthr; t += c.nthr) {
-    const int lane = t & 31;
-    for (int r = t >> 5; r < n; r += nw) {
-      T acc = 0;
-      for (int k = lane; k < n; k += 32) acc += dinv[(size_t)r * n + k] * bvec[k];
-#ifdef __CUDA_ARCH__
-      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-      if (lane == 0) scatter(r, acc);
-#else
-      // one host thread plays every lane of the warp: the lanes' partial sums
-      // are added in the device's butterfly order
-      if (lane == 0) {
-        T part[32];
-        for (int l = 0; l < 32; ++l) {
-          part[l] = 0;
-          for (int k = l; k < n; k += 32) part[l] += dinv[(size_t)r * n + k] * bvec[k];
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-          T nxt[32];
-          for (int l = 0; l < 32; ++l) nxt[l] = part[l] + part[l ^ o];
-          for (int l = 0; l < 32; ++l) part[l] = nxt[l];
-        }
-        scatter(r, part[0]);
-      }
-      (void)acc;
-#endif
-    }
-  }
-}
-
-template <class T>
-inline size_t mfu_bottom_smem(const int* Ns, int nl, int Nd) {
-  size_t e = 0;
-  for (int i = 0; i < nl; ++i) e += 5 * 4 * (size_t)(Ns[i] + 4) * (Ns[i] + 4);
-  e += 2 * 4 * (size_t)(Nd + 4) * (Nd + 4);
-  const size_t nd = 2 * (size_t)(2 * Nd - 1) * (2 * Nd - 1);
-  return e * 2 * sizeof(T) + ((nd * sizeof(T) + 15) & ~(size_t)15);
-}
-
-template <class T>
-__host__ __device__ void mfu_bottom_body(const MfBottomU<T>& a, const MfCta& cta) {
-  using T2 = typename Vec2<T>::type;
-  T2* sm = reinterpret_cast<T2*>(cta.sm);
-  // level i: B, X, Xt, D, Dt (5 frames); coarsest: B, X; then the dense buffer
-  auto lvl = [&](int i) {
-    T2* p = sm;
-    for (int j = 0; j < i; ++j) p += 5 * 4 * (a.op[j].N + 4) * (a.op[j].N + 4);
-    return p;
-  };
-  T2* dl = lvl(a.nl);
-  const MfFrame fd = mf_grid_frame(a.Nd);
-  T2* Bd = dl;
-  T2* Xd = dl + 4 * fd.plane();
-  T* bvec = reinterpret_cast<T*>(Xd + 4 * fd.plane());
-  const size_t total = (size_t)(reinterpret_cast<T2*>(bvec) - sm);
-  for (size_t e = cta.tid; e < total; e += cta.nthr) sm[e].x = sm[e].y = 0;   // zero borders
-  MF_SYNC();
-  {  // the first level's right-hand side
-    const MfFrame f = mf_grid_frame(a.op[0].N);
-    const int N = a.op[0].N;
-    T2* B = lvl(0);
-    mf_vsweep(cta, 2, f.pw - 2, 2, f.ph - 2, [&](auto tc, int px, int py) {
-      constexpr int TAU = decltype(tc)::value;
-      const int ix = f.ox + 2 * px + (TAU & 1), iy = f.oy + 2 * py + (TAU >> 1);
-      if (mf_vinterior(N, ix, iy))
-        B[f.at(TAU, px, py)] = *reinterpret_cast<const T2*>(a.b + 2 * (size_t)mf_vnode_t<TAU>(N, ix, iy));
-    });
-  }
-  MF_SYNC();
-  // down
-  for (int i = 0; i < a.nl; ++i) {
-    const MfVelOp<T>& op = a.op[i];
-    const MfCheb<T>& ch = a.ch[i];
-    const int N = op.N, K = ch.k;
-    const MfFrame f = mf_grid_frame(N);
-    const int V = 4 * f.plane();
-    T2* B = lvl(i);
-    T2 *Xc = B + V, *Xn = B + 2 * V, *Dc = B + 3 * V, *Dn = B + 4 * V;
-    mf_vsweep(cta, 2, f.pw - 2, 2, f.ph - 2, [&](auto tc, int px, int py) {
-      constexpr int TAU = decltype(tc)::value;
-      const int ix = f.ox + 2 * px + (TAU & 1), iy = f.oy + 2 * py + (TAU >> 1);
-      if (!mf_vinterior(N, ix, iy)) return;
-      const int e = f.at(TAU, px, py);
-      T2 x0;
-      x0.x = ch.c0 * op.dinv[TAU][0] * B[e].x;
-      x0.y = ch.c0 * op.dinv[TAU][1] * B[e].y;
-      Xc[e] = x0;
-      Dc[e] = x0;
-    });
-    MF_SYNC();
-    for (int s = 1; s < K; ++s) {
-      mf_vel_cheb<T>(cta, op, f, 2, B, Xc, Dc, Xn, Dn, false, ch.c1[s - 1], ch.c2[s - 1]);
-      T2* t = Xc; Xc = Xn; Xn = t;
-      t = Dc; Dc = Dn; Dn = t;
-      MF_SYNC();
-    }
-    T2* R = Dn;   // residual, in the free direction buffer
-    mf_vsweep(cta, 2, f.pw - 2, 2, f.ph - 2, [&](auto tc, int px, int py) {
-      constexpr int TAU = decltype(tc)::value;
-      const int ix = f.ox + 2 * px + (TAU & 1), iy = f.oy + 2 * py + (TAU >> 1);
-      if (!mf_vinterior(N, ix, iy)) return;
-      const int e = f.at(TAU, px, py);
-      T a0, a1;
-      mf_vel_apply<T, TAU>(op, Xc, f, px, py, a0, a1);
-      R[e].x = B[e].x - a0;
-      R[e].y = B[e].y - a1;
-    });
-    MF_SYNC();
-    // restriction into the next level's right-hand side
-    const int Nc = N / 2;
-    const MfFrame g = mf_grid_frame(Nc);
-    T2* Bc = (i + 1 < a.nl) ? lvl(i + 1) : Bd;
-    mf_vsweep(cta, 2, g.pw - 2, 2, g.ph - 2, [&](auto tc, int px, int py) {
-      constexpr int TAU = decltype(tc)::value;
-      const int X0 = g.ox + 2 * px + (TAU & 1), Y0 = g.oy + 2 * py + (TAU >> 1);
-      if (!mf_vinterior(Nc, X0, Y0)) return;
-      T s0 = 0, s1 = 0;
-      const int rx = (X0 & 1) ? 1 : 3, ry = (Y0 & 1) ? 1 : 3;
-      for (int dy = -ry; dy <= ry; ++dy) {
-        const float ty = (Y0 & 1) ? 0.25f * (float)(dy + 2) : 0.25f * (float)(dy < 0 ? -dy : dy);
-        const T wy = (T)((Y0 & 1) ? mf_l1(ty) : mf_l0(ty));
-        if (wy == (T)0) continue;
-        for (int dx = -rx; dx <= rx; ++dx) {
-          const float tx = (X0 & 1) ? 0.25f * (float)(dx + 2) : 0.25f * (float)(dx < 0 ? -dx : dx);
-          const T wx = (T)((X0 & 1) ? mf_l1(tx) : mf_l0(tx));
-          if (wx == (T)0) continue;
-          const T2 r = R[f.at_lattice(2 * X0 + dx, 2 * Y0 + dy)];
-          const T w = wx * wy;
-          s0 += w * r.x;
-          s1 += w * r.y;
-        }
-      }
-      T2 v;
-      v.x = s0;
-      v.y = s1;
-      Bc[g.at(TAU, px, py)] = v;
-    });
-    MF_SYNC();
-  }
-  // dense coarsest solve
-  {
-    const int Nd = a.Nd, n = 2 * (2 * Nd - 1) * (2 * Nd - 1);
-    mf_dense<T>(cta, a.dinv, n, bvec,
-                [&](int k) {
-                  int ix, iy;
-                  mf_vlattice(Nd, k >> 1, ix, iy);
-                  const T2 v = Bd[fd.at_lattice(ix, iy)];
-                  return (k & 1) ? v.y : v.x;
-                },
-                [&](int r, T y) {
-                  int ix, iy;
-                  mf_vlattice(Nd, r >> 1, ix, iy);
-                  T2& v = Xd[fd.at_lattice(ix, iy)];
-                  if (r & 1) v.y = y; else v.x = y;
-                });
-  }
-  MF_SYNC();
-  // up
-  const T2* xc = Xd;
-  for (int i = a.nl - 1; i >= 0; --i) {
-    const MfVelOp<T>& op = a.op[i];
-    const MfCheb<T>& ch = a.ch[i];
-    const int N = op.N, K = ch.k, Nc = N / 2;
-    const MfFrame f = mf_grid_frame(N), g = mf_grid_frame(Nc);
-    const int V = 4 * f.plane();
-    T2* B = lvl(i);
-    // the pre-smoothed iterate: X after an even number of steps, Xt after an odd one
-    T2* Xc = ((K - 1) & 1) ? B + 2 * V : B + V;
-    T2* Xn = ((K - 1) & 1) ? B + V : B + 2 * V;
-    T2 *Dc = B + 3 * V, *Dn = B + 4 * V;
-    mf_vsweep(cta, 2, f.pw - 2, 2, f.ph - 2, [&](auto tc, int px, int py) {
-      constexpr int TAU = decltype(tc)::value;
-      const int ix = f.ox + 2 * px + (TAU & 1), iy = f.oy + 2 * py + (TAU >> 1);
-      if (!mf_vinterior(N, ix, iy)) return;
-      const int ccx = mf_min(ix >> 2, Nc - 1), ccy = mf_min(iy >> 2, Nc - 1);
-      const float tx = 0.25f * (float)(ix - 4 * ccx), ty = 0.25f * (float)(iy - 4 * ccy);
-      const T wx[3] = {(T)mf_l0(tx), (T)mf_l1(tx), (T)mf_l2(tx)};
-      const T wy[3] = {(T)mf_l0(ty), (T)mf_l1(ty), (T)mf_l2(ty)};
-      T p0 = 0, p1 = 0;
-#pragma unroll
-      for (int bb = 0; bb < 3; ++bb) {
-#pragma unroll
-        for (int aa = 0; aa < 3; ++aa) {
-          const T w = wx[aa] * wy[bb];
-          const T2 c = xc[g.at_lattice(2 * ccx + aa, 2 * ccy + bb)];
-          p0 += w * c.x;
-          p1 += w * c.y;
-        }
-      }
-      const int e = f.at(TAU, px, py);
-      Xc[e].x = p0 + Xc[e].x;
-      Xc[e].y = p1 + Xc[e].y;
-    });
-    MF_SYNC();
-    for (int s = 0; s < K; ++s) {
-      mf_vel_cheb<T>(cta, op, f, 2, B, Xc, Dc, Xn, Dn, s == 0, s == 0 ? (T)0 : ch.c1[s - 1],
-                     s == 0 ? ch.c0 : ch.c2[s - 1]);
-      T2* t = Xc; Xc = Xn; Xn = t;
-      t = Dc; Dc = Dn; Dn = t;
-      MF_SYNC();
-    }
-    xc = Xc;
-  }
-  // result of the first level, with the epilogue
-  {
-    const MfFrame f = mf_grid_frame(a.op[0].N);
-    const int N = a.op[0].N;
-    mf_vsweep(cta, 2, f.pw - 2, 2, f.ph - 2, [&](auto tc, int px, int py) {
-      constexpr int TAU = decltype(tc)::value;
-      const int ix = f.ox + 2 * px + (TAU & 1), iy = f.oy + 2 * py + (TAU >> 1);
-      if (!mf_vinterior(N, ix, iy)) return;
-      const T2 y = xc[f.at(TAU, px, py)];
-      const size_t id = mf_vnode_t<TAU>(N, ix, iy);
-      *reinterpret_cast<T2*>(a.x + 2 * id) = y;
-      if (a.fin.acc) {
-        a.fin.acc[2 * id] += a.fin.omega * y.x;
-        a.fin.acc[2 * id + 1] += a.fin.omega * y.y;
-      }
-    });
-  }
-}
-
-// whole-grid pressure frame of an N-cell level: cells [-1, N + 1)
-__host__ __device__ __forceinline__ MfCells mf_grid_cells(int N) {
-  MfCells f;
-  f.ox = f.oy = -1;
-  f.w = N + 2;
-  return f;
-}
-
-template <class T>
-inline size_t mfp_bottom_smem(const int* Ns, int nl, int Nd) {
-  size_t e = (size_t)nl * ((kMfPresTab + 3) & ~3);
-  for (int i = 0; i < nl; ++i) e += 15 * (size_t)(Ns[i] + 2) * (Ns[i] + 2);
-  e += 6 * (size_t)(Nd + 2) * (Nd + 2) + 3 * (size_t)Nd * Nd;
-  return e * sizeof(T);
-}
-
-template <class T>
-__host__ __device__ void mfp_bottom_body(const MfBottomP<T>& a, const MfCta& cta) {
-  T* sm = reinterpret_cast<T*>(cta.sm);
-  constexpr int kTab = (kMfPresTab + 3) & ~3;
-  // stencil tables of the levels, then per level B, X, Xt, D, Dt (3 planes
-  // each), then the coarsest B, X and the dense buffer
-  auto lvl = [&](int i) {
-    T* p = sm + a.nl * kTab;
-    for (int j = 0; j < i; ++j) p += 15 * (a.N[j] + 2) * (a.N[j] + 2);
-    return p;
-  };
-  T* dl = lvl(a.nl);
-  const MfCells fd = mf_grid_cells(a.Nd);
-  T* Bd = dl;
-  T* Xd = dl + 3 * fd.n();
-  T* bvec = Xd + 3 * fd.n();
-  const size_t total = (size_t)(bvec - sm) + 3 * (size_t)a.Nd * a.Nd;
-  for (size_t e = cta.tid; e < total; e += cta.nthr) sm[e] = 0;
-  MF_SYNC();
-  for (int i = 0; i < a.nl; ++i)
-    for (int t = cta.tid; t < kMfPresTab; t += cta.nthr) sm[i * kTab + t] = a.tab[i][t];
-  {
-    const MfCells f = mf_grid_cells(a.N[0]);
-    const int N = a.N[0], n = f.n();
-    T* B = lvl(0);
-    mf_rows(cta, N, N, [&](int cx, int cy) {
-      const int e = (cy + 1) * f.w + cx + 1;
-      for (int k = 0; k < 3; ++k) B[k * n + e] = a.b[3 * ((size_t)cy * N + cx) + k];
-    });
-  }
-  MF_SYNC();
-  for (int i = 0; i < a.nl; ++i) {
-    const T* tab = sm + i * kTab;
-    const T* dv = tab + 729;
-    const MfCheb<T>& ch = a.ch[i];
-    const int N = a.N[i], K = ch.k, Nc = N / 2;
-    const MfCells f = mf_grid_cells(N);
-    const int n = f.n();
-    T* B = lvl(i);
-    T *Xc = B + 3 * n, *Xn = B + 6 * n, *Dc = B + 9 * n, *Dn = B + 12 * n;
-    mf_rows(cta, N, N, [&](int cx, int cy) {
-      const int e = (cy + 1) * f.w + cx + 1, v = mf_variant(N, cx, cy);
-      for (int k = 0; k < 3; ++k) {
-        const T x0 = ch.c0 * dv[3 * v + k] * B[k * n + e];
-        Xc[k * n + e] = x0;
-        Dc[k * n + e] = x0;
-      }
-    });
-    MF_SYNC();
-    for (int s = 1; s < K; ++s) {
-      mf_pres_cheb<T>(cta, tab, N, f, 1, B, Xc, Dc, Xn, Dn, false, ch.c1[s - 1], ch.c2[s - 1]);
-      T* t = Xc; Xc = Xn; Xn = t;
-      t = Dc; Dc = Dn; Dn = t;
-      MF_SYNC();
-    }
-    T* R = Dn;
-    mf_rows(cta, N, N, [&](int cx, int cy) {
-      const int e = (cy + 1) * f.w + cx + 1;
-      T y[3];
-      mf_pres_apply<T>(tab, Xc, f, N, cx, cy, e, y);
-      for (int k = 0; k < 3; ++k) R[k * n + e] = B[k * n + e] - y[k];
-    });
-    MF_SYNC();
-    const MfCells g = mf_grid_cells(Nc);
-    const int ng = g.n();
-    T* Bc = (i + 1 < a.nl) ? lvl(i + 1) : Bd;
-    mf_rows(cta, Nc, Nc, [&](int X0, int Y0) {
-      T s0 = 0, s1 = 0, s2 = 0;
-      for (int q = 0; q < 4; ++q) {
-        const int cx = 2 * X0 + (q & 1), cy = 2 * Y0 + (q >> 1);
-        const int e = (cy + 1) * f.w + cx + 1;
-        const T sx = (q & 1) ? (T)0.25 : (T)-0.25, sy = (q >> 1) ? (T)0.25 : (T)-0.25;
-        const T r0 = R[e], r1 = R[n + e], r2 = R[2 * n + e];
-        s0 += r0;
-        s1 += sx * r0 + (T)0.5 * r1;
-        s2 += sy * r0 + (T)0.5 * r2;
-      }
-      const int ec = (Y0 + 1) * g.w + X0 + 1;
-      Bc[ec] = s0;
-      Bc[ng + ec] = s1;
-      Bc[2 * ng + ec] = s2;
-    });
-    MF_SYNC();
-  }
-  {
-    const int Nd = a.Nd, n = 3 * Nd * Nd, nd = fd.n();
-    mf_dense<T>(cta, a.dinv, n, bvec,
-                [&](int k) {
-                  const int c = k / 3, j = k - 3 * c;
-                  return Bd[j * nd + (c / Nd + 1) * fd.w + c % Nd + 1];
-                },
-                [&](int r, T y) {
-                  const int c = r / 3, j = r - 3 * c;
-                  Xd[j * nd + (c / Nd + 1) * fd.w + c % Nd + 1] = y;
-                });
-  }
-  MF_SYNC();
-  const T* xc = Xd;
-  for (int i = a.nl - 1; i >= 0; --i) {
-    const T* tab = sm + i * kTab;
-    const MfCheb<T>& ch = a.ch[i];
-    const int N = a.N[i], K = ch.k, Nc = N / 2;
-    const MfCells f = mf_grid_cells(N), g = mf_grid_cells(Nc);
-    const int n = f.n(), ng = g.n();
-    T* B = lvl(i);
-    T* Xc = ((K - 1) & 1) ? B + 6 * n : B + 3 * n;
-    T* Xn = ((K - 1) & 1) ? B + 3 * n : B + 6 * n;
-    T *Dc = B + 9 * n, *Dn = B + 12 * n;
-    mf_rows(cta, N, N, [&](int cx, int cy) {
-      const int e = (cy + 1) * f.w + cx + 1, ec = ((cy >> 1) + 1) * g.w + (cx >> 1) + 1;
-      const T sx = (cx & 1) ? (T)0.25 : (T)-0.25, sy = (cy & 1) ? (T)0.25 : (T)-0.25;
-      const T c0 = xc[ec], c1 = xc[ng + ec], c2 = xc[2 * ng + ec];
-      const T p[3] = {c0 + sx * c1 + sy * c2, (T)0.5 * c1, (T)0.5 * c2};
-      for (int k = 0; k < 3; ++k) Xc[k * n + e] = p[k] + Xc[k * n + e];
-    });
-    MF_SYNC();
-    for (int s = 0; s < K; ++s) {
-      mf_pres_cheb<T>(cta, tab, N, f, 1, B, Xc, Dc, Xn, Dn, s == 0, s == 0 ? (T)0 : ch.c1[s - 1],
-                      s == 0 ? ch.c0 : ch.c2[s - 1]);
-      T* t = Xc; Xc = Xn; Xn = t;
-      t = Dc; Dc = Dn; Dn = t;
-      MF_SYNC();
-    }
-    xc = Xc;
-  }
-  {
-    const MfCells f = mf_grid_cells(a.N[0]);
-    const int N = a.N[0], n = f.n();
-    mf_rows(cta, N, N, [&](int cx, int cy) {
-      const int e = (cy + 1) * f.w + cx + 1;
-      const size_t id = 3 * ((size_t)cy * N + cx);
-      for (int k = 0; k < 3; ++k) {
-        const T yv = xc[k * n + e];
-        a.x[id + k] = yv;
-        T ov = yv;
-        if (a.fin.sout) {
-          ov = -(a.fin.snu * a.fin.smp[id + k] * a.fin.sv[id + k] + a.fin.srdt * yv);
-          a.fin.sout[id + k] = ov;
-        }
-        if (a.fin.acc) a.fin.acc[id + k] += a.fin.omega * ov;
-      }
-    });
-  }
-}
-
 #ifdef __CUDACC__
 // The kernels: one CTA per tile, NT threads.
 #define FSI_MF_KERNEL(name, body, Args)                                                      \
@@ -1222,18 +770,6 @@ FSI_MF_KERNEL(k_mfu_up, mfu_up_body, MfVelArgs)
 FSI_MF_KERNEL(k_mfp_down, mfp_down_body, MfPresArgs)
 FSI_MF_KERNEL(k_mfp_up, mfp_up_body, MfPresArgs)
 #undef FSI_MF_KERNEL
-
-#define FSI_MF_BOTTOM(name, body, Args)                                                      \
-  template <class T>                                                                         \
-  __global__ void __launch_bounds__(kMfBottomThreads) name(const __grid_constant__ Args<T> a) { \
-    asm volatile("griddepcontrol.wait;" ::: "memory");                                       \
-    extern __shared__ __align__(16) unsigned char mf_smem[];                                 \
-    const MfCta c{0, 0, (int)threadIdx.x, (int)blockDim.x, kMfBottomThreads, mf_smem};       \
-    body<T>(a, c);                                                                           \
-  }
-FSI_MF_BOTTOM(k_mfu_bottom, mfu_bottom_body, MfBottomU)
-FSI_MF_BOTTOM(k_mfp_bottom, mfp_bottom_body, MfBottomP)
-#undef FSI_MF_BOTTOM
 #endif
 
 // shared memory of one launch (bytes) for tile tc (velocity: coarse lattice

@@ -330,11 +330,6 @@ struct MG {
   int degree = 2;
   bool pressure = false;
   ClusterMG<T> cl;
-  // levels lb .. last in one single-CTA bottom launch (fsi_mgfused.cuh), -1: none
-  int lb = -1;
-  size_t bot_smem = 0;
-  MfBottomU<T> botU;
-  MfBottomP<T> botP;
 };
 
 constexpr double kChebRatioU = 6.0;   // smoothing interval [hi/ratio, hi]
@@ -470,55 +465,12 @@ static void cluster_launch(MG<T>& mg, const T* in_b, T* out_x, cudaStream_t s) {
 // matrix-free kernels when the hierarchy is FP32 and the smoothing degree is
 // at most kMfMaxDeg.
 template <class T>
-static MfCheb<T> mf_cheb(const MGLevel<T>& L, int degree);
-
-// Without a cluster, the smallest levels (at most kMfBottomMaxU cells for the
-// velocity, kMfBottomMaxP for the pressure) and the dense coarsest solve go
-// into one single-CTA bottom launch when they fit its shared memory, and the
-// levels above it take the fused launches.
-template <class T>
 static void select_mf(MG<T>& mg, const HostSetup& hs, int mg_fused, bool count_only) {
   const int last = (int)mg.lv.size() - 1;
   if (mg_fused == -1 || !std::is_same<T, float>::value || mg.degree > kMfMaxDeg) return;
-  if (!mg.cl.on && last >= 1) {
-    const int cap = mg.pressure ? kMfBottomMaxP : kMfBottomMaxU;
-    int lb = 0;
-    while (lb < last && hs.levels[lb].N > cap) ++lb;
-    bool ok = lb < last && last - lb <= kMfBottomLevels;
-    for (int l = lb; ok && l < last; ++l) ok = hs.levels[l].mf && hs.levels[l].N % 2 == 0;
-    if (ok) {
-      int Ns[kMfBottomLevels];
-      for (int l = lb; l < last; ++l) Ns[l - lb] = hs.levels[l].N;
-      const int Nd = hs.levels[last].N;
-      const size_t smem = mg.pressure ? mfp_bottom_smem<T>(Ns, last - lb, Nd) : mfu_bottom_smem<T>(Ns, last - lb, Nd);
-      if (smem <= kClSmemCap) {
-        mg.lb = lb;
-        mg.bot_smem = smem;
-        if (mg.pressure) {
-          mg.botP.nl = last - lb;
-          for (int l = lb; l < last; ++l) {
-            mg.botP.N[l - lb] = mg.lv[l].N;
-            mg.botP.tab[l - lb] = mg.lv[l].mftab;
-            mg.botP.ch[l - lb] = mf_cheb(mg.lv[l], mg.degree);
-          }
-          mg.botP.Nd = Nd;
-          mg.botP.dinv = mg.coarse_inv;
-        } else {
-          mg.botU.nl = last - lb;
-          for (int l = lb; l < last; ++l) {
-            mg.botU.op[l - lb] = mg.lv[l].mfu;
-            mg.botU.ch[l - lb] = mf_cheb(mg.lv[l], mg.degree);
-          }
-          mg.botU.Nd = Nd;
-          mg.botU.dinv = mg.coarse_inv;
-        }
-      }
-    }
-  }
-  bool any = mg.lb >= 0;
+  bool any = false;
   for (int l = 0; l < last; ++l) {
     if (mg.cl.on && l >= mg.cl.lc) break;
-    if (mg.lb >= 0 && l >= mg.lb) break;
     if (!hs.levels[l].mf || hs.levels[l].N < 16) break;
     mg.lv[l].mf = true;
     any = true;
@@ -542,8 +494,6 @@ static void select_mf(MG<T>& mg, const HostSetup& hs, int mg_fused, bool count_o
       };
       for (int N : {16, 512}) mf_with_tile_u(N, vel);
       for (int N : {16, 512}) mf_with_tile_p(N, pres);
-      CK(cudaFuncSetAttribute(k_mfu_bottom<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kClSmemCap));
-      CK(cudaFuncSetAttribute(k_mfp_bottom<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kClSmemCap));
     });
   }
 }
@@ -628,36 +578,16 @@ static void mf_up_launch(MG<T>& mg, int l, const T* b, const T* xc, T* dst, cons
   }
 }
 
-// The bottom launch: levels mg.lb .. last from right-hand side b to dst,
-// with the epilogue fin (used when the bottom starts at the finest level).
-template <class T>
-static T* bottom_launch(MG<T>& mg, const T* b, T* dst, const MfFin<T>* fin, cudaStream_t s) {
-  if (mg.pressure) {
-    MfBottomP<T> a = mg.botP;
-    a.b = b; a.x = dst;
-    if (fin) a.fin = *fin;
-    launch(k_mfp_bottom<T>, dim3(1), kMfBottomThreads, mg.bot_smem, s, a);
-  } else {
-    MfBottomU<T> a = mg.botU;
-    a.b = b; a.x = dst;
-    if (fin) a.fin = *fin;
-    launch(k_mfu_bottom<T>, dim3(1), kMfBottomThreads, mg.bot_smem, s, a);
-  }
-  return dst;
-}
-
 // One V-cycle from fused level l (mg.lv[l].mf) with right-hand side b: the
 // down launch, the coarser levels, the up launch.  The result goes to `out`,
-// else to L.x.  A level that starts the bottom launch takes it instead.
+// else to L.x.
 template <class T>
 static T* vcycle_mf(MG<T>& mg, int l, const T* b, cudaStream_t s, T* out, const MfFin<T>* fin) {
   MGLevel<T>& L = mg.lv[l];
-  T* dst = out ? out : L.x;
-  if (mg.lb == l) return bottom_launch<T>(mg, b, dst, fin, s);
   MGLevel<T>& C = mg.lv[l + 1];
+  T* dst = out ? out : L.x;
   mf_down_launch<T>(mg, l, b, s);
-  T* xc = (C.mf || mg.lb == l + 1) ? vcycle_mf<T>(mg, l + 1, C.b, s, nullptr, nullptr)
-                                   : vcycle<T>(mg, l + 1, s, (T*)nullptr);
+  T* xc = C.mf ? vcycle_mf<T>(mg, l + 1, C.b, s, nullptr, nullptr) : vcycle<T>(mg, l + 1, s, (T*)nullptr);
   mf_up_launch<T>(mg, l, b, xc, dst, fin, s);
   return dst;
 }
@@ -702,7 +632,7 @@ static T* vcycle(MG<T>& mg, int l, cudaStream_t s, T* out, const SpmvArgs<T>* fi
   const int last = (int)mg.lv.size() - 1;
   MGLevel<T>& L = mg.lv[l];
   if (fused) *fused = false;
-  if (L.mf || mg.lb == l) {  // fused levels and the bottom launch need only L.b
+  if (L.mf) {  // fused levels need only L.b
     MfFin<T> mfin;
     if (fin) mfin = mf_fin(*fin);
     if (fused) *fused = fin != nullptr;
@@ -923,7 +853,7 @@ static void stokes_pressure(Problem& P, Prec<T>& pr, const T* in_p, T* out_p, cu
   fin.sv = in_p; fin.smp = pr.mpinv; fin.sout = out_p;
   fin.snu = (T)P.prm.nu; fin.srdt = (T)(P.prm.rho_f / P.prm.dt);
   fin.acc = acc; fin.omega = omega;
-  if (L0p.mf || pr.mgP.lb == 0) {  // the fused finest level reads in_p itself and applies the epilogue
+  if (L0p.mf) {  // the fused finest level reads in_p itself and applies the epilogue
     const MfFin<T> mfin = mf_fin(fin);
     vcycle_mf<T>(pr.mgP, 0, in_p, s, nullptr, &mfin);
     return;
@@ -947,7 +877,7 @@ template <class T>
 static void stokes_velocity(Problem& P, Prec<T>& pr, const T* in_u, const T* p, T* out_u, cudaStream_t s,
                             T* acc = nullptr, T omega = 1) {
   MGLevel<T>& L0u = pr.mgU.lv[0];
-  if (L0u.mf || pr.mgU.lb == 0) {  // the fused finest level starts its smoother itself
+  if (L0u.mf) {  // the fused finest level starts its smoother itself
     const T* b = in_u;
     if (p) {
       sell_launch(pr.op.Bt, MODE_AXPBY, axpby<T>(p, L0u.b, in_u, (T)-1, (T)1), s);
@@ -1050,7 +980,7 @@ static void precond_launch(Problem& P, Prec<T>& pr, cudaStream_t s) {
     } else {
       // residual (starting the pressure smoother), then the pressure and
       // velocity corrections, each added to z by its own last kernel
-      if (L0p.mf || pr.mgP.lb == 0)
+      if (L0p.mf)
         launch(k_stokes_res<T>, pr.op.gU + pr.op.gP, 128, 0, s, pr.op, pr.zw, vu, vp, pr.t, (const T*)nullptr, (T)0,
                (T*)nullptr, (T*)nullptr, (T*)nullptr);
       else

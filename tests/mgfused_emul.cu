@@ -274,128 +274,6 @@ static void pressure(const HostSetup& hs, int l, int K, double tol, std::mt19937
   report("pressure up: Richardson update", N, K, l, rel(back(accT), acc_ref), tol);
 }
 
-// Plain V-cycle on the assembled level matrices from level l (rhs b) down to
-// the dense coarsest inverse, degree K Chebyshev smoothing with coefficients
-// ch[l], in double: the reference for the bottom launch.
-static std::vector<double> ref_vcycle(const HostSetup& hs, bool pressure, int l, const std::vector<double>& b,
-                                      const std::vector<Coef>& ch, int K) {
-  const int last = (int)hs.levels.size() - 1;
-  if (l == last) {
-    const std::vector<double>& Di = pressure ? hs.coarseLinv : hs.coarseAinv;
-    const int n = pressure ? hs.coarse_nL : hs.coarse_nA;
-    std::vector<double> y(n, 0.0);
-    for (int r = 0; r < n; ++r)
-      for (int c = 0; c < n; ++c) y[r] += Di[(size_t)r * n + c] * b[c];
-    return y;
-  }
-  const FluidLevelHost& H = hs.levels[l];
-  const HostBlockMatrix& A = pressure ? H.L : H.A;
-  const std::vector<double>& dinv = pressure ? H.dinvL : H.dinvA;
-  const int n = (int)b.size();
-  std::vector<double> x(n), d(n), Ax, r(n), bc, xc, Pxc;
-  for (int i = 0; i < n; ++i) x[i] = d[i] = ch[l].c0 * dinv[i] * b[i];
-  for (int s = 1; s < K; ++s) {
-    spmv(A, x, Ax);
-    for (int i = 0; i < n; ++i) {
-      d[i] = ch[l].c1[s - 1] * d[i] + ch[l].c2[s - 1] * dinv[i] * (b[i] - Ax[i]);
-      x[i] += d[i];
-    }
-  }
-  spmv(A, x, Ax);
-  for (int i = 0; i < n; ++i) r[i] = b[i] - Ax[i];
-  spmv(pressure ? H.Rp : H.Ru, r, bc);
-  xc = ref_vcycle(hs, pressure, l + 1, bc, ch, K);
-  spmv(pressure ? H.Pp : H.Pu, xc, Pxc);
-  for (int i = 0; i < n; ++i) x[i] += Pxc[i];
-  for (int s = 0; s < K; ++s) {
-    spmv(A, x, Ax);
-    for (int i = 0; i < n; ++i) {
-      const double res = b[i] - Ax[i];
-      d[i] = (s == 0) ? ch[l].c0 * dinv[i] * res : ch[l].c1[s - 1] * d[i] + ch[l].c2[s - 1] * dinv[i] * res;
-      x[i] += d[i];
-    }
-  }
-  return x;
-}
-
-// the bottom launch (levels of at most kMfBottomMax* cells down to the dense
-// coarsest) against the plain V-cycle, with the finest-level epilogue when the
-// bottom starts at level 0
-template <class T>
-static void bottom(const HostSetup& hs, bool pressure, int K, double tol, std::mt19937_64& rng) {
-  const int last = (int)hs.levels.size() - 1;
-  const int cap = pressure ? kMfBottomMaxP : kMfBottomMaxU;
-  int lb = 0;
-  while (lb < last && hs.levels[lb].N > cap) ++lb;
-  if (lb >= last || last - lb > kMfBottomLevels) return;
-  std::vector<Coef> ch(hs.levels.size());
-  for (int l = 0; l < last; ++l) ch[l] = cheb(0.25 + 0.01 * l, 2.2 - 0.05 * l, K);
-  const FluidLevelHost& H = hs.levels[lb];
-  const int n = pressure ? 3 * H.N * H.N : 2 * H.A.nrows;
-  std::uniform_real_distribution<double> U(-1.0, 1.0);
-  std::vector<double> b(n), acc0(n);
-  for (double& v : b) v = U(rng);
-  for (double& v : acc0) v = U(rng);
-  const std::vector<double> x = ref_vcycle(hs, pressure, lb, b, ch, K);
-  std::vector<T> bT = as<T>(b), xT(n, (T)7), accT = as<T>(acc0);
-  std::vector<T> dinvT = as<T>(pressure ? hs.coarseLinv : hs.coarseAinv);
-  int Ns[kMfBottomLevels];
-  for (int l = lb; l < last; ++l) Ns[l - lb] = hs.levels[l].N;
-  const int Nd = hs.levels[last].N;
-  std::vector<std::vector<T>> tabs;
-  if (pressure) {
-    MfBottomP<T> a;
-    a.nl = last - lb;
-    for (int l = lb; l < last; ++l) {
-      const FluidLevelHost& L = hs.levels[l];
-      std::vector<double> tab(kMfPresTab);
-      for (int v = 0; v < 9; ++v)
-        for (int y = 0; y < 3; ++y)
-          for (int xx = 0; xx < 3; ++xx)
-            for (int q = 0; q < 9; ++q) tab[81 * v + 9 * (3 * y + xx) + q] = L.stenL[v][y][xx][q];
-      for (int v = 0; v < 9; ++v)
-        for (int k = 0; k < 3; ++k) tab[729 + 3 * v + k] = L.dinvLv[v][k];
-      tabs.push_back(as<T>(tab));
-    }
-    for (int l = lb; l < last; ++l) {
-      a.N[l - lb] = hs.levels[l].N;
-      a.tab[l - lb] = tabs[l - lb].data();
-      a.ch[l - lb].k = K;
-      a.ch[l - lb].c0 = (T)ch[l].c0;
-      for (int i = 0; i + 1 < K; ++i) { a.ch[l - lb].c1[i] = (T)ch[l].c1[i]; a.ch[l - lb].c2[i] = (T)ch[l].c2[i]; }
-    }
-    a.Nd = Nd; a.dinv = dinvT.data(); a.b = bT.data(); a.x = xT.data();
-    a.fin.acc = accT.data(); a.fin.omega = (T)0.7;
-    run_grid(1, 1, kMfBottomThreads, mfp_bottom_smem<T>(Ns, last - lb, Nd), [&](const MfCta& c) { mfp_bottom_body<T>(a, c); });
-  } else {
-    MfBottomU<T> a;
-    a.nl = last - lb;
-    for (int l = lb; l < last; ++l) {
-      const FluidLevelHost& L = hs.levels[l];
-      MfVelOp<T>& op = a.op[l - lb];
-      op.N = L.N;
-      for (int t = 0; t < 4; ++t) {
-        for (int y = 0; y < 5; ++y)
-          for (int xx = 0; xx < 5; ++xx)
-            for (int q = 0; q < 4; ++q) op.c[t][y][xx][q] = (T)L.stenA[t][y][xx][q];
-        for (int c = 0; c < 2; ++c) op.dinv[t][c] = (T)L.dinvAt[t][c];
-      }
-      a.ch[l - lb].k = K;
-      a.ch[l - lb].c0 = (T)ch[l].c0;
-      for (int i = 0; i + 1 < K; ++i) { a.ch[l - lb].c1[i] = (T)ch[l].c1[i]; a.ch[l - lb].c2[i] = (T)ch[l].c2[i]; }
-    }
-    a.Nd = Nd; a.dinv = dinvT.data(); a.b = bT.data(); a.x = xT.data();
-    a.fin.acc = accT.data(); a.fin.omega = (T)0.7;
-    run_grid(1, 1, kMfBottomThreads, mfu_bottom_smem<T>(Ns, last - lb, Nd), [&](const MfCta& c) { mfu_bottom_body<T>(a, c); });
-  }
-  std::vector<double> acc_ref(n);
-  for (int i = 0; i < n; ++i) acc_ref[i] = acc0[i] + 0.7 * x[i];
-  report(pressure ? "pressure bottom: V-cycle from the bottom level" : "velocity bottom: V-cycle from the bottom level",
-         H.N, K, lb, rel(back(xT), x), tol);
-  report(pressure ? "pressure bottom: Richardson update" : "velocity bottom: Richardson update", H.N, K, lb,
-         rel(back(accT), acc_ref), tol);
-}
-
 int main(int argc, char** argv) {
   std::vector<int> grids{16, 24, 48, 128, 512};
   if (argc > 1) {
@@ -419,19 +297,6 @@ int main(int argc, char** argv) {
         velocity<float>(hs, l, K, 1e-5, rng);
         pressure<float>(hs, l, K, 1e-5, rng);
       }
-    }
-  }
-  for (int N : {8 * 2, 12, 24, 48, 64, 128}) {   // hierarchies whose bottoms hold 1 or 2 levels
-    const double xy[6] = {0.4, 0.4, 0.6, 0.4, 0.5, 0.6};
-    const int tris[3] = {0, 1, 2};
-    SetupParams sp{N, 1.1, 0.03, 10.0, 0.002, 1.0};
-    HostSetup hs;
-    build_setup(sp, 3, 1, xy, tris, hs);
-    for (int K = 1; K <= kMfMaxDeg; ++K) {
-      bottom<double>(hs, false, K, 1e-12, rng);
-      bottom<double>(hs, true, K, 1e-12, rng);
-      bottom<float>(hs, false, K, 1e-5, rng);
-      bottom<float>(hs, true, K, 1e-5, rng);
     }
   }
   std::printf("failures=%d\n", failures);
