@@ -86,6 +86,18 @@ __host__ __device__ __forceinline__ int mf_tile_p(int N) { return N >= 512 ? 8 :
 constexpr int mf_threads_u(int tc) { return tc >= 8 ? 512 : (tc == 4 ? 256 : 128); }
 constexpr int mf_threads_p(int tp) { return tp >= 4 ? 256 : 128; }
 
+// Call f(integral_constant<degree>) for a Chebyshev degree 1 .. kMfMaxDeg
+// (the frame sizes and the step loops of the kernels are compile-time).
+template <class F>
+inline void mf_with_degree(int K, F&& f) {
+  switch (K) {
+    case 1: f(std::integral_constant<int, 1>()); break;
+    case 2: f(std::integral_constant<int, 2>()); break;
+    case 3: f(std::integral_constant<int, 3>()); break;
+    default: f(std::integral_constant<int, 4>()); break;
+  }
+}
+
 // Call f(integral_constant<tile>) with the tile of the level.
 template <class F>
 inline void mf_with_tile_u(int N, F&& f) {
@@ -328,11 +340,11 @@ __host__ __device__ __forceinline__ void mf_vel_cheb(const MfCta& cta, const MfV
 }
 
 // down: grid (ceil(N / TC))^2 over the coarse lattice [0, N)^2
-template <class T, int TC>
+template <class T, int TC, int K>
 __host__ __device__ void mfu_down_body(const MfVelArgs<T>& a, const MfCta& cta) {
   using T2 = typename Vec2<T>::type;
   const MfVelOp<T>& op = a.op;
-  const int N = op.N, K = a.ch.k;
+  const int N = op.N;
   const int CX0 = cta.bx * TC, CY0 = cta.by * TC;
   MfFrame f;
   f.ox = 2 * CX0 - 4 - 2 * K;
@@ -423,12 +435,12 @@ __host__ __device__ void mfu_down_body(const MfVelArgs<T>& a, const MfCta& cta) 
 }
 
 // up: grid (ceil(2N / (2 TC)))^2 over the fine lattice [0, 2N)^2
-template <class T, int TC>
+template <class T, int TC, int K>
 __host__ __device__ void mfu_up_body(const MfVelArgs<T>& a, const MfCta& cta) {
   using T2 = typename Vec2<T>::type;
   constexpr int TF = 2 * TC;
   const MfVelOp<T>& op = a.op;
-  const int N = op.N, K = a.ch.k, Nc = N / 2;
+  const int N = op.N, Nc = N / 2;
   const int FX0 = cta.bx * TF, FY0 = cta.by * TF;
   MfFrame f;
   f.ox = FX0 - 2 * K;
@@ -599,9 +611,9 @@ __host__ __device__ __forceinline__ void mf_pres_cheb(const MfCta& cta, const T*
 }
 
 // down: grid (ceil(Nc / TP))^2 over the coarse cells
-template <class T, int TP>
+template <class T, int TP, int K>
 __host__ __device__ void mfp_down_body(const MfPresArgs<T>& a, const MfCta& cta) {
-  const int N = a.N, K = a.ch.k, Nc = N / 2;
+  const int N = a.N, Nc = N / 2;
   const int CX0 = cta.bx * TP, CY0 = cta.by * TP;
   MfCells f;
   f.ox = 2 * CX0 - K;
@@ -685,10 +697,10 @@ __host__ __device__ void mfp_down_body(const MfPresArgs<T>& a, const MfCta& cta)
 }
 
 // up: grid (ceil(N / (2 TP)))^2 over the fine cells
-template <class T, int TP>
+template <class T, int TP, int K>
 __host__ __device__ void mfp_up_body(const MfPresArgs<T>& a, const MfCta& cta) {
   constexpr int TPF = 2 * TP;
-  const int N = a.N, K = a.ch.k, Nc = N / 2;
+  const int N = a.N, Nc = N / 2;
   const int FX0 = cta.bx * TPF, FY0 = cta.by * TPF;
   MfCells f;
   f.ox = FX0 - K;
@@ -757,13 +769,13 @@ __host__ __device__ void mfp_up_body(const MfPresArgs<T>& a, const MfCta& cta) {
 #ifdef __CUDACC__
 // The kernels: one CTA per tile, NT threads.
 #define FSI_MF_KERNEL(name, body, Args)                                                      \
-  template <class T, int TILE, int NT>                                                       \
+  template <class T, int TILE, int K, int NT>                                                \
   __global__ void __launch_bounds__(NT) name(const __grid_constant__ Args<T> a) {            \
     asm volatile("griddepcontrol.wait;" ::: "memory");                                       \
     extern __shared__ __align__(16) unsigned char mf_smem[];                                 \
     const MfCta c{(int)blockIdx.x, (int)blockIdx.y, (int)threadIdx.x, (int)blockDim.x, NT,   \
                   mf_smem};                                                                  \
-    body<T, TILE>(a, c);                                                                     \
+    body<T, TILE, K>(a, c);                                                                  \
   }
 FSI_MF_KERNEL(k_mfu_down, mfu_down_body, MfVelArgs)
 FSI_MF_KERNEL(k_mfu_up, mfu_up_body, MfVelArgs)

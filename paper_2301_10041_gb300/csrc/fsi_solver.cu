@@ -479,18 +479,24 @@ static void select_mf(MG<T>& mg, const HostSetup& hs, int mg_fused, bool count_o
     static std::once_flag once;
     std::call_once(once, [] {
       auto vel = [](auto tc) {
-        constexpr int TC = decltype(tc)::value, NT = mf_threads_u(TC);
-        CK(cudaFuncSetAttribute(k_mfu_down<float, TC, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)mfu_down_smem<float>(TC, kMfMaxDeg)));
-        CK(cudaFuncSetAttribute(k_mfu_up<float, TC, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)mfu_up_smem<float>(TC, kMfMaxDeg)));
+        for (int K = 1; K <= kMfMaxDeg; ++K)
+          mf_with_degree(K, [&](auto kc) {
+            constexpr int TC = decltype(tc)::value, KD = decltype(kc)::value, NT = mf_threads_u(TC);
+            CK(cudaFuncSetAttribute(k_mfu_down<float, TC, KD, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)mfu_down_smem<float>(TC, KD)));
+            CK(cudaFuncSetAttribute(k_mfu_up<float, TC, KD, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)mfu_up_smem<float>(TC, KD)));
+          });
       };
       auto pres = [](auto tp) {
-        constexpr int TP = decltype(tp)::value, NT = mf_threads_p(TP);
-        CK(cudaFuncSetAttribute(k_mfp_down<float, TP, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)mfp_down_smem<float>(TP, kMfMaxDeg)));
-        CK(cudaFuncSetAttribute(k_mfp_up<float, TP, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)mfp_up_smem<float>(TP, kMfMaxDeg)));
+        for (int K = 1; K <= kMfMaxDeg; ++K)
+          mf_with_degree(K, [&](auto kc) {
+            constexpr int TP = decltype(tp)::value, KD = decltype(kc)::value, NT = mf_threads_p(TP);
+            CK(cudaFuncSetAttribute(k_mfp_down<float, TP, KD, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)mfp_down_smem<float>(TP, KD)));
+            CK(cudaFuncSetAttribute(k_mfp_up<float, TP, KD, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)mfp_up_smem<float>(TP, KD)));
+          });
       };
       for (int N : {16, 512}) mf_with_tile_u(N, vel);
       for (int N : {16, 512}) mf_with_tile_p(N, pres);
@@ -532,18 +538,22 @@ static void mf_down_launch(MG<T>& mg, int l, const T* b, cudaStream_t s) {
     a.N = N; a.tab = L.mftab; a.ch = mf_cheb(L, K);
     a.b = b; a.xout = L.x2; a.bc = C.b; a.ci = ci;
     mf_with_tile_p(N, [&](auto tp) {
-      constexpr int TP = decltype(tp)::value, NT = mf_threads_p(TP);
-      const unsigned g = nblk(N / 2, TP);
-      launch(k_mfp_down<T, TP, NT>, dim3(g, g), NT, mfp_down_smem<T>(TP, K), s, a);
+      mf_with_degree(K, [&](auto kc) {
+        constexpr int TP = decltype(tp)::value, KD = decltype(kc)::value, NT = mf_threads_p(TP);
+        const unsigned g = nblk(N / 2, TP);
+        launch(k_mfp_down<T, TP, KD, NT>, dim3(g, g), NT, mfp_down_smem<T>(TP, KD), s, a);
+      });
     });
   } else {
     MfVelArgs<T> a;
     a.op = L.mfu; a.ch = mf_cheb(L, K);
     a.b = b; a.xout = L.x2; a.bc = C.b; a.ci = ci;
     mf_with_tile_u(N, [&](auto tc) {
-      constexpr int TC = decltype(tc)::value, NT = mf_threads_u(TC);
-      const unsigned g = nblk(N, TC);
-      launch(k_mfu_down<T, TC, NT>, dim3(g, g), NT, mfu_down_smem<T>(TC, K), s, a);
+      mf_with_degree(K, [&](auto kc) {
+        constexpr int TC = decltype(tc)::value, KD = decltype(kc)::value, NT = mf_threads_u(TC);
+        const unsigned g = nblk(N, TC);
+        launch(k_mfu_down<T, TC, KD, NT>, dim3(g, g), NT, mfu_down_smem<T>(TC, KD), s, a);
+      });
     });
   }
 }
@@ -561,9 +571,11 @@ static void mf_up_launch(MG<T>& mg, int l, const T* b, const T* xc, T* dst, cons
     a.b = b; a.xpre = L.x2; a.xc = xc; a.xout = dst;
     if (fin) a.fin = *fin;
     mf_with_tile_p(N, [&](auto tp) {
-      constexpr int TP = decltype(tp)::value, NT = mf_threads_p(TP);
-      const unsigned g = nblk(N, 2 * TP);
-      launch(k_mfp_up<T, TP, NT>, dim3(g, g), NT, mfp_up_smem<T>(TP, K), s, a);
+      mf_with_degree(K, [&](auto kc) {
+        constexpr int TP = decltype(tp)::value, KD = decltype(kc)::value, NT = mf_threads_p(TP);
+        const unsigned g = nblk(N, 2 * TP);
+        launch(k_mfp_up<T, TP, KD, NT>, dim3(g, g), NT, mfp_up_smem<T>(TP, KD), s, a);
+      });
     });
   } else {
     MfVelArgs<T> a;
@@ -571,9 +583,11 @@ static void mf_up_launch(MG<T>& mg, int l, const T* b, const T* xc, T* dst, cons
     a.b = b; a.xpre = L.x2; a.xc = xc; a.xout = dst;
     if (fin) a.fin = *fin;
     mf_with_tile_u(N, [&](auto tc) {
-      constexpr int TC = decltype(tc)::value, NT = mf_threads_u(TC);
-      const unsigned g = nblk(2 * N, 2 * TC);
-      launch(k_mfu_up<T, TC, NT>, dim3(g, g), NT, mfu_up_smem<T>(TC, K), s, a);
+      mf_with_degree(K, [&](auto kc) {
+        constexpr int TC = decltype(tc)::value, KD = decltype(kc)::value, NT = mf_threads_u(TC);
+        const unsigned g = nblk(2 * N, 2 * TC);
+        launch(k_mfu_up<T, TC, KD, NT>, dim3(g, g), NT, mfu_up_smem<T>(TC, KD), s, a);
+      });
     });
   }
 }

@@ -135,7 +135,10 @@ static void velocity(const HostSetup& hs, int l, int K, double tol, std::mt19937
   mf_with_tile_u(N, [&](auto tc) {   // the tile the library uses on this level
     constexpr int TC = decltype(tc)::value;
     const int gd = (N + TC - 1) / TC;
-    run_grid(gd, gd, mf_threads_u(TC), mfu_down_smem<T>(TC, K), [&](const MfCta& c) { mfu_down_body<T, TC>(a, c); });
+    mf_with_degree(K, [&](auto kc) {
+      constexpr int KD = decltype(kc)::value;
+      run_grid(gd, gd, mf_threads_u(TC), mfu_down_smem<T>(TC, KD), [&](const MfCta& c) { mfu_down_body<T, TC, KD>(a, c); });
+    });
   });
   // reference: smoothing from x0 = c0 D^-1 b, then residual and restriction
   std::vector<double> x(n), d(n), Ax, r(n), Rr, xr;
@@ -165,7 +168,10 @@ static void velocity(const HostSetup& hs, int l, int K, double tol, std::mt19937
   mf_with_tile_u(N, [&](auto tc) {
     constexpr int TC = decltype(tc)::value;
     const int gu = (2 * N + 2 * TC - 1) / (2 * TC);
-    run_grid(gu, gu, mf_threads_u(TC), mfu_up_smem<T>(TC, K), [&](const MfCta& c) { mfu_up_body<T, TC>(u, c); });
+    mf_with_degree(K, [&](auto kc) {
+      constexpr int KD = decltype(kc)::value;
+      run_grid(gu, gu, mf_threads_u(TC), mfu_up_smem<T>(TC, KD), [&](const MfCta& c) { mfu_up_body<T, TC, KD>(u, c); });
+    });
   });
   std::vector<double> Pxc;
   spmv(H.Pu, xc, Pxc);
@@ -220,7 +226,10 @@ static void pressure(const HostSetup& hs, int l, int K, double tol, std::mt19937
   mf_with_tile_p(N, [&](auto tp) {
     constexpr int TP = decltype(tp)::value;
     const int gd = (N / 2 + TP - 1) / TP;
-    run_grid(gd, gd, mf_threads_p(TP), mfp_down_smem<T>(TP, K), [&](const MfCta& c) { mfp_down_body<T, TP>(a, c); });
+    mf_with_degree(K, [&](auto kc) {
+      constexpr int KD = decltype(kc)::value;
+      run_grid(gd, gd, mf_threads_p(TP), mfp_down_smem<T>(TP, KD), [&](const MfCta& c) { mfp_down_body<T, TP, KD>(a, c); });
+    });
   });
   std::vector<double> x(n), d(n), Lx, r(n), Rr;
   for (int i = 0; i < n; ++i) x[i] = d[i] = ch.c0 * H.dinvL[i] * b[i];
@@ -251,7 +260,10 @@ static void pressure(const HostSetup& hs, int l, int K, double tol, std::mt19937
   mf_with_tile_p(N, [&](auto tp) {
     constexpr int TP = decltype(tp)::value;
     const int gu = (N + 2 * TP - 1) / (2 * TP);
-    run_grid(gu, gu, mf_threads_p(TP), mfp_up_smem<T>(TP, K), [&](const MfCta& c) { mfp_up_body<T, TP>(u, c); });
+    mf_with_degree(K, [&](auto kc) {
+      constexpr int KD = decltype(kc)::value;
+      run_grid(gu, gu, mf_threads_p(TP), mfp_up_smem<T>(TP, KD), [&](const MfCta& c) { mfp_up_body<T, TP, KD>(u, c); });
+    });
   });
   std::vector<double> Pxc;
   spmv(H.Pp, xc, Pxc);
