@@ -324,31 +324,61 @@ def prob_dofs(case):
     return n_u + 3 * case.N ** 2 + 4 * case.ref_xy.shape[0]
 
 
+def fp32_peak_tflops(peaks):
+    """FP32 FMA peak of the GPU: SMs x 128 FP32 lanes x 2 FLOP x the maximum
+    SM clock (MEASURED_PEAKS.json sm_max_mhz, else 2070 MHz)."""
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    mhz = peaks.get("sm_max_mhz", 2070.0)
+    return sms * 128 * 2 * mhz * 1e6 / 1e12, {"sms": sms, "fp32_lanes_per_sm": 128, "sm_max_mhz": mhz}
+
+
+FUSED = (("velocity_down_fused_f32", 10), ("velocity_up_fused_f32", 11), ("pressure_down_fused_f32", 12),
+         ("pressure_up_fused_f32", 13))
+
+
+def fused_kernels(prob, hbm_peak, alu_peak, reps):
+    """Time of each fused finest-level launch (L2 evicted before each), its
+    algorithmic bytes and FLOPs, and both roofline fractions."""
+    out = {}
+    for name, which in FUSED:
+        try:
+            ms, by = prob.time_kernel(which, reps=reps)
+            fl = prob.kernel_flops(which)
+        except Exception:
+            continue
+        out[name] = {"us": ms * 1e3, "bytes": by, "flops": fl, "gbs": by / ms / 1e6, "hbm_frac": by / ms / 1e6 / hbm_peak,
+                     "tflops": fl / ms / 1e9, "alu_frac": fl / ms / 1e9 / alu_peak}
+    return out
+
+
 def roofline(prob, args):
-    """Roofline of the dominant HBM kernel of the mixed path: the Chebyshev
-    smoothing step on the finest Q2 velocity level (k_sell, 2x2 blocks, the
-    largest per-level kernel of the launch list in profiles/), timed live on
-    the library's stream with CUDA events, L2 evicted before every launch.
-    The FP32 full-system operator is reported beside it, and the
-    cluster-resident coarse V-cycle launches (the largest share of the step,
-    latency-bound, no HBM roofline) as launch times."""
+    """Roofline of the dominant kernel of the mixed path.  On the 128 x 128
+    cavity the largest share of the launch list (profiles/) is the fused
+    down launch of the velocity levels (pre-smoothing, residual, restriction;
+    k_mfu_down): it reads and writes vectors only, so its roofline is the
+    FP32 FMA rate (algorithmic FLOPs without the overlap work of the tiles)
+    and its HBM fraction is reported beside it.  Timed live on the library's
+    stream with CUDA events, L2 evicted before every launch.  The other fused
+    launches, the FP32 full-system operator (sparse, HBM-bound) and the
+    per-level sparse smoothing step (the kernel of the FP64 arm and of
+    mg_fused = -1) are reported beside it."""
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     peak = peaks.get("hbm_gbs", 6800.0)
+    alu_peak, alu_how = fp32_peak_tflops(peaks)
     out = {}
-    for name, which in (("full_operator_f32", 0), ("velocity_chebyshev_f32", 2)):
+    for name, which in (("full_operator_f32", 0), ("sell_velocity_chebyshev_f32", 2)):
         ms, by = prob.time_kernel(which, reps=30)
-        out[name] = {"ms": ms, "bytes": by, "gbs": by / ms / 1e6}
-    # the largest-share launches are the cluster-resident coarse V-cycle
-    # levels: latency-bound, reported as launch times (L2 warm)
-    for name, which in (("vcycle_cluster_velocity_f32", 6), ("vcycle_cluster_pressure_f32", 7),
-                        ("vcycle_velocity_f32", 4), ("vcycle_pressure_f32", 5)):
+        out[name] = {"us": ms * 1e3, "bytes": by, "gbs": by / ms / 1e6, "hbm_frac": by / ms / 1e6 / peak}
+    out.update(fused_kernels(prob, peak, alu_peak, 30))
+    # V-cycles as a whole (L2 warm, as inside a solve)
+    for name, which in (("vcycle_velocity_f32", 4), ("vcycle_pressure_f32", 5)):
         try:
             ms, _ = prob.time_kernel(which, reps=30)
             out[name] = {"us": ms * 1e3}
         except Exception:
             pass
-    dom = out["velocity_chebyshev_f32"]
     # C_f assembly (S2-S4) with the located-point rule of this workload, and
     # with the paper's exact rule (mesh intersection) on the same X^n
     try:
@@ -366,16 +396,24 @@ def roofline(prob, args):
     except Exception as e:  # report, do not fail the bench line
         out["cf_assembly_error"] = str(e)
     traffic = None   # DRAM bytes per launch from the committed ncu summary of this kernel
-    prof = os.path.join(ROOT, "profiles", "ncu_velocity_chebyshev_f32_cavity128.md")
+    prof = os.path.join(ROOT, "profiles", "ncu_velocity_down_fused_cavity128.md")
     if os.path.exists(prof):
         for line in open(prof):
             if line.startswith("dram_bytes_per_launch:"):
                 traffic = float(line.split(":")[1])
-    return {"bound": "hbm", "kernel": "k_sell<float,2,2,false,4,MODE_CHEB> (finest velocity level)",
-            "achieved": dom["gbs"], "peak": peak,
-            "unit": "GB/s", "frac": dom["gbs"] / peak, "traffic": traffic,
-            "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6800 GB/s",
-            "launch_us": dom["ms"] * 1e3, "algorithmic_bytes": dom["bytes"], "others": out}
+    dom = out.get("velocity_down_fused_f32")
+    if dom is None:   # fused levels off (--no-mg-fused): the per-level sparse smoothing step
+        d = out["sell_velocity_chebyshev_f32"]
+        return {"bound": "hbm", "kernel": "k_sell<float,2,2,false,4,MODE_CHEB> (finest velocity level)",
+                "achieved": d["gbs"], "peak": peak, "unit": "GB/s", "frac": d["hbm_frac"], "traffic": None,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6800 GB/s",
+                "launch_us": d["us"], "algorithmic_bytes": d["bytes"], "others": out}
+    return {"bound": "alu", "kernel": "k_mfu_down<float,8,2,512> (fused down launch, finest velocity level)",
+            "achieved": dom["tflops"], "peak": alu_peak, "unit": "TFLOP/s", "frac": dom["alu_frac"],
+            "traffic": traffic, "peak_source": "derived: FP32 FMA lanes x 2 x max SM clock",
+            "peak_derivation": alu_how, "launch_us": dom["us"], "algorithmic_flops": dom["flops"],
+            "algorithmic_bytes": dom["bytes"], "hbm_gbs": dom["gbs"], "hbm_frac": dom["hbm_frac"],
+            "hbm_peak": peak, "others": out}
 
 
 def large_n_roofline(fsi, stream, device_index, peak, N):
@@ -391,15 +429,19 @@ def large_n_roofline(fsi, stream, device_index, peak, N):
     clocks = ClockSampler(device_index)
     clocks.start()
     out = {"N": N, "dofs": int(prob_dofs(case)), "workload": "ellipse sweep member, m = ceil(0.4 N)"}
-    for name, which in (("full_operator_f32", 0), ("velocity_chebyshev_f32", 2), ("full_operator_f64", 1)):
+    for name, which in (("full_operator_f32", 0), ("sell_velocity_chebyshev_f32", 2), ("full_operator_f64", 1)):
         ms, by = prob.time_kernel(which, reps=30)
         out[name] = {"us": ms * 1e3, "bytes": by, "gbs": by / ms / 1e6, "frac": by / ms / 1e6 / peak}
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    out.update(fused_kernels(prob, peak, fp32_peak_tflops(peaks)[0], 20))
     prob.close()
     prob64 = fsi.problem_from_case(case, precision=0, precond=PRECOND, rtol=1e-8, stream=stream.cuda_stream,
                                    max_it=MAX_IT, stokes_its=STOKES_ITS, **arm_settings(0))
     prob64.assemble_step()
     ms, by = prob64.time_kernel(3, reps=30)
-    out["velocity_chebyshev_f64"] = {"us": ms * 1e3, "bytes": by, "gbs": by / ms / 1e6, "frac": by / ms / 1e6 / peak}
+    out["sell_velocity_chebyshev_f64"] = {"us": ms * 1e3, "bytes": by, "gbs": by / ms / 1e6,
+                                          "frac": by / ms / 1e6 / peak}
     prob64.close()
     out["clocks"] = clocks.stop()
     out["l2"] = "evicted before every launch (256 MiB write)"
@@ -555,6 +597,25 @@ def batch_arm(fsi, torch, cases, precision, args):
 
 
 BATCH_RESTART = 60
+
+
+def run_profile_kernel(args):
+    """A small run for a per-kernel profiler: one problem of the size sweep
+    (ellipse, --profile-n cells, --profile-precision) and --profile-reps
+    launches of the kernel --profile-kernel of fsi_time_kernel (each after an
+    L2-evicting write), nothing else."""
+    import fsi_inputs as fi
+    from paper_2301_10041_gb300 import build, fsi
+    build.build()
+    case = fi.ellipse_case(args.profile_n)
+    prob = fsi.problem_from_case(case, precision=args.profile_precision, precond=PRECOND, rtol=1e-8,
+                                 max_it=MAX_IT, stokes_its=STOKES_ITS, **arm_settings(args.profile_precision),
+                                 **mg_settings())
+    prob.assemble_step()
+    ms, by = prob.time_kernel(args.profile_kernel, reps=args.profile_reps)
+    print(json.dumps({"profile_kernel": args.profile_kernel, "N": args.profile_n,
+                      "precision": args.profile_precision, "us": ms * 1e3, "bytes": by}))
+    prob.close()
 
 
 def run_batch(args):
@@ -789,12 +850,18 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=300.0)
     ap.add_argument("--profile-step", action="store_true",
                     help="only build the mixed problem, run --warmup steps and one more (for ncu)")
+    ap.add_argument("--profile-kernel", type=int, default=-1,
+                    help="only time kernel WHICH of fsi_time_kernel on one ellipse problem (for ncu)")
+    ap.add_argument("--profile-n", type=int, default=512)
+    ap.add_argument("--profile-precision", type=int, default=0)
+    ap.add_argument("--profile-reps", type=int, default=2)
     ap.add_argument("--workload", choices=["cavity128", "batch", "serve", "sweep", "bar", "annulus"],
                     default="cavity128",
                     help="cavity128 (default, the contract line); the others print their own lines")
     ap.add_argument("--batch-instances", type=int, default=256)
-    ap.add_argument("--batch-stokes-its", type=int, default=STOKES_ITS,
-                    help="Richardson steps on the Stokes block per preconditioner application (batch workload)")
+    ap.add_argument("--batch-stokes-its", type=int, default=12,
+                    help="Richardson steps on the Stokes block per preconditioner application (batch workload; "
+                         "12: every instance-step reaches 1e-8, 8 left the stiffest instance stalled)")
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-budget-gb", type=float, default=64.0)
     ap.add_argument("--serve-max-resident", type=int, default=16)
@@ -849,6 +916,8 @@ def main():
         return run_annulus(args)
     if args.profile_step:
         return run_profile_step(args)
+    if args.profile_kernel >= 0:
+        return run_profile_kernel(args)
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     if args.impl == "reference":
