@@ -398,28 +398,45 @@ __host__ __device__ void mfu_down_body(const MfVelArgs<T>& a, const MfCta& cta) 
   });
   MF_SYNC();
   // restriction to the coarse nodes of the tile (coarse lattice interior
-  // 1 .. N - 1): the 1-D weight of a fine node at 2X + d is the coarse
-  // quadratic of node X there, L0(|d| / 4) at a cell corner, L1((d + 2) / 4)
-  // at an edge or cell midpoint (|d| <= 1)
+  // 1 .. N - 1).  The weight of a fine node at (2X + dx, 2Y + dy) is the
+  // product of 1-D weights, each the coarse quadratic of its node there:
+  // L0(|d| / 4) at a cell corner, L1((d + 2) / 4) at an edge or cell midpoint
+  // (|d| <= 1).  So the sum is taken in two passes, along x into the free
+  // buffer Xn (fine rows 2 CY0 - 3 .. 2 CY0 + 2 TC + 1 by coarse columns),
+  // then along y.
   const int Nc = N / 2;
+  constexpr int RR = 2 * TC + 5;
+  T2* Rx = Xn;
+  mf_rows(cta, TC, RR, [&](int i, int j) {
+    const int X0 = CX0 + i, iy = 2 * CY0 - 3 + j;
+    T s0 = 0, s1 = 0;
+#pragma unroll
+    for (int dx = -3; dx <= 3; ++dx) {
+      const float tx = (X0 & 1) ? 0.25f * (float)(dx + 2) : 0.25f * (float)(dx < 0 ? -dx : dx);
+      const T wx = (X0 & 1) ? ((dx >= -1 && dx <= 1) ? (T)mf_l1(tx) : (T)0) : (T)mf_l0(tx);
+      if (wx == (T)0) continue;
+      const T2 r = R[f.at_lattice(2 * X0 + dx, iy)];
+      s0 += wx * r.x;
+      s1 += wx * r.y;
+    }
+    T2 v;
+    v.x = s0;
+    v.y = s1;
+    Rx[j * TC + i] = v;
+  });
+  MF_SYNC();
   mf_rows(cta, TC, TC, [&](int i, int j) {
     const int X0 = CX0 + i, Y0 = CY0 + j;
     if (!mf_vinterior(Nc, X0, Y0)) return;
     T s0 = 0, s1 = 0;
-    const int rx = (X0 & 1) ? 1 : 3, ry = (Y0 & 1) ? 1 : 3;
-    for (int dy = -ry; dy <= ry; ++dy) {
+#pragma unroll
+    for (int dy = -3; dy <= 3; ++dy) {
       const float ty = (Y0 & 1) ? 0.25f * (float)(dy + 2) : 0.25f * (float)(dy < 0 ? -dy : dy);
-      const T wy = (T)((Y0 & 1) ? mf_l1(ty) : mf_l0(ty));
+      const T wy = (Y0 & 1) ? ((dy >= -1 && dy <= 1) ? (T)mf_l1(ty) : (T)0) : (T)mf_l0(ty);
       if (wy == (T)0) continue;
-      for (int dx = -rx; dx <= rx; ++dx) {
-        const float tx = (X0 & 1) ? 0.25f * (float)(dx + 2) : 0.25f * (float)(dx < 0 ? -dx : dx);
-        const T wx = (T)((X0 & 1) ? mf_l1(tx) : mf_l0(tx));
-        if (wx == (T)0) continue;
-        const T2 r = R[f.at_lattice(2 * X0 + dx, 2 * Y0 + dy)];
-        const T w = wx * wy;
-        s0 += w * r.x;
-        s1 += w * r.y;
-      }
+      const T2 r = Rx[(2 * j + 3 + dy) * TC + i];   // fine row 2 Y0 + dy
+      s0 += wy * r.x;
+      s1 += wy * r.y;
     }
     const int id = mf_vnode(Nc, X0, Y0);
     a.bc[2 * id] = s0;
