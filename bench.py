@@ -49,7 +49,8 @@ def workload_config(case):
                         "triangles), kappa=1e3, nu=0.01, rho=1, dt=1e-3, lid 1, rtol 1e-8",
             "preconditioner": "block upper-triangular; Stokes block by %d Richardson steps of a V-cycle pair "
                               "(Chebyshev degree %d)" % (STOKES_ITS, MG_DEGREE or 2),
-            "multigrid": {"fused_fine_levels": MG_FUSED == 0, "cluster": MG_CLUSTER},
+            "multigrid": {"fused_fine_levels": MG_FUSED == 0, "cluster": MG_CLUSTER,
+                          "coarsest_cells": MG_COARSE or 16},
             "restart": {"mixed": RESTART_MIXED, "fp64": RESTART}, "inner_rtol": INNER_RTOL,
             "N": case.N, "solid_nodes": int(case.ref_xy.shape[0]), "solid_tris": int(case.tris.shape[0]),
             "dofs": None, "l2": "flushed between timed steps (512 MiB write)"}
@@ -125,6 +126,7 @@ AUTOTUNE = 0     # 0: one fixed SpMV tile shape (faster inside a step); 1: the l
 MG_FUSED = 0     # 0: fused matrix-free kernels on the finest FP32 multigrid levels; -1: per-level sparse kernels
 MG_CLUSTER = 0   # 0: coarse levels in one cluster launch; -1: per-level launches; n > 0: cluster levels <= n cells
 MG_DEGREE = 0    # Chebyshev degree of each multigrid smoothing (0: the library's default, 2)
+MG_COARSE = 0    # coarsest multigrid grid in cells (0: the library's default, 16)
 
 
 def arm_settings(precision):
@@ -136,7 +138,7 @@ def arm_settings(precision):
 
 def mg_settings():
     """Multigrid kernel choice and smoothing degree of the bench's arms (command-line switches)."""
-    return dict(mg_fused=MG_FUSED, mg_cluster=MG_CLUSTER, mg_degree=MG_DEGREE)
+    return dict(mg_fused=MG_FUSED, mg_cluster=MG_CLUSTER, mg_degree=MG_DEGREE, mg_coarse=MG_COARSE)
 
 
 def time_arm(fsi, torch, case, precision, steps, warmup, stream, flush, precond=PRECOND, stokes_its=STOKES_ITS,
@@ -841,7 +843,7 @@ def run_serve(args):
 
 
 def main():
-    global AUTOTUNE, MG_FUSED, MG_CLUSTER, MG_DEGREE, STOKES_ITS
+    global AUTOTUNE, MG_FUSED, MG_CLUSTER, MG_DEGREE, MG_COARSE, STOKES_ITS
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
@@ -880,6 +882,8 @@ def main():
     ap.add_argument("--stokes-its", type=int, default=STOKES_ITS,
                     help="Richardson steps on the Stokes block per preconditioner application (bench workload)")
     ap.add_argument("--mg-degree", type=int, default=0, help="Chebyshev degree of each multigrid smoothing")
+    ap.add_argument("--mg-coarse", type=int, default=0,
+                    help="coarsest multigrid grid in cells (0: the library's default)")
     ap.add_argument("--mg-cluster", type=int, default=0,
                     help="0: coarse levels in one cluster launch; -1: per-level launches; n > 0: only levels of at "
                          "most n cells a side in the cluster")
@@ -903,6 +907,7 @@ def main():
     args = ap.parse_args()
     MG_CLUSTER = args.mg_cluster
     MG_DEGREE = args.mg_degree
+    MG_COARSE = args.mg_coarse
     STOKES_ITS = args.stokes_its
     if args.autotune:
         AUTOTUNE = 1

@@ -135,6 +135,13 @@ typedef struct fsi_params {
                           launches (pre-smoothing + residual + restriction;
                           prolongation + post-smoothing); -1: the per-level
                           sparse kernels on every level */
+    int    mg_coarse;  /* the coarsening stops at the first grid of at most
+                          mg_coarse cells a side, whose operators are inverted
+                          densely on the device when the problem is created
+                          (Gauss-Jordan in FP64, one launch per unknown);
+                          0 = 16 (a 16-cell grid: 1922 velocity unknowns, a
+                          15 MB FP32 or 30 MB FP64 inverse, held in L2); at
+                          most 32 (FSI_ERR_INVALID above) */
 } fsi_params;
 
 /* Solid reference mesh (the body at t = 0): P1 triangles, or Q1

@@ -56,6 +56,7 @@ struct ClArgs {
   int gbuf = -1;           // coarsest level: gathered right-hand side
   const T* dense_inv = nullptr;
   int dense_n = 0;
+  int dense_ld = 0;        // entries per row of dense_inv (>= dense_n)
   const T* in_b = nullptr; // right-hand side of the top cluster level (global)
   T* out_x = nullptr;      // its V-cycle result (global)
   ClLevel<T> lv[kClMaxLevels];
@@ -307,7 +308,7 @@ __global__ void __launch_bounds__(kClThreads, 1) k_vcycle_cluster(const __grid_c
     T* x = cl_ptr<T>(sm, C.x);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int i = warp; i < nown; i += nw) {
-      const T* __restrict__ arow = a.dense_inv + (size_t)(rc0 * B + i) * n;
+      const T* __restrict__ arow = a.dense_inv + (size_t)(rc0 * B + i) * a.dense_ld;
       // eight independent loads in flight per lane, one L2 round trip for
       // rows of up to 256 entries
       T acc8[8];

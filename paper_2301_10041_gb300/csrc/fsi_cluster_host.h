@@ -4,7 +4,7 @@
 // the shared-memory layout of the level vectors.
 //
 // Included after the definitions of Arena (upload, count_only), Cheb and
-// MG<T> (lv[l].ch, coarse_inv, coarse_n, degree, cl), by the solver and by
+// MG<T> (lv[l].ch, coarse_inv, coarse_n, coarse_ld, degree, cl), by the solver and by
 // the CPU test harness that emulates the cluster kernel.
 #pragma once
 #include <algorithm>
@@ -169,6 +169,7 @@ bool build_cluster(ArenaT& ar, const HostSetup& hs, bool pressure, MGT& mg, int 
       C.x = vec(n); C.x2 = vec(n); C.b = vec(n); C.r = vec(n); C.d = vec(n);
     }
     a.dense_n = mg.coarse_n;
+    a.dense_ld = mg.coarse_ld;
     a.gbuf = vec((size_t)a.dense_n);
     const size_t smem = (off + 15) & ~(size_t)15;
     if (smem > cap || !viable(smem)) continue;

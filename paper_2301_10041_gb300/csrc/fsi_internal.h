@@ -58,6 +58,7 @@ struct FluidLevelHost {
 struct SetupParams {
   int N; double rho, nu, kappa, dt, lid;
   int npe = 3;            // solid element: 3 = P1 triangle, 4 = Q1 quadrilateral
+  int coarse_max = 8;     // coarsening stops at the first grid of at most this many cells a side
 };
 
 struct HostSetup {
@@ -73,8 +74,12 @@ struct HostSetup {
   std::vector<double> mp_inv;  // inverse P1disc mass diagonal, 3 per cell
   std::vector<double> cs_dinv; // inverse diagonal of the solid mass
   std::vector<FluidLevelHost> levels;  // 0 = finest
-  std::vector<double> coarseAinv;   // dense inverse of the coarsest A_f (row-major)
-  std::vector<double> coarseLinv;   // dense pseudo-inverse of the coarsest pressure Laplacian
+  // the coarsest level as dense row-major matrices, inverted on the device
+  // when a problem is created: A_f, and the pressure Laplacian made regular
+  // by a rank-one term (L + t e e^T / |e|^2, whose inverse equals L^+ on
+  // right-hand sides orthogonal to the constants e, up to e-components)
+  std::vector<double> coarseA;
+  std::vector<double> coarseL;
   int coarse_nA = 0, coarse_nL = 0;
   std::vector<int> interior_lattice;   // internal node -> lattice id (finest)
   std::vector<int> lattice_to_node;    // lattice id -> internal node or -1

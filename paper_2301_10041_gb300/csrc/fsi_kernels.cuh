@@ -530,21 +530,108 @@ __global__ void k_cf_apply(int nS, int cap, const int* __restrict__ len, const i
 // ------------------------------------------------------------ small dense
 // y = A x for a dense row-major n x n matrix (coarsest multigrid level):
 // one warp per row, lanes over the columns, 8 rows per CTA
+// 16-byte vector of T
 template <class T>
-__global__ void k_dense_mv(int n, const T* __restrict__ A, const T* __restrict__ x, T* __restrict__ y) {
+struct Vec16;
+template <>
+struct Vec16<float> {
+  using type = float4;
+  __device__ static float dot(float4 a, float4 b, float s) {
+    return fmaf(a.w, b.w, fmaf(a.z, b.z, fmaf(a.y, b.y, fmaf(a.x, b.x, s))));
+  }
+};
+template <>
+struct Vec16<double> {
+  using type = double2;
+  __device__ static double dot(double2 a, double2 b, double s) { return fma(a.y, b.y, fma(a.x, b.x, s)); }
+};
+
+// y = A x with the dense inverse of the coarsest level: one warp per row,
+// rows of ld entries (16-byte multiples, zero padding), x padded to ld with
+// zeros; 16-byte loads, eight per lane in flight, so that a row of a few
+// thousand entries takes one or two L2 round trips.
+template <class T>
+__global__ void k_dense_mv(int n, int ld, const T* __restrict__ A, const T* __restrict__ x, T* __restrict__ y) {
   pdl_begin();
+  using V = typename Vec16<T>::type;
+  constexpr int W = 16 / (int)sizeof(T), U = 8;
   const int lane = threadIdx.x & 31;
   const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (i >= n) return;
-  const T* __restrict__ a = A + (size_t)i * n;
-  T s0 = 0, s1 = 0;
-  int j = lane;
-  for (; j + 32 < n; j += 64) { s0 += a[j] * x[j]; s1 += a[j + 32] * x[j + 32]; }
-  if (j < n) s0 += a[j] * x[j];
-  T s = s0 + s1;
+  const V* __restrict__ a = reinterpret_cast<const V*>(A + (size_t)i * ld);
+  const V* xv = reinterpret_cast<const V*>(x);
+  const int nv = ld / W;
+  T acc[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) acc[u] = 0;
+  for (int j0 = lane; j0 < nv; j0 += 32 * U) {
+    V av[U], bv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int j = j0 + 32 * u;
+      if (j < nv) {
+        av[u] = __ldg(a + j);
+        bv[u] = xv[j];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (j0 + 32 * u < nv) acc[u] = Vec16<T>::dot(av[u], bv[u], acc[u]);
+  }
+  T s = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
   if (lane == 0) y[i] = s;
+}
+
+// ------------------------------------------------ coarsest-level inverse
+// Gauss-Jordan elimination in place on a symmetric positive definite matrix
+// (the coarsest A_f, or the pressure Laplacian made regular): launch k
+// exchanges unknown k with equation k.  With p the pivot M_kk before the
+// launch, entry (i, j) becomes
+//   1 / p                   for i = j = k,
+//   M_kj / p                for i = k, j != k,
+//   -M_ik / p               for j = k, i != k,
+//   M_ij - M_ik M_kj / p    otherwise,
+// and after the launches for k = 0 .. n-1 the matrix holds its inverse.  The
+// pivots of a positive definite matrix stay positive, so no rows are
+// exchanged.  Row k and column k come from copies (rin, cin) written by the
+// previous launch, so the entries of one launch are independent; the launch
+// writes its row k+1 and column k+1 to (rout, cout) for the next one.
+__global__ void k_gj_step(int n, int ld, int k, double* __restrict__ M, const double* __restrict__ rin,
+                          const double* __restrict__ cin, double* __restrict__ rout, double* __restrict__ cout) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= n || j >= n) return;
+  const double ip = 1.0 / rin[k];
+  double v;
+  if (i == k)
+    v = (j == k) ? ip : rin[j] * ip;
+  else if (j == k)
+    v = -cin[i] * ip;
+  else
+    v = M[(size_t)i * ld + j] - cin[i] * (rin[j] * ip);
+  M[(size_t)i * ld + j] = v;
+  if (i == k + 1) rout[j] = v;
+  if (j == k + 1) cout[i] = v;
+}
+
+// row 0 and column 0 of M for the first k_gj_step
+__global__ void k_gj_first(int n, int ld, const double* __restrict__ M, double* __restrict__ r, double* __restrict__ c) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  r[i] = M[i];
+  c[i] = M[(size_t)i * ld];
+}
+
+// out = (T) in, n rows; rows of ldi (in) and ldo (out) entries, the padding
+// of out zero
+template <class T>
+__global__ void k_dense_round(int n, const double* __restrict__ in, int ldi, T* __restrict__ out, int ldo) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.y;
+  if (j >= ldo) return;
+  out[(size_t)i * ldo + j] = j < n ? (T)in[(size_t)i * ldi + j] : (T)0;
 }
 
 // ----------------------------------------------------------- vector kernels

@@ -464,35 +464,6 @@ static std::vector<double> dense_of(const HostBlockMatrix& A) {
   return D;
 }
 
-// Gauss-Jordan inverse with partial pivoting (row-major, in place).
-static void dense_inverse(std::vector<double>& a, int n) {
-  std::vector<double> inv((size_t)n * n, 0.0);
-  for (int i = 0; i < n; ++i) inv[(size_t)i * n + i] = 1.0;
-  for (int c = 0; c < n; ++c) {
-    int p = c;
-    for (int r = c + 1; r < n; ++r)
-      if (std::fabs(a[(size_t)r * n + c]) > std::fabs(a[(size_t)p * n + c])) p = r;
-    if (a[(size_t)p * n + c] == 0.0) throw std::runtime_error("singular coarse matrix");
-    if (p != c)
-      for (int k = 0; k < n; ++k) {
-        std::swap(a[(size_t)p * n + k], a[(size_t)c * n + k]);
-        std::swap(inv[(size_t)p * n + k], inv[(size_t)c * n + k]);
-      }
-    const double piv = 1.0 / a[(size_t)c * n + c];
-    for (int k = 0; k < n; ++k) { a[(size_t)c * n + k] *= piv; inv[(size_t)c * n + k] *= piv; }
-    for (int r = 0; r < n; ++r) {
-      if (r == c) continue;
-      const double f = a[(size_t)r * n + c];
-      if (f == 0.0) continue;
-      for (int k = 0; k < n; ++k) {
-        a[(size_t)r * n + k] -= f * a[(size_t)c * n + k];
-        inv[(size_t)r * n + k] -= f * inv[(size_t)c * n + k];
-      }
-    }
-  }
-  a.swap(inv);
-}
-
 void triangle_rule(double lam[6][3], double w[6]) {
   const double A1 = 0.44594849091596488632, W1 = 0.22338158967801146570;
   const double A2 = 0.091576213509770743460, W2 = 0.10995174365532186764;
@@ -619,10 +590,11 @@ void build_setup(const SetupParams& sp, int n_s, int n_tri, const double* ref_xy
     out.interior_lattice[k] = iy * n1 + ix;
     out.lattice_to_node[(size_t)iy * n1 + ix] = k;
   }
-  // ---- multigrid hierarchy: N, N/2, ... while even and > 8 (coarsest <= 8:
-  // at most 2*15^2 = 450 velocity unknowns, inverted densely)
+  // ---- multigrid hierarchy: N, N/2, ... while even and above coarse_max
+  // cells a side; the coarsest is solved with its dense inverse (a grid of 16
+  // cells has 2 * 31^2 = 1922 velocity unknowns)
   std::vector<int> Ns{N};
-  while (Ns.back() % 2 == 0 && Ns.back() > 8) Ns.push_back(Ns.back() / 2);
+  while (Ns.back() % 2 == 0 && Ns.back() > sp.coarse_max) Ns.push_back(Ns.back() / 2);
   out.levels.resize(Ns.size());
   for (size_t l = 0; l < Ns.size(); ++l) {
     FluidLevelHost& L = out.levels[l];
@@ -655,11 +627,10 @@ void build_setup(const SetupParams& sp, int n_s, int n_tri, const double* ref_xy
   }
   {
     const FluidLevelHost& C = out.levels.back();
-    out.coarseAinv = dense_of(C.A);
+    out.coarseA = dense_of(C.A);
     out.coarse_nA = C.A.nrows * 2;
-    dense_inverse(out.coarseAinv, out.coarse_nA);
-    // pseudo-inverse of the singular pressure Laplacian: (L + t e e^T/|e|^2)^-1;
-    // on right-hand sides orthogonal to e this equals L^+ up to e-components
+    // the singular pressure Laplacian plus t e e^T / |e|^2 (t its mean
+    // diagonal), e the constants (first dof of every cell)
     std::vector<double> Ld = dense_of(C.L);
     const int n = C.L.nrows * 3;
     out.coarse_nL = n;
@@ -669,8 +640,7 @@ void build_setup(const SetupParams& sp, int n_s, int n_tri, const double* ref_xy
     const double ee = (double)(n / 3);
     for (int i = 0; i < n; i += 3)
       for (int j = 0; j < n; j += 3) Ld[(size_t)i * n + j] += t / ee;
-    dense_inverse(Ld, n);
-    out.coarseLinv = Ld;
+    out.coarseL.swap(Ld);
   }
   // inverse P1disc mass: diag(h^2, h^2/12, h^2/12) per cell
   {

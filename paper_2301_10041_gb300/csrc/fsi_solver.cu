@@ -328,8 +328,9 @@ struct ClusterMG {
 template <class T>
 struct MG {
   std::vector<MGLevel<T>> lv;
-  T* coarse_inv = nullptr;
+  T* coarse_inv = nullptr;   // dense inverse of the coarsest level, rows of coarse_ld entries
   int coarse_n = 0;
+  int coarse_ld = 0;         // coarse_n rounded up to 16 bytes (the row padding is zero)
   int degree = 2;
   bool pressure = false;
   ClusterMG<T> cl;
@@ -338,8 +339,67 @@ struct MG {
 constexpr double kChebRatioU = 6.0;   // smoothing interval [hi/ratio, hi]
 constexpr double kChebRatioP = 8.0;
 
+// Dense inverse of the coarsest level in place on the device (FP64, rows of
+// ld entries, the padding zero): Gauss-Jordan elimination, one launch per
+// pivot (k_gj_step).  M holds the dense matrix on entry.
+static void dense_inverse_device(Arena& ar, double* M, int n, int ld, cudaStream_t s) {
+  double* rc = ar.alloc<double>(4 * (size_t)n);   // row and column copies, two pairs
+  if (ar.count_only) return;
+  double *r0 = rc, *c0 = rc + n, *r1 = rc + 2 * n, *c1 = rc + 3 * n;
+  k_gj_first<<<nblk(n, 256), 256, 0, s>>>(n, ld, M, r0, c0);
+  CK(cudaGetLastError());
+  const dim3 blk(32, 8), grd((n + 31) / 32, (n + 7) / 8);
+  for (int k = 0; k < n; ++k) {
+    k_gj_step<<<grd, blk, 0, s>>>(n, ld, k, M, r0, c0, r1, c1);
+    std::swap(r0, r1);
+    std::swap(c0, c1);
+  }
+  CK(cudaGetLastError());
+}
+
+// 16-byte row length of the dense coarsest inverse, in entries
 template <class T>
-static void build_mg(Arena& ar, const HostSetup& hs, bool pressure, int degree, MG<T>& mg, bool tune) {
+static int dense_ld(int n) {
+  constexpr int w = 16 / (int)sizeof(T);
+  return (n + w - 1) / w * w;
+}
+
+// The coarsest level's dense inverse: the FP64 hierarchy inverts the
+// assembled matrix in place; the FP32 one rounds the FP64 inverse (inv64,
+// rows of ld64 entries).  The FP64 hierarchy is built first.
+template <class T>
+static void build_coarse_inverse(Arena& ar, const HostSetup& hs, bool pressure, MG<T>& mg, const double* inv64,
+                                 int ld64, cudaStream_t s) {
+  const int n = pressure ? hs.coarse_nL : hs.coarse_nA;
+  mg.coarse_n = n;
+  mg.coarse_ld = dense_ld<T>(n);
+  const int ld = mg.coarse_ld;
+  mg.coarse_inv = ar.alloc<T>((size_t)n * ld);
+  if constexpr (std::is_same<T, double>::value) {
+    if (!ar.count_only) {
+      const std::vector<double>& D = pressure ? hs.coarseL : hs.coarseA;
+      CK(cudaMemsetAsync(mg.coarse_inv, 0, (size_t)n * ld * sizeof(double), s));
+      CK(cudaMemcpy2DAsync(mg.coarse_inv, (size_t)ld * sizeof(double), D.data(), (size_t)n * sizeof(double),
+                           (size_t)n * sizeof(double), n, cudaMemcpyHostToDevice, s));
+    }
+    dense_inverse_device(ar, mg.coarse_inv, n, ld, s);
+  } else if (!ar.count_only) {
+    if (!inv64) throw std::logic_error("the FP64 coarse inverse is built first");
+    k_dense_round<T><<<dim3((ld + 255) / 256, n), 256, 0, s>>>(n, inv64, ld64, mg.coarse_inv, ld);
+    CK(cudaGetLastError());
+  }
+  // the coarsest right-hand side, padded to ld with zeros, for the dense product
+  MGLevel<T>& C = mg.lv.back();
+  C.b = ar.alloc<T>(ld);
+  if (!ar.count_only) {
+    CK(cudaMemsetAsync(C.b, 0, (size_t)ld * sizeof(T), s));
+    CK(cudaStreamSynchronize(s));
+  }
+}
+
+template <class T>
+static void build_mg(Arena& ar, const HostSetup& hs, bool pressure, int degree, MG<T>& mg, bool tune,
+                     cudaStream_t s, const double* inv64 = nullptr, int ld64 = 0) {
   const int nl = (int)hs.levels.size();
   mg.degree = degree;
   mg.pressure = pressure;
@@ -359,7 +419,8 @@ static void build_mg(Arena& ar, const HostSetup& hs, bool pressure, int degree, 
       L.R = upload_sell<T>(ar, to_sell(pressure ? H.Rp : H.Ru));
       if (pressure) L.RA = upload_sell<T>(ar, to_sell(H.RAp));
     }
-    L.x = ar.alloc<T>(L.n); L.x2 = ar.alloc<T>(L.n); L.b = ar.alloc<T>(L.n);
+    L.x = ar.alloc<T>(L.n); L.x2 = ar.alloc<T>(L.n);
+    if (l + 1 < nl) L.b = ar.alloc<T>(L.n);   // the coarsest: build_coarse_inverse
     if (!pressure) L.r = ar.alloc<T>(L.n);
     L.d = ar.alloc<T>(L.n);
     const double hi = 1.05 * (pressure ? H.lmaxL : H.lmaxA);
@@ -383,8 +444,7 @@ static void build_mg(Arena& ar, const HostSetup& hs, bool pressure, int degree, 
       L.mftab = upload_as<T>(ar, tab);
     }
   }
-  mg.coarse_n = pressure ? hs.coarse_nL : hs.coarse_nA;
-  mg.coarse_inv = upload_as<T>(ar, pressure ? hs.coarseLinv : hs.coarseAinv);  // row-major
+  build_coarse_inverse<T>(ar, hs, pressure, mg, inv64, ld64, s);
 }
 
 // ------------------------------------------- cluster-resident coarse levels
@@ -661,7 +721,8 @@ static T* vcycle(MG<T>& mg, int l, cudaStream_t s, T* out, const SpmvArgs<T>* fi
     return dst;
   }
   if (l == last) {
-    launch(k_dense_mv<T>, nblk(mg.coarse_n, 8), 256, 0, s, mg.coarse_n, mg.coarse_inv, L.b, out ? out : L.x);
+    launch(k_dense_mv<T>, nblk(mg.coarse_n, 8), 256, 0, s, mg.coarse_n, mg.coarse_ld, (const T*)mg.coarse_inv,
+           (const T*)L.b, out ? out : L.x);
     return out ? out : L.x;
   }
   T* xc = L.x;
@@ -1393,6 +1454,7 @@ static void check_params(const fsi_params& p, int n_nodes, int n_tris) {
     throw std::invalid_argument("the Q1 solid takes the point rule and the linear law");
   if (p.mg_cluster < -1) throw std::invalid_argument("mg_cluster");
   if (p.mg_fused != 0 && p.mg_fused != -1) throw std::invalid_argument("mg_fused");
+  if (p.mg_coarse < 0 || p.mg_coarse > 32) throw std::invalid_argument("mg_coarse must be 0..32");
   if (p.coupling != 0 && p.coupling != 1) throw std::invalid_argument("coupling");
   if (p.solid_law != 0 && p.solid_law != 1) throw std::invalid_argument("solid_law");
   if (p.autotune != 0 && p.autotune != 1) throw std::invalid_argument("autotune");
@@ -1421,6 +1483,9 @@ static fsi_params with_defaults(fsi_params p) {
   if (!(p.stokes_omega > 0)) p.stokes_omega = 1.0;
   if (!(p.newton_tol > 0)) p.newton_tol = 1e-6;
   if (p.newton_max <= 0) p.newton_max = 20;
+  // coarsest grid 16 cells: one dense product (a 15 MB FP32 inverse, held in
+  // L2) in place of the 16-cell level's two launches and the 8-cell solve
+  if (p.mg_coarse <= 0) p.mg_coarse = 16;
   return p;
 }
 
@@ -1428,8 +1493,11 @@ template <class T>
 static void build_prec(Problem& P, Prec<T>& pr, const FullOp<T>& op, bool alloc_all) {
   (void)alloc_all;
   Arena& ar = P.ar;
-  build_mg<T>(ar, P.hs, false, P.prm.mg_degree, pr.mgU, P.prm.autotune == 1);
-  build_mg<T>(ar, P.hs, true, P.prm.mg_degree, pr.mgP, P.prm.autotune == 1);
+  const bool f64 = std::is_same<T, double>::value;
+  build_mg<T>(ar, P.hs, false, P.prm.mg_degree, pr.mgU, P.prm.autotune == 1, P.stream,
+              f64 ? nullptr : P.p64.mgU.coarse_inv, P.p64.mgU.coarse_ld);
+  build_mg<T>(ar, P.hs, true, P.prm.mg_degree, pr.mgP, P.prm.autotune == 1, P.stream,
+              f64 ? nullptr : P.p64.mgP.coarse_inv, P.p64.mgP.coarse_ld);
   // With the fused matrix-free levels (FP32, every level of 16 cells or more)
   // the automatic choice leaves the cluster out: two fused launches per level
   // measured faster than the cluster launch of the same levels on GB300
@@ -1872,6 +1940,7 @@ static size_t footprint_impl(const fsi_params& prm0, int n_nodes, int n_tris, co
   P.m = prm.restart;
   SetupParams sp{prm.N, prm.rho_f, prm.nu, prm.kappa, prm.dt, prm.lid_u};
   sp.npe = elem_nodes(prm);
+  sp.coarse_max = prm.mg_coarse;
   build_setup(sp, n_nodes, n_tris, ref_xy, tris, P.hs);
   allocate_problem(P, ref_xy, tris);
   return P.ar.bytes;
@@ -1996,6 +2065,7 @@ int fsi_create_problem_budget(const fsi_params* params, const fsi_solid_mesh* me
     P.m = prm.restart;
     SetupParams sp{prm.N, prm.rho_f, prm.nu, prm.kappa, prm.dt, prm.lid_u};
     sp.npe = elem_nodes(prm);
+    sp.coarse_max = prm.mg_coarse;
     build_setup(sp, P.nS, P.nTri, mesh->ref_xy, mesh->tris, P.hs);
     {
       double lam[6][3], w[6];

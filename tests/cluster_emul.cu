@@ -68,6 +68,7 @@ struct HostMG {
   std::vector<Lv> lv;
   T* coarse_inv = nullptr;
   int coarse_n = 0;
+  int coarse_ld = 0;
   int degree = 2;
   struct {
     bool on = false;
@@ -225,7 +226,7 @@ static std::vector<T> emulate(const ClArgs<T>& a, size_t smem, int B, bool tkron
         const size_t row = (size_t)s0 * kSliceRows * B + i;
         REQ(row < (size_t)n);
         T s = 0;
-        for (int j = 0; j < n; ++j) s += a.dense_inv[row * n + j] * g[r][j];
+        for (int j = 0; j < n; ++j) s += a.dense_inv[row * a.dense_ld + j] * g[r][j];
         e.at<T>(r, C.x, i) = s;
       }
     }
@@ -275,12 +276,40 @@ static std::vector<double> mv(const HostBlockMatrix& A, const std::vector<double
   return y;
 }
 
-static std::vector<double> ref_vcycle(const HostSetup& hs, bool pr, const std::vector<ChebCoef>& ch, int degree, int l,
-                                      const std::vector<double>& b) {
+// Gauss-Jordan inverse with partial pivoting (row-major, n x n): the dense
+// coarsest solve of the reference V-cycle and of the emulated cluster
+static std::vector<double> host_inverse(std::vector<double> a, int n) {
+  std::vector<double> inv((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) inv[(size_t)i * n + i] = 1.0;
+  for (int c = 0; c < n; ++c) {
+    int p = c;
+    for (int r = c + 1; r < n; ++r)
+      if (std::fabs(a[(size_t)r * n + c]) > std::fabs(a[(size_t)p * n + c])) p = r;
+    if (p != c)
+      for (int k = 0; k < n; ++k) {
+        std::swap(a[(size_t)p * n + k], a[(size_t)c * n + k]);
+        std::swap(inv[(size_t)p * n + k], inv[(size_t)c * n + k]);
+      }
+    const double piv = 1.0 / a[(size_t)c * n + c];
+    for (int k = 0; k < n; ++k) { a[(size_t)c * n + k] *= piv; inv[(size_t)c * n + k] *= piv; }
+    for (int r = 0; r < n; ++r) {
+      if (r == c) continue;
+      const double f = a[(size_t)r * n + c];
+      if (f == 0.0) continue;
+      for (int k = 0; k < n; ++k) {
+        a[(size_t)r * n + k] -= f * a[(size_t)c * n + k];
+        inv[(size_t)r * n + k] -= f * inv[(size_t)c * n + k];
+      }
+    }
+  }
+  return inv;
+}
+
+static std::vector<double> ref_vcycle(const HostSetup& hs, bool pr, const std::vector<double>& D,
+                                      const std::vector<ChebCoef>& ch, int degree, int l, const std::vector<double>& b) {
   const int last = (int)hs.levels.size() - 1;
   const int n = (int)b.size();
   if (l == last) {
-    const std::vector<double>& D = pr ? hs.coarseLinv : hs.coarseAinv;
     std::vector<double> x(n, 0.0);
     for (int i = 0; i < n; ++i)
       for (int j = 0; j < n; ++j) x[i] += D[(size_t)i * n + j] * b[j];
@@ -301,7 +330,7 @@ static std::vector<double> ref_vcycle(const HostSetup& hs, bool pr, const std::v
   const auto Ax = mv(A, x);
   std::vector<double> r(n);
   for (int q = 0; q < n; ++q) r[q] = b[q] - Ax[q];
-  const auto xc = ref_vcycle(hs, pr, ch, degree, l + 1, mv(pr ? H.Rp : H.Ru, r));
+  const auto xc = ref_vcycle(hs, pr, D, ch, degree, l + 1, mv(pr ? H.Rp : H.Ru, r));
   const auto Px = mv(pr ? H.Pp : H.Pu, xc);
   for (int q = 0; q < n; ++q) x[q] += Px[q];
   for (int i = 0; i < degree; ++i) {
@@ -327,10 +356,11 @@ static int run_case(const HostSetup& hs, int N, bool pr, int cs, int degree, siz
     ch[l] = cheb(hi / (pr ? 8.0 : 6.0), hi, degree);
     mg.lv[l].ch = ch[l];
   }
-  const std::vector<double>& D = pr ? hs.coarseLinv : hs.coarseAinv;
+  mg.coarse_n = pr ? hs.coarse_nL : hs.coarse_nA;
+  mg.coarse_ld = mg.coarse_n;
+  const std::vector<double> D = host_inverse(pr ? hs.coarseL : hs.coarseA, mg.coarse_n);
   std::vector<T> dense(D.begin(), D.end());
   mg.coarse_inv = dense.data();
-  mg.coarse_n = pr ? hs.coarse_nL : hs.coarse_nA;
   HostArena ar;
   if (!build_cluster<T>(ar, hs, pr, mg, cs, cap, [](size_t) { return true; })) {
     std::printf("N=%d %s cs=%d: no cluster suffix fits\n", N, pr ? "P" : "U", cs);
@@ -345,7 +375,7 @@ static int run_case(const HostSetup& hs, int N, bool pr, int cs, int degree, siz
   for (auto& v : b) v = nd(rng);
   std::vector<T> bt(b.begin(), b.end());
   const auto xe = emulate<T>(mg.cl.args, mg.cl.smem, B, !pr, bt, dense.size());
-  const auto xr = ref_vcycle(hs, pr, ch, degree, lc, b);
+  const auto xr = ref_vcycle(hs, pr, D, ch, degree, lc, b);
   double num = 0, den = 0;
   for (size_t i = 0; i < xr.size(); ++i) {
     num += ((double)xe[i] - xr[i]) * ((double)xe[i] - xr[i]);

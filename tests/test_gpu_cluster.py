@@ -37,8 +37,11 @@ CASES = {"disk16": fi.disk16_case, "ragged24": _ragged, "cavity128": fi.cavity12
 
 def _pair(fsi, case, precision, precond, stokes_its):
     # the per-level sparse kernels above the cluster (an FP32 hierarchy with
-    # the fused matrix-free levels leaves the cluster out by default)
-    kw = dict(precision=precision, precond=precond, stokes_its=stokes_its, restart=bench.RESTART, mg_fused=-1)
+    # the fused matrix-free levels leaves the cluster out by default), and an
+    # 8-cell coarsest grid (the default stops at 16 cells, and a 16-cell
+    # problem then has no level for the cluster)
+    kw = dict(precision=precision, precond=precond, stokes_its=stokes_its, restart=bench.RESTART, mg_fused=-1,
+              mg_coarse=8)
     on = fsi.problem_from_case(case, mg_cluster=0, **kw)
     off = fsi.problem_from_case(case, mg_cluster=-1, **kw)
     on.assemble_step()

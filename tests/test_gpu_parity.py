@@ -166,15 +166,18 @@ def test_quarter_annulus_one_step(fsi, precond):
     g.close()
 
 
-@pytest.mark.parametrize("N", [4, 6, 8, 12])
-def test_tiny_grids(fsi, N):
-    """Degenerate hierarchies: N <= 8 has a single level (the V-cycle is the
-    dense inverse, no cluster suffix); N = 12 coarsens once to an odd grid."""
+@pytest.mark.parametrize("N,mg_coarse", [(4, 0), (6, 0), (8, 0), (12, 0), (12, 8), (12, 4)])
+def test_tiny_grids(fsi, N, mg_coarse):
+    """Degenerate hierarchies: with the default coarsest grid (16 cells) every
+    N here is a single level (the V-cycle is the dense inverse, no cluster
+    suffix); N = 12 with mg_coarse 8 coarsens once (12, 6), with mg_coarse 4
+    twice, to an odd grid (12, 6, 3)."""
     xy, tris = fi.ring_disk_mesh(3, 0.2, (0.5, 0.5))
     case = fi.FsiCase(N=N, rho_f=1.0, nu=0.5, kappa=10.0, dt=0.01, lid_u=1.0, ref_xy=xy, tris=tris,
                       u0=fi.initial_velocity(N, 11, lid_u=1.0), X0=xy.copy(), precond=1, rtol=1e-12)
     for precision, tol in ((0, 1e-7), (1, 1e-5)):
-        g = fsi.problem_from_case(case, precision=precision, rtol=1e-12 if precision == 0 else 1e-9)
+        g = fsi.problem_from_case(case, precision=precision, rtol=1e-12 if precision == 0 else 1e-9,
+                                  mg_coarse=mg_coarse)
         info = g.step()
         assert info.status == 0
         u, p, X, lam = g.get_state()
@@ -182,6 +185,33 @@ def test_tiny_grids(fsi, N):
         assert rel(u, uo) < tol
         assert rel(lam, lamo) < tol
         g.close()
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-11), (1, 1e-5)])
+@pytest.mark.parametrize("name", ["disk16", "lidbody16"])
+def test_coarsest_inverse_is_the_velocity_solve(fsi, name, precision, tol):
+    """A 16-cell grid with mg_coarse = 16 is a one-level hierarchy: the
+    V-cycle is the dense inverse that Gauss-Jordan builds on the device.  The
+    velocity part of the preconditioner (precond 3, one Stokes step, v with
+    velocity entries only, so the solid and multiplier parts are zero) is
+    then A_II^-1 v_u, A_II the oracle's assembled velocity block (Section 5:
+    the first block of A_11), solved here by scipy's sparse LU."""
+    import scipy.sparse.linalg as spla
+    case = CASES[name]()
+    g = fsi.problem_from_case(case, precision=precision, precond=3, stokes_its=1, mg_coarse=16)
+    g.assemble_step()
+    o = _oracle(case)
+    K, _, _ = o.system(case.u0, case.X0)
+    q = oracle_to_gpu_perm(o, g)
+    nu = g.n_u
+    rng = np.random.default_rng(5)
+    vo = np.zeros(K.shape[0])
+    vo[:nu] = rng.standard_normal(nu)
+    zo = np.zeros(K.shape[0])
+    zo[:nu] = spla.spsolve(sp.csc_matrix(K)[:nu, :nu], vo[:nu])
+    z = g.apply_preconditioner(vo[q], precision=precision)
+    assert rel(z[:nu], zo[q][:nu]) < tol
+    g.close()
 
 
 def test_symmetric_annulus_one_step_is_mirror_symmetric(fsi):
