@@ -139,7 +139,7 @@ typedef struct fsi_params {
                           mg_coarse cells a side, whose operators are inverted
                           densely on the device when the problem is created
                           (Gauss-Jordan in FP64, one launch per unknown);
-                          0 = 16 (a 16-cell grid: 1922 velocity unknowns, a
+                          0 or less = 16 (a 16-cell grid: 1922 velocity unknowns, a
                           15 MB FP32 or 30 MB FP64 inverse, held in L2); at
                           most 32 (FSI_ERR_INVALID above) */
 } fsi_params;

@@ -1454,7 +1454,7 @@ static void check_params(const fsi_params& p, int n_nodes, int n_tris) {
     throw std::invalid_argument("the Q1 solid takes the point rule and the linear law");
   if (p.mg_cluster < -1) throw std::invalid_argument("mg_cluster");
   if (p.mg_fused != 0 && p.mg_fused != -1) throw std::invalid_argument("mg_fused");
-  if (p.mg_coarse < 0 || p.mg_coarse > 32) throw std::invalid_argument("mg_coarse must be 0..32");
+  if (p.mg_coarse > 32) throw std::invalid_argument("mg_coarse must be at most 32");
   if (p.coupling != 0 && p.coupling != 1) throw std::invalid_argument("coupling");
   if (p.solid_law != 0 && p.solid_law != 1) throw std::invalid_argument("solid_law");
   if (p.autotune != 0 && p.autotune != 1) throw std::invalid_argument("autotune");
