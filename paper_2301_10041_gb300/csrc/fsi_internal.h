@@ -53,6 +53,10 @@ struct FluidLevelHost {
   double dinvAt[4][2] = {};          // D^-1 per type and component
   double stenL[9][3][3][9] = {};     // [variant][dy+1][dx+1][3x3 row-major]
   double dinvLv[9][3] = {};          // D^-1 per variant and pressure dof
+  // the entries of -B and of -B^T (the same numbers): [pressure dof][node of
+  // the cell, 3 y + x][velocity component]; one cell contributes to each
+  // (cell, node) pair, so they are the assembled values
+  double divB[3][9][2] = {};
 };
 
 struct SetupParams {

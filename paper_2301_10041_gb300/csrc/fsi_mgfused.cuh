@@ -163,6 +163,21 @@ struct MfFin {
   T omega = 1;
 };
 
+// Residual start of a finest-level down launch inside a Richardson step on
+// the Stokes block (Section 5): the level's right-hand side is the Stokes
+// residual of the current iterate, computed on the tile's frame from the
+// input b (the Richardson input r), the velocity iterate zu and the pressure
+// iterate zp (either null: zero):
+//   velocity: b - A_f zu - (-B^T) zp,   pressure: b - (-B) zu.
+// Its owned part goes to bout, which the up launch reads as its b.
+template <class T>
+struct MfRes {
+  const T* zu = nullptr;
+  const T* zp = nullptr;
+  T* bout = nullptr;
+  T divB[3][9][2];          // entries of -B and -B^T: [pressure dof][node of the cell][component]
+};
+
 template <class T>
 struct MfVelArgs {
   MfVelOp<T> op;
@@ -174,6 +189,7 @@ struct MfVelArgs {
   T* bc = nullptr;          // down: coarse right-hand side
   MfInit<T> ci;
   MfFin<T> fin;
+  MfRes<T> res;             // down: residual start when res.zu or res.zp
 };
 
 template <class T>
@@ -188,6 +204,7 @@ struct MfPresArgs {
   T* bc = nullptr;
   MfInit<T> ci;
   MfFin<T> fin;
+  MfRes<T> res;             // down: residual start when res.zu (res.zp unused)
 };
 
 // Quadratic Lagrange basis on [0, 1] (nodes 0, 1/2, 1) at t; exact in
@@ -345,6 +362,27 @@ __host__ __device__ __forceinline__ void mf_vel_cheb(const MfCta& cta, const MfV
   });
 }
 
+// y += (-B^T zp) at the interior node (ix, iy) of type TAU: the sum over the
+// node's cells (one or two per direction: an odd lattice index lies inside a
+// cell, at local node 1; an even one on the edge between two, at local node 2
+// of the lower and 0 of the upper), lower cells first
+template <class T, int TAU>
+__host__ __device__ __forceinline__ void mf_vel_btp(const MfRes<T>& r, int N, int ix, int iy, T& y0, T& y1) {
+  constexpr int PX = TAU & 1, PY = TAU >> 1;
+#pragma unroll
+  for (int j = 0; j < (PY ? 1 : 2); ++j) {
+#pragma unroll
+    for (int i = 0; i < (PX ? 1 : 2); ++i) {
+      const int aa = PX ? 1 : (i == 0 ? 2 : 0), ab = PY ? 1 : (j == 0 ? 2 : 0);
+      const int cx = (ix - aa) >> 1, cy = (iy - ab) >> 1, al = 3 * ab + aa;
+      const T* __restrict__ p = r.zp + 3 * ((size_t)cy * N + cx);
+      const T p0 = p[0], p1 = p[1], p2 = p[2];
+      y0 += r.divB[0][al][0] * p0 + r.divB[1][al][0] * p1 + r.divB[2][al][0] * p2;
+      y1 += r.divB[0][al][1] * p0 + r.divB[1][al][1] * p1 + r.divB[2][al][1] * p2;
+    }
+  }
+}
+
 // down: grid (ceil(N / TC))^2 over the coarse lattice [0, N)^2
 template <class T, int TC, int K>
 __host__ __device__ void mfu_down_body(const MfVelArgs<T>& a, const MfCta& cta) {
@@ -360,13 +398,49 @@ __host__ __device__ void mfu_down_body(const MfVelArgs<T>& a, const MfCta& cta) 
   T2* B = reinterpret_cast<T2*>(cta.sm);
   T2 *Xc = B + nf, *Xn = B + 2 * nf, *Dc = B + 3 * nf, *Dn = B + 4 * nf;   // current / next iterate
   T2* R = B + 5 * nf;
-  // b on the frame; x0 = d0 = c0 D^-1 b
+  const int o = 2 + K;   // owned fine nodes: plane entries [o, o + TC) of the frame
+  const MfRes<T>& rs = a.res;
+  // residual start: the velocity iterate on the frame grown by one plane
+  // entry (two lattice nodes, the reach of A), in Dn and R, which are
+  // contiguous and unused until the smoothing (2 nf = 8 pw^2 entries, at
+  // least 4 (pw + 2)^2 since pw >= 8)
+  MfFrame g;
+  g.ox = f.ox - 2;
+  g.oy = f.oy - 2;
+  g.pw = f.pw + 2;
+  g.ph = f.ph + 2;
+  T2* Z = Dn;
+  static_assert(TC + 4 + 2 * K >= 8, "the grown frame must fit in Dn and R");
+  if (rs.zu) {
+    mf_vsweep(cta, 0, g.pw, 0, g.ph, [&](auto tc, int px, int py) {
+      constexpr int TAU = decltype(tc)::value;
+      const int ix = g.ox + 2 * px + (TAU & 1), iy = g.oy + 2 * py + (TAU >> 1);
+      T2 v;
+      v.x = v.y = 0;
+      if (mf_vinterior(N, ix, iy)) v = *reinterpret_cast<const T2*>(rs.zu + 2 * (size_t)mf_vnode_t<TAU>(N, ix, iy));
+      Z[g.at(TAU, px, py)] = v;
+    });
+    MF_SYNC();
+  }
+  // b on the frame (with the residual start: b - A zu - (-B^T) zp, its owned
+  // part to rs.bout); x0 = d0 = c0 D^-1 b
   mf_vsweep(cta, 0, f.pw, 0, f.ph, [&](auto tc, int px, int py) {
     constexpr int TAU = decltype(tc)::value;
     const int ix = f.ox + 2 * px + (TAU & 1), iy = f.oy + 2 * py + (TAU >> 1);
     T2 v;
     v.x = v.y = 0;
-    if (mf_vinterior(N, ix, iy)) v = *reinterpret_cast<const T2*>(a.b + 2 * (size_t)mf_vnode_t<TAU>(N, ix, iy));
+    if (mf_vinterior(N, ix, iy)) {
+      const size_t id = 2 * (size_t)mf_vnode_t<TAU>(N, ix, iy);
+      v = *reinterpret_cast<const T2*>(a.b + id);
+      if (rs.zu || rs.zp) {
+        T y0 = 0, y1 = 0;
+        if (rs.zu) mf_vel_apply<T, TAU>(op, Z, g, px + 1, py + 1, y0, y1);
+        if (rs.zp) mf_vel_btp<T, TAU>(rs, N, ix, iy, y0, y1);
+        v.x -= y0;
+        v.y -= y1;
+        if (px >= o && px < o + TC && py >= o && py < o + TC) *reinterpret_cast<T2*>(rs.bout + id) = v;
+      }
+    }
     const int e = f.at(TAU, px, py);
     B[e] = v;
     T2 x0;
@@ -385,7 +459,6 @@ __host__ __device__ void mfu_down_body(const MfVelArgs<T>& a, const MfCta& cta) 
   // residual on the frame shrunk by K (plane units): the restriction's
   // support; the pre-smoothed iterate on the owned fine nodes [2 CX0, 2 CX0
   // + 2 tile), plane entries [o, o + tile), goes out in the same sweep
-  const int o = 2 + K;
   mf_vsweep(cta, K, f.pw - K, K, f.ph - K, [&](auto tc, int px, int py) {
     constexpr int TAU = decltype(tc)::value;
     const int ix = f.ox + 2 * px + (TAU & 1), iy = f.oy + 2 * py + (TAU >> 1);
@@ -633,6 +706,20 @@ __host__ __device__ __forceinline__ void mf_pres_cheb(const MfCta& cta, const T*
   });
 }
 
+// b -= (-B zu) at cell (cx, cy): its nine Q2 nodes, the interior ones
+template <class T>
+__host__ __device__ __forceinline__ void mf_pres_bu(const MfRes<T>& r, int N, int cx, int cy, T b[3]) {
+#pragma unroll
+  for (int be = 0; be < 9; ++be) {
+    const int jx = 2 * cx + be % 3, jy = 2 * cy + be / 3;
+    if (!mf_vinterior(N, jx, jy)) continue;
+    const size_t id = 2 * (size_t)mf_vnode(N, jx, jy);
+    const T u0 = r.zu[id], u1 = r.zu[id + 1];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) b[k] -= r.divB[k][be][0] * u0 + r.divB[k][be][1] * u1;
+  }
+}
+
 // down: grid (ceil(Nc / TP))^2 over the coarse cells
 template <class T, int TP, int K>
 __host__ __device__ void mfp_down_body(const MfPresArgs<T>& a, const MfCta& cta) {
@@ -649,14 +736,25 @@ __host__ __device__ void mfp_down_body(const MfPresArgs<T>& a, const MfCta& cta)
   for (int t = cta.tid; t < kMfPresTab; t += cta.nthr) tab[t] = a.tab[t];
   MF_SYNC();
   const T* dv = tab + 729;
+  // b on the frame (with the residual start: b - (-B) zu, its owned part, the
+  // cells [K, K + 2 TP) of the frame, to res.bout); x0 = d0 = c0 D^-1 b
   mf_rows(cta, f.w, f.w, [&](int i, int j) {
     const int e = j * f.w + i, cx = f.ox + i, cy = f.oy + j;
     const bool in = mf_cin(N, cx, cy);
     const int v = in ? mf_variant(N, cx, cy) : 0;
+    T bv[3] = {0, 0, 0};
+    if (in) {
+      const size_t id = 3 * ((size_t)cy * N + cx);
+      for (int k = 0; k < 3; ++k) bv[k] = a.b[id + k];
+      if (a.res.zu) {
+        mf_pres_bu<T>(a.res, N, cx, cy, bv);
+        if (i >= K && i < K + 2 * TP && j >= K && j < K + 2 * TP)
+          for (int k = 0; k < 3; ++k) a.res.bout[id + k] = bv[k];
+      }
+    }
     for (int k = 0; k < 3; ++k) {
-      const T bv = in ? a.b[3 * ((size_t)cy * N + cx) + k] : (T)0;
-      B[k * n + e] = bv;
-      const T x0 = a.ch.c0 * dv[3 * v + k] * bv;
+      B[k * n + e] = bv[k];
+      const T x0 = a.ch.c0 * dv[3 * v + k] * bv[k];
       Xc[k * n + e] = x0;
       Dc[k * n + e] = x0;
     }

@@ -569,6 +569,11 @@ static void matrix_free_stencils(double h, double ma, double nu, FluidLevelHost&
           for (int i = 0; i < 3; ++i) L.dinvLv[v][i] = 1.0 / L4.val[9 * (size_t)k + 4 * i];
       }
     }
+  Elem e;
+  element(h, 0.0, 0.0, e);
+  for (int k = 0; k < 3; ++k)
+    for (int al = 0; al < 9; ++al)
+      for (int d = 0; d < 2; ++d) L.divB[k][al][d] = 0.0 - e.B[k][al][d];
   L.mf = true;
 }
 

@@ -313,6 +313,7 @@ struct MGLevel {
   bool mf = false;
   MfVelOp<T> mfu;        // velocity hierarchy
   T* mftab = nullptr;    // pressure hierarchy: kMfPresTab values
+  T divB[3][9][2] = {};  // entries of -B and -B^T on this level (residual start)
 };
 
 // Coarse levels run as one thread-block-cluster launch per V-cycle
@@ -425,6 +426,10 @@ static void build_mg(Arena& ar, const HostSetup& hs, bool pressure, int degree, 
     L.d = ar.alloc<T>(L.n);
     const double hi = 1.05 * (pressure ? H.lmaxL : H.lmaxA);
     L.ch = cheb_coeffs(hi / (pressure ? kChebRatioP : kChebRatioU), hi, degree);
+    if (H.mf)
+      for (int k = 0; k < 3; ++k)
+        for (int q = 0; q < 9; ++q)
+          for (int d = 0; d < 2; ++d) L.divB[k][q][d] = (T)H.divB[k][q][d];
     if (H.mf && !pressure) {
       L.mfu.N = H.N;
       for (int t = 0; t < 4; ++t) {
@@ -587,7 +592,7 @@ static T* vcycle(MG<T>& mg, int l, cudaStream_t s, T* out, const SpmvArgs<T>* fi
 // coarse right-hand side to C.b (and the coarse smoother start when the next
 // level runs the per-level sparse kernels).
 template <class T>
-static void mf_down_launch(MG<T>& mg, int l, const T* b, cudaStream_t s) {
+static void mf_down_launch(MG<T>& mg, int l, const T* b, cudaStream_t s, const MfRes<T>* res = nullptr) {
   const int last = (int)mg.lv.size() - 1;
   MGLevel<T>& L = mg.lv[l];
   MGLevel<T>& C = mg.lv[l + 1];
@@ -596,10 +601,15 @@ static void mf_down_launch(MG<T>& mg, int l, const T* b, cudaStream_t s) {
   const int N = L.N, K = mg.degree;
   MfInit<T> ci;
   if (c_sell) { ci.x = C.x; ci.d = C.d; ci.dinv = C.dinv; ci.c0 = (T)C.ch.c0; }
+  MfRes<T> r;
+  if (res) {
+    r = *res;
+    std::memcpy(r.divB, L.divB, sizeof(r.divB));
+  }
   if (mg.pressure) {
     MfPresArgs<T> a;
     a.N = N; a.tab = L.mftab; a.ch = mf_cheb(L, K);
-    a.b = b; a.xout = L.x2; a.bc = C.b; a.ci = ci;
+    a.b = b; a.xout = L.x2; a.bc = C.b; a.ci = ci; a.res = r;
     mf_with_tile_p(N, [&](auto tp) {
       mf_with_degree(K, [&](auto kc) {
         constexpr int TP = decltype(tp)::value, KD = decltype(kc)::value, NT = mf_threads_p(TP);
@@ -610,7 +620,7 @@ static void mf_down_launch(MG<T>& mg, int l, const T* b, cudaStream_t s) {
   } else {
     MfVelArgs<T> a;
     a.op = L.mfu; a.ch = mf_cheb(L, K);
-    a.b = b; a.xout = L.x2; a.bc = C.b; a.ci = ci;
+    a.b = b; a.xout = L.x2; a.bc = C.b; a.ci = ci; a.res = r;
     mf_with_tile_u(N, [&](auto tc) {
       mf_with_degree(K, [&](auto kc) {
         constexpr int TC = decltype(tc)::value, KD = decltype(kc)::value, NT = mf_threads_u(TC);
@@ -657,15 +667,17 @@ static void mf_up_launch(MG<T>& mg, int l, const T* b, const T* xc, T* dst, cons
 
 // One V-cycle from fused level l (mg.lv[l].mf) with right-hand side b: the
 // down launch, the coarser levels, the up launch.  The result goes to `out`,
-// else to L.x.
+// else to L.x.  With res, the down launch starts from the Stokes residual
+// (MfRes) and the up launch reads the right-hand side it wrote to res->bout.
 template <class T>
-static T* vcycle_mf(MG<T>& mg, int l, const T* b, cudaStream_t s, T* out, const MfFin<T>* fin) {
+static T* vcycle_mf(MG<T>& mg, int l, const T* b, cudaStream_t s, T* out, const MfFin<T>* fin,
+                    const MfRes<T>* res = nullptr) {
   MGLevel<T>& L = mg.lv[l];
   MGLevel<T>& C = mg.lv[l + 1];
   T* dst = out ? out : L.x;
-  mf_down_launch<T>(mg, l, b, s);
+  mf_down_launch<T>(mg, l, b, s, res);
   T* xc = C.mf ? vcycle_mf<T>(mg, l + 1, C.b, s, nullptr, nullptr) : vcycle<T>(mg, l + 1, s, (T*)nullptr);
-  mf_up_launch<T>(mg, l, b, xc, dst, fin, s);
+  mf_up_launch<T>(mg, l, res ? res->bout : b, xc, dst, fin, s);
   return dst;
 }
 
@@ -921,10 +933,11 @@ __global__ void k_cft_sub(int nU, const int* __restrict__ ptr, const int* __rest
 // L0.x = L0.d = c0 D^-1 in_p (k_stokes_res does it); with acc, also
 // acc += omega * out_p.  Both the Schur combination and the update ride on
 // the last smoothing kernel of the finest pressure level when it is a
-// per-level kernel.
+// per-level kernel.  With zu (fused finest level only) the input is the
+// residual in_p - (-B) zu, formed by the finest down launch.
 template <class T>
 static void stokes_pressure(Problem& P, Prec<T>& pr, const T* in_p, T* out_p, cudaStream_t s, bool started = false,
-                            T* acc = nullptr, T omega = 1) {
+                            T* acc = nullptr, T omega = 1, const T* zu = nullptr) {
   const int n3 = 3 * P.nP;
   MGLevel<T>& L0p = pr.mgP.lv[0];
   SpmvArgs<T> fin;
@@ -932,10 +945,20 @@ static void stokes_pressure(Problem& P, Prec<T>& pr, const T* in_p, T* out_p, cu
   fin.snu = (T)P.prm.nu; fin.srdt = (T)(P.prm.rho_f / P.prm.dt);
   fin.acc = acc; fin.omega = omega;
   if (L0p.mf) {  // the fused finest level reads in_p itself and applies the epilogue
+    if (zu) {   // the Schur combination takes the residual the down launch wrote
+      MfRes<T> r;
+      r.zu = zu;
+      r.bout = L0p.b;
+      fin.sv = L0p.b;
+      const MfFin<T> mfin = mf_fin(fin);
+      vcycle_mf<T>(pr.mgP, 0, in_p, s, nullptr, &mfin, &r);
+      return;
+    }
     const MfFin<T> mfin = mf_fin(fin);
     vcycle_mf<T>(pr.mgP, 0, in_p, s, nullptr, &mfin);
     return;
   }
+  if (zu) throw std::logic_error("stokes_pressure: the residual start needs the fused finest level");
   if (!started)
     launch(k_cheb_first<T>, nblk(n3, 256), 256, 0, s, n3, in_p, L0p.dinv, (T)L0p.ch.c0, L0p.d, L0p.x, (T)1, L0p.b);
   bool fused = false;
@@ -950,22 +973,28 @@ static void stokes_pressure(Problem& P, Prec<T>& pr, const T* in_p, T* out_p, cu
 // Velocity part: u = A_f^-1 (in_u + B^T p) by one V-cycle with
 // Chebyshev-Jacobi smoothing on the Q2 hierarchy (p = nullptr: u = A_f^-1 in_u).
 // With acc, also acc += omega * out_u (on the last smoothing kernel when the
-// finest level is a per-level kernel).
+// finest level is a per-level kernel).  With zu (fused finest level only)
+// the input is the residual in_u - A_f zu + B^T p.  On the fused level the
+// finest down launch forms the input itself.
 template <class T>
 static void stokes_velocity(Problem& P, Prec<T>& pr, const T* in_u, const T* p, T* out_u, cudaStream_t s,
-                            T* acc = nullptr, T omega = 1) {
+                            T* acc = nullptr, T omega = 1, const T* zu = nullptr) {
   MGLevel<T>& L0u = pr.mgU.lv[0];
   if (L0u.mf) {  // the fused finest level starts its smoother itself
-    const T* b = in_u;
-    if (p) {
-      sell_launch(pr.op.Bt, MODE_AXPBY, axpby<T>(p, L0u.b, in_u, (T)-1, (T)1), s);
-      b = L0u.b;
-    }
     MfFin<T> mfin;
     mfin.acc = acc; mfin.omega = omega;
-    vcycle_mf<T>(pr.mgU, 0, b, s, out_u, acc ? &mfin : nullptr);
+    if (p || zu) {
+      MfRes<T> r;
+      r.zu = zu;
+      r.zp = p;
+      r.bout = L0u.b;
+      vcycle_mf<T>(pr.mgU, 0, in_u, s, out_u, acc ? &mfin : nullptr, &r);
+    } else {
+      vcycle_mf<T>(pr.mgU, 0, in_u, s, out_u, acc ? &mfin : nullptr);
+    }
     return;
   }
+  if (zu) throw std::logic_error("stokes_velocity: the residual start needs the fused finest level");
   if (p) {
     SpmvArgs<T> a;
     a.x = p; a.y = L0u.b; a.z = in_u; a.alpha = -1; a.beta = 1;
@@ -1055,6 +1084,14 @@ static void precond_launch(Problem& P, Prec<T>& pr, cudaStream_t s) {
              (T*)nullptr, (T*)nullptr, (T*)nullptr);
       stokes_apply(P, pr, pr.t, pr.t + P.offP, pr.dz, pr.dz + P.offP, s, split);
       launch(k_axpy<T>, nblk(nf, 256), 256, 0, s, nf, pr.stokes_omega, pr.dz, pr.zw);
+    } else if (L0p.mf && pr.mgU.lv[0].mf && (double)pr.stokes_omega == 1.0) {
+      // the Stokes residual formed inside the finest down launches: the
+      // pressure correction from v_p - (-B) z_u, added to z_p; then, since
+      // z_p then holds the corrected pressure (omega = 1), the velocity
+      // correction from v_u - A_f z_u - (-B^T) z_p, which is the upper
+      // triangular step's right-hand side t_u - (-B^T) dz_p
+      stokes_pressure(P, pr, vp, pr.dz + P.offP, s, false, pr.zw + P.offP, pr.stokes_omega, (const T*)pr.zw);
+      stokes_velocity(P, pr, vu, (const T*)(pr.zw + P.offP), pr.dz, s, pr.zw, pr.stokes_omega, (const T*)pr.zw);
     } else {
       // residual (starting the pressure smoother), then the pressure and
       // velocity corrections, each added to z by its own last kernel

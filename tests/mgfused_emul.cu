@@ -188,6 +188,62 @@ static void velocity(const HostSetup& hs, int l, int K, double tol, std::mt19937
   for (int i = 0; i < n; ++i) acc_ref[i] = acc0[i] + 0.8 * x[i];
   report("velocity up: post-smoothed result", N, K, l, rel(back(out), x), tol);
   report("velocity up: Richardson update", N, K, l, rel(back(accT), acc_ref), tol);
+  if (l != 0) return;
+  // -------------------------------- down with the Stokes residual start
+  // b = r - A zu - (-B^T) zp on the finest level, against the assembled
+  // A_f and -B^T; then the same smoothing, residual and restriction
+  const int np = 3 * N * N;
+  std::vector<double> zu(n), zp(np);
+  for (double& v : zu) v = U(rng);
+  for (double& v : zp) v = U(rng);
+  std::vector<double> Az, Btz, bres(n);
+  spmv(H.A, zu, Az);
+  spmv(hs.Bt, zp, Btz);
+  for (int i = 0; i < n; ++i) bres[i] = b[i] - Az[i] - Btz[i];
+  std::vector<T> zuT = as<T>(zu), zpT = as<T>(zp), bout(n, (T)7), xout2(n, (T)7), bc2(nc, (T)7);
+  MfVelArgs<T> w = a;
+  w.ci = MfInit<T>();
+  w.b = bT.data(); w.xout = xout2.data(); w.bc = bc2.data();
+  w.res.zu = zuT.data(); w.res.zp = zpT.data(); w.res.bout = bout.data();
+  for (int k = 0; k < 3; ++k)
+    for (int q = 0; q < 9; ++q)
+      for (int c = 0; c < 2; ++c) w.res.divB[k][q][c] = (T)H.divB[k][q][c];
+  mf_with_tile_u(N, [&](auto tc) {
+    constexpr int TC = decltype(tc)::value;
+    const int gd = (N + TC - 1) / TC;
+    mf_with_degree(K, [&](auto kc) {
+      constexpr int KD = decltype(kc)::value;
+      run_grid(gd, gd, mf_threads_u(TC), mfu_down_smem<T>(TC, KD), [&](const MfCta& c) { mfu_down_body<T, TC, KD>(w, c); });
+    });
+  });
+  for (int i = 0; i < n; ++i) x[i] = d[i] = ch.c0 * H.dinvA[i] * bres[i];
+  for (int s = 1; s < K; ++s) {
+    spmv(H.A, x, Ax);
+    for (int i = 0; i < n; ++i) {
+      d[i] = ch.c1[s - 1] * d[i] + ch.c2[s - 1] * H.dinvA[i] * (bres[i] - Ax[i]);
+      x[i] += d[i];
+    }
+  }
+  spmv(H.A, x, Ax);
+  for (int i = 0; i < n; ++i) r[i] = bres[i] - Ax[i];
+  spmv(H.Ru, r, Rr);
+  report("velocity down, residual start: right-hand side", N, K, l, rel(back(bout), bres), tol);
+  report("velocity down, residual start: pre-smoothed iterate", N, K, l, rel(back(xout2), x), tol);
+  report("velocity down, residual start: restricted residual", N, K, l, rel(back(bc2), Rr), tol);
+  // zu absent (the first Stokes application): b = r - (-B^T) zp
+  std::vector<T> bout3(n, (T)7);
+  w.res.zu = nullptr;
+  w.res.bout = bout3.data();
+  mf_with_tile_u(N, [&](auto tc) {
+    constexpr int TC = decltype(tc)::value;
+    const int gd = (N + TC - 1) / TC;
+    mf_with_degree(K, [&](auto kc) {
+      constexpr int KD = decltype(kc)::value;
+      run_grid(gd, gd, mf_threads_u(TC), mfu_down_smem<T>(TC, KD), [&](const MfCta& c) { mfu_down_body<T, TC, KD>(w, c); });
+    });
+  });
+  for (int i = 0; i < n; ++i) bres[i] = b[i] - Btz[i];
+  report("velocity down, pressure only: right-hand side", N, K, l, rel(back(bout3), bres), tol);
 }
 
 template <class T>
@@ -284,6 +340,44 @@ static void pressure(const HostSetup& hs, int l, int K, double tol, std::mt19937
   report("pressure up: post-smoothed result", N, K, l, rel(back(out), x), tol);
   report("pressure up: Cahouet-Chabard combination", N, K, l, rel(back(sout), s_ref), tol);
   report("pressure up: Richardson update", N, K, l, rel(back(accT), acc_ref), tol);
+  if (l != 0) return;
+  // -------------------------------- down with the Stokes residual start
+  // b = r - (-B) zu on the finest level, against the assembled -B
+  const int nu = 2 * hs.Bt.nrows;
+  std::vector<double> zu(nu), Bz, bres(n);
+  for (double& v : zu) v = U(rng);
+  spmv(hs.Bneg, zu, Bz);
+  for (int i = 0; i < n; ++i) bres[i] = b[i] - Bz[i];
+  std::vector<T> zuT = as<T>(zu), bout(n, (T)7), xout2(n, (T)7), bc2(nc, (T)7);
+  MfPresArgs<T> w = a;
+  w.ci = MfInit<T>();
+  w.b = bT.data(); w.xout = xout2.data(); w.bc = bc2.data();
+  w.res.zu = zuT.data(); w.res.bout = bout.data();
+  for (int k = 0; k < 3; ++k)
+    for (int q = 0; q < 9; ++q)
+      for (int c = 0; c < 2; ++c) w.res.divB[k][q][c] = (T)H.divB[k][q][c];
+  mf_with_tile_p(N, [&](auto tp) {
+    constexpr int TP = decltype(tp)::value;
+    const int gd = (N / 2 + TP - 1) / TP;
+    mf_with_degree(K, [&](auto kc) {
+      constexpr int KD = decltype(kc)::value;
+      run_grid(gd, gd, mf_threads_p(TP), mfp_down_smem<T>(TP, KD), [&](const MfCta& c) { mfp_down_body<T, TP, KD>(w, c); });
+    });
+  });
+  for (int i = 0; i < n; ++i) x[i] = d[i] = ch.c0 * H.dinvL[i] * bres[i];
+  for (int s = 1; s < K; ++s) {
+    spmv(H.L, x, Lx);
+    for (int i = 0; i < n; ++i) {
+      d[i] = ch.c1[s - 1] * d[i] + ch.c2[s - 1] * H.dinvL[i] * (bres[i] - Lx[i]);
+      x[i] += d[i];
+    }
+  }
+  spmv(H.L, x, Lx);
+  for (int i = 0; i < n; ++i) r[i] = bres[i] - Lx[i];
+  spmv(H.Rp, r, Rr);
+  report("pressure down, residual start: right-hand side", N, K, l, rel(back(bout), bres), tol);
+  report("pressure down, residual start: pre-smoothed iterate", N, K, l, rel(back(xout2), x), tol);
+  report("pressure down, residual start: restricted residual", N, K, l, rel(back(bc2), Rr), tol);
 }
 
 int main(int argc, char** argv) {

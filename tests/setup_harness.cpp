@@ -7,7 +7,8 @@
 //     level: {"level": l, "rel_err": e});
 //   setup_harness stencils N
 //     every row of the assembled level operators against their matrix-free
-//     stencils (one line per level);
+//     stencils, and the finest -B and -B^T against the divergence table (one
+//     line per level);
 //   setup_harness solid <mesh file> <kappa>
 //     build the solid operators of a Q1 mesh (file: n_nodes n_el, then x y
 //     per node, then 4 node ids per element) and print C_s and A_s as
@@ -155,8 +156,35 @@ static int stencils(int N) {
       for (int i = 0; i < 3; ++i)
         if (L.dinvL[3 * (size_t)r + i] != L.dinvLv[v][i]) ++l_bad;
     }
-    std::printf("{\"level\": %zu, \"N\": %d, \"a_mismatch\": %ld, \"l_mismatch\": %ld, \"a_rows\": %d, "
-                "\"l_rows\": %d}\n", l, L.N, a_bad, l_bad, L.A.nrows, L.L.nrows);
+    // the finest level's divergence table against -B (cell rows) and -B^T
+    // (node rows) of the finest grid, entry for entry
+    long b_bad = 0;
+    if (l == 0) {
+      for (int c = 0; c < hs.Bneg.nrows; ++c) {
+        const int cx = c % L.N, cy = c / L.N;
+        for (int j = hs.Bneg.ptr[c]; j < hs.Bneg.ptr[c + 1]; ++j) {
+          int jx, jy;
+          vn.lattice(hs.Bneg.col[j], jx, jy);
+          const int al = (jy - 2 * cy) * 3 + (jx - 2 * cx);
+          for (int k = 0; k < 3; ++k)
+            for (int d = 0; d < 2; ++d)
+              if (al < 0 || al > 8 || hs.Bneg.val[6 * (size_t)j + 2 * k + d] != L.divB[k][al][d]) ++b_bad;
+        }
+      }
+      for (int r = 0; r < hs.Bt.nrows; ++r) {
+        int ix, iy;
+        vn.lattice(r, ix, iy);
+        for (int j = hs.Bt.ptr[r]; j < hs.Bt.ptr[r + 1]; ++j) {
+          const int c = hs.Bt.col[j], cx = c % L.N, cy = c / L.N;
+          const int al = (iy - 2 * cy) * 3 + (ix - 2 * cx);
+          for (int d = 0; d < 2; ++d)
+            for (int k = 0; k < 3; ++k)
+              if (al < 0 || al > 8 || hs.Bt.val[6 * (size_t)j + 3 * d + k] != L.divB[k][al][d]) ++b_bad;
+        }
+      }
+    }
+    std::printf("{\"level\": %zu, \"N\": %d, \"a_mismatch\": %ld, \"l_mismatch\": %ld, \"b_mismatch\": %ld, "
+                "\"a_rows\": %d, \"l_rows\": %d}\n", l, L.N, a_bad, l_bad, b_bad, L.A.nrows, L.L.nrows);
   }
   return 0;
 }

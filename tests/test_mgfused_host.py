@@ -8,7 +8,11 @@ of the host setup: the down launch (Chebyshev pre-smoothing from
 c0 D^-1 b, residual, Q2 / P1disc restriction, coarse smoother start) and the
 up launch (prolongation, post-smoothing, Richardson and Cahouet-Chabard
 epilogues), velocity and pressure, degrees 1-4, grids N = 16, 24, 48, 128 and the next coarser level, and N = 512 (the
-larger tiles): FP64 to 1e-12, FP32 to 1e-5.
+larger tiles): FP64 to 1e-12, FP32 to 1e-5.  On the finest level the down
+launch is also checked with the Stokes residual start of a Richardson step
+(Section 5): its right-hand side b - A_f z_u - (-B^T) z_p (velocity; also
+without z_u) and b - (-B) z_u (pressure) against the assembled A_f, -B^T and
+-B, and the smoothing and restriction that follow.
 """
 import os
 import shutil
@@ -37,3 +41,4 @@ def test_fused_multigrid_kernels_match_the_assembled_levels(tmp_path):
     r = subprocess.run([exe], capture_output=True, text=True, timeout=900)
     assert r.returncode == 0, r.stdout[-4000:] + r.stderr[-4000:]
     assert "failures=0" in r.stdout
+    assert r.stdout.count("residual start: right-hand side") >= 20

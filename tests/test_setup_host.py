@@ -51,12 +51,13 @@ def test_matrix_free_stencils_are_the_assembled_rows(harness, N):
     """The constant-coefficient stencils used by the matrix-free multigrid
     kernels reproduce every row of the assembled velocity operator and
     pressure Laplacian of every level bit for bit (walls only remove
-    neighbours of A; L has one stencil per wall variant)."""
+    neighbours of A; L has one stencil per wall variant), and the finest
+    level's divergence table reproduces every entry of -B and -B^T."""
     out = subprocess.run([harness, "stencils", str(N)], capture_output=True, text=True, check=True).stdout
     rows = [json.loads(l) for l in out.splitlines() if l.strip()]
     assert len(rows) >= 1
     for r in rows:
-        assert r["a_mismatch"] == 0 and r["l_mismatch"] == 0, r
+        assert r["a_mismatch"] == 0 and r["l_mismatch"] == 0 and r["b_mismatch"] == 0, r
 
 
 def _solid(harness, tmp_path, xy, quads, kappa):
