@@ -398,7 +398,7 @@ def roofline(prob, args):
     except Exception as e:  # report, do not fail the bench line
         out["cf_assembly_error"] = str(e)
     traffic = None   # DRAM bytes per launch from the committed ncu summary of this kernel
-    prof = os.path.join(ROOT, "profiles", "ncu_velocity_down_fused_cavity128.md")
+    prof = os.path.join(ROOT, "profiles", "ncu_velocity_down_fused_n128.md")
     if os.path.exists(prof):
         for line in open(prof):
             if line.startswith("dram_bytes_per_launch:"):
