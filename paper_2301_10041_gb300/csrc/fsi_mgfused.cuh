@@ -280,9 +280,22 @@ __host__ __device__ __forceinline__ bool mf_vinterior(int N, int ix, int iy) {
   return ix >= 1 && iy >= 1 && ix <= 2 * N - 1 && iy <= 2 * N - 1;
 }
 
+// a b + c in one rounding on the device (a multiply-add the stencil sums are
+// chains of); the host emulation rounds twice
+template <class T>
+__host__ __device__ __forceinline__ T mf_fma(T a, T b, T c) {
+#ifdef __CUDA_ARCH__
+  return fma(a, b, c);
+#else
+  return a * b + c;
+#endif
+}
+
 // A lattice frame in shared memory: origin (ox, oy) even, 4 parity planes
 // (one per node type) of pw x ph entries; lattice (ox + 2 px + (t & 1),
-// oy + 2 py + (t >> 1)) is entry (t ph + py) pw + px.
+// oy + 2 py + (t >> 1)) is entry (t ph + py) pw + px.  MfFrame has run-time
+// sides; MfFrameT<PW, PH> compile-time ones, so that every stencil tap is a
+// constant offset from the node's entry.
 struct MfFrame {
   int ox, oy, pw, ph;
   __host__ __device__ __forceinline__ int plane() const { return pw * ph; }
@@ -291,30 +304,40 @@ struct MfFrame {
     return at((ix & 1) | ((iy & 1) << 1), (ix - ox) >> 1, (iy - oy) >> 1);
   }
 };
+template <int PW, int PH>
+struct MfFrameT {
+  int ox, oy;
+  static constexpr int pw = PW, ph = PH;
+  __host__ __device__ static constexpr int plane() { return PW * PH; }
+  __host__ __device__ static constexpr int at(int t, int px, int py) { return (t * PH + py) * PW + px; }
+  __host__ __device__ __forceinline__ int at_lattice(int ix, int iy) const {
+    return at((ix & 1) | ((iy & 1) << 1), (ix - ox) >> 1, (iy - oy) >> 1);
+  }
+};
 
-// y = A v at the node of type TAU with plane coordinates (px, py); the
-// neighbours of even and odd rows go to two accumulator pairs (two shorter
-// dependency chains), added at the end
-template <class T, int TAU>
+// y = A v at the node of type TAU with plane coordinates (px, py) of frame
+// f; the neighbours of even and odd rows go to two accumulator pairs (two
+// shorter dependency chains of multiply-adds), added at the end
+template <class T, int TAU, class F>
 __host__ __device__ __forceinline__ void mf_vel_apply(const MfVelOp<T>& op, const typename Vec2<T>::type* __restrict__ v,
-                                                      const MfFrame& f, int px, int py, T& y0, T& y1) {
+                                                      const F& f, int px, int py, T& y0, T& y1) {
   constexpr int PX = TAU & 1, PY = TAU >> 1;
   constexpr int RX = PX ? 1 : 2, RY = PY ? 1 : 2;
   T a0 = 0, a1 = 0, b0 = 0, b1 = 0;
+  const typename Vec2<T>::type* __restrict__ w = v + f.at(0, px, py);
 #pragma unroll
   for (int dy = -RY; dy <= RY; ++dy) {
 #pragma unroll
     for (int dx = -RX; dx <= RX; ++dx) {
       const int t2 = ((PX + dx) & 1) | (((PY + dy) & 1) << 1);
-      const int qx = px + ((PX + dx) >> 1), qy = py + ((PY + dy) >> 1);
-      const auto x = v[(t2 * f.ph + qy) * f.pw + qx];
+      const auto x = w[(t2 * f.ph + ((PY + dy) >> 1)) * f.pw + ((PX + dx) >> 1)];
       const T* c = op.c[TAU][dy + 2][dx + 2];
       if ((dy & 1) == 0) {
-        a0 += c[0] * x.x + c[1] * x.y;
-        a1 += c[2] * x.x + c[3] * x.y;
+        a0 = mf_fma(c[1], x.y, mf_fma(c[0], x.x, a0));
+        a1 = mf_fma(c[3], x.y, mf_fma(c[2], x.x, a1));
       } else {
-        b0 += c[0] * x.x + c[1] * x.y;
-        b1 += c[2] * x.x + c[3] * x.y;
+        b0 = mf_fma(c[1], x.y, mf_fma(c[0], x.x, b0));
+        b1 = mf_fma(c[3], x.y, mf_fma(c[2], x.x, b1));
       }
     }
   }
@@ -325,8 +348,8 @@ __host__ __device__ __forceinline__ void mf_vel_apply(const MfVelOp<T>& op, cons
 // One Chebyshev step on the plane rectangle shrunk by `s` from the frame:
 // first (CHEB0 / after init): dn = c2 D^-1 (b - A xo); otherwise
 // dn = c1 do + c2 D^-1 (b - A xo); xn = xo + dn.  Outside the interior 0.
-template <class T>
-__host__ __device__ __forceinline__ void mf_vel_cheb(const MfCta& cta, const MfVelOp<T>& op, const MfFrame& f, int s,
+template <class T, class F>
+__host__ __device__ __forceinline__ void mf_vel_cheb(const MfCta& cta, const MfVelOp<T>& op, const F& f, int s,
                                                      const typename Vec2<T>::type* __restrict__ B,
                                                      const typename Vec2<T>::type* __restrict__ Xo,
                                                      const typename Vec2<T>::type* __restrict__ Do,
@@ -390,11 +413,11 @@ __host__ __device__ void mfu_down_body(const MfVelArgs<T>& a, const MfCta& cta) 
   const MfVelOp<T>& op = a.op;
   const int N = op.N;
   const int CX0 = cta.bx * TC, CY0 = cta.by * TC;
-  MfFrame f;
+  constexpr int PW = TC + 4 + 2 * K;   // (2 TC + 8 + 4 K) lattice nodes a side
+  MfFrameT<PW, PW> f;
   f.ox = 2 * CX0 - 4 - 2 * K;
   f.oy = 2 * CY0 - 4 - 2 * K;
-  f.pw = f.ph = (2 * TC + 8 + 4 * K) / 2;
-  const int nf = 4 * f.plane();
+  constexpr int nf = 4 * PW * PW;
   T2* B = reinterpret_cast<T2*>(cta.sm);
   T2 *Xc = B + nf, *Xn = B + 2 * nf, *Dc = B + 3 * nf, *Dn = B + 4 * nf;   // current / next iterate
   T2* R = B + 5 * nf;
@@ -404,11 +427,9 @@ __host__ __device__ void mfu_down_body(const MfVelArgs<T>& a, const MfCta& cta) 
   // entry (two lattice nodes, the reach of A), in Dn and R, which are
   // contiguous and unused until the smoothing (2 nf = 8 pw^2 entries, at
   // least 4 (pw + 2)^2 since pw >= 8)
-  MfFrame g;
+  MfFrameT<PW + 2, PW + 2> g;
   g.ox = f.ox - 2;
   g.oy = f.oy - 2;
-  g.pw = f.pw + 2;
-  g.ph = f.ph + 2;
   T2* Z = Dn;
   static_assert(TC + 4 + 2 * K >= 8, "the grown frame must fit in Dn and R");
   if (rs.zu) {
@@ -538,10 +559,10 @@ __host__ __device__ void mfu_up_body(const MfVelArgs<T>& a, const MfCta& cta) {
   const MfVelOp<T>& op = a.op;
   const int N = op.N, Nc = N / 2;
   const int FX0 = cta.bx * TF, FY0 = cta.by * TF;
-  MfFrame f;
+  constexpr int PW = TC + 2 * K;   // (TF + 4 K) lattice nodes a side
+  MfFrameT<PW, PW> f;
   f.ox = FX0 - 2 * K;
   f.oy = FY0 - 2 * K;
-  f.pw = f.ph = (TF + 4 * K) / 2;
   // coarse lattice frame covering the prolongation taps of the fine frame
   MfFrame g;
   {
@@ -552,7 +573,7 @@ __host__ __device__ void mfu_up_body(const MfVelArgs<T>& a, const MfCta& cta) {
     g.pw = hix - lox + 2;   // coarse lattice 2 lo .. 2 hi + 2, i.e. 2 (hi - lo) + 3 nodes
     g.ph = hiy - loy + 2;
   }
-  const int nf = 4 * f.plane();
+  constexpr int nf = 4 * PW * PW;
   T2* B = reinterpret_cast<T2*>(cta.sm);
   T2 *Xc = B + nf, *Xn = B + 2 * nf, *Dc = B + 3 * nf, *Dn = B + 4 * nf;
   T2* XC = B + 5 * nf;
@@ -672,7 +693,7 @@ __host__ __device__ __forceinline__ void mf_pres_apply(const T* __restrict__ tab
       const T x0 = v[q], x1 = v[n + q], x2 = v[2 * n + q];
       const T* c = base + 9 * ((dy + 1) * 3 + dx + 1);
 #pragma unroll
-      for (int i = 0; i < 3; ++i) p[dy + 1][i] += c[3 * i] * x0 + c[3 * i + 1] * x1 + c[3 * i + 2] * x2;
+      for (int i = 0; i < 3; ++i) p[dy + 1][i] = mf_fma(c[3 * i + 2], x2, mf_fma(c[3 * i + 1], x1, mf_fma(c[3 * i], x0, p[dy + 1][i])));
     }
   }
 #pragma unroll
