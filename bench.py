@@ -127,6 +127,7 @@ MG_FUSED = 0     # 0: fused matrix-free kernels on the finest FP32 multigrid lev
 MG_CLUSTER = 0   # 0: coarse levels in one cluster launch; -1: per-level launches; n > 0: cluster levels <= n cells
 MG_DEGREE = 0    # Chebyshev degree of each multigrid smoothing (0: the library's default, 2)
 MG_COARSE = 0    # coarsest multigrid grid in cells (0: the library's default, 16)
+CS_DEGREE = 0    # Chebyshev steps per solid mass solve (0: the library's default)
 
 
 def arm_settings(precision):
@@ -138,7 +139,8 @@ def arm_settings(precision):
 
 def mg_settings():
     """Multigrid kernel choice and smoothing degree of the bench's arms (command-line switches)."""
-    return dict(mg_fused=MG_FUSED, mg_cluster=MG_CLUSTER, mg_degree=MG_DEGREE, mg_coarse=MG_COARSE)
+    return dict(mg_fused=MG_FUSED, mg_cluster=MG_CLUSTER, mg_degree=MG_DEGREE, mg_coarse=MG_COARSE,
+                cs_degree=CS_DEGREE)
 
 
 def time_arm(fsi, torch, case, precision, steps, warmup, stream, flush, precond=PRECOND, stokes_its=STOKES_ITS,
@@ -374,11 +376,15 @@ def roofline(prob, args):
         ms, by = prob.time_kernel(which, reps=30)
         out[name] = {"us": ms * 1e3, "bytes": by, "gbs": by / ms / 1e6, "hbm_frac": by / ms / 1e6 / peak}
     out.update(fused_kernels(prob, peak, alu_peak, 30))
-    # V-cycles as a whole (L2 warm, as inside a solve)
+    # V-cycles as a whole (L2 warm, as inside a solve): algorithmic bytes
+    # (vectors once per level, the dense coarsest inverse once) and FLOPs
     for name, which in (("vcycle_velocity_f32", 4), ("vcycle_pressure_f32", 5)):
         try:
-            ms, _ = prob.time_kernel(which, reps=30)
-            out[name] = {"us": ms * 1e3}
+            ms, by = prob.time_kernel(which, reps=30)
+            fl = prob.kernel_flops(which)
+            out[name] = {"us": ms * 1e3, "bytes": by, "flops": fl, "gbs": by / ms / 1e6,
+                         "hbm_frac": by / ms / 1e6 / peak, "tflops": fl / ms / 1e9,
+                         "alu_frac": fl / ms / 1e9 / alu_peak}
         except Exception:
             pass
     # C_f assembly (S2-S4) with the located-point rule of this workload, and
@@ -436,7 +442,13 @@ def large_n_roofline(fsi, stream, device_index, peak, N):
         out[name] = {"us": ms * 1e3, "bytes": by, "gbs": by / ms / 1e6, "frac": by / ms / 1e6 / peak}
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
-    out.update(fused_kernels(prob, peak, fp32_peak_tflops(peaks)[0], 20))
+    alu_peak = fp32_peak_tflops(peaks)[0]
+    out.update(fused_kernels(prob, peak, alu_peak, 20))
+    for name, which in (("vcycle_velocity_f32", 4), ("vcycle_pressure_f32", 5)):
+        ms, by = prob.time_kernel(which, reps=10)
+        fl = prob.kernel_flops(which)
+        out[name] = {"us": ms * 1e3, "bytes": by, "flops": fl, "gbs": by / ms / 1e6, "hbm_frac": by / ms / 1e6 / peak,
+                     "tflops": fl / ms / 1e9, "alu_frac": fl / ms / 1e9 / alu_peak}
     prob.close()
     prob64 = fsi.problem_from_case(case, precision=0, precond=PRECOND, rtol=1e-8, stream=stream.cuda_stream,
                                    max_it=MAX_IT, stokes_its=STOKES_ITS, **arm_settings(0))
@@ -843,7 +855,7 @@ def run_serve(args):
 
 
 def main():
-    global AUTOTUNE, MG_FUSED, MG_CLUSTER, MG_DEGREE, MG_COARSE, STOKES_ITS
+    global AUTOTUNE, MG_FUSED, MG_CLUSTER, MG_DEGREE, MG_COARSE, CS_DEGREE, STOKES_ITS
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
@@ -882,6 +894,8 @@ def main():
     ap.add_argument("--stokes-its", type=int, default=STOKES_ITS,
                     help="Richardson steps on the Stokes block per preconditioner application (bench workload)")
     ap.add_argument("--mg-degree", type=int, default=0, help="Chebyshev degree of each multigrid smoothing")
+    ap.add_argument("--cs-degree", type=int, default=0,
+                    help="Chebyshev steps per solid mass solve (0: the library's default)")
     ap.add_argument("--mg-coarse", type=int, default=0,
                     help="coarsest multigrid grid in cells (0: the library's default)")
     ap.add_argument("--mg-cluster", type=int, default=0,
@@ -908,6 +922,7 @@ def main():
     MG_CLUSTER = args.mg_cluster
     MG_DEGREE = args.mg_degree
     MG_COARSE = args.mg_coarse
+    CS_DEGREE = args.cs_degree
     STOKES_ITS = args.stokes_its
     if args.autotune:
         AUTOTUNE = 1

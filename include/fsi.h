@@ -273,7 +273,9 @@ int fsi_graph_kernel_counts(const fsi_problem* p, int* counts);
  * velocity Chebyshev smoothing step in FP32 (precision 1 only), 3 the same in
  * FP64; 4 and 5 (precision 1 only): one whole V-cycle on the velocity /
  * pressure-Laplacian hierarchy in FP32, with L2 left warm as inside a solve
- * (bytes = 0: a latency figure); 6 and 7: the cluster launch of that
+ * (bytes: every level's vectors once, the stored matrices of the levels that
+ * run the per-level kernels once per application, the dense coarsest inverse
+ * once); 6 and 7: the cluster launch of that
  * hierarchy's coarse levels alone (FSI_ERR_INVALID when they run as
  * per-level kernels); 8: the C_f row assembly by located points (coupling
  * 0 only), 9: by mesh intersection (coupling 1 only), both on the current
@@ -287,9 +289,11 @@ int fsi_graph_kernel_counts(const fsi_problem* p, int* counts);
 int fsi_time_kernel(fsi_problem* p, int which, int reps, double* avg_ms, double* bytes);
 
 /* Measurement hook: algorithmic floating-point operations of one launch of
- * kernel `which` (10 .. 13 of fsi_time_kernel): two per stored scalar entry
- * of each operator and transfer application, six per unknown per smoothing
- * step, without the work the tiles repeat on their overlaps. */
+ * kernel `which` (10 .. 13 of fsi_time_kernel), or of one V-cycle (4, 5):
+ * two per stored scalar entry of each operator and transfer application,
+ * six per unknown per smoothing step, two per entry of the dense coarsest
+ * inverse, without the work the tiles repeat on their overlaps.  Precision
+ * 1 only (FSI_ERR_INVALID otherwise). */
 int fsi_kernel_flops(fsi_problem* p, int which, double* flops);
 
 /* Right-hand side of the last fsi_assemble_step in block order (n_total). */

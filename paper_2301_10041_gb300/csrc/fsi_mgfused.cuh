@@ -83,13 +83,16 @@ constexpr int kMfPresTab = 9 * 9 * 9 + 9 * 3;  // pressure stencil table: blocks
 // repeat less of their neighbours' work.
 __host__ __device__ __forceinline__ int mf_tile_u(int N) { return N >= 512 ? 16 : 8; }
 __host__ __device__ __forceinline__ int mf_tile_p(int N) { return N >= 512 ? 8 : 4; }
-// 1024 threads for the 8-node velocity tiles: there a launch's time is one
-// CTA's chain of phases, and twice the threads halve each thread's share of a
-// phase (1 frame entry each in the down launch, against 2 with 512; the
-// 128 x 128 cavity step went from 16.3 to 17.0 steps/s).  The 16-node tiles
-// of the large grids keep 512 (1024 measured slower there: 228 against
-// 149 us for the up launch at N = 1024).
-constexpr int mf_threads_u(int tc) { return tc == 8 ? 1024 : (tc >= 16 ? 512 : (tc == 4 ? 256 : 128)); }
+// Threads of a velocity launch: one frame entry per thread at the default
+// degree (2).  A launch's time on these grids is one CTA's chain of phases,
+// and the threads' share of a phase sets it: the 8-node down launch went from
+// 16.3 to 17.0 steps/s on the 128 x 128 cavity with 1024 threads instead of
+// 512.  The 16-node tiles of the large grids keep 512 (1024 measured slower
+// there: 228 against 149 us for the up launch at N = 1024).  Down frames have
+// TC + 8 plane entries a side (four planes), up frames TC + 4; a warp takes
+// two rows of up to 16 entries, four rows of up to 8.
+constexpr int mf_threads_ud(int tc) { return tc >= 16 ? 512 : (tc == 8 ? 1024 : (tc == 4 ? 768 : 640)); }
+constexpr int mf_threads_uu(int tc) { return tc >= 16 ? 512 : (tc == 8 ? 1024 : (tc == 4 ? 256 : 192)); }
 constexpr int mf_threads_p(int tp) { return tp >= 4 ? 256 : 128; }
 
 // Call f(integral_constant<degree>) for a Chebyshev degree 1 .. kMfMaxDeg

@@ -549,10 +549,11 @@ static void select_mf(MG<T>& mg, const HostSetup& hs, int mg_fused, bool count_o
       auto vel = [](auto tc) {
         for (int K = 1; K <= kMfMaxDeg; ++K)
           mf_with_degree(K, [&](auto kc) {
-            constexpr int TC = decltype(tc)::value, KD = decltype(kc)::value, NT = mf_threads_u(TC);
-            CK(cudaFuncSetAttribute(k_mfu_down<float, TC, KD, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            constexpr int TC = decltype(tc)::value, KD = decltype(kc)::value;
+            constexpr int ND = mf_threads_ud(TC), NU = mf_threads_uu(TC);
+            CK(cudaFuncSetAttribute(k_mfu_down<float, TC, KD, ND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)mfu_down_smem<float>(TC, KD)));
-            CK(cudaFuncSetAttribute(k_mfu_up<float, TC, KD, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            CK(cudaFuncSetAttribute(k_mfu_up<float, TC, KD, NU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)mfu_up_smem<float>(TC, KD)));
           });
       };
@@ -566,8 +567,8 @@ static void select_mf(MG<T>& mg, const HostSetup& hs, int mg_fused, bool count_o
                                     (int)mfp_up_smem<float>(TP, KD)));
           });
       };
-      for (int N : {16, 512}) mf_with_tile_u(N, vel);
-      for (int N : {16, 512}) mf_with_tile_p(N, pres);
+      for (int N : {16, 64, 128, 512}) mf_with_tile_u(N, vel);   // every tile the maps choose
+      for (int N : {16, 64, 128, 512}) mf_with_tile_p(N, pres);
     });
   }
 }
@@ -623,7 +624,7 @@ static void mf_down_launch(MG<T>& mg, int l, const T* b, cudaStream_t s, const M
     a.b = b; a.xout = L.x2; a.bc = C.b; a.ci = ci; a.res = r;
     mf_with_tile_u(N, [&](auto tc) {
       mf_with_degree(K, [&](auto kc) {
-        constexpr int TC = decltype(tc)::value, KD = decltype(kc)::value, NT = mf_threads_u(TC);
+        constexpr int TC = decltype(tc)::value, KD = decltype(kc)::value, NT = mf_threads_ud(TC);
         const unsigned g = nblk(N, TC);
         launch(k_mfu_down<T, TC, KD, NT>, dim3(g, g), NT, mfu_down_smem<T>(TC, KD), s, a);
       });
@@ -657,7 +658,7 @@ static void mf_up_launch(MG<T>& mg, int l, const T* b, const T* xc, T* dst, cons
     if (fin) a.fin = *fin;
     mf_with_tile_u(N, [&](auto tc) {
       mf_with_degree(K, [&](auto kc) {
-        constexpr int TC = decltype(tc)::value, KD = decltype(kc)::value, NT = mf_threads_u(TC);
+        constexpr int TC = decltype(tc)::value, KD = decltype(kc)::value, NT = mf_threads_uu(TC);
         const unsigned g = nblk(2 * N, 2 * TC);
         launch(k_mfu_up<T, TC, KD, NT>, dim3(g, g), NT, mfu_up_smem<T>(TC, KD), s, a);
       });
@@ -700,6 +701,42 @@ static MfWork mf_work(const HostSetup& hs, int l, bool pressure, bool up, int K,
   MfWork w;
   w.flops = K * 2.0 * a_entries + 2.0 * t_entries + 6.0 * K * n;
   w.bytes = up ? (3.0 * n + nc) * tsize : (2.0 * n + nc) * tsize;
+  return w;
+}
+
+// Algorithmic work of one V-cycle of hierarchy mg from its finest level:
+// the fused levels' launches (mf_work), the per-level sparse kernels of the
+// other levels above the coarsest (2K applications of the stored level
+// matrix and one residual, the transfers, a few vectors each), and the
+// dense coarsest product (the inverse read once).
+template <class T>
+static MfWork vcycle_work(const HostSetup& hs, const MG<T>& mg, bool pressure) {
+  MfWork w;
+  const int last = (int)mg.lv.size() - 1, K = mg.degree;
+  const double ts = sizeof(T);
+  for (int l = 0; l < last; ++l) {
+    if (mg.lv[l].mf) {
+      for (bool up : {false, true}) {
+        const MfWork m = mf_work(hs, l, pressure, up, K, sizeof(T));
+        w.bytes += m.bytes;
+        w.flops += m.flops;
+      }
+      continue;
+    }
+    const FluidLevelHost& H = hs.levels[l];
+    const HostBlockMatrix& A = pressure ? H.L : H.A;
+    const HostBlockMatrix& R = pressure ? H.Rp : H.Ru;
+    const HostBlockMatrix& Pm = pressure ? H.Pp : H.Pu;
+    const double n = (double)A.nrows * A.BR;
+    const double a_bytes = (double)A.nnzb() * (A.NV * ts + 4.0);
+    const double t_bytes = (double)(R.nnzb() * (R.NV * ts + 4.0) + Pm.nnzb() * (Pm.NV * ts + 4.0));
+    const double a_flops = 2.0 * A.nnzb() * A.BR * A.BC;
+    w.bytes += (2 * K + 1) * (a_bytes + 4.0 * n * ts) + t_bytes;
+    w.flops += (2 * K + 1) * a_flops + 2.0 * (R.nnzb() + Pm.nnzb()) * (R.kron ? R.BR : R.BR * R.BC);
+  }
+  const double nc = mg.coarse_n;
+  w.bytes += nc * mg.coarse_ld * ts + 2.0 * nc * ts;
+  w.flops += 2.0 * nc * nc;
   return w;
 }
 
@@ -2575,7 +2612,7 @@ int fsi_time_kernel(fsi_problem* h, int which, int reps, double* avg_ms, double*
         case 5: {  // one V-cycle on the pressure Laplacian hierarchy, FP32
           MG<float>& mg = (which == 4) ? P.p32.mgU : P.p32.mgP;
           vcycle<float>(mg, 0, s, mg.lv[0].mf ? mg.lv[0].x : mg.lv[0].x2);
-          *bytes = 0;
+          *bytes = vcycle_work<float>(P.hs, mg, which == 5).bytes;
           break;
         }
         case 8:    // C_f rows by the point rule at located points (S2 + S4)
@@ -2639,7 +2676,12 @@ int fsi_time_kernel(fsi_problem* h, int which, int reps, double* avg_ms, double*
 int fsi_kernel_flops(fsi_problem* h, int which, double* flops) {
   if (!h || !flops) return FSI_ERR_INVALID;
   Problem& P = h->P;
-  if (which < 10 || which > 13 || P.prm.precision != 1) return FSI_ERR_INVALID;
+  if (P.prm.precision != 1) return FSI_ERR_INVALID;
+  if (which == 4 || which == 5) {
+    *flops = vcycle_work<float>(P.hs, which == 4 ? P.p32.mgU : P.p32.mgP, which == 5).flops;
+    return FSI_OK;
+  }
+  if (which < 10 || which > 13) return FSI_ERR_INVALID;
   const MG<float>& mg = (which <= 11) ? P.p32.mgU : P.p32.mgP;
   if (mg.lv.empty() || !mg.lv[0].mf) return FSI_ERR_INVALID;
   *flops = mf_work(P.hs, 0, which >= 12, (which & 1) != 0, mg.degree, sizeof(float)).flops;

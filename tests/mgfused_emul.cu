@@ -137,7 +137,7 @@ static void velocity(const HostSetup& hs, int l, int K, double tol, std::mt19937
     const int gd = (N + TC - 1) / TC;
     mf_with_degree(K, [&](auto kc) {
       constexpr int KD = decltype(kc)::value;
-      run_grid(gd, gd, mf_threads_u(TC), mfu_down_smem<T>(TC, KD), [&](const MfCta& c) { mfu_down_body<T, TC, KD>(a, c); });
+      run_grid(gd, gd, mf_threads_ud(TC), mfu_down_smem<T>(TC, KD), [&](const MfCta& c) { mfu_down_body<T, TC, KD>(a, c); });
     });
   });
   // reference: smoothing from x0 = c0 D^-1 b, then residual and restriction
@@ -170,7 +170,7 @@ static void velocity(const HostSetup& hs, int l, int K, double tol, std::mt19937
     const int gu = (2 * N + 2 * TC - 1) / (2 * TC);
     mf_with_degree(K, [&](auto kc) {
       constexpr int KD = decltype(kc)::value;
-      run_grid(gu, gu, mf_threads_u(TC), mfu_up_smem<T>(TC, KD), [&](const MfCta& c) { mfu_up_body<T, TC, KD>(u, c); });
+      run_grid(gu, gu, mf_threads_uu(TC), mfu_up_smem<T>(TC, KD), [&](const MfCta& c) { mfu_up_body<T, TC, KD>(u, c); });
     });
   });
   std::vector<double> Pxc;
@@ -213,7 +213,7 @@ static void velocity(const HostSetup& hs, int l, int K, double tol, std::mt19937
     const int gd = (N + TC - 1) / TC;
     mf_with_degree(K, [&](auto kc) {
       constexpr int KD = decltype(kc)::value;
-      run_grid(gd, gd, mf_threads_u(TC), mfu_down_smem<T>(TC, KD), [&](const MfCta& c) { mfu_down_body<T, TC, KD>(w, c); });
+      run_grid(gd, gd, mf_threads_ud(TC), mfu_down_smem<T>(TC, KD), [&](const MfCta& c) { mfu_down_body<T, TC, KD>(w, c); });
     });
   });
   for (int i = 0; i < n; ++i) x[i] = d[i] = ch.c0 * H.dinvA[i] * bres[i];
@@ -239,7 +239,7 @@ static void velocity(const HostSetup& hs, int l, int K, double tol, std::mt19937
     const int gd = (N + TC - 1) / TC;
     mf_with_degree(K, [&](auto kc) {
       constexpr int KD = decltype(kc)::value;
-      run_grid(gd, gd, mf_threads_u(TC), mfu_down_smem<T>(TC, KD), [&](const MfCta& c) { mfu_down_body<T, TC, KD>(w, c); });
+      run_grid(gd, gd, mf_threads_ud(TC), mfu_down_smem<T>(TC, KD), [&](const MfCta& c) { mfu_down_body<T, TC, KD>(w, c); });
     });
   });
   for (int i = 0; i < n; ++i) bres[i] = b[i] - Btz[i];
