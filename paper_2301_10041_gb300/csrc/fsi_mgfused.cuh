@@ -35,6 +35,7 @@
 // per CTA computes the same values; the host test of these kernels runs the
 // bodies that way.
 #pragma once
+#include <cstdlib>
 #include <cuda_runtime.h>
 
 #include <type_traits>
@@ -83,16 +84,16 @@ constexpr int kMfPresTab = 9 * 9 * 9 + 9 * 3;  // pressure stencil table: blocks
 // repeat less of their neighbours' work.
 __host__ __device__ __forceinline__ int mf_tile_u(int N) { return N >= 512 ? 16 : 8; }
 __host__ __device__ __forceinline__ int mf_tile_p(int N) { return N >= 512 ? 8 : 4; }
-// Threads of a velocity launch: one frame entry per thread at the default
-// degree (2).  A launch's time on these grids is one CTA's chain of phases,
-// and the threads' share of a phase sets it: the 8-node down launch went from
-// 16.3 to 17.0 steps/s on the 128 x 128 cavity with 1024 threads instead of
-// 512.  The 16-node tiles of the large grids keep 512 (1024 measured slower
-// there: 228 against 149 us for the up launch at N = 1024).  Down frames have
+// Threads of a velocity launch.  A launch's time on these grids is one CTA's
+// chain of phases, and the threads' share of a phase sets it.  The stencil
+// sweeps give each thread two plane rows (mf_vsweep2), so 512 threads cover
+// the smoothing and residual sweeps of an 8-node tile once; the loads and
+// sweeps of whole frames take two rounds.  The 16-node tiles of the large
+// grids use 512 as well (1024 measured slower there).  Down frames have
 // TC + 8 plane entries a side (four planes), up frames TC + 4; a warp takes
 // two rows of up to 16 entries, four rows of up to 8.
-constexpr int mf_threads_ud(int tc) { return tc >= 16 ? 512 : (tc == 8 ? 1024 : (tc == 4 ? 768 : 640)); }
-constexpr int mf_threads_uu(int tc) { return tc >= 16 ? 512 : (tc == 8 ? 1024 : (tc == 4 ? 256 : 192)); }
+constexpr int mf_threads_ud(int tc) { return tc >= 16 ? 512 : (tc == 8 ? 512 : (tc == 4 ? 768 : 640)); }
+constexpr int mf_threads_uu(int tc) { return tc >= 16 ? 512 : (tc == 8 ? 512 : (tc == 4 ? 256 : 192)); }
 constexpr int mf_threads_p(int tp) { return tp >= 4 ? 256 : 128; }
 
 // Call f(integral_constant<degree>) for a Chebyshev degree 1 .. kMfMaxDeg
@@ -258,6 +259,39 @@ __host__ __device__ __forceinline__ void mf_vsweep(const MfCta& c, int qx0, int 
   }
 }
 
+// fn(type, px, py) over the same rectangle, a thread taking the two
+// entries (px, py) and (px, py + 1) of a plane: fn computes both, so that
+// the stencil taps the two share (two of three plane rows) and their
+// coefficients are loaded once.  The row count of the rectangle is even
+// (every frame side and shrink used here keeps it so).
+template <class F>
+__host__ __device__ __forceinline__ void mf_vsweep2(const MfCta& c, int qx0, int qx1, int qy0, int qy1, F&& fn) {
+  const int nqx = qx1 - qx0, npr = (qy1 - qy0) >> 1;
+#ifndef __CUDA_ARCH__
+  if ((qy1 - qy0) & 1) std::abort();
+#endif
+  const int sh = nqx <= 8 ? 3 : (nqx <= 16 ? 4 : 5);
+  const int cw = 1 << sh, rsh = 5 - sh, rpw = 1 << rsh;
+  const int nyp = ((npr + rpw - 1) >> rsh) << rsh;
+  const int nrow = 4 * nyp, step = (c.vthr >> 5) * rpw;
+  for (int t = c.tid; t < c.vthr; t += c.nthr) {
+    const int lane = t & 31;
+    for (int yy = (t >> 5) * rpw + (lane >> sh); yy < nrow; yy += step) {
+      const int tau = (yy >= nyp) + (yy >= 2 * nyp) + (yy >= 3 * nyp);
+      const int y = yy - tau * nyp;
+      if (y >= npr) continue;
+      for (int x = lane & (cw - 1); x < nqx; x += cw) {
+        switch (tau) {
+          case 0: fn(std::integral_constant<int, 0>(), qx0 + x, qy0 + 2 * y); break;
+          case 1: fn(std::integral_constant<int, 1>(), qx0 + x, qy0 + 2 * y); break;
+          case 2: fn(std::integral_constant<int, 2>(), qx0 + x, qy0 + 2 * y); break;
+          default: fn(std::integral_constant<int, 3>(), qx0 + x, qy0 + 2 * y); break;
+        }
+      }
+    }
+  }
+}
+
 // --------------------------------------------------------------- velocity
 // interior Q2 node (1 <= ix, iy <= 2N-1) -> id in the type-blocked order
 // (corners, x-edge midpoints, y-edge midpoints, centres; lattice order inside)
@@ -360,31 +394,38 @@ __host__ __device__ __forceinline__ void mf_vel_cheb(const MfCta& cta, const MfV
                                                      typename Vec2<T>::type* __restrict__ Dn, bool first, T c1, T c2) {
   using T2 = typename Vec2<T>::type;
   const int N = op.N;
-  mf_vsweep(cta, s, f.pw - s, s, f.ph - s, [&](auto tc, int px, int py) {
+  // two plane rows per thread: A applied at both (the reads stay inside the
+  // frame since s >= 1; outside the interior the result is not used)
+  mf_vsweep2(cta, s, f.pw - s, s, f.ph - s, [&](auto tc, int px, int py) {
     constexpr int TAU = decltype(tc)::value;
-    const int ix = f.ox + 2 * px + (TAU & 1), iy = f.oy + 2 * py + (TAU >> 1);
-    const int e = f.at(TAU, px, py);
-    T2 xn, dn;
-    if (mf_vinterior(N, ix, iy)) {
-      T a0, a1;
-      mf_vel_apply<T, TAU>(op, Xo, f, px, py, a0, a1);
-      const T2 b = B[e], xo = Xo[e];
-      const T r0 = b.x - a0, r1 = b.y - a1;
-      if (first) {
-        dn.x = c2 * op.dinv[TAU][0] * r0;
-        dn.y = c2 * op.dinv[TAU][1] * r1;
+    T a[2][2];
+    mf_vel_apply<T, TAU>(op, Xo, f, px, py, a[0][0], a[0][1]);
+    mf_vel_apply<T, TAU>(op, Xo, f, px, py + 1, a[1][0], a[1][1]);
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const int qy = py + k;
+      const int ix = f.ox + 2 * px + (TAU & 1), iy = f.oy + 2 * qy + (TAU >> 1);
+      const int e = f.at(TAU, px, qy);
+      T2 xn, dn;
+      if (mf_vinterior(N, ix, iy)) {
+        const T2 b = B[e], xo = Xo[e];
+        const T r0 = b.x - a[k][0], r1 = b.y - a[k][1];
+        if (first) {
+          dn.x = c2 * op.dinv[TAU][0] * r0;
+          dn.y = c2 * op.dinv[TAU][1] * r1;
+        } else {
+          const T2 d = Do[e];
+          dn.x = c1 * d.x + c2 * op.dinv[TAU][0] * r0;
+          dn.y = c1 * d.y + c2 * op.dinv[TAU][1] * r1;
+        }
+        xn.x = xo.x + dn.x;
+        xn.y = xo.y + dn.y;
       } else {
-        const T2 d = Do[e];
-        dn.x = c1 * d.x + c2 * op.dinv[TAU][0] * r0;
-        dn.y = c1 * d.y + c2 * op.dinv[TAU][1] * r1;
+        xn.x = xn.y = dn.x = dn.y = 0;
       }
-      xn.x = xo.x + dn.x;
-      xn.y = xo.y + dn.y;
-    } else {
-      xn.x = xn.y = dn.x = dn.y = 0;
+      Xn[e] = xn;
+      Dn[e] = dn;
     }
-    Xn[e] = xn;
-    Dn[e] = dn;
   });
 }
 
@@ -483,21 +524,26 @@ __host__ __device__ void mfu_down_body(const MfVelArgs<T>& a, const MfCta& cta) 
   // residual on the frame shrunk by K (plane units): the restriction's
   // support; the pre-smoothed iterate on the owned fine nodes [2 CX0, 2 CX0
   // + 2 tile), plane entries [o, o + tile), goes out in the same sweep
-  mf_vsweep(cta, K, f.pw - K, K, f.ph - K, [&](auto tc, int px, int py) {
+  mf_vsweep2(cta, K, f.pw - K, K, f.ph - K, [&](auto tc, int px, int py) {
     constexpr int TAU = decltype(tc)::value;
-    const int ix = f.ox + 2 * px + (TAU & 1), iy = f.oy + 2 * py + (TAU >> 1);
-    const int e = f.at(TAU, px, py);
-    T2 r;
-    r.x = r.y = 0;
-    if (mf_vinterior(N, ix, iy)) {
-      T a0, a1;
-      mf_vel_apply<T, TAU>(op, Xc, f, px, py, a0, a1);
-      r.x = B[e].x - a0;
-      r.y = B[e].y - a1;
-      if (px >= o && px < o + TC && py >= o && py < o + TC)
-        *reinterpret_cast<T2*>(a.xout + 2 * (size_t)mf_vnode_t<TAU>(N, ix, iy)) = Xc[e];
+    T ap[2][2];
+    mf_vel_apply<T, TAU>(op, Xc, f, px, py, ap[0][0], ap[0][1]);
+    mf_vel_apply<T, TAU>(op, Xc, f, px, py + 1, ap[1][0], ap[1][1]);
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const int qy = py + k;
+      const int ix = f.ox + 2 * px + (TAU & 1), iy = f.oy + 2 * qy + (TAU >> 1);
+      const int e = f.at(TAU, px, qy);
+      T2 r;
+      r.x = r.y = 0;
+      if (mf_vinterior(N, ix, iy)) {
+        r.x = B[e].x - ap[k][0];
+        r.y = B[e].y - ap[k][1];
+        if (px >= o && px < o + TC && qy >= o && qy < o + TC)
+          *reinterpret_cast<T2*>(a.xout + 2 * (size_t)mf_vnode_t<TAU>(N, ix, iy)) = Xc[e];
+      }
+      R[e] = r;
     }
-    R[e] = r;
   });
   MF_SYNC();
   // restriction to the coarse nodes of the tile (coarse lattice interior
@@ -633,30 +679,35 @@ __host__ __device__ void mfu_up_body(const MfVelArgs<T>& a, const MfCta& cta) {
   // last step on the owned tile: write the result and the epilogue
   const int s = K - 1;
   const T c1 = s == 0 ? (T)0 : a.ch.c1[s - 1], c2 = s == 0 ? a.ch.c0 : a.ch.c2[s - 1];
-  mf_vsweep(cta, K, f.pw - K, K, f.ph - K, [&](auto tc, int px, int py) {
+  mf_vsweep2(cta, K, f.pw - K, K, f.ph - K, [&](auto tc, int px, int py) {
     constexpr int TAU = decltype(tc)::value;
-    const int ix = f.ox + 2 * px + (TAU & 1), iy = f.oy + 2 * py + (TAU >> 1);
-    if (!mf_vinterior(N, ix, iy)) return;
-    const int e = f.at(TAU, px, py);
-    T a0, a1;
-    mf_vel_apply<T, TAU>(op, Xc, f, px, py, a0, a1);
-    const T2 b = B[e], xo = Xc[e];
-    const T r0 = b.x - a0, r1 = b.y - a1;
-    T d0 = c2 * op.dinv[TAU][0] * r0, d1 = c2 * op.dinv[TAU][1] * r1;
-    if (s > 0) {
-      const T2 d = Dc[e];
-      d0 = c1 * d.x + c2 * op.dinv[TAU][0] * r0;
-      d1 = c1 * d.y + c2 * op.dinv[TAU][1] * r1;
-    }
-    const size_t id = mf_vnode_t<TAU>(N, ix, iy);
-    const T y0 = xo.x + d0, y1 = xo.y + d1;
-    T2 y;
-    y.x = y0;
-    y.y = y1;
-    *reinterpret_cast<T2*>(a.xout + 2 * id) = y;
-    if (a.fin.acc) {
-      a.fin.acc[2 * id] += a.fin.omega * y0;
-      a.fin.acc[2 * id + 1] += a.fin.omega * y1;
+    T ap[2][2];
+    mf_vel_apply<T, TAU>(op, Xc, f, px, py, ap[0][0], ap[0][1]);
+    mf_vel_apply<T, TAU>(op, Xc, f, px, py + 1, ap[1][0], ap[1][1]);
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const int qy = py + k;
+      const int ix = f.ox + 2 * px + (TAU & 1), iy = f.oy + 2 * qy + (TAU >> 1);
+      if (!mf_vinterior(N, ix, iy)) continue;
+      const int e = f.at(TAU, px, qy);
+      const T2 b = B[e], xo = Xc[e];
+      const T r0 = b.x - ap[k][0], r1 = b.y - ap[k][1];
+      T d0 = c2 * op.dinv[TAU][0] * r0, d1 = c2 * op.dinv[TAU][1] * r1;
+      if (s > 0) {
+        const T2 d = Dc[e];
+        d0 = c1 * d.x + c2 * op.dinv[TAU][0] * r0;
+        d1 = c1 * d.y + c2 * op.dinv[TAU][1] * r1;
+      }
+      const size_t id = mf_vnode_t<TAU>(N, ix, iy);
+      const T y0 = xo.x + d0, y1 = xo.y + d1;
+      T2 y;
+      y.x = y0;
+      y.y = y1;
+      *reinterpret_cast<T2*>(a.xout + 2 * id) = y;
+      if (a.fin.acc) {
+        a.fin.acc[2 * id] += a.fin.omega * y0;
+        a.fin.acc[2 * id + 1] += a.fin.omega * y1;
+      }
     }
   });
 }
