@@ -128,6 +128,7 @@ MG_CLUSTER = 0   # 0: coarse levels in one cluster launch; -1: per-level launche
 MG_DEGREE = 0    # Chebyshev degree of each multigrid smoothing (0: the library's default, 2)
 MG_COARSE = 0    # coarsest multigrid grid in cells (0: the library's default, 16)
 CS_DEGREE = 0    # Chebyshev steps per solid mass solve (0: the library's default)
+MG_COARSE_P = 0  # coarsest pressure grid in cells (0: the library's default)
 
 
 def arm_settings(precision):
@@ -140,7 +141,7 @@ def arm_settings(precision):
 def mg_settings():
     """Multigrid kernel choice and smoothing degree of the bench's arms (command-line switches)."""
     return dict(mg_fused=MG_FUSED, mg_cluster=MG_CLUSTER, mg_degree=MG_DEGREE, mg_coarse=MG_COARSE,
-                cs_degree=CS_DEGREE)
+                cs_degree=CS_DEGREE, mg_coarse_p=MG_COARSE_P)
 
 
 def time_arm(fsi, torch, case, precision, steps, warmup, stream, flush, precond=PRECOND, stokes_its=STOKES_ITS,
@@ -855,7 +856,7 @@ def run_serve(args):
 
 
 def main():
-    global AUTOTUNE, MG_FUSED, MG_CLUSTER, MG_DEGREE, MG_COARSE, CS_DEGREE, STOKES_ITS
+    global AUTOTUNE, MG_FUSED, MG_CLUSTER, MG_DEGREE, MG_COARSE, MG_COARSE_P, CS_DEGREE, STOKES_ITS
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
@@ -894,6 +895,8 @@ def main():
     ap.add_argument("--stokes-its", type=int, default=STOKES_ITS,
                     help="Richardson steps on the Stokes block per preconditioner application (bench workload)")
     ap.add_argument("--mg-degree", type=int, default=0, help="Chebyshev degree of each multigrid smoothing")
+    ap.add_argument("--mg-coarse-p", type=int, default=0,
+                    help="coarsest pressure multigrid grid in cells (0: the library's default)")
     ap.add_argument("--cs-degree", type=int, default=0,
                     help="Chebyshev steps per solid mass solve (0: the library's default)")
     ap.add_argument("--mg-coarse", type=int, default=0,
@@ -923,6 +926,7 @@ def main():
     MG_DEGREE = args.mg_degree
     MG_COARSE = args.mg_coarse
     CS_DEGREE = args.cs_degree
+    MG_COARSE_P = args.mg_coarse_p
     STOKES_ITS = args.stokes_its
     if args.autotune:
         AUTOTUNE = 1

@@ -142,6 +142,10 @@ typedef struct fsi_params {
                           0 or less = 16 (a 16-cell grid: 1922 velocity unknowns, a
                           15 MB FP32 or 30 MB FP64 inverse, held in L2); at
                           most 32 (FSI_ERR_INVALID above) */
+    int    mg_coarse_p; /* the same for the pressure-Laplacian hierarchy alone;
+                          0 or less = mg_coarse; at most 32 (FSI_ERR_INVALID
+                          above; a 32-cell grid has 3072 pressure unknowns,
+                          a 38 MB FP32 inverse) */
 } fsi_params;
 
 /* Solid reference mesh (the body at t = 0): P1 triangles, or Q1

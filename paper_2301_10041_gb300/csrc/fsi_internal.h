@@ -63,6 +63,7 @@ struct SetupParams {
   int N; double rho, nu, kappa, dt, lid;
   int npe = 3;            // solid element: 3 = P1 triangle, 4 = Q1 quadrilateral
   int coarse_max = 8;     // coarsening stops at the first grid of at most this many cells a side
+  int coarse_max_p = 0;   // the same for the pressure hierarchy (0: coarse_max)
 };
 
 struct HostSetup {
@@ -78,6 +79,7 @@ struct HostSetup {
   std::vector<double> mp_inv;  // inverse P1disc mass diagonal, 3 per cell
   std::vector<double> cs_dinv; // inverse diagonal of the solid mass
   std::vector<FluidLevelHost> levels;  // 0 = finest
+  int nlev_u = 0, nlev_p = 0;          // levels of the velocity / pressure hierarchy (the first ones)
   // the coarsest level as dense row-major matrices, inverted on the device
   // when a problem is created: A_f, and the pressure Laplacian made regular
   // by a rank-one term (L + t e e^T / |e|^2, whose inverse equals L^+ on

@@ -598,8 +598,18 @@ void build_setup(const SetupParams& sp, int n_s, int n_tri, const double* ref_xy
   // ---- multigrid hierarchy: N, N/2, ... while even and above coarse_max
   // cells a side; the coarsest is solved with its dense inverse (a grid of 16
   // cells has 2 * 31^2 = 1922 velocity unknowns)
+  const int cu = sp.coarse_max, cp = sp.coarse_max_p > 0 ? sp.coarse_max_p : sp.coarse_max;
   std::vector<int> Ns{N};
-  while (Ns.back() % 2 == 0 && Ns.back() > sp.coarse_max) Ns.push_back(Ns.back() / 2);
+  while (Ns.back() % 2 == 0 && Ns.back() > std::min(cu, cp)) Ns.push_back(Ns.back() / 2);
+  // each hierarchy ends at its first grid of at most its coarse_max cells
+  // (or at the last, odd, one)
+  auto levels_to = [&](int c) {
+    int l = 0;
+    while (l + 1 < (int)Ns.size() && Ns[l] > c) ++l;
+    return l + 1;
+  };
+  out.nlev_u = levels_to(cu);
+  out.nlev_p = levels_to(cp);
   out.levels.resize(Ns.size());
   for (size_t l = 0; l < Ns.size(); ++l) {
     FluidLevelHost& L = out.levels[l];
@@ -631,13 +641,14 @@ void build_setup(const SetupParams& sp, int n_s, int n_tri, const double* ref_xy
     L.lmaxL = power_lmax(Lp, block_diag_inverse_scalar(Lp), 60);
   }
   {
-    const FluidLevelHost& C = out.levels.back();
+    const FluidLevelHost& C = out.levels[out.nlev_u - 1];
     out.coarseA = dense_of(C.A);
     out.coarse_nA = C.A.nrows * 2;
     // the singular pressure Laplacian plus t e e^T / |e|^2 (t its mean
     // diagonal), e the constants (first dof of every cell)
-    std::vector<double> Ld = dense_of(C.L);
-    const int n = C.L.nrows * 3;
+    const FluidLevelHost& Cp = out.levels[out.nlev_p - 1];
+    std::vector<double> Ld = dense_of(Cp.L);
+    const int n = Cp.L.nrows * 3;
     out.coarse_nL = n;
     double t = 0;
     for (int i = 0; i < n; ++i) t += Ld[(size_t)i * n + i];

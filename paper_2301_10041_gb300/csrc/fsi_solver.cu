@@ -401,7 +401,7 @@ static void build_coarse_inverse(Arena& ar, const HostSetup& hs, bool pressure, 
 template <class T>
 static void build_mg(Arena& ar, const HostSetup& hs, bool pressure, int degree, MG<T>& mg, bool tune,
                      cudaStream_t s, const double* inv64 = nullptr, int ld64 = 0) {
-  const int nl = (int)hs.levels.size();
+  const int nl = pressure ? hs.nlev_p : hs.nlev_u;
   mg.degree = degree;
   mg.pressure = pressure;
   mg.lv.resize(nl);
@@ -491,7 +491,7 @@ template <class T>
 static void setup_cluster(Arena& ar, const HostSetup& hs, MG<T>& mg, bool pressure, int max_n) {
   int lc_min = 0;   // with max_n > 0 the cluster's finest level has at most max_n cells a side
   if (max_n > 0)
-    while (lc_min + 1 < (int)hs.levels.size() && hs.levels[lc_min].N > max_n) ++lc_min;
+    while (lc_min + 1 < (int)mg.lv.size() && hs.levels[lc_min].N > max_n) ++lc_min;
   for (int cs : {16, 8}) {
     auto viable = [&](size_t smem) {
       if (ar.count_only) return true;
@@ -1529,6 +1529,7 @@ static void check_params(const fsi_params& p, int n_nodes, int n_tris) {
   if (p.mg_cluster < -1) throw std::invalid_argument("mg_cluster");
   if (p.mg_fused != 0 && p.mg_fused != -1) throw std::invalid_argument("mg_fused");
   if (p.mg_coarse > 32) throw std::invalid_argument("mg_coarse must be at most 32");
+  if (p.mg_coarse_p > 32) throw std::invalid_argument("mg_coarse_p must be at most 32");
   if (p.coupling != 0 && p.coupling != 1) throw std::invalid_argument("coupling");
   if (p.solid_law != 0 && p.solid_law != 1) throw std::invalid_argument("solid_law");
   if (p.autotune != 0 && p.autotune != 1) throw std::invalid_argument("autotune");
@@ -1560,6 +1561,7 @@ static fsi_params with_defaults(fsi_params p) {
   // coarsest grid 16 cells: one dense product (a 15 MB FP32 inverse, held in
   // L2) in place of the 16-cell level's two launches and the 8-cell solve
   if (p.mg_coarse <= 0) p.mg_coarse = 16;
+  if (p.mg_coarse_p <= 0) p.mg_coarse_p = p.mg_coarse;
   return p;
 }
 
@@ -2015,6 +2017,7 @@ static size_t footprint_impl(const fsi_params& prm0, int n_nodes, int n_tris, co
   SetupParams sp{prm.N, prm.rho_f, prm.nu, prm.kappa, prm.dt, prm.lid_u};
   sp.npe = elem_nodes(prm);
   sp.coarse_max = prm.mg_coarse;
+  sp.coarse_max_p = prm.mg_coarse_p;
   build_setup(sp, n_nodes, n_tris, ref_xy, tris, P.hs);
   allocate_problem(P, ref_xy, tris);
   return P.ar.bytes;
@@ -2140,6 +2143,7 @@ int fsi_create_problem_budget(const fsi_params* params, const fsi_solid_mesh* me
     SetupParams sp{prm.N, prm.rho_f, prm.nu, prm.kappa, prm.dt, prm.lid_u};
     sp.npe = elem_nodes(prm);
     sp.coarse_max = prm.mg_coarse;
+  sp.coarse_max_p = prm.mg_coarse_p;
     build_setup(sp, P.nS, P.nTri, mesh->ref_xy, mesh->tris, P.hs);
     {
       double lam[6][3], w[6];

@@ -37,7 +37,7 @@ class fsi_params(C.Structure):
                 ("coupling", C.c_int), ("solid_law", C.c_int), ("gamma", C.c_double), ("eta", C.c_double),
                 ("newton_tol", C.c_double), ("newton_max", C.c_int), ("autotune", C.c_int),
                 ("solid_elem", C.c_int), ("mg_fused", C.c_int),
-                ("mg_coarse", C.c_int)]
+                ("mg_coarse", C.c_int), ("mg_coarse_p", C.c_int)]
 
 
 class fsi_solid_mesh(C.Structure):
@@ -118,12 +118,12 @@ def _f64(a) -> np.ndarray:
 def make_params(N, rho_f, nu, kappa, dt, lid_u=0.0, precond=1, precision=0, restart=0, rtol=0.0, max_it=0,
                 mg_degree=0, cs_degree=0, inner_rtol=0.0, max_refine=0, stokes_its=0,
                 stokes_omega=0.0, mg_cluster=0, coupling=0, solid_law=0, gamma=0.0, eta=0.0, newton_tol=0.0,
-                newton_max=0, autotune=0, solid_elem=0, mg_fused=0, mg_coarse=0) -> fsi_params:
+                newton_max=0, autotune=0, solid_elem=0, mg_fused=0, mg_coarse=0, mg_coarse_p=0) -> fsi_params:
     return fsi_params(int(N), float(rho_f), float(nu), float(kappa), float(dt), float(lid_u), int(precond),
                       int(precision), int(restart), float(rtol), int(max_it), int(mg_degree), int(cs_degree),
                       float(inner_rtol), int(max_refine), int(stokes_its), float(stokes_omega), int(mg_cluster),
                       int(coupling), int(solid_law), float(gamma), float(eta), float(newton_tol), int(newton_max),
-                      int(autotune), int(solid_elem), int(mg_fused), int(mg_coarse))
+                      int(autotune), int(solid_elem), int(mg_fused), int(mg_coarse), int(mg_coarse_p))
 
 
 def footprint_bytes(params: fsi_params, n_nodes: int, n_tris: int) -> int:

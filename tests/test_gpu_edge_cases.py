@@ -157,8 +157,8 @@ def test_restart_and_stokes_steps_above_their_limits_are_refused(fsi):
     than 16 inner Stokes steps and a coarsest grid above 32 cells are
     refused at creation, not clamped."""
     case = fi.disk16_case()
-    for kw in (dict(restart=251), dict(stokes_its=17), dict(mg_coarse=33)):
+    for kw in (dict(restart=251), dict(stokes_its=17), dict(mg_coarse=33), dict(mg_coarse_p=33)):
         with pytest.raises(fsi.FsiError) as e:
             fsi.problem_from_case(case, **kw)
         assert e.value.code == fsi.FSI_ERR_INVALID
-    fsi.problem_from_case(case, restart=250, stokes_its=16, mg_coarse=32).close()
+    fsi.problem_from_case(case, restart=250, stokes_its=16, mg_coarse=32, mg_coarse_p=32).close()
