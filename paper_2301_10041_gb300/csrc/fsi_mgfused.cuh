@@ -72,7 +72,15 @@ __host__ __device__ __forceinline__ int mf_min(int a, int b) { return a < b ? a 
 __host__ __device__ __forceinline__ int mf_max(int a, int b) { return a > b ? a : b; }
 
 constexpr int kMfMaxDeg = 4;      // Chebyshev degrees 1..4 (the default is 2)
-constexpr int kMfPresTab = 9 * 9 * 9 + 9 * 3;  // pressure stencil table: blocks, then D^-1
+// pressure stencil table: per wall variant 9 blocks of 3x3, each padded to
+// 12 values (16-byte aligned: three 16-byte loads per block), then D^-1
+// (3 per variant)
+constexpr int kMfPresBlk = 12;
+constexpr int kMfPresVar = 9 * kMfPresBlk;
+constexpr int kMfPresDinv = 9 * kMfPresVar;
+constexpr int kMfPresTab = kMfPresDinv + 9 * 3;
+// table index of block (dy + 1, dx + 1) = (y, x) of variant v
+constexpr int mf_pres_blk(int v, int y, int x) { return kMfPresVar * v + kMfPresBlk * (3 * y + x); }
 
 // Tile sizes by level: velocity down TC coarse lattice nodes a side (up:
 // 2 TC fine lattice nodes), pressure down TP coarse cells (up: 2 TP fine
@@ -729,12 +737,32 @@ __host__ __device__ __forceinline__ bool mf_cin(int N, int cx, int cy) {
   return cx >= 0 && cy >= 0 && cx < N && cy < N;
 }
 
+// the 12 values of a padded pressure block from shared memory (16-byte aligned)
+template <class T>
+__host__ __device__ __forceinline__ void mf_load12(const T* __restrict__ p, T c[12]);
+template <>
+__host__ __device__ __forceinline__ void mf_load12<float>(const float* __restrict__ p, float c[12]) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float4 v = reinterpret_cast<const float4*>(p)[k];
+    c[4 * k] = v.x; c[4 * k + 1] = v.y; c[4 * k + 2] = v.z; c[4 * k + 3] = v.w;
+  }
+}
+template <>
+__host__ __device__ __forceinline__ void mf_load12<double>(const double* __restrict__ p, double c[12]) {
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    const double2 v = reinterpret_cast<const double2*>(p)[k];
+    c[2 * k] = v.x; c[2 * k + 1] = v.y;
+  }
+}
+
 // y = L v at cell (cx, cy) (frame entry e) with the stencil table in shared
 // memory; the three cell rows go to separate partial sums
 template <class T>
 __host__ __device__ __forceinline__ void mf_pres_apply(const T* __restrict__ tab, const T* __restrict__ v,
                                                        const MfCells& f, int N, int cx, int cy, int e, T y[3]) {
-  const T* base = tab + 81 * mf_variant(N, cx, cy);
+  const T* base = tab + kMfPresVar * mf_variant(N, cx, cy);
   const int n = f.n();
   T p[3][3];
 #pragma unroll
@@ -745,7 +773,8 @@ __host__ __device__ __forceinline__ void mf_pres_apply(const T* __restrict__ tab
     for (int dx = -1; dx <= 1; ++dx) {
       const int q = e + dy * f.w + dx;
       const T x0 = v[q], x1 = v[n + q], x2 = v[2 * n + q];
-      const T* c = base + 9 * ((dy + 1) * 3 + dx + 1);
+      T c[kMfPresBlk];
+      mf_load12<T>(base + kMfPresBlk * ((dy + 1) * 3 + dx + 1), c);
 #pragma unroll
       for (int i = 0; i < 3; ++i) p[dy + 1][i] = mf_fma(c[3 * i + 2], x2, mf_fma(c[3 * i + 1], x1, mf_fma(c[3 * i], x0, p[dy + 1][i])));
     }
@@ -761,7 +790,7 @@ __host__ __device__ __forceinline__ void mf_pres_cheb(const MfCta& cta, const T*
                                                       const T* __restrict__ Xo, const T* __restrict__ Do,
                                                       T* __restrict__ Xn, T* __restrict__ Dn, bool first, T c1, T c2) {
   const int m = f.w - 2 * s, n = f.n();
-  const T* dv = tab + 729;
+  const T* dv = tab + kMfPresDinv;
   mf_rows(cta, m, m, [&](int i, int j) {
     const int lx = s + i, ly = s + j, e = ly * f.w + lx;
     const int cx = f.ox + lx, cy = f.oy + ly;
@@ -810,7 +839,7 @@ __host__ __device__ void mfp_down_body(const MfPresArgs<T>& a, const MfCta& cta)
   T *Xc = B + 3 * n, *Xn = B + 6 * n, *Dc = B + 9 * n, *Dn = B + 12 * n;
   for (int t = cta.tid; t < kMfPresTab; t += cta.nthr) tab[t] = a.tab[t];
   MF_SYNC();
-  const T* dv = tab + 729;
+  const T* dv = tab + kMfPresDinv;
   // b on the frame (with the residual start: b - (-B) zu, its owned part, the
   // cells [K, K + 2 TP) of the frame, to res.bout); x0 = d0 = c0 D^-1 b
   mf_rows(cta, f.w, f.w, [&](int i, int j) {
@@ -927,7 +956,7 @@ __host__ __device__ void mfp_up_body(const MfPresArgs<T>& a, const MfCta& cta) {
     }
   });
   MF_SYNC();
-  const T* dv = tab + 729;
+  const T* dv = tab + kMfPresDinv;
   for (int s = 0; s < K - 1; ++s) {
     mf_pres_cheb<T>(cta, tab, N, f, s + 1, B, Xc, Dc, Xn, Dn, s == 0,
                     s == 0 ? (T)0 : a.ch.c1[s - 1], s == 0 ? a.ch.c0 : a.ch.c2[s - 1]);

@@ -443,9 +443,9 @@ static void build_mg(Arena& ar, const HostSetup& hs, bool pressure, int degree, 
       for (int v = 0; v < 9; ++v)
         for (int y = 0; y < 3; ++y)
           for (int x = 0; x < 3; ++x)
-            for (int q = 0; q < 9; ++q) tab[81 * v + 9 * (3 * y + x) + q] = H.stenL[v][y][x][q];
+            for (int q = 0; q < 9; ++q) tab[mf_pres_blk(v, y, x) + q] = H.stenL[v][y][x][q];
       for (int v = 0; v < 9; ++v)
-        for (int k = 0; k < 3; ++k) tab[729 + 3 * v + k] = H.dinvLv[v][k];
+        for (int k = 0; k < 3; ++k) tab[kMfPresDinv + 3 * v + k] = H.dinvLv[v][k];
       L.mftab = upload_as<T>(ar, tab);
     }
   }
