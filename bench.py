@@ -417,7 +417,7 @@ def roofline(prob, args):
                 "achieved": d["gbs"], "peak": peak, "unit": "GB/s", "frac": d["hbm_frac"], "traffic": None,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6800 GB/s",
                 "launch_us": d["us"], "algorithmic_bytes": d["bytes"], "others": out}
-    return {"bound": "alu", "kernel": "k_mfu_down<float,8,2,1024> (fused down launch, finest velocity level)",
+    return {"bound": "alu", "kernel": "k_mfu_down<float,8,2,512> (fused down launch, finest velocity level)",
             "achieved": dom["tflops"], "peak": alu_peak, "unit": "TFLOP/s", "frac": dom["alu_frac"],
             "traffic": traffic, "peak_source": "derived: FP32 FMA lanes x 2 x max SM clock",
             "peak_derivation": alu_how, "launch_us": dom["us"], "algorithmic_flops": dom["flops"],
