@@ -440,9 +440,12 @@ __host__ __device__ __forceinline__ void mf_vel_cheb(const MfCta& cta, const MfV
 // y += (-B^T zp) at the interior node (ix, iy) of type TAU: the sum over the
 // node's cells (one or two per direction: an odd lattice index lies inside a
 // cell, at local node 1; an even one on the edge between two, at local node 2
-// of the lower and 0 of the upper), lower cells first
+// of the lower and 0 of the upper), lower cells first.  zp holds the three
+// values of cell (cx, cy) at 3 ((cy - cy0) stride + cx - cx0): the global
+// vector (0, 0, N) or a copy of the cells around a frame.
 template <class T, int TAU>
-__host__ __device__ __forceinline__ void mf_vel_btp(const MfRes<T>& r, int N, int ix, int iy, T& y0, T& y1) {
+__host__ __device__ __forceinline__ void mf_vel_btp(const MfRes<T>& r, const T* __restrict__ zp, int cx0, int cy0,
+                                                    int stride, int ix, int iy, T& y0, T& y1) {
   constexpr int PX = TAU & 1, PY = TAU >> 1;
 #pragma unroll
   for (int j = 0; j < (PY ? 1 : 2); ++j) {
@@ -450,7 +453,7 @@ __host__ __device__ __forceinline__ void mf_vel_btp(const MfRes<T>& r, int N, in
     for (int i = 0; i < (PX ? 1 : 2); ++i) {
       const int aa = PX ? 1 : (i == 0 ? 2 : 0), ab = PY ? 1 : (j == 0 ? 2 : 0);
       const int cx = (ix - aa) >> 1, cy = (iy - ab) >> 1, al = 3 * ab + aa;
-      const T* __restrict__ p = r.zp + 3 * ((size_t)cy * N + cx);
+      const T* __restrict__ p = zp + 3 * ((size_t)(cy - cy0) * stride + (cx - cx0));
       const T p0 = p[0], p1 = p[1], p2 = p[2];
       y0 += r.divB[0][al][0] * p0 + r.divB[1][al][0] * p1 + r.divB[2][al][0] * p2;
       y1 += r.divB[0][al][1] * p0 + r.divB[1][al][1] * p1 + r.divB[2][al][1] * p2;
@@ -484,6 +487,15 @@ __host__ __device__ void mfu_down_body(const MfVelArgs<T>& a, const MfCta& cta) 
   g.oy = f.oy - 2;
   T2* Z = Dn;
   static_assert(TC + 4 + 2 * K >= 8, "the grown frame must fit in Dn and R");
+  // With zu, the frame's b and the pressure of the cells around the frame
+  // (cells f.ox / 2 - 1 .. f.ox / 2 + PW, PW + 1 a side, after Z when they
+  // fit) come in the same phase, so the launch makes one global round trip
+  // before its first barrier.
+  constexpr int ZPW = PW + 1;
+  constexpr bool zp_frame = 4 * (PW + 2) * (PW + 2) * 2 + 3 * ZPW * ZPW <= 2 * nf * 2;
+  T* ZP = reinterpret_cast<T*>(Z + 4 * (PW + 2) * (PW + 2));
+  const int zcx0 = (f.ox >> 1) - 1, zcy0 = (f.oy >> 1) - 1;
+  const bool zp_smem = zp_frame && rs.zu && rs.zp;
   if (rs.zu) {
     mf_vsweep(cta, 0, g.pw, 0, g.ph, [&](auto tc, int px, int py) {
       constexpr int TAU = decltype(tc)::value;
@@ -493,6 +505,21 @@ __host__ __device__ void mfu_down_body(const MfVelArgs<T>& a, const MfCta& cta) 
       if (mf_vinterior(N, ix, iy)) v = *reinterpret_cast<const T2*>(rs.zu + 2 * (size_t)mf_vnode_t<TAU>(N, ix, iy));
       Z[g.at(TAU, px, py)] = v;
     });
+    mf_vsweep(cta, 0, f.pw, 0, f.ph, [&](auto tc, int px, int py) {
+      constexpr int TAU = decltype(tc)::value;
+      const int ix = f.ox + 2 * px + (TAU & 1), iy = f.oy + 2 * py + (TAU >> 1);
+      T2 v;
+      v.x = v.y = 0;
+      if (mf_vinterior(N, ix, iy)) v = *reinterpret_cast<const T2*>(a.b + 2 * (size_t)mf_vnode_t<TAU>(N, ix, iy));
+      B[f.at(TAU, px, py)] = v;
+    });
+    if (zp_smem)
+      mf_rows(cta, ZPW, ZPW, [&](int i, int j) {
+        const int cx = zcx0 + i, cy = zcy0 + j;
+        const bool in = cx >= 0 && cy >= 0 && cx < N && cy < N;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) ZP[3 * (j * ZPW + i) + k] = in ? rs.zp[3 * ((size_t)cy * N + cx) + k] : (T)0;
+      });
     MF_SYNC();
   }
   // b on the frame (with the residual start: b - A zu - (-B^T) zp, its owned
@@ -500,21 +527,22 @@ __host__ __device__ void mfu_down_body(const MfVelArgs<T>& a, const MfCta& cta) 
   mf_vsweep(cta, 0, f.pw, 0, f.ph, [&](auto tc, int px, int py) {
     constexpr int TAU = decltype(tc)::value;
     const int ix = f.ox + 2 * px + (TAU & 1), iy = f.oy + 2 * py + (TAU >> 1);
+    const int e = f.at(TAU, px, py);
     T2 v;
     v.x = v.y = 0;
     if (mf_vinterior(N, ix, iy)) {
       const size_t id = 2 * (size_t)mf_vnode_t<TAU>(N, ix, iy);
-      v = *reinterpret_cast<const T2*>(a.b + id);
+      v = rs.zu ? B[e] : *reinterpret_cast<const T2*>(a.b + id);
       if (rs.zu || rs.zp) {
         T y0 = 0, y1 = 0;
         if (rs.zu) mf_vel_apply<T, TAU>(op, Z, g, px + 1, py + 1, y0, y1);
-        if (rs.zp) mf_vel_btp<T, TAU>(rs, N, ix, iy, y0, y1);
+        if (zp_smem) mf_vel_btp<T, TAU>(rs, ZP, zcx0, zcy0, ZPW, ix, iy, y0, y1);
+        else if (rs.zp) mf_vel_btp<T, TAU>(rs, rs.zp, 0, 0, N, ix, iy, y0, y1);
         v.x -= y0;
         v.y -= y1;
         if (px >= o && px < o + TC && py >= o && py < o + TC) *reinterpret_cast<T2*>(rs.bout + id) = v;
       }
     }
-    const int e = f.at(TAU, px, py);
     B[e] = v;
     T2 x0;
     x0.x = a.ch.c0 * op.dinv[TAU][0] * v.x;
@@ -837,9 +865,10 @@ __host__ __device__ void mfp_down_body(const MfPresArgs<T>& a, const MfCta& cta)
   T* tab = reinterpret_cast<T*>(cta.sm);
   T* B = tab + ((kMfPresTab + 3) & ~3);
   T *Xc = B + 3 * n, *Xn = B + 6 * n, *Dc = B + 9 * n, *Dn = B + 12 * n;
+  // the table to shared memory in the same phase as the frame's b: the
+  // smoother start takes D^-1 from the global table (one round trip for all)
   for (int t = cta.tid; t < kMfPresTab; t += cta.nthr) tab[t] = a.tab[t];
-  MF_SYNC();
-  const T* dv = tab + kMfPresDinv;
+  const T* dv = a.tab + kMfPresDinv;
   // b on the frame (with the residual start: b - (-B) zu, its owned part, the
   // cells [K, K + 2 TP) of the frame, to res.bout); x0 = d0 = c0 D^-1 b
   mf_rows(cta, f.w, f.w, [&](int i, int j) {
