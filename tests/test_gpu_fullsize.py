@@ -152,8 +152,9 @@ def ellipse64_oracle_step():
 
 
 def _disk64():
-    """configs[0] scaled to N = 64: disk R = 0.2 (m = 24, 3456 triangles),
-    nu = 1, kappa = 10, dt = 0.01, seeded u_0, a moving lid."""
+    """The small disk case (16-cell grid) scaled to N = 64: disk R = 0.2
+    (m = 24, 3456 triangles), nu = 1, kappa = 10, dt = 0.01, seeded u_0, a
+    moving lid."""
     xy, tris = fi.ring_disk_mesh(24, 0.2, (0.5, 0.5))
     return fi.FsiCase(N=64, rho_f=1.0, nu=1.0, kappa=10.0, dt=0.01, lid_u=1.0, ref_xy=xy, tris=tris,
                       u0=fi.initial_velocity(64, 2301, lid_u=1.0), X0=xy.copy(), precond=1, rtol=1e-12)
