@@ -705,7 +705,23 @@ __host__ __device__ void mfu_up_body(const MfVelArgs<T>& a, const MfCta& cta) {
     Xc[e] = xv;
   });
   MF_SYNC();
+  // The Richardson update of the last step reads the iterate it adds to.
+  // With K >= 2 those reads go out in the phase before the last step, into
+  // the coarse frame's buffer (free after the prolongation; the owned tile,
+  // TC x TC entries per plane, fits in it for the 8-node tile), so the last
+  // step makes no global round trip of its own.
+  constexpr int GW = 2 * ((2 * TC + 4 * K + 3) / 4 + 2);
+  constexpr bool acc_pre = K >= 2 && 4 * TC * TC <= GW * GW;
+  T2* ACC = XC;
   for (int s = 0; s + 1 < K; ++s) {  // post-smoothing: CHEB0, then CHEB steps, each on a frame 1 plane entry smaller
+    if (acc_pre && s + 2 == K && a.fin.acc)
+      mf_vsweep(cta, K, f.pw - K, K, f.ph - K, [&](auto tc, int px, int py) {
+        constexpr int TAU = decltype(tc)::value;
+        const int ix = f.ox + 2 * px + (TAU & 1), iy = f.oy + 2 * py + (TAU >> 1);
+        if (!mf_vinterior(N, ix, iy)) return;
+        const size_t id = mf_vnode_t<TAU>(N, ix, iy);
+        ACC[(TAU * TC + py - K) * TC + px - K] = *reinterpret_cast<const T2*>(a.fin.acc + 2 * id);
+      });
     mf_vel_cheb<T>(cta, op, f, s + 1, B, Xc, Dc, Xn, Dn, s == 0,
                    s == 0 ? (T)0 : a.ch.c1[s - 1], s == 0 ? a.ch.c0 : a.ch.c2[s - 1]);
     T2* t = Xc; Xc = Xn; Xn = t;
@@ -741,8 +757,12 @@ __host__ __device__ void mfu_up_body(const MfVelArgs<T>& a, const MfCta& cta) {
       y.y = y1;
       *reinterpret_cast<T2*>(a.xout + 2 * id) = y;
       if (a.fin.acc) {
-        a.fin.acc[2 * id] += a.fin.omega * y0;
-        a.fin.acc[2 * id + 1] += a.fin.omega * y1;
+        T2 z;
+        if (acc_pre) z = ACC[(TAU * TC + qy - K) * TC + px - K];
+        else z = *reinterpret_cast<const T2*>(a.fin.acc + 2 * id);
+        z.x += a.fin.omega * y0;
+        z.y += a.fin.omega * y1;
+        *reinterpret_cast<T2*>(a.fin.acc + 2 * id) = z;
       }
     }
   });
@@ -964,6 +984,11 @@ __host__ __device__ void mfp_up_body(const MfPresArgs<T>& a, const MfCta& cta) {
   T* tab = reinterpret_cast<T*>(cta.sm);
   T* B = tab + ((kMfPresTab + 3) & ~3);
   T *Xc = B + 3 * n, *Xn = B + 6 * n, *Dc = B + 9 * n, *Dn = B + 12 * n;
+  // the epilogue's operands on the owned cells (sv, smp, acc: 3 per cell
+  // each), read in the first phase so that the last step makes no global
+  // round trip of its own
+  constexpr int M = TPF;                     // owned cells a side (f.w - 2 K)
+  T* E = B + 15 * n;
   for (int t = cta.tid; t < kMfPresTab; t += cta.nthr) tab[t] = a.tab[t];
   // b and x + P x_coarse (each fine cell from its parent: [1 sx sy; 0 1/2 0; 0 0 1/2])
   mf_rows(cta, f.w, f.w, [&](int i, int j) {
@@ -977,6 +1002,16 @@ __host__ __device__ void mfp_up_body(const MfPresArgs<T>& a, const MfCta& cta) {
       for (int k = 0; k < 3; ++k) {
         bv[k] = a.b[id + k];
         xv[k] = p[k] + a.xpre[id + k];
+      }
+      if (i >= K && i < K + M && j >= K && j < K + M) {
+        T* eo = E + 9 * ((j - K) * M + (i - K));
+        for (int k = 0; k < 3; ++k) {
+          if (a.fin.sout) {
+            eo[k] = a.fin.sv[id + k];
+            eo[3 + k] = a.fin.smp[id + k];
+          }
+          if (a.fin.acc) eo[6 + k] = a.fin.acc[id + k];
+        }
       }
     }
     for (int k = 0; k < 3; ++k) {
@@ -1005,6 +1040,7 @@ __host__ __device__ void mfp_up_body(const MfPresArgs<T>& a, const MfCta& cta) {
     mf_pres_apply<T>(tab, Xc, f, N, cx, cy, e, y);
     const int v = mf_variant(N, cx, cy);
     const size_t id = 3 * ((size_t)cy * N + cx);
+    const T* eo = E + 9 * (j * M + i);
     for (int k = 0; k < 3; ++k) {
       const T r = B[k * n + e] - y[k];
       const T dn = (s == 0) ? c2 * dv[3 * v + k] * r : c1 * Dc[k * n + e] + c2 * dv[3 * v + k] * r;
@@ -1012,10 +1048,10 @@ __host__ __device__ void mfp_up_body(const MfPresArgs<T>& a, const MfCta& cta) {
       a.xout[id + k] = yv;
       T ov = yv;
       if (a.fin.sout) {
-        ov = -(a.fin.snu * a.fin.smp[id + k] * a.fin.sv[id + k] + a.fin.srdt * yv);
+        ov = -(a.fin.snu * eo[3 + k] * eo[k] + a.fin.srdt * yv);
         a.fin.sout[id + k] = ov;
       }
-      if (a.fin.acc) a.fin.acc[id + k] += a.fin.omega * ov;
+      if (a.fin.acc) a.fin.acc[id + k] = eo[6 + k] + a.fin.omega * ov;
     }
   });
 }
@@ -1059,7 +1095,7 @@ inline size_t mfp_down_smem(int tp, int K) {
 template <class T>
 inline size_t mfp_up_smem(int tp, int K) {
   const int w = 2 * tp + 2 * K;
-  return (((kMfPresTab + 3) & ~3) + 15 * (size_t)w * w) * sizeof(T);
+  return (((kMfPresTab + 3) & ~3) + 15 * (size_t)w * w + 9 * (size_t)(2 * tp) * (2 * tp)) * sizeof(T);
 }
 
 }  // namespace fsi
