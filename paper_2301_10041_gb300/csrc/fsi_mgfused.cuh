@@ -488,7 +488,7 @@ __host__ __device__ void mfu_down_body(const MfVelArgs<T>& a, const MfCta& cta) 
   T2* Z = Dn;
   static_assert(TC + 4 + 2 * K >= 8, "the grown frame must fit in Dn and R");
   // With zu, the frame's b and the pressure of the cells around the frame
-  // (cells f.ox / 2 - 1 .. f.ox / 2 + PW, PW + 1 a side, after Z when they
+  // (cells f.ox / 2 - 1 .. f.ox / 2 + PW - 1, PW + 1 a side, after Z when they
   // fit) come in the same phase, so the launch makes one global round trip
   // before its first barrier.
   constexpr int ZPW = PW + 1;
