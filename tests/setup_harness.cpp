@@ -9,6 +9,8 @@
 //     every row of the assembled level operators against their matrix-free
 //     stencils, and the finest -B and -B^T against the divergence table (one
 //     line per level);
+//   setup_harness levels N cu cp
+//     the velocity and pressure hierarchies for coarsest-grid limits cu, cp;
 //   setup_harness solid <mesh file> <kappa>
 //     build the solid operators of a Q1 mesh (file: n_nodes n_el, then x y
 //     per node, then 4 node ids per element) and print C_s and A_s as
@@ -189,9 +191,30 @@ static int stencils(int N) {
   return 0;
 }
 
+// The two hierarchies of grid N with coarse_max cu and coarse_max_p cp: the
+// grid sides of all levels, the level counts of each hierarchy and the sizes
+// of the dense coarsest matrices, as one JSON object.
+static int levels(int N, int cu, int cp) {
+  const double xy[6] = {0.4, 0.4, 0.6, 0.4, 0.5, 0.6};
+  const int tris[3] = {0, 1, 2};
+  SetupParams sp{N, 1.0, 0.1, 10.0, 0.01, 0.0};
+  sp.coarse_max = cu;
+  sp.coarse_max_p = cp;
+  HostSetup hs;
+  build_setup(sp, 3, 1, xy, tris, hs);
+  std::printf("{\"Ns\": [");
+  for (size_t l = 0; l < hs.levels.size(); ++l) std::printf("%s%d", l ? ", " : "", hs.levels[l].N);
+  std::printf("], \"nlev_u\": %d, \"nlev_p\": %d, \"coarse_nA\": %d, \"coarse_nL\": %d, "
+              "\"dense_A\": %zu, \"dense_L\": %zu}\n", hs.nlev_u, hs.nlev_p, hs.coarse_nA, hs.coarse_nL,
+              hs.coarseA.size(), hs.coarseL.size());
+  return 0;
+}
+
 int main(int argc, char** argv) {
   if (argc >= 3 && std::string(argv[1]) == "stencils") return stencils(std::atoi(argv[2]));
   if (argc >= 3 && std::string(argv[1]) == "products") return products(std::atoi(argv[2]));
+  if (argc >= 5 && std::string(argv[1]) == "levels")
+    return levels(std::atoi(argv[2]), std::atoi(argv[3]), std::atoi(argv[4]));
   if (argc >= 4 && std::string(argv[1]) == "solid") return solid(argv[2], std::atof(argv[3]));
   std::fprintf(stderr, "usage: setup_harness products N | solid mesh kappa\n");
   return 1;

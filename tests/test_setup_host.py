@@ -101,3 +101,25 @@ def test_q1_interval_on_squares_is_a_quarter_to_nine_quarters(harness, tmp_path)
     d = np.diag(C)
     ev = np.linalg.eigvalsh(C / np.sqrt(np.outer(d, d)))
     assert lo <= ev.min() + 1e-13 and ev.max() <= hi + 1e-13
+
+
+@pytest.mark.parametrize("N,cu,cp,Ns,nu,np_", [
+    (128, 16, 0, [128, 64, 32, 16], 4, 4),      # the default: both stop at 16 cells
+    (128, 16, 32, [128, 64, 32, 16], 4, 3),     # a coarser pressure hierarchy
+    (128, 8, 0, [128, 64, 32, 16, 8], 5, 5),
+    (96, 16, 0, [96, 48, 24, 12], 4, 4),        # 3 * 2^5: the coarsest is 12 cells
+    (24, 16, 32, [24, 12], 2, 1),               # the pressure takes the finest grid itself
+    (16, 16, 0, [16], 1, 1),
+    (12, 4, 0, [12, 6, 3], 3, 3),               # odd coarsest grid
+])
+def test_hierarchy_levels_and_dense_coarsest(harness, N, cu, cp, Ns, nu, np_):
+    """Each hierarchy ends at its first grid of at most its limit of cells (or
+    at an odd one); the dense coarsest matrices have the unknowns of that
+    level: 2 (2 n - 1)^2 velocity, 3 n^2 pressure."""
+    out = subprocess.run([harness, "levels", str(N), str(cu), str(cp)], capture_output=True, text=True,
+                         check=True).stdout
+    d = json.loads(out)
+    assert d["Ns"] == Ns and d["nlev_u"] == nu and d["nlev_p"] == np_
+    nc_u, nc_p = Ns[nu - 1], Ns[np_ - 1]
+    assert d["coarse_nA"] == 2 * (2 * nc_u - 1) ** 2 and d["coarse_nL"] == 3 * nc_p ** 2
+    assert d["dense_A"] == d["coarse_nA"] ** 2 and d["dense_L"] == d["coarse_nL"] ** 2
